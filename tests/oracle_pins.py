@@ -1,0 +1,385 @@
+"""Checks that pin the FP64 oracle to facts fixed by the paper and by
+mathematics, independently of the oracle itself.
+
+Each check takes an optional path to an oracle build so that
+``test_oracle_planted.py`` can run the same battery against copies of the
+oracle with a deliberately planted mistake and show that some check fails.
+"""
+import json
+import math
+import os
+
+import numpy as np
+
+import oracle
+from handmade import corridor, one_road
+from paper_2406_10661_gb300 import scenario as sc
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _gold(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+def _oracle(scen, state=None, libpath=None, step=0):
+    o = oracle.Oracle(scen.net, scen.veh, scen.params, libpath=libpath)
+    if state is not None:
+        o.set_state(state["status"], state["lane"], state["s"], state["v"], state["rc"], step)
+    return o
+
+
+def _probe(libpath=None):
+    scen, st = one_road(1, 1000.0, [(0, 10.0, 0.0)])
+    return _oracle(scen, st, libpath)
+
+
+# --------------------------------------------------------------------------
+# IDM (App. B.3, equations (1)-(2))
+# --------------------------------------------------------------------------
+def check_idm_free_road(libpath=None):
+    g = _gold("idm_mobil_hand_cases.json")["idm_free_road"]
+    o = _probe(libpath)
+    a = o.idm_free(g["v"], 13.89)
+    assert abs(a - g["expected"]) < 1e-12, a
+    # interaction vanishes for a very distant leader at equal speed
+    a_far = o.idm(g["v"], 13.89, 1e9, 0.0)
+    assert abs(a_far - g["expected"]) < 1e-9, a_far
+
+
+def check_idm_equilibrium(libpath=None):
+    """a = 0 at the equilibrium gap s_e(v) of a uniform platoon (closed form)."""
+    g = _gold("idm_mobil_hand_cases.json")["equilibrium_gap"]
+    o = _probe(libpath)
+    for v, se in zip(g["v"], g["s_e"]):
+        a = o.idm(v, 13.89, se, 0.0)
+        assert abs(a) < 1e-9, (v, a)
+        # slightly closer -> braking, slightly farther -> accelerating
+        assert o.idm(v, 13.89, se * 0.99, 0.0) < 0 < o.idm(v, 13.89, se * 1.01, 0.0)
+    # standstill at the minimum gap s0: a = 0
+    assert abs(o.idm(0.0, 13.89, 2.0, 0.0)) < 1e-12
+    # approaching (dv > 0) brakes harder than following at equal speed
+    assert o.idm(10.0, 13.89, 30.0, 3.0) < o.idm(10.0, 13.89, 30.0, 0.0) < o.idm(10.0, 13.89, 30.0, -3.0)
+
+
+def check_p_lc(libpath=None):
+    g = _gold("idm_mobil_hand_cases.json")["p_lc"]
+    o = _probe(libpath)
+    for u, e in zip(g["uT"], g["expected"]):
+        assert abs(o.p_lc(u) - e) < 1e-15, (u, o.p_lc(u), e)
+
+
+# --------------------------------------------------------------------------
+# MOBIL hand cases (App. B.3, readings R1-R2)
+# --------------------------------------------------------------------------
+def _mobil_params():
+    return sc.Params(p_attempt=1.0)
+
+
+def check_mobil_case_A(libpath=None):
+    g = _gold("idm_mobil_hand_cases.json")["case_A"]
+    scen, st = one_road(2, 1000.0, [(1, 100.0, 10.0), (1, 120.0, 5.0)], params=_mobil_params())
+    d = _oracle(scen, st, libpath).decision(0)
+    assert d["attempted"] == 1
+    assert abs(d["a_own"] - g["a_own"]) < 1e-9, d["a_own"]
+    assert abs(d["at_ego_L"] - g["at_ego_L"]) < 1e-9, d["at_ego_L"]
+    assert abs(d["uL"] - g["uL"]) < 1e-9, d["uL"]
+    assert d["feasL"] == 1 and d["feasR"] == 0
+    assert abs(d["pLC"] - 0.9) < 1e-15  # u_T >= 1
+
+
+def check_mobil_case_B(libpath=None):
+    g = _gold("idm_mobil_hand_cases.json")["case_B"]
+    scen, st = one_road(2, 1000.0, [(1, 100.0, 10.0), (1, 120.0, 5.0), (0, 92.0, 15.0)],
+                        params=_mobil_params())
+    d = _oracle(scen, st, libpath).decision(0)
+    assert abs(d["at_new_L"] - g["at_new_L"]) < 1e-6, d["at_new_L"]
+    assert abs(d["a_new_L"] - g["a_new_L"]) < 1e-9, d["a_new_L"]
+    assert d["feasL"] == g["feasL"]
+    assert d["cand"] == 0 or d["dir"] != -1
+
+
+def check_mobil_case_C(libpath=None):
+    g = _gold("idm_mobil_hand_cases.json")["case_C"]
+    scen, st = one_road(2, 1000.0, [(1, 100.0, 10.0), (1, 120.0, 5.0), (0, 65.0, 8.0)],
+                        params=_mobil_params())
+    d = _oracle(scen, st, libpath).decision(0)
+    assert abs(d["a_new_L"] - g["a_new_L"]) < 1e-9, d["a_new_L"]
+    assert abs(d["at_new_L"] - g["at_new_L"]) < 1e-9, d["at_new_L"]
+    assert abs(d["uL"] - g["uL"]) < 1e-9, d["uL"]
+    assert d["feasL"] == 1
+    assert d["TF_left"] == 2 and d["TL_left"] == -1
+
+
+def check_mobil_case_D(libpath=None):
+    g = _gold("idm_mobil_hand_cases.json")["case_D"]
+    scen, st = one_road(2, 1000.0, [(1, 100.0, 10.0), (1, 120.0, 5.0), (1, 80.0, 10.0)],
+                        params=_mobil_params())
+    d = _oracle(scen, st, libpath).decision(0)
+    assert abs(d["a_old"] - g["a_old"]) < 1e-9, d["a_old"]
+    assert abs(d["at_old"] - g["at_old"]) < 1e-9, d["at_old"]
+    assert abs(d["uL"] - g["uL"]) < 1e-9, d["uL"]
+    assert d["OF"] == 2 and d["OL"] == 1
+
+
+def check_mobil_mirror(libpath=None):
+    """Mirroring a 3-lane state left<->right swaps u_L and u_R."""
+    rng = np.random.default_rng(5)
+    cars = [(1, 200.0, 9.0)]
+    for k in range(8):
+        cars.append((int(rng.integers(0, 3)), float(rng.uniform(120, 280)), float(rng.uniform(0, 14))))
+    # keep every car at least a length apart from the ego on other lanes to avoid overlaps
+    cars = [c for i, c in enumerate(cars) if i == 0 or abs(c[1] - 200.0) > 6.0]
+    mir = [(2 - c[0], c[1], c[2]) for c in cars]
+    p = _mobil_params()
+    s1, st1 = one_road(3, 1000.0, cars, params=p)
+    s2, st2 = one_road(3, 1000.0, mir, params=p)
+    d1 = _oracle(s1, st1, libpath).decision(0)
+    d2 = _oracle(s2, st2, libpath).decision(0)
+    assert abs(d1["uL"] - d2["uR"]) < 1e-12 and abs(d1["uR"] - d2["uL"]) < 1e-12, (d1, d2)
+    assert d1["feasL"] == d2["feasR"] and d1["feasR"] == d2["feasL"]
+
+
+# --------------------------------------------------------------------------
+# Sensing: brute force over tiny lanes (§3.1 sensing index; reading R16)
+# --------------------------------------------------------------------------
+def _ahead(a, b):
+    return a[0] > b[0] or (a[0] == b[0] and a[1] < b[1])
+
+
+def check_neighbours_bruteforce(libpath=None, trials=40):
+    rng = np.random.default_rng(11)
+    p = _mobil_params()
+    for _ in range(trials):
+        n = int(rng.integers(2, 9))
+        cars = []
+        for k in range(n):
+            s = float(rng.integers(0, 40)) * 2.5  # coarse grid -> exact ties happen
+            cars.append((int(rng.integers(0, 3)), s, float(rng.uniform(0, 14))))
+        scen, st = one_road(3, 500.0, cars, params=p)
+        o = _oracle(scen, st, libpath)
+        for ego in range(n):
+            d = o.decision(ego)
+            key = (st["s"][ego], ego)
+
+            def lead(lane):
+                c = [(st["s"][k], k) for k in range(n) if k != ego and st["lane"][k] == lane
+                     and _ahead((st["s"][k], k), key)]
+                return min(c, key=lambda x: (x[0], -x[1]))[1] if c else -1
+
+            def foll(lane):
+                c = [(st["s"][k], k) for k in range(n) if k != ego and st["lane"][k] == lane
+                     and not _ahead((st["s"][k], k), key)]
+                return max(c, key=lambda x: (x[0], -x[1]))[1] if c else -1
+
+            el = st["lane"][ego]
+            assert d["own_leader"] == lead(el), (cars, ego, d["own_leader"])
+            assert d["OL"] == lead(el) and d["OF"] == foll(el)
+            if el > 0:
+                assert d["TL_left"] == lead(el - 1) and d["TF_left"] == foll(el - 1)
+            if el < 2:
+                assert d["TL_right"] == lead(el + 1) and d["TF_right"] == foll(el + 1)
+
+
+# --------------------------------------------------------------------------
+# Kinematics (reading R12): textbook reductions
+# --------------------------------------------------------------------------
+def check_free_road_vs_rk4(libpath=None):
+    """A lone car on a free lane follows dv/dt = a(1-(v/v0)^4).  The ballistic
+    update is first order in dt; its speed stays within 0.5 m/s (0.39 at worst for
+    dt = 1 s) of a fine RK4
+    solution and converges to v0; displacement per step is the trapezoid of
+    the two speeds while no clamp binds."""
+    scen, st = one_road(1, 5000.0, [(0, 0.0, 0.0)])
+    o = _oracle(scen, st, libpath)
+    v0, a = 13.89, 2.0
+    f = lambda v: a * (1 - (v / v0) ** 4)  # noqa: E731
+    vr, h = 0.0, 1e-3
+    prev = o.state()
+    for t in range(1, 60):
+        o.step(1)
+        cur = o.state()
+        for _ in range(1000):
+            k1 = f(vr); k2 = f(vr + h / 2 * k1); k3 = f(vr + h / 2 * k2); k4 = f(vr + h * k3)
+            vr += h / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+        assert abs(cur["v"][0] - vr) < 0.5, (t, cur["v"][0], vr)
+        ds = cur["s"][0] - prev["s"][0]
+        assert abs(ds - 0.5 * (cur["v"][0] + prev["v"][0])) < 1e-9, (t, ds)
+        prev = cur
+    assert abs(prev["v"][0] - v0) < 1e-3
+
+
+def check_platoon_equilibrium(libpath=None):
+    """Followers of a uniform platoon at s_e(v) keep a = 0 (speed unchanged,
+    displacement v dt) during the step."""
+    v, v0 = 10.0, 14.0  # v0 exactly representable in the float32 lane table
+    se = (2.0 + v * 1.5) / math.sqrt(1.0 - (v / v0) ** 4)  # closed form, a = 0
+    n = 6
+    cars = [(0, 100.0 + k * (se + 5.0), v) for k in range(n)]  # car n-1 is the head
+    scen, st = one_road(1, 5000.0, cars, vmax=v0)
+    o = _oracle(scen, st, libpath)
+    o.step(1)
+    cur = o.state()
+    for k in range(n - 1):
+        assert abs(cur["v"][k] - v) < 1e-9, (k, cur["v"][k])
+        assert abs(cur["s"][k] - (st["s"][k] + v)) < 1e-9
+    assert cur["v"][n - 1] > v  # the head is on free road below v0
+
+
+def check_red_light(libpath=None):
+    """Manual red: the car stops before the line (App. B.3 signal rule) and
+    never enters the junction; after switching to green it crosses, transfers
+    with exact kinematics and arrives."""
+    scen = corridor((300.0, 300.0), [(0, 0)])
+    o = _oracle(scen, None, libpath)
+    o.set_signal([0], oracle.POLICY_MANUAL, [1])  # phase 1: corridor red
+    L0 = float(scen.net.lane_length[0])
+    for t in range(120):
+        o.step(1)
+        st = o.state()
+        if st["status"][0] == 1:
+            assert st["lane"][0] == 0, "entered a red junction lane"
+            assert -1e-12 <= L0 - st["s"][0]
+    st = o.state()
+    assert st["v"][0] < 1e-6 and 0.0 <= L0 - st["s"][0] <= 2.0 + 1e-6, st
+    o.set_signal([0], oracle.POLICY_MANUAL, [0])  # green
+    crossed = False
+    for t in range(200):
+        before = o.state()
+        o.step(1)
+        after = o.state()
+        if after["status"][0] == 1 and before["lane"][0] == 0 and after["lane"][0] != 0:
+            crossed = True
+            # exact transfer: s'' = s + d - L where d = trapezoid displacement
+            d = 0.5 * (before["v"][0] + after["v"][0])
+            if after["lane"][0] == 2:  # the junction lane
+                assert abs(after["s"][0] - (before["s"][0] + d - L0)) < 1e-9
+        if after["status"][0] == 2:
+            break
+    assert crossed and o.state()["status"][0] == 2
+    m = o.metrics()
+    assert m["n_arrived"] == 1 and m["errors"] == 0
+
+
+def check_signal_program(libpath=None):
+    """Fixed-time program (reading R19): phases 0,1 of 30 green + 3 amber;
+    the corridor lane is green in phase 0 only."""
+    scen = corridor((300.0, 300.0), [(0, 0)], green=30, amber=3)
+    o = _oracle(scen, None, libpath)
+    jl = scen.net.n_road_lanes  # the only junction lane
+    exp = [oracle.LIGHT_GREEN] * 30 + [oracle.LIGHT_AMBER] * 3 + [oracle.LIGHT_RED] * 33
+    got = [o.light(jl, t) for t in range(66)]
+    assert got == exp
+    assert [o.light(jl, t + 66) for t in range(66)] == exp  # periodic
+    o.set_signal([0], oracle.POLICY_NONE)
+    assert all(o.light(jl, t) == oracle.LIGHT_GREEN for t in range(66))
+
+
+def check_arrival_and_travel_time(libpath=None):
+    """A lone car departing at step 5 on an always-green corridor: it is
+    inserted at step 5 (at t=6 it is at s=0), drives 600 m + junction and
+    arrives; ATT = arrival time - departure time."""
+    scen = corridor((300.0, 300.0), [(0, 5)], turn_len=10.0)
+    o = _oracle(scen, None, libpath)
+    o.set_signal([0], oracle.POLICY_NONE)
+    total = 610.0
+    pos = 0.0
+    arrived_at = None
+    for t in range(200):
+        b = o.state()
+        o.step(1)
+        a = o.state()
+        if b["status"][0] == 0 and a["status"][0] == 1:
+            assert t == 5 and a["s"][0] == 0.0 and a["v"][0] == 0.0
+        if b["status"][0] == 1:
+            pos += 0.5 * (b["v"][0] + a["v"][0])
+        if a["status"][0] == 2:
+            arrived_at = t + 1
+            break
+    assert arrived_at is not None
+    assert pos >= total - 1e-9 and pos - 0.5 * (b["v"][0] + a["v"][0]) < total
+    m = o.metrics()
+    assert m["n_arrived"] == 1 and abs(m["tt_sum"] - (arrived_at - 5)) < 1e-12
+
+
+def check_insertion(libpath=None):
+    """Two cars on one start lane, both due at step 0: FIFO by id, the second
+    waits until the first has s - len >= s0 in the step's snapshot."""
+    scen = corridor((1000.0, 300.0), [(0, 0), (0, 0)])
+    o = _oracle(scen, None, libpath)
+    o.set_signal([0], oracle.POLICY_NONE)
+    o.step(1)
+    st = o.state()
+    assert st["status"].tolist() == [1, 0]
+    t = 1
+    while True:
+        snap = o.state()
+        o.step(1)
+        st = o.state()
+        if st["status"][1] == 1:
+            assert snap["s"][0] - 5.0 >= 2.0
+            break
+        assert snap["s"][0] - 5.0 < 2.0
+        t += 1
+        assert t < 50
+    assert o.metrics()["inserted"] == 2
+
+
+def _find_step(scen, st, ids, libpath, want):
+    o = _oracle(scen, st, libpath)
+    for t in range(0, 400):
+        o.set_state(st["status"], st["lane"], st["s"], st["v"], st["rc"], t)
+        ds = [o.decision(i) for i in ids]
+        if all(want(d) for d in ds):
+            return t, ds
+    raise AssertionError("no step with the wanted draws")
+
+
+def check_conflict(libpath=None):
+    """Reading R9: candidates entering lane 1 from lanes 0 and 2 into the same
+    gap: only the larger utility changes lanes; in different gaps both do."""
+    p = _mobil_params()
+    cars = [(0, 100.0, 10.0), (0, 115.0, 0.0),   # car 0 behind a stopped car
+            (2, 140.0, 10.0), (2, 165.0, 3.0)]  # car 2 behind a slow car (smaller u)
+    scen, st = one_road(3, 1000.0, cars, params=p)
+    t, ds = _find_step(scen, st, [0, 2], libpath, lambda d: d["cand"] == 1)
+    assert ds[0]["dir"] == 1 and ds[1]["dir"] == -1 and ds[0]["u"] > ds[1]["u"]
+    assert (ds[0]["TL"], ds[0]["TF"]) == (ds[1]["TL"], ds[1]["TF"]) == (-1, -1)
+    o = _oracle(scen, st, libpath, step=t)
+    o.step(1)
+    a = o.state()
+    assert a["lane"][0] == 1 and a["flags"][0] & oracle.F_CHANGED
+    assert a["lane"][2] == 2 and a["flags"][2] & oracle.F_CONFLICT_LOST
+    assert o.metrics()["lane_changes"] == 1
+    # a car in lane 1 between them separates the two gaps -> both change
+    cars2 = cars + [(1, 120.0, 10.0)]
+    scen2, st2 = one_road(3, 1000.0, cars2, params=p)
+    t2, ds2 = _find_step(scen2, st2, [0, 2], libpath, lambda d: d["cand"] == 1)
+    assert (ds2[0]["TL"], ds2[0]["TF"]) == (4, -1) and (ds2[1]["TL"], ds2[1]["TF"]) == (-1, 4)
+    o2 = _oracle(scen2, st2, libpath, step=t2)
+    o2.step(1)
+    a2 = o2.state()
+    assert a2["lane"][0] == 1 and a2["lane"][2] == 1
+
+
+def check_permutation_invariance(libpath=None, steps=150):
+    """Two-phase read/write separation (§3.1): processing vehicles in reverse
+    order gives bit-identical states and metrics."""
+    scen = sc.small_scenario()
+    o1 = oracle.Oracle(scen.net, scen.veh, scen.params, libpath=libpath)
+    o2 = oracle.Oracle(scen.net, scen.veh, scen.params, libpath=libpath)
+    o2.set_reverse_order(True)
+    o1.step(steps); o2.step(steps)
+    a, b = o1.state(), o2.state()
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    assert o1.metrics() == o2.metrics()
+
+
+ALL_CHECKS = [
+    check_idm_free_road, check_idm_equilibrium, check_p_lc, check_mobil_case_A,
+    check_mobil_case_B, check_mobil_case_C, check_mobil_case_D, check_mobil_mirror, check_neighbours_bruteforce,
+    check_free_road_vs_rk4, check_platoon_equilibrium, check_red_light, check_signal_program,
+    check_arrival_and_travel_time, check_insertion, check_conflict,
+]
