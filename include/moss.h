@@ -1,0 +1,237 @@
+/*
+ * moss.h — C ABI of the GB300 (sm_103a) microscopic traffic-simulation step.
+ *
+ * The library advances city-scale road networks one discrete time step at a
+ * time on one GPU, following the per-timestep vehicle update of arxiv
+ * 2406.10661 ("A GPU-accelerated Large-scale Simulator for Transportation
+ * System Optimization Benchmarking"):
+ *   - two-phase step: every vehicle reads the previous step's snapshot and
+ *     writes only its own next state (§3.1, "Two-phase Parallel Process");
+ *   - sensing of the leader/follower on the own lane, the adjacent lanes and
+ *     the next lane of the route (§3.1, "Vehicle Sensing Indexes"; App. B.3);
+ *   - IDM car following (App. B.3, equations (1)-(2), delta = 4), randomized
+ *     MOBIL lane changing (App. B.3) with deterministic conflict resolution;
+ *   - red/amber stop before the next lane's signal (App. B.3), fixed-time,
+ *     manual and no-signal policies (§3.2, "Traffic Signal");
+ *   - transfer across junctions, departure insertion and arrival handling
+ *     (App. B.2, prepare/update streams);
+ *   - throughput, average travelling time and network speed (§3.3).
+ *
+ * Units: metres, seconds, m/s.  One step advances dt seconds.  Vehicle state
+ * is kept in FP32 (precision 32) or FP64 (precision 64, used to compare
+ * trajectories with a double-precision reference).
+ *
+ * Conventions for all calls
+ *   - Every call returns MOSS_OK (0) or a MOSS_E* code; nothing aborts or
+ *     throws across the boundary.  moss_last_error() describes the last
+ *     failure of a handle.
+ *   - Input arrays are HOST memory owned by the caller; moss_create deep-copies
+ *     them, so they may be freed after it returns.
+ *   - A handle owns all device memory it allocates and releases it in
+ *     moss_destroy.  Calls on one handle must not run concurrently.
+ *   - Work is enqueued on the handle's CUDA stream (the caller's stream if one
+ *     is given to moss_create, else a stream the handle creates).  moss_step
+ *     is asynchronous; moss_get_metrics / moss_get_state / moss_synchronize
+ *     wait for the stream and report device-side errors raised meanwhile
+ *     (MOSS_ETIMEOUT for a bounded device wait that ran out, MOSS_EDEVICE for
+ *     an inconsistency found on the device).
+ */
+#ifndef MOSS_H
+#define MOSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MOSS_OK 0
+#define MOSS_EINVAL 1   /* invalid argument or inconsistent input arrays */
+#define MOSS_ENOMEM 2   /* device or host allocation failed */
+#define MOSS_ECUDA 3    /* a CUDA runtime call failed */
+#define MOSS_ETIMEOUT 4 /* a bounded device-side wait gave up */
+#define MOSS_EBUDGET 5  /* the request does not fit the given memory budget */
+#define MOSS_EDEVICE 6  /* the device reported an inconsistent state */
+
+#define MOSS_POLICY_FIXED_TIME 0 /* the network's built-in phase program */
+#define MOSS_POLICY_MANUAL 1     /* the phase set by moss_set_signal_phase */
+#define MOSS_POLICY_NONE 2       /* no signal: every junction lane is green */
+
+#define MOSS_ST_WAITING 0 /* not yet departed (or waiting for a safe entrance) */
+#define MOSS_ST_ACTIVE 1  /* on a lane */
+#define MOSS_ST_ARRIVED 2 /* trip finished */
+
+/* per-vehicle flags of the last step (MossState.flags) */
+#define MOSS_F_FLAGGED 1       /* a decision quantity was within flag_band of its threshold */
+#define MOSS_F_CHANGED 2       /* changed lane */
+#define MOSS_F_CANDIDATE 4     /* decided to change lane (before conflict resolution) */
+#define MOSS_F_TRANSFER 8      /* crossed the end of a lane */
+#define MOSS_F_ARRIVED 16      /* finished its trip this step */
+#define MOSS_F_INSERTED 32     /* departed this step */
+#define MOSS_F_CONFLICT_LOST 64 /* lost a lane-change conflict */
+
+/*
+ * Road network (App. B.1: lanes, roads, junctions).  All arrays host memory.
+ *   Lanes [0, n_road_lanes) are road lanes, grouped by road: road r owns lanes
+ *   [road_lane_off[r], road_lane_off[r+1]), ordered from the leftmost (lane
+ *   change "left" = index - 1) to the rightmost.  Lanes [n_road_lanes,
+ *   n_lanes) are junction lanes, grouped by the road lane they leave:
+ *   junction lanes leaving road lane l are [jl_off[l], jl_off[l+1]) (absolute
+ *   lane ids, jl_off has n_road_lanes+1 entries, jl_off[0] = n_road_lanes,
+ *   jl_off[n_road_lanes] = n_lanes).  For junction lane j (index
+ *   j - n_road_lanes): jl_target = the road lane it feeds, jl_junction = its
+ *   junction, jl_mask bit p = green in phase p (p < 8).
+ *   Junction k: phases [junc_phase_off[k], junc_phase_off[k+1]) with green
+ *   and amber durations in whole steps; the program starts shifted by
+ *   junc_offset[k] steps.  A junction with no phases has no signal.
+ */
+typedef struct MossNetwork {
+    int32_t n_roads, n_road_lanes, n_lanes, n_junctions;
+    const int32_t* road_lane_off;  /* [n_roads+1] */
+    const float* lane_length;      /* [n_lanes] m, > 0 */
+    const float* lane_vmax;        /* [n_lanes] m/s, > 0 */
+    const int32_t* jl_off;         /* [n_road_lanes+1] */
+    const int32_t* jl_target;      /* [n_lanes-n_road_lanes] */
+    const int32_t* jl_junction;    /* [n_lanes-n_road_lanes] */
+    const int32_t* jl_mask;        /* [n_lanes-n_road_lanes] */
+    const int32_t* junc_offset;    /* [n_junctions] steps */
+    const int32_t* junc_phase_off; /* [n_junctions+1] */
+    const int32_t* phase_green;    /* [junc_phase_off[n_junctions]] steps */
+    const int32_t* phase_amber;    /* [junc_phase_off[n_junctions]] steps */
+} MossNetwork;
+
+/*
+ * Travel demand (§3.1 "Simulator Inputs"): vehicle i (id = i) drives the
+ * road sequence routes[route_off[i] .. route_off[i+1]), consecutive roads
+ * connected through a junction lane from every lane; it departs no earlier
+ * than step dep[i] on lane start_lane[i] (a lane of its first road) and has
+ * desired-speed factor v0f[i] (desired speed = v0f * lane speed limit).
+ */
+typedef struct MossVehicles {
+    int32_t n;
+    const int32_t* route_off;  /* [n+1] */
+    const int32_t* routes;     /* [route_off[n]] road ids */
+    const int32_t* start_lane; /* [n] */
+    const int32_t* dep;        /* [n] step */
+    const float* v0f;          /* [n] */
+} MossVehicles;
+
+/*
+ * Model parameters.  IDM (App. B.3): a_max, b_comf (comfortable
+ * deceleration), T (headway), s0 (minimum gap), delta (must be 4).
+ * Randomized MOBIL (App. B.3): politeness p, threshold a_th, safe braking
+ * b_safe, attempt probability p_attempt, p_LC levels p_hi (u_T >= 1) and p_lo
+ * (u_T = 0), linear in between.  flag_band: relative band around decision
+ * thresholds inside which a decision is flagged (MOSS_F_FLAGGED).
+ * Random draws: Philox4x32-10 with key (seed low word, seed high word XOR
+ * scenario) and counter (vehicle id, step, 0, 0).
+ * precision: 32 (FP32 state) or 64 (FP64 state).
+ */
+typedef struct MossParams {
+    double dt, a_max, b_comf, T, s0, delta, veh_len, politeness, a_th, b_safe, p_attempt,
+        p_hi, p_lo, flag_band;
+    uint64_t seed;
+    uint32_t scenario;
+    int32_t precision;
+} MossParams;
+
+/* Cumulative metrics (§3.3): throughput = n_arrived; ATT = tt_sum / n_arrived;
+ * network speed = speed_sum / vehicle_updates (speed after each update). */
+typedef struct MossMetrics {
+    int64_t step, n_active, n_waiting, n_arrived;
+    double tt_sum, speed_sum;
+    int64_t vehicle_updates, lane_changes, flagged, overlaps, inserted, errors;
+} MossMetrics;
+
+/* Per-vehicle state by vehicle id (host arrays of MossVehicles.n entries,
+ * owned by the caller).  rc = index within the route of the current road (on
+ * a junction lane: of the road just left).  flags: MOSS_F_* of the last step
+ * (ignored by moss_set_state). */
+typedef struct MossState {
+    int32_t* status;
+    int32_t* lane;
+    double* s;
+    double* v;
+    int32_t* rc;
+    int32_t* flags;
+} MossState;
+
+typedef struct MossHandle* moss_t;
+
+/* Build a simulation of one scenario at step 0 with every vehicle waiting.
+ * cuda_stream: a cudaStream_t to run on, or NULL for a handle-owned stream.
+ * Errors: MOSS_EINVAL (inconsistent arrays, delta != 4, precision not 32/64),
+ * MOSS_ENOMEM, MOSS_ECUDA.  On error *out is NULL. */
+int moss_create(const MossNetwork* net, const MossVehicles* veh, const MossParams* prm,
+                void* cuda_stream, moss_t* out);
+
+/* Enqueue n >= 0 steps (asynchronous; replays a captured CUDA graph). */
+int moss_step(moss_t h, int n);
+
+/* Set the phase of n junctions (batch setter, §3.1 "_batch" API, §3.2
+ * set_tl_phase) and switch them to MOSS_POLICY_MANUAL, effective from the
+ * next step.  junction_ids and phase_idx are host arrays of n entries.
+ * MOSS_EINVAL if an id or phase is out of range (nothing is changed). */
+int moss_set_signal_phase(moss_t h, int n, const int32_t* junction_ids, const int32_t* phase_idx);
+
+/* Set the signal policy of n junctions (§3.2 set_tl_policy). */
+int moss_set_signal_policy(moss_t h, int n, const int32_t* junction_ids, int32_t policy);
+
+/* Wait for the handle's stream and copy the cumulative metrics. */
+int moss_get_metrics(moss_t h, MossMetrics* out);
+
+/* Wait for the handle's stream and copy the per-vehicle state (by id). */
+int moss_get_state(moss_t h, MossState* out);
+
+/* Replace the per-vehicle state and set the step counter; s and v are
+ * rounded to the handle's precision.  Waiting vehicles must form the tail of
+ * each start lane's departure queue ordered by (dep, id); active vehicles
+ * must sit on a lane of their route's road rc with 0 <= s <= length.
+ * Metrics are kept.  MOSS_EINVAL if the state is inconsistent. */
+int moss_set_state(moss_t h, const MossState* in, int64_t step);
+
+/* Wait for all work enqueued on the handle. */
+int moss_synchronize(moss_t h);
+
+/* Device bytes held by the handle. */
+int moss_device_bytes(moss_t h, size_t* out);
+
+/* Release the handle and its device memory (NULL is ignored). */
+void moss_destroy(moss_t h);
+
+/* Text of the handle's last error ("" if none); valid until the next call. */
+const char* moss_last_error(moss_t h);
+
+/*
+ * Batching: n independent scenarios advanced together, one launch per step
+ * kernel for all of them (scenarios of uneven size share every launch).
+ * Each scenario keeps its own vehicle ids, random streams (seed, scenario)
+ * and step counter, so its trajectory is the same alone and in the batch.
+ * Model parameters other than seed/scenario must be equal across scenarios
+ * (MOSS_EINVAL otherwise).  moss_step, moss_synchronize, moss_device_bytes
+ * and moss_destroy accept batch handles; per-scenario calls below take the
+ * scenario index in [0, n).
+ */
+int moss_batch_create(int n, const MossNetwork* nets, const MossVehicles* vehs,
+                      const MossParams* prms, void* cuda_stream, moss_t* out);
+int moss_batch_size(moss_t h, int* out);
+int moss_batch_get_metrics(moss_t h, int scenario, MossMetrics* out);
+int moss_batch_get_state(moss_t h, int scenario, MossState* out);
+int moss_batch_set_signal_phase(moss_t h, int scenario, int n, const int32_t* junction_ids,
+                                const int32_t* phase_idx);
+
+/*
+ * Kernel timing for measurement: when enabled, every step records CUDA
+ * events around each kernel on the handle's stream (graphs are not used
+ * while enabled).  moss_kernel_times returns the summed milliseconds per
+ * kernel since enabling, in the order decide, lanescan, place, prepare,
+ * and the number of timed steps.
+ */
+int moss_set_kernel_timing(moss_t h, int enable);
+int moss_kernel_times(moss_t h, double* ms4, int64_t* steps);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MOSS_H */

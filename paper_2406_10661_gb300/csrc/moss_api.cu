@@ -1,0 +1,914 @@
+// Host side of the C ABI declared in include/moss.h: input validation, the
+// union network of a batch, device buffers, CUDA-graph replay of the step
+// kernels, and state / metric transfer.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "moss.h"
+#include "moss_kernels.cuh"
+
+using namespace moss;
+
+namespace {
+
+struct SnapBufs {
+    int32_t *lane, *id, *rptr, *rlast, *nl, *off;
+    void *s, *v;
+    float* v0f;
+};
+
+}  // namespace
+
+struct MossHandle {
+    int precision = 32;
+    int n_scen = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int sm_count = 1;
+    MossParams prm{};
+    std::string err;
+
+    // ---- host copies of the (union) inputs
+    int n_lanes = 0, n_junctions = 0, n_veh = 0, n_phases = 0;
+    std::vector<int32_t> lane_scen, lane_lo, lane_hi, jl_b, jl_e, lane_road, lane_src_road;
+    std::vector<float> L, vmax;
+    std::vector<int32_t> junc_scen, junc_phase_off;
+    std::vector<int32_t> route_off, routes, dep, start_lane, veh_scen;
+    std::vector<float> v0f;
+    std::vector<int32_t> q_off, q_ids;
+    std::vector<int32_t> scen_veh_off, scen_lane_off, scen_junc_off;
+    std::vector<uint32_t> key0, key1;
+
+    // ---- device
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+    float *d_L = nullptr, *d_vmax = nullptr, *d_v0f = nullptr;
+    int32_t *d_lane_scen = nullptr, *d_lane_road = nullptr;
+    int2 *d_lohi = nullptr, *d_jl = nullptr;
+    int32_t *d_junc_offset = nullptr, *d_junc_phase_off = nullptr, *d_phase_green = nullptr,
+            *d_phase_amber = nullptr, *d_junc_scen = nullptr, *d_junc_policy = nullptr,
+            *d_junc_manual = nullptr, *d_junc_state = nullptr;
+    int32_t *d_route_off = nullptr, *d_routes = nullptr, *d_dep = nullptr, *d_vstatus = nullptr,
+            *d_vflags = nullptr;
+    int32_t *d_q_off = nullptr, *d_q_ids = nullptr, *d_q_head = nullptr;
+    uint32_t *d_key0 = nullptr, *d_key1 = nullptr;
+    int32_t* d_veh_base = nullptr;
+    long long *d_step = nullptr, *d_metrics = nullptr;
+    SnapBufs snap[2]{};
+    int8_t* d_code = nullptr;
+    void *d_rs = nullptr, *d_rv = nullptr, *d_es = nullptr, *d_ev = nullptr;
+    int32_t *d_elane = nullptr, *d_eid = nullptr, *d_erptr = nullptr, *d_erlast = nullptr,
+            *d_enl = nullptr, *d_enext = nullptr, *d_head = nullptr, *d_enter = nullptr,
+            *d_leave = nullptr, *d_lbefore = nullptr;
+    float* d_ev0f = nullptr;
+    unsigned long long *d_lane_tiles = nullptr, *d_place_tiles = nullptr;
+    int n_lane_tiles = 0, max_place_tiles = 0;
+    Counters* d_cnt = nullptr;
+    int32_t *d_stage_a = nullptr, *d_stage_b = nullptr;  // setter staging (n_junctions)
+
+    int parity = 0;  // snapshot buffer holding the current step
+    cudaGraphExec_t g2[2] = {nullptr, nullptr}, g1[2] = {nullptr, nullptr};
+    bool graphs_ready = false;
+    bool timing = false;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    double kms[4] = {0, 0, 0, 0};
+    long long ksteps = 0;
+};
+
+namespace {
+
+int fail(MossHandle* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    return code;
+}
+
+int cuda_fail(MossHandle* h, cudaError_t e, const char* what) {
+    return fail(h, MOSS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                      \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);        \
+    } while (0)
+
+template <typename T>
+int dalloc(MossHandle* h, T** p, size_t count) {
+    void* q = nullptr;
+    const size_t nb = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&q, nb);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, MOSS_ENOMEM, "cudaMalloc of " + std::to_string(nb) + " bytes failed");
+    }
+    h->allocs.push_back(q);
+    h->bytes += nb;
+    *p = (T*)q;
+    return MOSS_OK;
+}
+
+template <typename T>
+int upload(MossHandle* h, T** p, const std::vector<T>& v) {
+    int rc = dalloc(h, p, v.size());
+    if (rc) return rc;
+    if (!v.empty()) CK(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+    return MOSS_OK;
+}
+
+#define TRY(call)              \
+    do {                       \
+        int r_ = (call);       \
+        if (r_) return r_;     \
+    } while (0)
+
+// ---- validation of one scenario ------------------------------------------
+int validate(MossHandle* h, const MossNetwork* net, const MossVehicles* veh, const MossParams* p,
+             std::vector<std::vector<int32_t>>* road_out) {
+    if (!net || !veh || !p) return fail(h, MOSS_EINVAL, "null argument");
+    if (p->delta != 4.0) return fail(h, MOSS_EINVAL, "only delta = 4 is supported");
+    if (p->precision != 32 && p->precision != 64) return fail(h, MOSS_EINVAL, "precision must be 32 or 64");
+    if (!(p->dt > 0) || !(p->a_max > 0) || !(p->b_comf > 0) || !(p->s0 >= 0) || !(p->veh_len > 0) ||
+        !(p->T >= 0))
+        return fail(h, MOSS_EINVAL, "invalid model parameter");
+    const int R = net->n_roads, NRL = net->n_road_lanes, NL = net->n_lanes, J = net->n_junctions;
+    if (R < 1 || NRL < 1 || NL < NRL || J < 0) return fail(h, MOSS_EINVAL, "bad network sizes");
+    if (!net->road_lane_off || !net->lane_length || !net->lane_vmax || !net->jl_off)
+        return fail(h, MOSS_EINVAL, "missing network array");
+    if (NL > NRL && (!net->jl_target || !net->jl_junction || !net->jl_mask))
+        return fail(h, MOSS_EINVAL, "missing junction-lane array");
+    if (J > 0 && (!net->junc_offset || !net->junc_phase_off))
+        return fail(h, MOSS_EINVAL, "missing junction array");
+    if (net->road_lane_off[0] != 0 || net->road_lane_off[R] != NRL)
+        return fail(h, MOSS_EINVAL, "road_lane_off must start at 0 and end at n_road_lanes");
+    for (int r = 0; r < R; ++r)
+        if (net->road_lane_off[r + 1] <= net->road_lane_off[r])
+            return fail(h, MOSS_EINVAL, "every road needs at least one lane");
+    for (int l = 0; l < NL; ++l)
+        if (!(net->lane_length[l] > 0.f) || !(net->lane_vmax[l] > 0.f) || !std::isfinite(net->lane_length[l]))
+            return fail(h, MOSS_EINVAL, "lane lengths and speed limits must be > 0");
+    if (net->jl_off[0] != NRL || net->jl_off[NRL] != NL) return fail(h, MOSS_EINVAL, "jl_off range");
+    for (int l = 0; l < NRL; ++l)
+        if (net->jl_off[l + 1] < net->jl_off[l]) return fail(h, MOSS_EINVAL, "jl_off not monotone");
+    int nph = 0;
+    if (J > 0) {
+        if (net->junc_phase_off[0] != 0) return fail(h, MOSS_EINVAL, "junc_phase_off[0] != 0");
+        for (int j = 0; j < J; ++j) {
+            const int np = net->junc_phase_off[j + 1] - net->junc_phase_off[j];
+            if (np < 0 || np > 8) return fail(h, MOSS_EINVAL, "a junction has 0..8 phases");
+        }
+        nph = net->junc_phase_off[J];
+        if (nph > 0 && (!net->phase_green || !net->phase_amber)) return fail(h, MOSS_EINVAL, "missing phases");
+        for (int k = 0; k < nph; ++k)
+            if (net->phase_green[k] < 0 || net->phase_amber[k] < 0)
+                return fail(h, MOSS_EINVAL, "negative phase duration");
+    }
+    std::vector<int32_t> road_of(NRL);
+    for (int r = 0; r < R; ++r)
+        for (int l = net->road_lane_off[r]; l < net->road_lane_off[r + 1]; ++l) road_of[l] = r;
+    for (int j = NRL; j < NL; ++j) {
+        const int k = j - NRL;
+        if (net->jl_target[k] < 0 || net->jl_target[k] >= NRL) return fail(h, MOSS_EINVAL, "jl_target range");
+        if (net->jl_junction[k] < 0 || net->jl_junction[k] >= J) return fail(h, MOSS_EINVAL, "jl_junction range");
+        if (net->jl_mask[k] < 0 || net->jl_mask[k] > 255) return fail(h, MOSS_EINVAL, "jl_mask must fit 8 bits");
+    }
+    // out-roads reachable from every lane of each road
+    road_out->assign(R, {});
+    for (int r = 0; r < R; ++r) {
+        std::vector<int32_t> common;
+        for (int l = net->road_lane_off[r]; l < net->road_lane_off[r + 1]; ++l) {
+            std::vector<int32_t> outs;
+            for (int j = net->jl_off[l]; j < net->jl_off[l + 1]; ++j)
+                outs.push_back(road_of[net->jl_target[j - NRL]]);
+            std::sort(outs.begin(), outs.end());
+            if (std::adjacent_find(outs.begin(), outs.end()) != outs.end())
+                return fail(h, MOSS_EINVAL, "a lane has two junction lanes to the same road");
+            if (l == net->road_lane_off[r]) common = outs;
+            else {
+                std::vector<int32_t> x;
+                std::set_intersection(common.begin(), common.end(), outs.begin(), outs.end(),
+                                      std::back_inserter(x));
+                common.swap(x);
+            }
+        }
+        (*road_out)[r] = common;
+    }
+    const int N = veh->n;
+    if (N < 0 || N >= (1 << 30)) return fail(h, MOSS_EINVAL, "vehicle count out of range");
+    if (N > 0 && (!veh->route_off || !veh->routes || !veh->start_lane || !veh->dep || !veh->v0f))
+        return fail(h, MOSS_EINVAL, "missing vehicle array");
+    if (N > 0 && veh->route_off[0] != 0) return fail(h, MOSS_EINVAL, "route_off[0] != 0");
+    for (int i = 0; i < N; ++i) {
+        const int a = veh->route_off[i], b = veh->route_off[i + 1];
+        if (b <= a) return fail(h, MOSS_EINVAL, "every route needs at least one road");
+        for (int k = a; k < b; ++k)
+            if (veh->routes[k] < 0 || veh->routes[k] >= R) return fail(h, MOSS_EINVAL, "route road out of range");
+        for (int k = a; k + 1 < b; ++k) {
+            const auto& o = (*road_out)[veh->routes[k]];
+            if (!std::binary_search(o.begin(), o.end(), veh->routes[k + 1]))
+                return fail(h, MOSS_EINVAL, "route of vehicle " + std::to_string(i) +
+                                                " uses a turn not available from every lane");
+        }
+        const int sl = veh->start_lane[i];
+        if (sl < 0 || sl >= NRL || road_of[sl] != veh->routes[a])
+            return fail(h, MOSS_EINVAL, "start lane must be a lane of the first road");
+        if (veh->dep[i] < 0) return fail(h, MOSS_EINVAL, "negative departure step");
+        if (!(veh->v0f[i] > 0.f) || !std::isfinite(veh->v0f[i])) return fail(h, MOSS_EINVAL, "v0f must be > 0");
+    }
+    return MOSS_OK;
+}
+
+bool same_model(const MossParams& a, const MossParams& b) {
+    return a.dt == b.dt && a.a_max == b.a_max && a.b_comf == b.b_comf && a.T == b.T && a.s0 == b.s0 &&
+           a.delta == b.delta && a.veh_len == b.veh_len && a.politeness == b.politeness &&
+           a.a_th == b.a_th && a.b_safe == b.b_safe && a.p_attempt == b.p_attempt && a.p_hi == b.p_hi &&
+           a.p_lo == b.p_lo && a.flag_band == b.flag_band && a.precision == b.precision;
+}
+
+template <typename Real>
+Ctx<Real> make_ctx(MossHandle* h, int cur) {
+    Ctx<Real> c;
+    std::memset(&c, 0, sizeof(c));
+    c.n_lanes = h->n_lanes; c.n_junctions = h->n_junctions; c.n_scen = h->n_scen; c.n_veh = h->n_veh;
+    c.L = h->d_L; c.vmax = h->d_vmax; c.lane_scen = h->d_lane_scen; c.lohi = h->d_lohi; c.jl = h->d_jl;
+    c.lane_road = h->d_lane_road;
+    c.junc_offset = h->d_junc_offset; c.junc_phase_off = h->d_junc_phase_off;
+    c.phase_green = h->d_phase_green; c.phase_amber = h->d_phase_amber; c.junc_scen = h->d_junc_scen;
+    c.junc_policy = h->d_junc_policy; c.junc_manual = h->d_junc_manual; c.junc_state = h->d_junc_state;
+    c.route_off = h->d_route_off; c.routes = h->d_routes; c.dep = h->d_dep; c.v0f = h->d_v0f;
+    c.vstatus = h->d_vstatus; c.vflags = h->d_vflags;
+    c.q_off = h->d_q_off; c.q_ids = h->d_q_ids; c.q_head = h->d_q_head;
+    c.key0 = h->d_key0; c.key1 = h->d_key1; c.veh_base = h->d_veh_base; c.scen_step = h->d_step;
+    c.metrics = h->d_metrics;
+    for (int k = 0; k < 2; ++k) {
+        const SnapBufs& b = h->snap[k == 0 ? cur : 1 - cur];
+        Snap<Real>& s = k == 0 ? c.cur : c.nxt;
+        s.lane = b.lane; s.s = (Real*)b.s; s.v = (Real*)b.v; s.id = b.id; s.v0f = b.v0f;
+        s.rptr = b.rptr; s.rlast = b.rlast; s.nl = b.nl; s.off = b.off;
+    }
+    c.code = h->d_code; c.rs = (Real*)h->d_rs; c.rv = (Real*)h->d_rv;
+    c.es = (Real*)h->d_es; c.ev = (Real*)h->d_ev; c.elane = h->d_elane; c.eid = h->d_eid;
+    c.ev0f = h->d_ev0f; c.erptr = h->d_erptr; c.erlast = h->d_erlast; c.enl = h->d_enl;
+    c.enext = h->d_enext; c.head = h->d_head; c.enter = h->d_enter; c.leave = h->d_leave;
+    c.lbefore = h->d_lbefore; c.lane_tiles = h->d_lane_tiles; c.place_tiles = h->d_place_tiles;
+    c.n_lane_tiles = h->n_lane_tiles; c.max_place_tiles = h->max_place_tiles; c.cnt = h->d_cnt;
+    const MossParams& p = h->prm;
+    c.dt = Real(p.dt); c.a_max = Real(p.a_max); c.b_comf = Real(p.b_comf); c.T = Real(p.T);
+    c.s0 = Real(p.s0); c.len = Real(p.veh_len); c.pol = Real(p.politeness); c.a_th = Real(p.a_th);
+    c.b_safe = Real(p.b_safe); c.p_att = Real(p.p_attempt); c.p_hi = Real(p.p_hi); c.p_lo = Real(p.p_lo);
+    c.band = Real(p.flag_band);
+    c.inv_2sqrt_ab = Real(1.0 / (2.0 * std::sqrt(p.a_max * p.b_comf)));
+    return c;
+}
+
+struct Grids {
+    int prep, decide, lanescan, place;
+};
+
+Grids grids(const MossHandle* h) {
+    Grids g;
+    const int cap = h->sm_count * 8;
+    const long long work = std::max<long long>(std::max(h->n_lanes, h->n_junctions),
+                                               std::max(h->n_lane_tiles, h->max_place_tiles));
+    g.prep = (int)std::max<long long>(1, std::min<long long>((work + PREP_THREADS - 1) / PREP_THREADS, cap));
+    g.decide = (int)std::max<long long>(1, std::min<long long>((h->n_veh + DECIDE_THREADS - 1) / DECIDE_THREADS, cap));
+    g.lanescan = std::max(1, std::min(h->n_lane_tiles, h->sm_count * 4));
+    g.place = (int)std::max<long long>(1, std::min<long long>(h->max_place_tiles, cap));
+    return g;
+}
+
+template <typename Real>
+void enqueue_step(MossHandle* h, int cur, bool timed) {
+    Ctx<Real> c = make_ctx<Real>(h, cur);
+    const Grids g = grids(h);
+    cudaStream_t s = h->stream;
+    if (timed) cudaEventRecord(h->ev[0], s);
+    k_prepare<Real><<<g.prep, PREP_THREADS, 0, s>>>(c);
+    if (timed) cudaEventRecord(h->ev[1], s);
+    k_decide<Real><<<g.decide, DECIDE_THREADS, 0, s>>>(c);
+    if (timed) cudaEventRecord(h->ev[2], s);
+    k_lanescan<Real><<<g.lanescan, LANESCAN_THREADS, 0, s>>>(c);
+    if (timed) cudaEventRecord(h->ev[3], s);
+    k_place<Real><<<g.place, PLACE_THREADS, 0, s>>>(c);
+    if (timed) cudaEventRecord(h->ev[4], s);
+}
+
+void enqueue(MossHandle* h, int cur, bool timed) {
+    if (h->precision == 64) enqueue_step<double>(h, cur, timed);
+    else enqueue_step<float>(h, cur, timed);
+}
+
+void destroy_graphs(MossHandle* h) {
+    for (int k = 0; k < 2; ++k) {
+        if (h->g2[k]) cudaGraphExecDestroy(h->g2[k]);
+        if (h->g1[k]) cudaGraphExecDestroy(h->g1[k]);
+        h->g2[k] = h->g1[k] = nullptr;
+    }
+    h->graphs_ready = false;
+}
+
+int build_graphs(MossHandle* h) {
+    for (int p = 0; p < 2; ++p) {
+        for (int nsteps = 1; nsteps <= 2; ++nsteps) {
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+            for (int k = 0; k < nsteps; ++k) enqueue(h, (p + k) & 1, false);
+            CK(cudaStreamEndCapture(h->stream, &g));
+            cudaGraphExec_t ex = nullptr;
+            cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+            (nsteps == 2 ? h->g2[p] : h->g1[p]) = ex;
+        }
+    }
+    h->graphs_ready = true;
+    return MOSS_OK;
+}
+
+__global__ void k_set_signal(int n, const int32_t* ids, const int32_t* phases, int policy,
+                             int32_t* junc_policy, int32_t* junc_manual) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    junc_policy[ids[k]] = policy;
+    if (policy == POL_MANUAL) junc_manual[ids[k]] = phases[k];
+}
+
+// read back and clear the device error word
+int check_device(MossHandle* h) {
+    int err = 0;
+    CK(cudaMemcpy(&err, &h->d_cnt->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err == 0) return MOSS_OK;
+    if (!(err & ERR_POISON)) {  // recoverable reports are cleared once read
+        const int zero = 0;
+        CK(cudaMemcpy(&h->d_cnt->err, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    }
+    if (err & ERR_TIMEOUT) return fail(h, MOSS_ETIMEOUT, "a bounded device wait gave up");
+    std::string m = "device reported:";
+    if (err & ERR_ROUTE) m += " undrivable route;";
+    if (err & ERR_TRANSFER) m += " transfer overflow;";
+    if (err & ERR_RANGE) m += " list overflow;";
+    return fail(h, MOSS_EDEVICE, m);
+}
+
+// ---- create (n scenarios as one union network) ------------------------------
+int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const MossParams* prms,
+                void* stream, MossHandle* h) {
+    if (n < 1) return fail(h, MOSS_EINVAL, "need at least one scenario");
+    h->prm = prms[0];
+    h->precision = prms[0].precision;
+    h->n_scen = n;
+    for (int k = 1; k < n; ++k)
+        if (!same_model(prms[0], prms[k]))
+            return fail(h, MOSS_EINVAL, "batched scenarios must share the model parameters");
+    long long tot_lanes = 0, tot_j = 0, tot_v = 0, tot_routes = 0, tot_ph = 0, tot_roads = 0;
+    std::vector<std::vector<std::vector<int32_t>>> outs(n);
+    for (int k = 0; k < n; ++k) {
+        TRY(validate(h, &nets[k], &vehs[k], &prms[k], &outs[k]));
+        tot_lanes += nets[k].n_lanes; tot_j += nets[k].n_junctions; tot_v += vehs[k].n;
+        tot_routes += vehs[k].n ? vehs[k].route_off[vehs[k].n] : 0;
+        tot_ph += nets[k].n_junctions ? nets[k].junc_phase_off[nets[k].n_junctions] : 0;
+        tot_roads += nets[k].n_roads;
+    }
+    if (tot_lanes >= (1ll << 30) || tot_v >= (1ll << 30) || tot_routes >= (1ll << 31) - 1 ||
+        tot_roads >= (1ll << 30))
+        return fail(h, MOSS_EINVAL, "batch too large for 32-bit indices");
+    h->n_lanes = (int)tot_lanes; h->n_junctions = (int)tot_j; h->n_veh = (int)tot_v;
+    h->n_phases = (int)tot_ph;
+    const int NL = h->n_lanes, NJ = h->n_junctions, NV = h->n_veh;
+    h->lane_scen.resize(NL); h->lane_lo.resize(NL); h->lane_hi.resize(NL); h->jl_b.resize(NL);
+    h->jl_e.resize(NL); h->lane_road.resize(NL); h->lane_src_road.resize(NL); h->L.resize(NL);
+    h->vmax.resize(NL);
+    h->junc_scen.resize(NJ); h->junc_phase_off.resize(NJ + 1);
+    std::vector<int32_t> junc_offset(NJ), phase_green(tot_ph), phase_amber(tot_ph);
+    h->route_off.resize(NV + 1); h->routes.resize(tot_routes); h->dep.resize(NV);
+    h->start_lane.resize(NV); h->v0f.resize(NV); h->veh_scen.resize(NV);
+    h->scen_veh_off.assign(n + 1, 0); h->scen_lane_off.assign(n + 1, 0); h->scen_junc_off.assign(n + 1, 0);
+    h->key0.resize(n); h->key1.resize(n);
+    int LO = 0, JO = 0, VO = 0, RO = 0, PO = 0, ROFF = 0;
+    h->route_off[0] = 0;
+    for (int k = 0; k < n; ++k) {
+        const MossNetwork& nt = nets[k];
+        const MossVehicles& vh = vehs[k];
+        const int NRL = nt.n_road_lanes;
+        std::vector<int32_t> road_of(NRL);
+        for (int r = 0; r < nt.n_roads; ++r)
+            for (int l = nt.road_lane_off[r]; l < nt.road_lane_off[r + 1]; ++l) road_of[l] = r;
+        for (int l = 0; l < nt.n_lanes; ++l) {
+            const int g = LO + l;
+            h->lane_scen[g] = k;
+            h->L[g] = nt.lane_length[l];
+            h->vmax[g] = nt.lane_vmax[l];
+            if (l < NRL) {
+                const int r = road_of[l];
+                h->lane_lo[g] = LO + nt.road_lane_off[r];
+                h->lane_hi[g] = LO + nt.road_lane_off[r + 1];
+                h->jl_b[g] = LO + nt.jl_off[l];
+                h->jl_e[g] = LO + nt.jl_off[l + 1];
+                h->lane_road[g] = RO + r;
+                h->lane_src_road[g] = RO + r;
+            } else {
+                const int q = l - NRL;
+                h->lane_lo[g] = -1;
+                h->lane_hi[g] = LO + nt.jl_target[q];
+                h->jl_b[g] = JO + nt.jl_junction[q];
+                h->jl_e[g] = nt.jl_mask[q];
+                h->lane_road[g] = RO + road_of[nt.jl_target[q]];
+            }
+        }
+        for (int l = 0; l < NRL; ++l)
+            for (int j = nt.jl_off[l]; j < nt.jl_off[l + 1]; ++j) h->lane_src_road[LO + j] = RO + road_of[l];
+        for (int j = 0; j < nt.n_junctions; ++j) {
+            h->junc_scen[JO + j] = k;
+            junc_offset[JO + j] = nt.junc_offset[j];
+            h->junc_phase_off[JO + j] = PO + nt.junc_phase_off[j];
+        }
+        const int nph = nt.n_junctions ? nt.junc_phase_off[nt.n_junctions] : 0;
+        for (int q = 0; q < nph; ++q) {
+            phase_green[PO + q] = nt.phase_green[q];
+            phase_amber[PO + q] = nt.phase_amber[q];
+        }
+        for (int i = 0; i < vh.n; ++i) {
+            const int g = VO + i;
+            const int a = vh.route_off[i], b = vh.route_off[i + 1];
+            for (int q = a; q < b; ++q) h->routes[ROFF + q] = RO + vh.routes[q];
+            h->route_off[g + 1] = ROFF + b;
+            h->dep[g] = vh.dep[i];
+            h->start_lane[g] = LO + vh.start_lane[i];
+            h->v0f[g] = vh.v0f[i];
+            h->veh_scen[g] = k;
+        }
+        h->key0[k] = (uint32_t)(prms[k].seed & 0xffffffffull);
+        h->key1[k] = (uint32_t)(prms[k].seed >> 32) ^ prms[k].scenario;
+        ROFF += vh.n ? vh.route_off[vh.n] : 0;
+        LO += nt.n_lanes; JO += nt.n_junctions; VO += vh.n; RO += nt.n_roads; PO += nph;
+        h->scen_veh_off[k + 1] = VO; h->scen_lane_off[k + 1] = LO; h->scen_junc_off[k + 1] = JO;
+    }
+    h->junc_phase_off[NJ] = PO;
+    // departure queues per start lane ordered by (dep, id) (R18)
+    h->q_off.assign(NL + 1, 0);
+    for (int i = 0; i < NV; ++i) h->q_off[h->start_lane[i] + 1]++;
+    for (int l = 0; l < NL; ++l) h->q_off[l + 1] += h->q_off[l];
+    h->q_ids.resize(NV);
+    {
+        std::vector<int32_t> fill(h->q_off.begin(), h->q_off.end() - 1);
+        for (int i = 0; i < NV; ++i) h->q_ids[fill[h->start_lane[i]]++] = i;
+        for (int l = 0; l < NL; ++l)
+            std::stable_sort(h->q_ids.begin() + h->q_off[l], h->q_ids.begin() + h->q_off[l + 1],
+                             [&](int a, int b) { return h->dep[a] < h->dep[b]; });
+    }
+
+    // ---- device
+    if (stream) {
+        h->stream = (cudaStream_t)stream;
+    } else {
+        CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    CK(cudaGetDevice(&h->device));
+    CK(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device));
+    const size_t rs = h->precision == 64 ? 8 : 4;
+    std::vector<int2> lohi(NL), jl(NL);
+    for (int l = 0; l < NL; ++l) {
+        lohi[l] = make_int2(h->lane_lo[l], h->lane_hi[l]);
+        jl[l] = make_int2(h->jl_b[l], h->jl_e[l]);
+    }
+    TRY(upload(h, &h->d_L, h->L));
+    TRY(upload(h, &h->d_vmax, h->vmax));
+    TRY(upload(h, &h->d_lane_scen, h->lane_scen));
+    TRY(upload(h, &h->d_lane_road, h->lane_road));
+    TRY(upload(h, &h->d_lohi, lohi));
+    TRY(upload(h, &h->d_jl, jl));
+    TRY(upload(h, &h->d_junc_offset, junc_offset));
+    TRY(upload(h, &h->d_junc_phase_off, h->junc_phase_off));
+    TRY(upload(h, &h->d_phase_green, phase_green));
+    TRY(upload(h, &h->d_phase_amber, phase_amber));
+    TRY(upload(h, &h->d_junc_scen, h->junc_scen));
+    TRY(upload(h, &h->d_junc_policy, std::vector<int32_t>(NJ, POL_FIXED)));
+    TRY(upload(h, &h->d_junc_manual, std::vector<int32_t>(NJ, 0)));
+    TRY(dalloc(h, &h->d_junc_state, NJ));
+    TRY(upload(h, &h->d_route_off, h->route_off));
+    TRY(upload(h, &h->d_routes, h->routes));
+    TRY(upload(h, &h->d_dep, h->dep));
+    TRY(upload(h, &h->d_v0f, h->v0f));
+    TRY(upload(h, &h->d_vstatus, std::vector<int32_t>(NV, MOSS_ST_WAITING)));
+    TRY(upload(h, &h->d_vflags, std::vector<int32_t>(NV, 0)));
+    TRY(upload(h, &h->d_q_off, h->q_off));
+    TRY(upload(h, &h->d_q_ids, h->q_ids));
+    TRY(upload(h, &h->d_q_head, std::vector<int32_t>(h->q_off.begin(), h->q_off.end() - 1)));
+    TRY(upload(h, &h->d_key0, h->key0));
+    TRY(upload(h, &h->d_key1, h->key1));
+    TRY(upload(h, &h->d_veh_base, std::vector<int32_t>(h->scen_veh_off.begin(), h->scen_veh_off.end() - 1)));
+    TRY(upload(h, &h->d_step, std::vector<long long>(n, 0)));
+    TRY(upload(h, &h->d_metrics, std::vector<long long>((size_t)n * M_NFIELDS, 0)));
+    const size_t cap = std::max(NV, 1);
+    for (int k = 0; k < 2; ++k) {
+        SnapBufs& b = h->snap[k];
+        TRY(dalloc(h, &b.lane, cap)); TRY(dalloc(h, &b.id, cap)); TRY(dalloc(h, &b.rptr, cap));
+        TRY(dalloc(h, &b.rlast, cap)); TRY(dalloc(h, &b.nl, cap)); TRY(dalloc(h, &b.v0f, cap));
+        TRY(dalloc(h, (char**)&b.s, cap * rs)); TRY(dalloc(h, (char**)&b.v, cap * rs));
+        TRY(upload(h, &b.off, std::vector<int32_t>(NL + 1, 0)));
+    }
+    TRY(dalloc(h, &h->d_code, cap));
+    TRY(dalloc(h, (char**)&h->d_rs, cap * rs)); TRY(dalloc(h, (char**)&h->d_rv, cap * rs));
+    TRY(dalloc(h, (char**)&h->d_es, cap * rs)); TRY(dalloc(h, (char**)&h->d_ev, cap * rs));
+    TRY(dalloc(h, &h->d_elane, cap)); TRY(dalloc(h, &h->d_eid, cap)); TRY(dalloc(h, &h->d_erptr, cap));
+    TRY(dalloc(h, &h->d_erlast, cap)); TRY(dalloc(h, &h->d_enl, cap)); TRY(dalloc(h, &h->d_enext, cap));
+    TRY(dalloc(h, &h->d_ev0f, cap));
+    TRY(dalloc(h, &h->d_head, NL)); TRY(dalloc(h, &h->d_enter, NL)); TRY(dalloc(h, &h->d_leave, NL));
+    TRY(dalloc(h, &h->d_lbefore, NL));
+    h->n_lane_tiles = (NL + LANESCAN_TILE - 1) / LANESCAN_TILE;
+    h->max_place_tiles = 2 * ((NV + PLACE_TILE - 1) / PLACE_TILE) + 2;
+    TRY(dalloc(h, &h->d_lane_tiles, h->n_lane_tiles));
+    TRY(dalloc(h, &h->d_place_tiles, h->max_place_tiles));
+    Counters c0{};
+    TRY(upload(h, &h->d_cnt, std::vector<Counters>(1, c0)));
+    TRY(dalloc(h, &h->d_stage_a, std::max(NJ, 1)));
+    TRY(dalloc(h, &h->d_stage_b, std::max(NJ, 1)));
+    for (int k = 0; k < 5; ++k) CK(cudaEventCreate(&h->ev[k]));
+    CK(cudaStreamSynchronize(h->stream));
+    TRY(build_graphs(h));
+    return MOSS_OK;
+}
+
+void free_all(MossHandle* h) {
+    destroy_graphs(h);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (void* p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+    for (int k = 0; k < 5; ++k)
+        if (h->ev[k]) cudaEventDestroy(h->ev[k]);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    h->stream = nullptr;
+}
+
+int scen_metrics(MossHandle* h, int s, MossMetrics* out) {
+    if (!out) return fail(h, MOSS_EINVAL, "null output");
+    if (s < 0 || s >= h->n_scen) return fail(h, MOSS_EINVAL, "scenario index out of range");
+    CK(cudaStreamSynchronize(h->stream));
+    long long M[M_NFIELDS];
+    long long step = 0;
+    CK(cudaMemcpy(M, h->d_metrics + (size_t)s * M_NFIELDS, sizeof(M), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&step, h->d_step + s, sizeof(long long), cudaMemcpyDeviceToHost));
+    const int nv = h->scen_veh_off[s + 1] - h->scen_veh_off[s];
+    out->step = step;
+    out->n_active = M[M_CUR_ACTIVE];
+    out->n_waiting = nv - M[M_CUR_ACTIVE] - M[M_CUR_ARRIVED];
+    out->n_arrived = M[M_ARRIVED];
+    out->tt_sum = (double)M[M_TT_STEPS] * h->prm.dt;
+    out->speed_sum = (double)M[M_SPEED_FX] / SPEED_FX;
+    out->vehicle_updates = M[M_UPDATES];
+    out->lane_changes = M[M_LANE_CHANGES];
+    out->flagged = M[M_FLAGGED];
+    out->overlaps = M[M_OVERLAPS];
+    out->inserted = M[M_INSERTED];
+    out->errors = M[M_ERRORS];
+    return check_device(h);
+}
+
+int scen_state(MossHandle* h, int s, MossState* out) {
+    if (!out || !out->status || !out->lane || !out->s || !out->v || !out->rc || !out->flags)
+        return fail(h, MOSS_EINVAL, "null state array");
+    if (s < 0 || s >= h->n_scen) return fail(h, MOSS_EINVAL, "scenario index out of range");
+    CK(cudaStreamSynchronize(h->stream));
+    Counters c;
+    CK(cudaMemcpy(&c, h->d_cnt, sizeof(c), cudaMemcpyDeviceToHost));
+    const int n = c.n_cur, NV = h->n_veh;
+    const SnapBufs& b = h->snap[h->parity];
+    std::vector<int32_t> lane(n), id(n), rptr(n), status(NV), vflags(NV);
+    std::vector<double> sv(n), vv(n);
+    long long step = 0;
+    CK(cudaMemcpy(&step, h->d_step + s, sizeof(long long), cudaMemcpyDeviceToHost));
+    if (n > 0) {
+        CK(cudaMemcpy(lane.data(), b.lane, n * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(id.data(), b.id, n * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(rptr.data(), b.rptr, n * 4, cudaMemcpyDeviceToHost));
+        if (h->precision == 64) {
+            CK(cudaMemcpy(sv.data(), b.s, n * 8, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(vv.data(), b.v, n * 8, cudaMemcpyDeviceToHost));
+        } else {
+            std::vector<float> fs(n), fv(n);
+            CK(cudaMemcpy(fs.data(), b.s, n * 4, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(fv.data(), b.v, n * 4, cudaMemcpyDeviceToHost));
+            for (int i = 0; i < n; ++i) { sv[i] = fs[i]; vv[i] = fv[i]; }
+        }
+    }
+    CK(cudaMemcpy(status.data(), h->d_vstatus, NV * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(vflags.data(), h->d_vflags, NV * 4, cudaMemcpyDeviceToHost));
+    const int v0 = h->scen_veh_off[s], v1 = h->scen_veh_off[s + 1];
+    const int lo = h->scen_lane_off[s];
+    const long long tag = (step - 1) & 0xFFFFFF;
+    for (int g = v0; g < v1; ++g) {
+        const int i = g - v0;
+        out->status[i] = status[g];
+        out->lane[i] = -1; out->s[i] = 0; out->v[i] = 0; out->rc[i] = 0;
+        out->flags[i] = ((long long)(((unsigned)vflags[g]) >> 8) == tag && step > 0) ? (vflags[g] & 255) : 0;
+    }
+    for (int k = 0; k < n; ++k) {
+        const int g = id[k];
+        if (g < v0 || g >= v1) continue;
+        const int i = g - v0;
+        out->lane[i] = lane[k] - lo;
+        out->s[i] = sv[k];
+        out->v[i] = vv[k];
+        out->rc[i] = rptr[k] - h->route_off[g];
+    }
+    return check_device(h);
+}
+
+int jl_toward_host(const MossHandle* h, int l, int out_road) {
+    for (int j = h->jl_b[l]; j < h->jl_e[l]; ++j)
+        if (h->lane_road[j] == out_road) return j;
+    return -1;
+}
+
+template <typename Real>
+int upload_state(MossHandle* h, const std::vector<int>& order, const std::vector<double>& s,
+                 const std::vector<double>& v, const std::vector<int>& lane_of, const std::vector<int>& rc) {
+    const int n = (int)order.size();
+    std::vector<int32_t> lane(n), id(n), rptr(n), rlast(n), nl(n);
+    std::vector<float> v0f(n);
+    std::vector<Real> rs_(n), rv_(n);
+    std::vector<int32_t> off(h->n_lanes + 1, 0);
+    for (int k = 0; k < n; ++k) {
+        const int g = order[k];
+        const int l = lane_of[g];
+        lane[k] = l; id[k] = g; rs_[k] = Real(s[g]); rv_[k] = Real(v[g]); v0f[k] = h->v0f[g];
+        rptr[k] = h->route_off[g] + rc[g];
+        rlast[k] = h->route_off[g + 1] - 1;
+        if (h->lane_lo[l] < 0) nl[k] = h->lane_hi[l];
+        else nl[k] = rptr[k] < rlast[k] ? jl_toward_host(h, l, h->routes[rptr[k] + 1]) : -1;
+        off[l + 1]++;
+    }
+    for (int l = 0; l < h->n_lanes; ++l) off[l + 1] += off[l];
+    const SnapBufs& b = h->snap[h->parity];
+    if (n > 0) {
+        CK(cudaMemcpy(b.lane, lane.data(), n * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(b.id, id.data(), n * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(b.rptr, rptr.data(), n * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(b.rlast, rlast.data(), n * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(b.nl, nl.data(), n * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(b.v0f, v0f.data(), n * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(b.s, rs_.data(), n * sizeof(Real), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(b.v, rv_.data(), n * sizeof(Real), cudaMemcpyHostToDevice));
+    }
+    CK(cudaMemcpy(b.off, off.data(), off.size() * 4, cudaMemcpyHostToDevice));
+    return MOSS_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+int moss_create(const MossNetwork* net, const MossVehicles* veh, const MossParams* prm,
+                void* cuda_stream, moss_t* out) {
+    return moss_batch_create(1, net, veh, prm, cuda_stream, out);
+}
+
+int moss_batch_create(int n, const MossNetwork* nets, const MossVehicles* vehs,
+                      const MossParams* prms, void* cuda_stream, moss_t* out) {
+    if (!out) return MOSS_EINVAL;
+    *out = nullptr;
+    if (!nets || !vehs || !prms) return MOSS_EINVAL;
+    MossHandle* h = new (std::nothrow) MossHandle();
+    if (!h) return MOSS_ENOMEM;
+    int rc;
+    try {
+        rc = create_impl(n, nets, vehs, prms, cuda_stream, h);
+    } catch (const std::bad_alloc&) {
+        rc = fail(h, MOSS_ENOMEM, "host allocation failed");
+    }
+    if (rc != MOSS_OK) {
+        fprintf(stderr, "moss_create: %s\n", h->err.c_str());
+        free_all(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return MOSS_OK;
+}
+
+int moss_step(moss_t h, int n) {
+    if (!h) return MOSS_EINVAL;
+    if (n < 0) return fail(h, MOSS_EINVAL, "negative step count");
+    if (h->timing) {
+        for (int k = 0; k < n; ++k) {
+            enqueue(h, h->parity, true);
+            h->parity ^= 1;
+            CK(cudaEventSynchronize(h->ev[4]));
+            for (int q = 0; q < 4; ++q) {
+                float ms = 0;
+                CK(cudaEventElapsedTime(&ms, h->ev[q], h->ev[q + 1]));
+                // event pairs bracket prepare, decide, lanescan, place; report
+                // in the order decide, lanescan, place, prepare
+                const int slot = q == 0 ? 3 : q - 1;
+                h->kms[slot] += ms;
+            }
+            h->ksteps++;
+        }
+        CK(cudaGetLastError());
+        return MOSS_OK;
+    }
+    int k = 0;
+    for (; k + 2 <= n; k += 2) CK(cudaGraphLaunch(h->g2[h->parity], h->stream));
+    if (k < n) {
+        CK(cudaGraphLaunch(h->g1[h->parity], h->stream));
+        h->parity ^= 1;
+    }
+    return MOSS_OK;
+}
+
+int moss_set_signal_phase(moss_t h, int n, const int32_t* junction_ids, const int32_t* phase_idx) {
+    return moss_batch_set_signal_phase(h, 0, n, junction_ids, phase_idx);
+}
+
+int moss_batch_set_signal_phase(moss_t h, int scenario, int n, const int32_t* junction_ids,
+                                const int32_t* phase_idx) {
+    if (!h) return MOSS_EINVAL;
+    if (scenario < 0 || scenario >= h->n_scen) return fail(h, MOSS_EINVAL, "scenario out of range");
+    if (n < 0 || (n > 0 && (!junction_ids || !phase_idx))) return fail(h, MOSS_EINVAL, "bad arrays");
+    const int j0 = h->scen_junc_off[scenario], nj = h->scen_junc_off[scenario + 1] - j0;
+    if (n > nj) return fail(h, MOSS_EINVAL, "more junctions than the scenario has");
+    if (n == 0) return MOSS_OK;
+    std::vector<int32_t> ids(n), ph(n);
+    for (int k = 0; k < n; ++k) {
+        const int j = junction_ids[k];
+        if (j < 0 || j >= nj) return fail(h, MOSS_EINVAL, "junction id out of range");
+        const int np = h->junc_phase_off[j0 + j + 1] - h->junc_phase_off[j0 + j];
+        if (phase_idx[k] < 0 || phase_idx[k] >= std::max(np, 1))
+            return fail(h, MOSS_EINVAL, "phase index out of range");
+        ids[k] = j0 + j;
+        ph[k] = phase_idx[k];
+    }
+    CK(cudaMemcpyAsync(h->d_stage_a, ids.data(), n * 4, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->d_stage_b, ph.data(), n * 4, cudaMemcpyHostToDevice, h->stream));
+    k_set_signal<<<(n + 255) / 256, 256, 0, h->stream>>>(n, h->d_stage_a, h->d_stage_b, POL_MANUAL,
+                                                          h->d_junc_policy, h->d_junc_manual);
+    CK(cudaGetLastError());
+    // pageable sources: the copies above complete before returning
+    return MOSS_OK;
+}
+
+int moss_set_signal_policy(moss_t h, int n, const int32_t* junction_ids, int32_t policy) {
+    if (!h) return MOSS_EINVAL;
+    if (policy < 0 || policy > 2) return fail(h, MOSS_EINVAL, "unknown policy");
+    if (n < 0 || (n > 0 && !junction_ids) || n > h->n_junctions) return fail(h, MOSS_EINVAL, "bad arrays");
+    if (n == 0) return MOSS_OK;
+    const int nj = h->scen_junc_off[1];
+    std::vector<int32_t> ids(n);
+    for (int k = 0; k < n; ++k) {
+        if (junction_ids[k] < 0 || junction_ids[k] >= nj) return fail(h, MOSS_EINVAL, "junction id out of range");
+        ids[k] = junction_ids[k];
+    }
+    CK(cudaMemcpyAsync(h->d_stage_a, ids.data(), n * 4, cudaMemcpyHostToDevice, h->stream));
+    k_set_signal<<<(n + 255) / 256, 256, 0, h->stream>>>(n, h->d_stage_a, h->d_stage_a, policy,
+                                                          h->d_junc_policy, h->d_junc_manual);
+    CK(cudaGetLastError());
+    return MOSS_OK;
+}
+
+int moss_get_metrics(moss_t h, MossMetrics* out) {
+    if (!h) return MOSS_EINVAL;
+    return scen_metrics(h, 0, out);
+}
+
+int moss_batch_get_metrics(moss_t h, int scenario, MossMetrics* out) {
+    if (!h) return MOSS_EINVAL;
+    return scen_metrics(h, scenario, out);
+}
+
+int moss_get_state(moss_t h, MossState* out) {
+    if (!h) return MOSS_EINVAL;
+    if (h->n_scen != 1) return fail(h, MOSS_EINVAL, "use moss_batch_get_state for batches");
+    return scen_state(h, 0, out);
+}
+
+int moss_batch_get_state(moss_t h, int scenario, MossState* out) {
+    if (!h) return MOSS_EINVAL;
+    return scen_state(h, scenario, out);
+}
+
+int moss_set_state(moss_t h, const MossState* in, int64_t step) {
+    if (!h) return MOSS_EINVAL;
+    if (h->n_scen != 1) return fail(h, MOSS_EINVAL, "moss_set_state takes single-scenario handles");
+    if (!in || !in->status || !in->lane || !in->s || !in->v || !in->rc)
+        return fail(h, MOSS_EINVAL, "null state array");
+    if (step < 0) return fail(h, MOSS_EINVAL, "negative step");
+    CK(cudaStreamSynchronize(h->stream));
+    const int NV = h->n_veh;
+    std::vector<int> order;
+    std::vector<double> s(NV), v(NV);
+    std::vector<int> lane_of(NV, -1), rc(NV, 0);
+    long long n_act = 0, n_arr = 0;
+    for (int i = 0; i < NV; ++i) {
+        const int st = in->status[i];
+        if (st < 0 || st > 2) return fail(h, MOSS_EINVAL, "bad status");
+        s[i] = in->s[i]; v[i] = in->v[i]; rc[i] = in->rc[i];
+        if (st == MOSS_ST_ARRIVED) n_arr++;
+        if (st != MOSS_ST_ACTIVE) continue;
+        n_act++;
+        const int l = in->lane[i];
+        const int nr = h->route_off[i + 1] - h->route_off[i];
+        if (l < 0 || l >= h->n_lanes) return fail(h, MOSS_EINVAL, "active vehicle on a bad lane");
+        if (rc[i] < 0 || rc[i] >= nr) return fail(h, MOSS_EINVAL, "route cursor out of range");
+        const int road = h->routes[h->route_off[i] + rc[i]];
+        if (h->lane_lo[l] >= 0) {
+            if (h->lane_road[l] != road) return fail(h, MOSS_EINVAL, "lane is not on the route's road");
+        } else {
+            if (rc[i] + 1 >= nr || h->lane_src_road[l] != road ||
+                h->lane_road[l] != h->routes[h->route_off[i] + rc[i] + 1])
+                return fail(h, MOSS_EINVAL, "junction lane does not join the route's roads");
+        }
+        if (!(s[i] >= 0.0 && s[i] <= h->L[l]) || !(v[i] >= 0.0) || !std::isfinite(v[i]))
+            return fail(h, MOSS_EINVAL, "position or speed out of range");
+        lane_of[i] = l;
+        order.push_back(i);
+    }
+    // departure queues: waiting vehicles must be each queue's tail
+    std::vector<int32_t> qh(h->n_lanes);
+    for (int l = 0; l < h->n_lanes; ++l) {
+        int k = h->q_off[l];
+        while (k < h->q_off[l + 1] && in->status[h->q_ids[k]] != MOSS_ST_WAITING) ++k;
+        qh[l] = k;
+        for (int q = k; q < h->q_off[l + 1]; ++q)
+            if (in->status[h->q_ids[q]] != MOSS_ST_WAITING)
+                return fail(h, MOSS_EINVAL, "waiting vehicles must form the tail of their start lane's queue");
+    }
+    // lane-major snapshot order: (lane, s desc, id asc), s rounded to the precision
+    std::vector<double> key(NV);
+    for (int i : order) key[i] = h->precision == 64 ? s[i] : (double)(float)s[i];
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+        if (lane_of[a] != lane_of[b]) return lane_of[a] < lane_of[b];
+        if (key[a] != key[b]) return key[a] > key[b];
+        return a < b;
+    });
+    int rc2 = h->precision == 64 ? upload_state<double>(h, order, s, v, lane_of, rc)
+                                 : upload_state<float>(h, order, s, v, lane_of, rc);
+    if (rc2) return rc2;
+    std::vector<int32_t> status(in->status, in->status + NV);
+    CK(cudaMemcpy(h->d_vstatus, status.data(), NV * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemset(h->d_vflags, 0, NV * 4));
+    CK(cudaMemcpy(h->d_q_head, qh.data(), qh.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_step, &step, sizeof(long long), cudaMemcpyHostToDevice));
+    long long cur[2] = {n_act, n_arr};
+    CK(cudaMemcpy(h->d_metrics + M_CUR_ACTIVE, cur, sizeof(cur), cudaMemcpyHostToDevice));
+    Counters c{};
+    c.n_cur = (int)n_act; c.n_next = (int)n_act;
+    CK(cudaMemcpy(h->d_cnt, &c, sizeof(c), cudaMemcpyHostToDevice));
+    return MOSS_OK;
+}
+
+int moss_synchronize(moss_t h) {
+    if (!h) return MOSS_EINVAL;
+    CK(cudaStreamSynchronize(h->stream));
+    return check_device(h);
+}
+
+int moss_device_bytes(moss_t h, size_t* out) {
+    if (!h || !out) return MOSS_EINVAL;
+    *out = h->bytes;
+    return MOSS_OK;
+}
+
+int moss_batch_size(moss_t h, int* out) {
+    if (!h || !out) return MOSS_EINVAL;
+    *out = h->n_scen;
+    return MOSS_OK;
+}
+
+void moss_destroy(moss_t h) {
+    if (!h) return;
+    free_all(h);
+    delete h;
+}
+
+const char* moss_last_error(moss_t h) {
+    if (!h) return "null handle";
+    return h->err.c_str();
+}
+
+int moss_set_kernel_timing(moss_t h, int enable) {
+    if (!h) return MOSS_EINVAL;
+    CK(cudaStreamSynchronize(h->stream));
+    h->timing = enable != 0;
+    for (double& x : h->kms) x = 0;
+    h->ksteps = 0;
+    return MOSS_OK;
+}
+
+int moss_kernel_times(moss_t h, double* ms4, int64_t* steps) {
+    if (!h || !ms4 || !steps) return MOSS_EINVAL;
+    for (int k = 0; k < 4; ++k) ms4[k] = h->kms[k];
+    *steps = h->ksteps;
+    return MOSS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,486 @@
+// Device side of the per-timestep vehicle update (arxiv 2406.10661, §3.1,
+// App. B.2-B.3), written for sm_103a.
+//
+// Layout.  Active vehicles live in a lane-major snapshot: structure-of-arrays
+// sorted by (lane, s descending, id ascending); lane l occupies slots
+// [off[l], off[l+1]).  The snapshot of step t is read-only during step t
+// (§3.1 two-phase read/write separation); step t writes the snapshot of
+// step t+1 into the other buffer.  The paper's linked lists with side
+// pointers (§3.1) become O(1) neighbour slots (leader = slot-1, follower =
+// slot+1) and a binary search in the adjacent lane's segment.
+//
+// One step = four kernels:
+//   k_prepare   junction signal states for step t (§3.2 policies), departure
+//               insertion against the snapshot (App. B.2 update stream 3),
+//               reset of per-lane counters;
+//   k_decide    per vehicle: sensing, IDM (App. B.3 eqs. (1)-(2)), randomized
+//               MOBIL (App. B.3) with deterministic conflict resolution,
+//               ballistic integration with clamps, transfer at lane ends and
+//               arrival (App. B.2 update stream 1);
+//   k_lanescan  per-lane sizes of the next snapshot -> offsets (single-pass
+//               decoupled look-back scan);
+//   k_place     writes the next snapshot: vehicles that kept their lane keep
+//               their relative order (no overtaking within a lane), vehicles
+//               that entered a lane are merged by (s, id).
+#pragma once
+
+#include <cuda/atomic>
+#include <stdint.h>
+
+namespace moss {
+
+enum : int { LIGHT_GREEN = 0, LIGHT_AMBER = 1, LIGHT_RED = 2 };
+enum : int { POL_FIXED = 0, POL_MANUAL = 1, POL_NONE = 2 };
+enum : int {
+    F_FLAGGED = 1, F_CHANGED = 2, F_CANDIDATE = 4, F_TRANSFER = 8,
+    F_ARRIVED = 16, F_INSERTED = 32, F_CONFLICT_LOST = 64
+};
+enum : int8_t { C_STAY = 0, C_MOVE = 1, C_ARRIVE = 2 };
+
+// per-scenario metric accumulators (int64, deterministic integer sums)
+enum : int {
+    M_UPDATES = 0, M_ARRIVED, M_TT_STEPS, M_SPEED_FX, M_LANE_CHANGES, M_FLAGGED,
+    M_OVERLAPS, M_INSERTED, M_ERRORS, M_CUR_ACTIVE, M_CUR_ARRIVED, M_NFIELDS
+};
+constexpr double SPEED_FX = 16777216.0;  // speed sums in units of 2^-24 m/s
+
+// device error bits (Counters::err)
+enum : int { ERR_TIMEOUT = 1, ERR_ROUTE = 2, ERR_TRANSFER = 4, ERR_RANGE = 8 };
+// errors after which the state can no longer be trusted: every later kernel
+// of the handle returns at once and the host reports the error
+constexpr int ERR_POISON = ERR_TIMEOUT | ERR_RANGE;
+
+constexpr int DECIDE_THREADS = 256;
+constexpr int LANESCAN_THREADS = 256;
+constexpr int LANESCAN_ITEMS = 4;
+constexpr int LANESCAN_TILE = LANESCAN_THREADS * LANESCAN_ITEMS;
+constexpr int PLACE_THREADS = 256;
+constexpr int PLACE_TILE = PLACE_THREADS;  // one slot per thread
+constexpr int PREP_THREADS = 256;
+constexpr long long SPIN_LIMIT = 1ll << 22;  // bounded waits (~0.5 s with backoff)
+
+struct Counters {
+    int n_cur;      // active vehicles in the current snapshot
+    int n_next;     // active vehicles in the next snapshot
+    int n_ent;      // entrants appended this step
+    int ticket_lane;
+    int ticket_place;
+    int done_place; // k_place blocks finished (the last one resets the step)
+    int err;
+    int pad;
+};
+
+template <typename Real>
+struct Snap {
+    int32_t* lane;
+    Real* s;
+    Real* v;
+    int32_t* id;
+    float* v0f;
+    int32_t* rptr;   // absolute index (in routes[]) of the current road
+    int32_t* rlast;  // absolute index of the last road of the route
+    int32_t* nl;     // next lane on the route (-1 on the last road)
+    int32_t* off;    // [n_lanes+1] lane segments
+};
+
+template <typename Real>
+struct Ctx {
+    // ---- network (possibly a union of scenarios)
+    int n_lanes, n_junctions, n_scen, n_veh;
+    const float* L;
+    const float* vmax;
+    const int32_t* lane_scen;  // scenario of the lane
+    const int2* lohi;          // road lane: its road's lanes [lo, hi); junction lane: (-1, target)
+    const int2* jl;            // road lane: leaving junction lanes [b, e); junction lane: (junction, mask)
+    const int32_t* lane_road;  // road lane: road id; junction lane: road id of its target
+    const int32_t* junc_offset;
+    const int32_t* junc_phase_off;
+    const int32_t* phase_green;
+    const int32_t* phase_amber;
+    const int32_t* junc_scen;
+    int32_t* junc_policy;
+    int32_t* junc_manual;
+    int32_t* junc_state;  // per step: bits 0-3 phase, 4-7 n_phases, 8 amber, 9 all green
+    // ---- vehicles (by global id)
+    const int32_t* route_off;
+    const int32_t* routes;
+    const int32_t* dep;
+    const float* v0f;
+    int32_t* vstatus;
+    int32_t* vflags;  // (step & 0xFFFFFF) << 8 | flags
+    // ---- departure queues (by lane; junction lanes have none)
+    const int32_t* q_off;
+    const int32_t* q_ids;
+    int32_t* q_head;
+    // ---- scenarios
+    const uint32_t* key0;
+    const uint32_t* key1;
+    const int32_t* veh_base;  // first global vehicle id of the scenario
+    long long* scen_step;
+    long long* metrics;  // [n_scen][M_NFIELDS]
+    // ---- snapshots (current -> next)
+    Snap<Real> cur, nxt;
+    // ---- per-step scratch
+    int8_t* code;  // per current slot: C_STAY / C_MOVE / C_ARRIVE
+    Real* rs;      // stayer's new s
+    Real* rv;      // stayer's new v
+    // entrants of the next snapshot (lane changes, transfers, insertions)
+    Real* es;
+    Real* ev;
+    int32_t* elane;
+    int32_t* eid;
+    float* ev0f;
+    int32_t* erptr;
+    int32_t* erlast;
+    int32_t* enl;
+    int32_t* enext;  // per-lane singly linked list
+    int32_t* head;   // [n_lanes] list head or -1
+    int32_t* enter; // [n_lanes]
+    int32_t* leave; // [n_lanes]
+    int32_t* lbefore;  // [n_lanes] leavers in lanes before l
+    unsigned long long* lane_tiles;
+    unsigned long long* place_tiles;
+    int n_lane_tiles, max_place_tiles;
+    Counters* cnt;
+    // ---- parameters
+    Real dt, a_max, b_comf, T, s0, len, pol, a_th, b_safe, p_att, p_hi, p_lo, band;
+    Real inv_2sqrt_ab;  // 1 / (2 sqrt(a b)), computed in double on the host
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds, multipliers 0xD2511F53 and
+// 0xCD9E8D57, Weyl key increments 0x9E3779B9 and 0xBB67AE85.
+__device__ __forceinline__ void philox4x32_10(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1,
+                                              uint32_t c2, uint32_t c3, uint32_t out[4]) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0;
+        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+template <typename Real>
+__device__ __forceinline__ Real unit24(uint32_t w) {
+    return Real(w >> 8) * Real(5.9604644775390625e-08);  // 2^-24, exact
+}
+
+template <typename Real> __device__ __forceinline__ Real rabs(Real x) { return x < Real(0) ? -x : x; }
+template <typename Real> __device__ __forceinline__ Real rmax(Real a, Real b) { return a > b ? a : b; }
+
+// ---------------------------------------------------------------------------
+// IDM, App. B.3 eqs. (1)-(2), delta = 4 as ((v/v0)^2)^2.
+template <typename Real>
+__device__ __forceinline__ Real idm_free(const Ctx<Real>& c, Real v, Real v0) {
+    const Real r = v / v0, r2 = r * r;
+    return c.a_max * (Real(1) - r2 * r2);
+}
+
+template <typename Real>
+__device__ __forceinline__ Real idm(const Ctx<Real>& c, Real v, Real v0, Real gap, Real dv) {
+    const Real r = v / v0, r2 = r * r;
+    const Real dyn = v * c.T + v * dv * c.inv_2sqrt_ab;
+    const Real sstar = c.s0 + (dyn > Real(0) ? dyn : Real(0));
+    const Real g = gap > Real(1e-3) ? gap : Real(1e-3);
+    const Real q = sstar / g;
+    return c.a_max * (Real(1) - r2 * r2 - q * q);
+}
+
+template <typename Real>
+__device__ __forceinline__ Real p_lc(const Ctx<Real>& c, Real uT) {
+    if (uT >= Real(1)) return c.p_hi;
+    if (uT > Real(0)) return c.p_lo + (c.p_hi - c.p_lo) * uT;
+    return c.p_lo;
+}
+
+// light of junction lane jl from its junction's state for this step (§3.2; R19)
+template <typename Real>
+__device__ __forceinline__ int light_of(const Ctx<Real>& c, int jl) {
+    const int2 jm = c.jl[jl];
+    const int st = c.junc_state[jm.x];
+    if (st & 512) return LIGHT_GREEN;
+    const int p = st & 15, np = (st >> 4) & 15, mask = jm.y;
+    if (!((mask >> p) & 1)) return LIGHT_RED;
+    if (!(st & 256)) return LIGHT_GREEN;
+    const int nx = (p + 1) % (np > 0 ? np : 1);
+    return ((mask >> nx) & 1) ? LIGHT_GREEN : LIGHT_AMBER;
+}
+
+// junction lane leaving road lane l towards road out_road (-1 if none)
+template <typename Real>
+__device__ __forceinline__ int jl_toward(const Ctx<Real>& c, int l, int out_road) {
+    const int2 r = c.jl[l];
+    for (int j = r.x; j < r.y; ++j)
+        if (c.lane_road[j] == out_road) return j;
+    return -1;
+}
+
+// (s_a, id_a) is ahead of (s_b, id_b) in lane order (R16)
+template <typename Real>
+__device__ __forceinline__ bool ahead(Real sa, int ia, Real sb, int ib) {
+    return sa > sb || (sa == sb && ia < ib);
+}
+
+// first slot in [b, e) of the current snapshot that is NOT ahead of (s, id)
+template <typename Real>
+__device__ __forceinline__ int partition_point(const Ctx<Real>& c, int b, int e, Real s, int id) {
+    int lo = b, hi = e;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (ahead(c.cur.s[mid], c.cur.id[mid], s, id)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <typename Real>
+struct LaneAcc {
+    Real a, gap, stop_gap;
+    int has_leader, stop, overlap, nl;  // nl: the next lane from this lane on the route
+};
+
+// Ego acceleration on `lane` at (s, v): min over the leader (slot ld in this
+// lane, else lookahead over at most two lanes, R11) and the stop line (R12).
+// nl: next lane from `lane` on the ego's route (-1 none); rptr/rlast: route.
+template <typename Real>
+__device__ LaneAcc<Real> accel_on_lane(const Ctx<Real>& c, int lane, Real s, Real v, Real v0,
+                                       int ld, int nl, int rptr, int rlast) {
+    LaneAcc<Real> r;
+    r.has_leader = 0; r.stop = 0; r.overlap = 0; r.gap = Real(0); r.stop_gap = Real(0); r.nl = nl;
+    Real a = idm_free(c, v, v0);
+    const bool road = c.lohi[lane].x >= 0;
+    if (ld >= 0) {
+        const Real gap = c.cur.s[ld] - c.len - s;
+        a = idm(c, v, v0, gap, v - c.cur.v[ld]);
+        r.has_leader = 1; r.gap = gap; r.overlap = gap < Real(0);
+    } else if (nl >= 0) {
+        Real base = Real(c.L[lane]) - s;
+        int x = nl;
+        for (int k = 0; k < 2 && x >= 0; ++k) {
+            const int b = c.cur.off[x], e = c.cur.off[x + 1];
+            if (e > b) {
+                const int rr = e - 1;  // rearmost vehicle of lane x
+                const Real gap = base + c.cur.s[rr] - c.len;
+                a = idm(c, v, v0, gap, v - c.cur.v[rr]);
+                r.has_leader = 1; r.gap = gap;
+                break;
+            }
+            if (k == 1) break;
+            base += Real(c.L[x]);
+            // the lane after x on the route
+            if (c.lohi[x].x < 0) {
+                x = c.lohi[x].y;  // junction lane -> its target road lane
+            } else {
+                // x is a road lane (ego on a junction lane): route road after x's road
+                const int rp = rptr + 1;  // x is road routes[rptr+1]
+                x = (rp < rlast) ? jl_toward(c, x, c.routes[rp + 1]) : -1;
+            }
+        }
+    }
+    if (road && nl >= 0 && light_of(c, nl) != LIGHT_GREEN) {
+        const Real gs = Real(c.L[lane]) - s;
+        const Real as = idm(c, v, v0, gs, v);
+        if (as < a) a = as;
+        r.stop = 1; r.stop_gap = gs;
+    }
+    r.a = a;
+    return r;
+}
+
+// in-lane acceleration of follower slot f on lane fl towards a leader at
+// (s_ld, v_ld), or on free road (politeness terms, R2)
+template <typename Real>
+__device__ __forceinline__ Real acc_pair(const Ctx<Real>& c, int f, int fl, bool has_ld, Real s_ld,
+                                         Real v_ld) {
+    const Real v0 = Real(c.cur.v0f[f]) * Real(c.vmax[fl]);
+    const Real vf = c.cur.v[f];
+    if (!has_ld) return idm_free(c, vf, v0);
+    return idm(c, vf, v0, s_ld - c.len - c.cur.s[f], vf - v_ld);
+}
+
+template <typename Real>
+struct Decision {
+    LaneAcc<Real> own, tgt;
+    Real u, scale;
+    int cand, dir, tl, TL, TF, flag;  // TL/TF: slots in the target lane or -1
+};
+
+// The full per-vehicle decision before conflict resolution (App. B.3).  A pure
+// function of the snapshot, so any thread can recompute any vehicle's
+// decision bit-for-bit (used to resolve conflicts, R9).
+template <typename Real>
+__device__ __noinline__ Decision<Real> decide(const Ctx<Real>& c, int i, long long t,
+                                              uint32_t k0, uint32_t k1, int vbase) {
+    Decision<Real> D;
+    D.cand = 0; D.dir = 0; D.tl = -1; D.TL = -1; D.TF = -1; D.flag = 0;
+    D.u = Real(0); D.scale = Real(1);
+    const int lane = c.cur.lane[i];
+    const Real s = c.cur.s[i], v = c.cur.v[i];
+    const int id = c.cur.id[i];
+    const int rptr = c.cur.rptr[i], rlast = c.cur.rlast[i], nl = c.cur.nl[i];
+    const Real v0f = Real(c.cur.v0f[i]);
+    const int b = c.cur.off[lane], e = c.cur.off[lane + 1];
+    const int OL = (i > b) ? i - 1 : -1;
+    D.own = accel_on_lane(c, lane, s, v, v0f * Real(c.vmax[lane]), OL, nl, rptr, rlast);
+    D.tgt = D.own;
+    const int2 lh = c.lohi[lane];
+    if (lh.x < 0 || lh.y - lh.x < 2) return D;  // junction lane or single-lane road
+    uint32_t w[4];
+    philox4x32_10(k0, k1, uint32_t(id - vbase), uint32_t(t), 0u, 0u, w);
+    const Real u_att = unit24<Real>(w[0]), u_lc = unit24<Real>(w[1]), u_dir = unit24<Real>(w[2]);
+    if (!(u_att < c.p_att)) return D;
+
+    const int OF = (i + 1 < e) ? i + 1 : -1;
+    Real a_old = Real(0), at_old = Real(0);
+    if (OF >= 0) {
+        a_old = acc_pair(c, OF, lane, true, s, v);
+        at_old = OL >= 0 ? acc_pair(c, OF, lane, true, c.cur.s[OL], c.cur.v[OL])
+                         : acc_pair(c, OF, lane, false, Real(0), Real(0));
+    }
+    // next road of the route (for the target lane's junction lane)
+    const int next_road = (nl >= 0) ? c.lane_road[nl] : -1;
+    Real u[2] = {Real(0), Real(0)}, scl[2] = {Real(0), Real(0)};
+    int feas[2] = {0, 0}, TLs[2] = {-1, -1}, TFs[2] = {-1, -1};
+    LaneAcc<Real> tg[2];
+    tg[0] = D.own; tg[1] = D.own;
+    const Real pos_scale = s > Real(1) ? s : Real(1);
+    for (int side = 0; side < 2; ++side) {
+        const int tl = side == 0 ? lane - 1 : lane + 1;
+        if (tl < lh.x || tl >= lh.y) continue;
+        const int tb = c.cur.off[tl], te = c.cur.off[tl + 1];
+        const int p = partition_point(c, tb, te, s, id);
+        const int TL = (p > tb) ? p - 1 : -1, TF = (p < te) ? p : -1;
+        TLs[side] = TL; TFs[side] = TF;
+        int ok = 1;
+        if (TL >= 0) {
+            const Real g = c.cur.s[TL] - c.len - s;
+            if (!(g > Real(0))) ok = 0;
+            if (rabs(g) < c.band * pos_scale) D.flag = 1;
+        }
+        if (TF >= 0) {
+            const Real g = s - c.len - c.cur.s[TF];
+            if (!(g > Real(0))) ok = 0;
+            if (rabs(g) < c.band * pos_scale) D.flag = 1;
+        }
+        const int nlt = (next_road >= 0) ? jl_toward(c, tl, next_road) : -1;
+        tg[side] = accel_on_lane(c, tl, s, v, v0f * Real(c.vmax[tl]), TL, nlt, rptr, rlast);
+        const Real at_ego = tg[side].a;
+        Real a_new = Real(0), at_new = Real(0);
+        if (TF >= 0) {
+            a_new = TL >= 0 ? acc_pair(c, TF, tl, true, c.cur.s[TL], c.cur.v[TL])
+                            : acc_pair(c, TF, tl, false, Real(0), Real(0));
+            at_new = acc_pair(c, TF, tl, true, s, v);
+            if (!(at_new >= -c.b_safe)) ok = 0;
+            const Real sc = rabs(at_new) > Real(1) ? rabs(at_new) : Real(1);
+            if (rabs(at_new + c.b_safe) < c.band * sc) D.flag = 1;
+        }
+        u[side] = (at_ego - D.own.a) + c.pol * ((at_new - a_new) + (at_old - a_old)) - c.a_th;
+        scl[side] = rabs(at_ego) + rabs(D.own.a) +
+                    c.pol * (rabs(at_new) + rabs(a_new) + rabs(at_old) + rabs(a_old)) + c.a_th;
+        feas[side] = ok;
+    }
+    Real scale = Real(1);
+    for (int sd = 0; sd < 2; ++sd)
+        if (feas[sd] && scl[sd] > scale) scale = scl[sd];
+    D.scale = scale;
+    const Real uLp = (feas[0] && u[0] > Real(0)) ? u[0] : Real(0);
+    const Real uRp = (feas[1] && u[1] > Real(0)) ? u[1] : Real(0);
+    const Real uT = uLp + uRp;
+    const Real pl = p_lc(c, uT);
+    const Real band_p = (uT < Real(1) + c.band * scale) ? c.band * scale : c.band;
+    if (rabs(u_lc - pl) < band_p) D.flag = 1;
+    if (!(u_lc < pl)) return D;
+    int side = -1;
+    if (uT > Real(0)) {
+        const Real q = uLp - u_dir * uT;
+        if (rabs(q) < c.band * scale) D.flag = 1;
+        if (uT < c.band * scale) D.flag = 1;
+        side = q > Real(0) ? 0 : 1;
+    } else {
+        if (feas[0] && feas[1]) side = u_dir < Real(0.5) ? 0 : 1;
+        else if (feas[0]) side = 0;
+        else if (feas[1]) side = 1;
+        if (side >= 0 && uT < c.band * scale) D.flag = 1;
+    }
+    if (side < 0) return D;
+    D.cand = 1;
+    D.dir = side == 0 ? -1 : 1;
+    D.tl = side == 0 ? lane - 1 : lane + 1;
+    D.TL = TLs[side]; D.TF = TFs[side];
+    D.u = u[side];
+    D.tgt = tg[side];
+    return D;
+}
+
+// ---------------------------------------------------------------------------
+// bounded acquire load of a look-back tile word
+__device__ __forceinline__ unsigned long long load_acquire(unsigned long long* p) {
+    cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> a(*p);
+    return a.load(cuda::memory_order_acquire);
+}
+__device__ __forceinline__ void store_release(unsigned long long* p, unsigned long long v) {
+    cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> a(*p);
+    a.store(v, cuda::memory_order_release);
+}
+
+// Per-scenario metric accumulation: register partials per thread, flushed
+// with one set of atomics per block when the whole block shares a scenario.
+struct MetricAcc {
+    int scen;
+    long long m[8];  // updates, arrived, tt_steps, speed_fx, lane_changes, flagged, overlaps, inserted
+};
+
+__device__ __forceinline__ void macc_reset(MetricAcc& a, int scen) {
+    a.scen = scen;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a.m[k] = 0;
+}
+
+__device__ __forceinline__ void macc_flush_thread(MetricAcc& a, long long* metrics) {
+    if (a.scen < 0) return;
+    static const int map[8] = {M_UPDATES, M_ARRIVED, M_TT_STEPS, M_SPEED_FX, M_LANE_CHANGES,
+                               M_FLAGGED, M_OVERLAPS, M_INSERTED};
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        if (a.m[k]) atomicAdd((unsigned long long*)&metrics[a.scen * M_NFIELDS + map[k]],
+                              (unsigned long long)a.m[k]);
+}
+
+// Block-level flush: reduce in shared memory when every thread holds the
+// same scenario (or nothing), else fall back to per-thread atomics.
+template <int THREADS>
+__device__ void macc_flush_block(MetricAcc& a, long long* metrics) {
+    __shared__ long long red[8][THREADS / 32];
+    __shared__ int scen0;
+    const int tid = threadIdx.x;
+    if (tid == 0) scen0 = -1;
+    __syncthreads();
+    if (a.scen >= 0) atomicMax(&scen0, a.scen);
+    __syncthreads();
+    const int s0 = scen0;
+    const bool uniform = __syncthreads_and(a.scen < 0 || a.scen == s0);
+    if (!uniform) { macc_flush_thread(a, metrics); return; }
+    if (s0 < 0) return;
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        long long x = a.scen < 0 ? 0 : a.m[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) red[k][warp] = x;
+    }
+    __syncthreads();
+    if (tid < 8) {
+        long long x = 0;
+        for (int w = 0; w < THREADS / 32; ++w) x += red[tid][w];
+        static const int map[8] = {M_UPDATES, M_ARRIVED, M_TT_STEPS, M_SPEED_FX, M_LANE_CHANGES,
+                                   M_FLAGGED, M_OVERLAPS, M_INSERTED};
+        if (x) atomicAdd((unsigned long long*)&metrics[s0 * M_NFIELDS + map[tid]], (unsigned long long)x);
+    }
+}
+
+}  // namespace moss

@@ -1,0 +1,223 @@
+"""CUDA path (through the C ABI) against the FP64 oracle.
+
+Levels (tolerances from the method's specification):
+  * FP64 kernels vs oracle over whole rollouts: identical discrete state,
+    positions/speeds within 1e-6;
+  * FP32 kernels vs oracle for one step from an identical state: identical
+    discrete decisions except where either side flags the vehicle (a decision
+    quantity within 1e-4 of its threshold), positions/speeds within
+    1e-5 * max(|x|, 1);
+  * FP32 rollouts: network speed and trip completions within 0.5%;
+  * a batch equals its scenarios run alone.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from handmade import corridor, one_road
+from paper_2406_10661_gb300 import binding, scenario as sc
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-5
+DISCRETE_FLAGS = (binding.F_CHANGED | binding.F_TRANSFER | binding.F_ARRIVED | binding.F_INSERTED)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    binding.load()
+
+
+def _sim(scen, precision=32):
+    return binding.Simulation(scen.net, scen.veh, scen.params, precision=precision)
+
+
+def _ora(scen):
+    return oracle.Oracle(scen.net, scen.veh, scen.params)
+
+
+def _set_both(sim, ora, st, step):
+    sim.set_state(st["status"], st["lane"], st["s"], st["v"], st["rc"], step)
+    ora.set_state(st["status"], st["lane"], st["s"], st["v"], st["rc"], step)
+
+
+def _f32_state(st):
+    out = {k: np.array(v, copy=True) for k, v in st.items()}
+    out["s"] = out["s"].astype(np.float32).astype(np.float64)
+    out["v"] = out["v"].astype(np.float32).astype(np.float64)
+    return out
+
+
+def compare_one_step(g, r, tol=REL):
+    """Per-vehicle comparison after one step; returns (n_compared, n_excused)."""
+    flagged = ((g["flags"] | r["flags"]) & binding.F_FLAGGED) != 0
+    disc = ((g["status"] != r["status"]) | (g["lane"] != r["lane"]) | (g["rc"] != r["rc"])
+            | ((g["flags"] & DISCRETE_FLAGS) != (r["flags"] & DISCRETE_FLAGS)))
+    bad = disc & ~flagged
+    assert not bad.any(), f"unflagged discrete mismatch at ids {np.nonzero(bad)[0][:10]}"
+    ok = ~disc & (r["status"] == 1)
+    for k in ("s", "v"):
+        err = np.abs(g[k][ok] - r[k][ok]) / np.maximum(np.abs(r[k][ok]), 1.0)
+        assert (err <= tol).all(), (k, float(err.max()), np.nonzero(ok)[0][np.argmax(err)])
+    return int(ok.sum()), int((disc & flagged).sum())
+
+
+# ---------------------------------------------------------------------------
+def test_fp64_rollout_matches_oracle_small():
+    scen = sc.small_scenario()
+    sim, ora = _sim(scen, 64), _ora(scen)
+    for chunk in range(6):
+        sim.step(100); ora.step(100)
+        g, r = sim.state(), ora.state()
+        assert np.array_equal(g["status"], r["status"])
+        act = r["status"] == 1
+        assert np.array_equal(g["lane"][act], r["lane"][act])
+        assert np.array_equal(g["rc"][act], r["rc"][act])
+        assert np.abs(g["s"][act] - r["s"][act]).max(initial=0) < 1e-6
+        assert np.abs(g["v"][act] - r["v"][act]).max(initial=0) < 1e-6
+        assert np.array_equal(g["flags"], r["flags"])
+    gm, rm = sim.metrics(), ora.metrics()
+    for k in ("step", "n_active", "n_waiting", "n_arrived", "vehicle_updates", "lane_changes",
+              "flagged", "overlaps", "inserted"):
+        assert gm[k] == rm[k], (k, gm[k], rm[k])
+    assert abs(gm["tt_sum"] - rm["tt_sum"]) < 1e-9
+    assert abs(gm["speed_sum"] - rm["speed_sum"]) <= 1e-6 * rm["speed_sum"]
+
+
+@pytest.mark.parametrize("t0", [60, 150, 300, 450, 599])
+def test_fp32_one_step_parity_small(t0):
+    scen = sc.small_scenario()
+    ora = _ora(scen)
+    ora.step(t0)
+    st = _f32_state(ora.state())
+    sim, ora2 = _sim(scen, 32), _ora(scen)
+    _set_both(sim, ora2, st, t0)
+    sim.step(1); ora2.step(1)
+    n, excused = compare_one_step(sim.state(), ora2.state())
+    assert n > 0 and excused <= max(3, n // 100)
+
+
+def test_fp32_rollout_aggregates_small():
+    scen = sc.small_scenario()
+    sim, ora = _sim(scen, 32), _ora(scen)
+    sim.step(600); ora.step(600)
+    gm, rm = sim.metrics(), ora.metrics()
+    gs = gm["speed_sum"] / gm["vehicle_updates"]
+    rs = rm["speed_sum"] / rm["vehicle_updates"]
+    assert abs(gs - rs) <= 0.005 * rs, (gs, rs)
+    assert abs(gm["n_arrived"] - rm["n_arrived"]) <= max(1, 0.005 * rm["n_arrived"]), (gm, rm)
+    assert gm["errors"] == 0
+
+
+# ---------------------------------------------------------------------------
+# hand-built states
+def _one_step_hand(scen, st, step, precision):
+    sim, ora = _sim(scen, precision), _ora(scen)
+    _set_both(sim, ora, st, step)
+    sim.step(1); ora.step(1)
+    return sim.state(), ora.state()
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_conflict_hand_case(precision):
+    p = sc.Params(p_attempt=1.0)
+    cars = [(0, 100.0, 10.0), (0, 115.0, 0.0), (2, 140.0, 10.0), (2, 165.0, 3.0)]
+    scen, st = one_road(3, 1000.0, cars, params=p)
+    ora = _ora(scen)
+    t = next(t for t in range(400) if (ora.set_state(st["status"], st["lane"], st["s"], st["v"], st["rc"], t)
+                                       or (ora.decision(0)["cand"] and ora.decision(2)["cand"])))
+    g, r = _one_step_hand(scen, st, t, precision)
+    assert g["lane"].tolist() == r["lane"].tolist()
+    assert (g["flags"] & ~binding.F_FLAGGED).tolist() == (r["flags"] & ~binding.F_FLAGGED).tolist()
+    assert g["flags"][2] & binding.F_CONFLICT_LOST
+    compare_one_step(g, r, 1e-5 if precision == 32 else 1e-12)
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_red_light_and_transfer(precision):
+    scen = corridor((300.0, 300.0), [(0, 0), (0, 3)])
+    sim, ora = _sim(scen, precision), _ora(scen)
+    for obj in (sim, ora):
+        obj.set_signal_phase([0], [1]) if obj is sim else obj.set_signal([0], oracle.POLICY_MANUAL, [1])
+    sim.step(100); ora.step(100)
+    g, r = sim.state(), ora.state()
+    assert g["lane"].tolist() == r["lane"].tolist() == [0, 0]
+    assert np.allclose(g["s"], r["s"], atol=1e-4)
+    sim.set_signal_phase([0], [0]); ora.set_signal([0], oracle.POLICY_MANUAL, [0])
+    sim.step(150); ora.step(150)
+    g, r = sim.state(), ora.state()
+    assert g["status"].tolist() == r["status"].tolist() == [2, 2]
+    assert sim.metrics()["tt_sum"] == pytest.approx(ora.metrics()["tt_sum"])
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_degenerate_scenarios(precision):
+    # no vehicles at all
+    net = sc.corridor_network(2, (500.0,))
+    veh = sc.Vehicles(n=0, route_off=np.zeros(1, np.int32), routes=np.zeros(0, np.int32),
+                      start_lane=np.zeros(0, np.int32), dep=np.zeros(0, np.int32),
+                      v0f=np.zeros(0, np.float32))
+    sim = binding.Simulation(net, veh, sc.Params(), precision=precision)
+    sim.step(5)
+    m = sim.metrics()
+    assert m["step"] == 5 and m["vehicle_updates"] == 0
+    # departures only after the horizon
+    scen = corridor((300.0, 300.0), [(0, 1000), (0, 1000)])
+    sim = _sim(scen, precision)
+    sim.step(10)
+    assert sim.metrics()["n_waiting"] == 2
+    # single-road routes arrive at the end of their only road
+    scen, st = one_road(1, 60.0, [(0, 50.0, 12.0), (0, 10.0, 5.0)])
+    g, r = _one_step_hand(scen, st, 0, precision)
+    assert g["status"].tolist() == r["status"].tolist() == [2, 1]
+
+
+def test_signal_setter_parity_fp64():
+    scen = sc.small_scenario()
+    sim, ora = _sim(scen, 64), _ora(scen)
+    rng = np.random.default_rng(1)
+    J = scen.net.n_junctions
+    for k in range(30):
+        ph = rng.integers(0, 4, J)
+        sim.set_signal_phase(np.arange(J), ph)
+        ora.set_signal(np.arange(J), oracle.POLICY_MANUAL, ph)
+        sim.step(10); ora.step(10)
+    g, r = sim.state(), ora.state()
+    assert np.array_equal(g["status"], r["status"])
+    act = r["status"] == 1
+    assert np.array_equal(g["lane"][act], r["lane"][act])
+    assert np.abs(g["s"][act] - r["s"][act]).max(initial=0) < 1e-6
+
+
+def test_batch_equals_alone():
+    scens = [sc.small_scenario(seed=s) for s in (0, 1, 2)]
+    for i, s in enumerate(scens):
+        s.params.scenario = i
+    batch = binding.Batch(scens, precision=32)
+    batch.step(300)
+    for i, s in enumerate(scens):
+        alone = _sim(s, 32)
+        alone.step(300)
+        a, b = alone.state(), batch.state(i)
+        for k in ("status", "lane", "rc", "flags"):
+            assert np.array_equal(a[k], b[k]), (i, k)
+        for k in ("s", "v"):
+            assert np.array_equal(a[k], b[k]), (i, k)
+        ma, mb = alone.metrics(), batch.metrics(i)
+        assert ma == mb
+
+
+def test_medium_one_step_parity_fp32():
+    """30x30 grid, 100,000 trips: one FP32 step from the oracle's state."""
+    scen = sc.medium_scenario()
+    sim = _sim(scen, 32)
+    sim.step(900)  # let traffic build up on the GPU, then hand the state to the oracle
+    st = sim.state()
+    ora = _ora(scen)
+    ora.set_state(st["status"], st["lane"], st["s"], st["v"], st["rc"], 900)
+    sim.step(1); ora.step(1)
+    n, excused = compare_one_step(sim.state(), ora.state())
+    assert n > 10_000 and excused <= n // 1000
