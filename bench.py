@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark of the per-timestep vehicle update on GB300.
+
+Workload: the city-scale synthetic scenario (perturbed 100x100 grid, 39,600
+roads, 2,464,950 trips departing uniformly over 3,600 s), started from a warm
+state at step 1,800 built by ``scenario.warm_state`` (inputs resident in HBM
+before timing).  A step is one pass of the whole hot path (signals,
+insertion, sensing, IDM, MOBIL with conflict resolution, integration,
+transfer, arrival, snapshot rebuild) over all active vehicles.
+
+Metric: vehicle-updates/s = sum over timed steps of the active vehicles
+updated / summed device time of those steps (CUDA events on the simulation
+stream; L2 flushed by a 256 MiB write between timed steps, outside the
+events).  ``--impl reference`` times the FP64 CPU oracle instead, on a
+bounded slice of the same warm state.
+
+Multi-GPU: replicas only (one independent city per rank, no collective on
+the data path); value = all ranks' vehicle updates / max over ranks of the
+timed duration.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+T_WARM = 1800
+SPEC_BYTES = {  # algorithmic bytes per unit, FP32 state
+    "decide": 41.0,    # per active vehicle: read 8x4 B state record, write code + s' + v'
+    "place": 65.0,     # per active vehicle: read code, s', v', 6x4 B fields; write 8x4 B record
+    "lanescan": 20.0,  # per lane: read 2 offsets + leave + enter, write offset + leavers-before
+    "prepare": 20.0,   # per lane: reset 3 counters, read queue head + bound
+}
+STEP_BYTES = 64.0      # whole step: read and write one 8x4 B state record per vehicle update
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.path = tempfile.mktemp(prefix="clk", suffix=".csv")
+        self.proc = None
+        self.index = index
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 7:
+                    continue
+                try:
+                    sm.append(float(parts[0])); mx.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[3:7]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        except Exception:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def city(args):
+    from paper_2406_10661_gb300 import scenario as sc
+    scen = sc.city_scenario(seed=args.seed)
+    warm = sc.warm_state(scen.net, scen.veh, T_WARM, seed=args.seed)
+    return scen, warm
+
+
+def cpu_oracle_rate(scen, warm, budget_s=15.0, max_road=4000, steps_cap=60):
+    """The FP64 oracle, as it stands, on the roads with id < max_road of the
+    warm state (a contiguous band of the grid at the same density)."""
+    import oracle
+    from paper_2406_10661_gb300 import scenario as sc
+    sample = sc.region_sample(warm, scen.net, max_road)
+    o = oracle.Oracle(scen.net, scen.veh, scen.params)
+    o.set_state(sample["status"], sample["lane"], sample["s"], sample["v"], sample["rc"], T_WARM)
+    o.step(1)  # untimed warm-up
+    m0 = o.metrics()
+    t0 = time.perf_counter()
+    n = 0
+    while n < steps_cap and (time.perf_counter() - t0) < budget_s:
+        o.step(1)
+        n += 1
+    dt = time.perf_counter() - t0
+    m1 = o.metrics()
+    upd = m1["vehicle_updates"] - m0["vehicle_updates"]
+    return {"value": upd / dt, "unit": "vehicle-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle, {n} steps from the step-{T_WARM} warm state restricted to roads "
+                      f"0..{max_road - 1} ({int((sample['status'] == 1).sum())} active vehicles), "
+                      f"single thread, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    scen, warm = city(args)
+    import oracle
+    from paper_2406_10661_gb300 import scenario as sc
+    sample = sc.region_sample(warm, scen.net, args.ref_roads)
+    o = oracle.Oracle(scen.net, scen.veh, scen.params)
+    o.set_state(sample["status"], sample["lane"], sample["s"], sample["v"], sample["rc"], T_WARM)
+    o.step(args.warmup)
+    m0 = o.metrics()
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    m1 = o.metrics()
+    upd = m1["vehicle_updates"] - m0["vehicle_updates"]
+    value = upd / dt
+    line = {
+        "impl": "reference", "metric": "vehicle-updates/s", "value": value, "unit": "vehicle-updates/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": scen.name, "roads": int(scen.net.n_roads), "vehicles": int(scen.veh.n),
+                   "start": f"warm state at step {T_WARM}", "sample_roads": args.ref_roads},
+        "cpu_baseline": {"value": value, "unit": "vehicle-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step: the FP64 oracle over roads 0..{args.ref_roads - 1} of the "
+                                   f"warm state ({int((sample['status'] == 1).sum())} active vehicles)"},
+        "e2e": {"value": value, "unit": "vehicle-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    from paper_2406_10661_gb300 import binding
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    binding.load()
+    scen, warm = city(args)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        sim = binding.Simulation(scen.net, scen.veh, scen.params, precision=32, stream=stream.cuda_stream)
+        sim.set_state(warm["status"], warm["lane"], warm["s"], warm["v"], warm["rc"], T_WARM)
+        for _ in range(args.warmup):
+            sim.step(1)
+        sim.synchronize()
+        m0 = sim.metrics()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with Clocks(local) as clk:
+            w0 = time.perf_counter()
+            for k in range(args.steps):
+                flush.add_(1.0)           # > L2: evicts the previous step's lines
+                evs[k][0].record(stream)
+                sim.step(1)
+                evs[k][1].record(stream)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - w0
+        if dist:
+            dist.barrier()
+        step_ms = [a.elapsed_time(b) for a, b in evs]
+        m1 = sim.metrics()
+        upd = m1["vehicle_updates"] - m0["vehicle_updates"]
+        dev_s = sum(step_ms) / 1e3
+        if dist:
+            t = torch.tensor([dev_s, float(upd)], dtype=torch.float64, device="cuda")
+            tmax = t.clone(); dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+            tsum = t.clone(); dist.all_reduce(tsum[1:], op=dist.ReduceOp.SUM)
+            dev_s_all, upd_all = float(tmax[0]), float(tsum[1])
+        else:
+            dev_s_all, upd_all = dev_s, float(upd)
+        value = upd_all / dev_s_all
+        ms_per_step = 1e3 * dev_s_all / args.steps
+
+        # per-kernel durations (events around each kernel, same L2 flushing)
+        ksteps = max(3, min(args.steps, 20))
+        m2 = sim.metrics()
+        sim.set_kernel_timing(True)
+        for _ in range(ksteps):
+            flush.add_(1.0)
+            sim.step(1)
+        sim.synchronize()
+        kt, kn = sim.kernel_times()
+        m3 = sim.metrics()
+        sim.set_kernel_timing(False)
+        upd_k = (m3["vehicle_updates"] - m2["vehicle_updates"]) / max(kn, 1)
+        avg_ms = {k: v / max(kn, 1) for k, v in kt.items()}
+        dom = max(avg_ms, key=avg_ms.get)
+        n_lanes = int(scen.net.n_lanes)
+        units = {"decide": upd_k, "place": upd_k, "lanescan": n_lanes, "prepare": n_lanes}
+        peak, peak_kind = _peaks()
+        achieved = SPEC_BYTES[dom] * units[dom] / (avg_ms[dom] * 1e-3) / 1e9
+        step_ms_k = sum(avg_ms.values())
+        step_ach = STEP_BYTES * upd_k / (step_ms_k * 1e-3) / 1e9
+
+        # end to end through the public API: every step the host writes the
+        # signal actions of all junctions (pinned host arrays -> device), steps,
+        # and reads the metrics back (device -> host)
+        J = int(scen.net.n_junctions)
+        jids = torch.arange(J, dtype=torch.int32).pin_memory().numpy()
+        phases = torch.zeros(J, dtype=torch.int32).pin_memory().numpy()
+        offs = scen.net.junc_offset.astype(np.int64)
+        e2e_steps = args.steps
+        me0 = sim.metrics()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(e2e_steps):
+            t_now = T_WARM + args.warmup + args.steps + ksteps + k
+            phases[:] = ((t_now + offs) % 132) // 33
+            sim.set_signal_phase(jids, phases)
+            sim.step(1)
+            mk = sim.metrics()
+        e2e_s = time.perf_counter() - t0
+        e2e_upd = mk["vehicle_updates"] - me0["vehicle_updates"]
+        e2e_val = e2e_upd / e2e_s
+        if dist:
+            t = torch.tensor([e2e_s, float(e2e_upd)], dtype=torch.float64, device="cuda")
+            a = t.clone(); dist.all_reduce(a[:1], op=dist.ReduceOp.MAX)
+            b = t.clone(); dist.all_reduce(b[1:], op=dist.ReduceOp.SUM)
+            e2e_val = float(b[1]) / float(a[0])
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None if world > 1 else cpu_oracle_rate(scen, warm, budget_s=args.cpu_budget)
+    n_total = int(scen.veh.n)
+    line = {
+        "metric": "vehicle-updates/s", "value": value, "unit": "vehicle-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": scen.name, "roads": int(scen.net.n_roads), "lanes": n_lanes,
+                   "vehicles": n_total, "dt_s": 1.0, "start": f"warm state at step {T_WARM}",
+                   "active_per_step": upd / args.steps,
+                   "l2": "flushed between timed steps by a 256 MiB write (outside the events)",
+                   "parallelism": f"replicas x{world}"},
+        "step_hz": 1e3 / ms_per_step,
+        "nominal_vehicle_steps_per_s": n_total * 1e3 / ms_per_step,
+        "paper_context": {"step_hz": 84.09, "vehicles": 2464950, "hardware": "RTX 4090 + Xeon 8462Y",
+                          "note": "different network (CBLab Roadnet-L); context only"},
+        "roofline": {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": peak_kind,
+                     "bytes_per_unit": SPEC_BYTES[dom], "units_per_launch": units[dom],
+                     "avg_launch_ms": avg_ms[dom]},
+        "kernel_ms": avg_ms,
+        "step_roofline": {"achieved": step_ach, "frac": step_ach / peak, "bytes_per_update": STEP_BYTES},
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_val, "unit": "vehicle-updates/s", "h2d_bytes_per_step": 8 * J,
+                "d2h_bytes_per_step": 8 * 12 + 4, "steps": e2e_steps,
+                "api": "moss_set_signal_phase + moss_step(1) + moss_get_metrics per step"},
+        "gpu_launches": 4 * args.steps,
+        "wall_s_timed_region": wall,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-roads", type=int, default=1000)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

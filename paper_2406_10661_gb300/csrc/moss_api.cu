@@ -74,6 +74,8 @@ struct MossHandle {
     int n_lane_tiles = 0, max_place_tiles = 0;
     Counters* d_cnt = nullptr;
     int32_t *d_stage_a = nullptr, *d_stage_b = nullptr;  // setter staging (n_junctions)
+    int32_t* h_stage = nullptr;          // pinned host staging of setter arguments (2 * n_junctions)
+    cudaEvent_t stage_free = nullptr;    // recorded after the last copy out of h_stage
 
     int parity = 0;  // snapshot buffer holding the current step
     cudaGraphExec_t g2[2] = {nullptr, nullptr}, g1[2] = {nullptr, nullptr};
@@ -530,8 +532,11 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
     TRY(dalloc(h, &h->d_place_tiles, h->max_place_tiles));
     Counters c0{};
     TRY(upload(h, &h->d_cnt, std::vector<Counters>(1, c0)));
-    TRY(dalloc(h, &h->d_stage_a, std::max(NJ, 1)));
+    TRY(dalloc(h, &h->d_stage_a, 2 * std::max(NJ, 1)));
     TRY(dalloc(h, &h->d_stage_b, std::max(NJ, 1)));
+    CK(cudaHostAlloc((void**)&h->h_stage, sizeof(int32_t) * 2 * std::max(NJ, 1), cudaHostAllocDefault));
+    CK(cudaEventCreateWithFlags(&h->stage_free, cudaEventDisableTiming));
+    CK(cudaEventRecord(h->stage_free, h->stream));
     for (int k = 0; k < 5; ++k) CK(cudaEventCreate(&h->ev[k]));
     CK(cudaStreamSynchronize(h->stream));
     TRY(build_graphs(h));
@@ -545,6 +550,9 @@ void free_all(MossHandle* h) {
     h->allocs.clear();
     for (int k = 0; k < 5; ++k)
         if (h->ev[k]) cudaEventDestroy(h->ev[k]);
+    if (h->stage_free) cudaEventDestroy(h->stage_free);
+    if (h->h_stage) cudaFreeHost(h->h_stage);
+    h->h_stage = nullptr;
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     h->stream = nullptr;
 }
@@ -738,22 +746,26 @@ int moss_batch_set_signal_phase(moss_t h, int scenario, int n, const int32_t* ju
     const int j0 = h->scen_junc_off[scenario], nj = h->scen_junc_off[scenario + 1] - j0;
     if (n > nj) return fail(h, MOSS_EINVAL, "more junctions than the scenario has");
     if (n == 0) return MOSS_OK;
-    std::vector<int32_t> ids(n), ph(n);
     for (int k = 0; k < n; ++k) {
         const int j = junction_ids[k];
         if (j < 0 || j >= nj) return fail(h, MOSS_EINVAL, "junction id out of range");
         const int np = h->junc_phase_off[j0 + j + 1] - h->junc_phase_off[j0 + j];
         if (phase_idx[k] < 0 || phase_idx[k] >= std::max(np, 1))
             return fail(h, MOSS_EINVAL, "phase index out of range");
-        ids[k] = j0 + j;
+    }
+    // the pinned staging area is reused: wait until the previous copy out of it ran
+    CK(cudaEventSynchronize(h->stage_free));
+    int32_t* ids = h->h_stage;
+    int32_t* ph = h->h_stage + n;
+    for (int k = 0; k < n; ++k) {
+        ids[k] = j0 + junction_ids[k];
         ph[k] = phase_idx[k];
     }
-    CK(cudaMemcpyAsync(h->d_stage_a, ids.data(), n * 4, cudaMemcpyHostToDevice, h->stream));
-    CK(cudaMemcpyAsync(h->d_stage_b, ph.data(), n * 4, cudaMemcpyHostToDevice, h->stream));
-    k_set_signal<<<(n + 255) / 256, 256, 0, h->stream>>>(n, h->d_stage_a, h->d_stage_b, POL_MANUAL,
+    CK(cudaMemcpyAsync(h->d_stage_a, h->h_stage, 2 * n * 4, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaEventRecord(h->stage_free, h->stream));
+    k_set_signal<<<(n + 255) / 256, 256, 0, h->stream>>>(n, h->d_stage_a, h->d_stage_a + n, POL_MANUAL,
                                                           h->d_junc_policy, h->d_junc_manual);
     CK(cudaGetLastError());
-    // pageable sources: the copies above complete before returning
     return MOSS_OK;
 }
 
@@ -763,12 +775,12 @@ int moss_set_signal_policy(moss_t h, int n, const int32_t* junction_ids, int32_t
     if (n < 0 || (n > 0 && !junction_ids) || n > h->n_junctions) return fail(h, MOSS_EINVAL, "bad arrays");
     if (n == 0) return MOSS_OK;
     const int nj = h->scen_junc_off[1];
-    std::vector<int32_t> ids(n);
-    for (int k = 0; k < n; ++k) {
+    for (int k = 0; k < n; ++k)
         if (junction_ids[k] < 0 || junction_ids[k] >= nj) return fail(h, MOSS_EINVAL, "junction id out of range");
-        ids[k] = junction_ids[k];
-    }
-    CK(cudaMemcpyAsync(h->d_stage_a, ids.data(), n * 4, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaEventSynchronize(h->stage_free));
+    for (int k = 0; k < n; ++k) h->h_stage[k] = junction_ids[k];
+    CK(cudaMemcpyAsync(h->d_stage_a, h->h_stage, n * 4, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaEventRecord(h->stage_free, h->stream));
     k_set_signal<<<(n + 255) / 256, 256, 0, h->stream>>>(n, h->d_stage_a, h->d_stage_a, policy,
                                                           h->d_junc_policy, h->d_junc_manual);
     CK(cudaGetLastError());

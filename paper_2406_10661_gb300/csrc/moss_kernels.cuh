@@ -198,6 +198,7 @@ __global__ void __launch_bounds__(DECIDE_THREADS) k_decide(Ctx<Real> c) {
             }
         }
         // ---- outputs
+        if (arrived) fl |= F_ARRIVED;
         const int id = c.cur.id[i];
         acc.m[0] += 1;
         acc.m[3] += (long long)llrint(double(vn) * SPEED_FX);

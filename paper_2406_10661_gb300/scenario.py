@@ -590,3 +590,79 @@ def corridor_vehicles(net: Network, start_lanes, deps, v0f=None, n_roads=None) -
     v0 = np.ones(n) if v0f is None else np.asarray(v0f)
     return Vehicles(n=n, route_off=_i32(route_off), routes=_i32(routes),
                     start_lane=_i32(start_lanes), dep=_i32(deps), v0f=_f32(v0))
+
+
+# ----------------------------------------------------------------------------
+# Warm-start states (inputs for measurement)
+# ----------------------------------------------------------------------------
+def warm_state(net: Network, veh: Vehicles, t_warm: int, spacing: float = 20.0,
+               speed_frac: float = 0.8, seed: int = 0, rounds: int = 8):
+    """A plausible mid-rollout state at step ``t_warm`` built directly from the
+    inputs (no simulation): every trip with departure < t_warm is placed on a
+    uniformly chosen road of its route and a uniform lane of that road; a lane
+    holds at most floor(length / spacing) vehicles (20 m is about 35% of jam
+    density for 5 m vehicles); a trip whose lane is full draws another road
+    of its route, up to ``rounds`` times, and is marked finished if it never
+    fits.  Vehicles of a lane are spaced evenly; speeds are speed_frac of the
+    desired speed.  Trips with departure >= t_warm are waiting, so each start
+    lane's queue keeps its (dep, id) order.  Returns per-vehicle arrays
+    (status, lane, s, v, rc) for ``set_state``."""
+    st = Stream(seed, 505)
+    n = veh.n
+    status = np.zeros(n, dtype=np.int32)
+    lane = np.full(n, -1, dtype=np.int32)
+    s = np.zeros(n, dtype=np.float64)
+    v = np.zeros(n, dtype=np.float64)
+    rc = np.zeros(n, dtype=np.int32)
+    L = net.lane_length.astype(np.float64)
+    cap = np.floor(L / spacing).astype(np.int64)
+    cap[net.n_road_lanes:] = 0
+    free = cap.copy()
+    todo = np.nonzero(veh.dep < t_warm)[0]
+    status[todo] = 2
+    for _ in range(rounds):
+        if todo.size == 0:
+            break
+        rlen = np.diff(veh.route_off)[todo]
+        k = (st.uniform(len(todo)) * rlen).astype(np.int64)
+        road = veh.routes[veh.route_off[todo] + k]
+        nl = np.diff(net.road_lane_off)[road]
+        ln = net.road_lane_off[road] + (st.uniform(len(todo)) * nl).astype(np.int64)
+        order = np.lexsort((todo, ln))
+        ids, ln, k = todo[order], ln[order], k[order]
+        first = np.searchsorted(ln, ln, side="left")
+        rank = np.arange(len(ids)) - first
+        fits = rank < free[ln]
+        a = ids[fits]
+        status[a] = 1
+        lane[a] = ln[fits]
+        rc[a] = k[fits]
+        np.subtract.at(free, ln[fits], 1)
+        todo = np.sort(ids[~fits])
+    act = np.nonzero(status == 1)[0]
+    la = lane[act]
+    order = np.lexsort((act, la))
+    act, la = act[order], la[order]
+    first = np.searchsorted(la, la, side="left")
+    rank = np.arange(len(act)) - first
+    m = (cap - free)[la]
+    s[act] = L[la] * (m - rank) / (m + 1.0)
+    v[act] = speed_frac * veh.v0f[act].astype(np.float64) * net.lane_vmax[la].astype(np.float64)
+    s = s.astype(np.float32).astype(np.float64)
+    v = v.astype(np.float32).astype(np.float64)
+    return dict(status=status, lane=lane, s=s, v=v, rc=rc)
+
+
+def region_sample(state: dict, net: Network, max_road: int) -> dict:
+    """The vehicles of ``state`` on roads with id < max_road (a contiguous band
+    of the grid); every other non-waiting vehicle is marked finished.  Used to
+    time the slow CPU oracle on a bounded slice of a city-scale state with
+    the same density."""
+    out = {k: np.array(x, copy=True) for k, x in state.items()}
+    lr = net.lane_road()
+    act = out["status"] == 1
+    keep = act & (lr[np.maximum(out["lane"], 0)] < max_road) & (out["lane"] < net.n_road_lanes)
+    drop = act & ~keep
+    out["status"][drop] = 2
+    out["lane"][drop] = -1
+    return out

@@ -54,7 +54,8 @@ def _f32_state(st):
 def compare_one_step(g, r, tol=REL):
     """Per-vehicle comparison after one step; returns (n_compared, n_excused)."""
     flagged = ((g["flags"] | r["flags"]) & binding.F_FLAGGED) != 0
-    disc = ((g["status"] != r["status"]) | (g["lane"] != r["lane"]) | (g["rc"] != r["rc"])
+    act = (g["status"] == 1) | (r["status"] == 1)
+    disc = ((g["status"] != r["status"]) | (act & ((g["lane"] != r["lane"]) | (g["rc"] != r["rc"])))
             | ((g["flags"] & DISCRETE_FLAGS) != (r["flags"] & DISCRETE_FLAGS)))
     bad = disc & ~flagged
     assert not bad.any(), f"unflagged discrete mismatch at ids {np.nonzero(bad)[0][:10]}"
