@@ -167,25 +167,28 @@ __global__ void __launch_bounds__(DECIDE_THREADS) k_decide(Ctx<Real> c) {
         if (la.stop) { const Real cl = la.stop_gap > Real(0) ? la.stop_gap : Real(0); if (disp > cl) disp = cl; }
         Real sn = s + disp;
         if (la.stop && sn > Real(c.L[nlane])) sn = Real(c.L[nlane]);
-        // ---- transfer and arrival (R17)
+        // ---- transfer and arrival (R17).  The overshoot past the lane end is
+        // taken as disp - (L - s): L - s is exact for s >= L/2 (Sterbenz), so
+        // the position on the next lane does not lose the bits of L.
         int rptr = c.cur.rptr[i];
         const int rlast = c.cur.rlast[i];
         int nl = la.nl;
         bool arrived = false;
+        Real ex = disp - (Real(c.L[nlane]) - s);  // distance beyond the end of nlane
         for (int iter = 0;; ) {
             const Real Ll = Real(c.L[nlane]);
             const Real scl = Ll > Real(1) ? Ll : Real(1);
             if (la.stop && iter == 0) break;
             const bool road = c.lohi[nlane].x >= 0;
             if (road && rptr == rlast) {
-                if (rabs(sn - Ll) < c.band * scl) fl |= F_FLAGGED;
-                if (sn >= Ll) arrived = true;
+                if (rabs(ex) < c.band * scl) fl |= F_FLAGGED;
+                if (ex >= Real(0)) arrived = true;
                 break;
             }
-            if (rabs(sn - Ll) < c.band * scl) fl |= F_FLAGGED;
-            if (!(sn > Ll)) break;
+            if (rabs(ex) < c.band * scl) fl |= F_FLAGGED;
+            if (!(ex > Real(0))) break;
             if (++iter > 4 || nl < 0) { atomicOr(&c.cnt->err, ERR_TRANSFER); sn = Ll; break; }
-            sn -= Ll;
+            sn = ex;
             fl |= F_TRANSFER;
             if (road) {
                 nlane = nl;                 // into the junction lane
@@ -196,6 +199,7 @@ __global__ void __launch_bounds__(DECIDE_THREADS) k_decide(Ctx<Real> c) {
                 nl = (rptr < rlast) ? jl_toward(c, nlane, c.routes[rptr + 1]) : -1;
                 if (rptr < rlast && nl < 0) atomicOr(&c.cnt->err, ERR_ROUTE);
             }
+            ex = sn - Real(c.L[nlane]);
         }
         // ---- outputs
         if (arrived) fl |= F_ARRIVED;
