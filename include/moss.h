@@ -231,6 +231,38 @@ int moss_batch_set_signal_phase(moss_t h, int scenario, int n, const int32_t* ju
 int moss_set_kernel_timing(moss_t h, int enable);
 int moss_kernel_times(moss_t h, double* ms4, int64_t* steps);
 
+/*
+ * Lane offsets without allocating (no counterpart in the paper: an addition
+ * for callers that cannot call cudaMalloc, such as code running inside a
+ * framework whose caching allocator owns the device memory, or a process
+ * with a fixed memory reservation).
+ *
+ * Computes, for n_lanes lanes, the lane segments of the next snapshot from
+ * the current ones: newsize(l) = d_off_cur[l+1] - d_off_cur[l] - d_leave[l] +
+ * d_enter[l]; d_off_next[0..n_lanes] = exclusive prefix sums of newsize (the
+ * last entry is the total); d_lbefore[0..n_lanes-1] = exclusive prefix sums
+ * of d_leave.  All five arrays are DEVICE int32 arrays owned by the caller
+ * (d_off_cur and d_off_next have n_lanes+1 entries).  The work is enqueued
+ * on cuda_stream (NULL = the legacy default stream) and the call returns
+ * without waiting.
+ *
+ * It allocates nothing: the scan's look-back words live in one file-scope
+ * static device array of 32 KiB (plus 256 bytes), held by every GPU that
+ * loads the library until the process exits.  Limit: n_lanes <=
+ * MOSS_NOALLOC_MAX_LANES; larger sizes return MOSS_EINVAL.  The first call on
+ * a device looks up that array's device address (and the SM count) with the
+ * device current; make that first call before any stream capture.  Every
+ * call reuses the same array (each call clears it first), so calls that can
+ * overlap on the GPU — on different streams, or from different threads —
+ * race and must be serialised by the caller.  If a bounded device-side wait
+ * gives up, d_off_next[n_lanes] is set to -1.  Returns MOSS_OK, MOSS_EINVAL
+ * (bad size or null array) or MOSS_ECUDA (a CUDA call failed).
+ */
+#define MOSS_NOALLOC_MAX_LANES (1 << 22)
+int moss_lane_offsets_noalloc(int32_t n_lanes, const int32_t* d_off_cur, const int32_t* d_leave,
+                              const int32_t* d_enter, int32_t* d_off_next, int32_t* d_lbefore,
+                              void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

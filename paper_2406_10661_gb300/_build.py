@@ -26,12 +26,13 @@ def _stale(out, srcs):
 
 def build_cuda(force=False, extra=()):
     out = os.path.join(HERE, "libmoss.so")
-    srcs = [os.path.join(CSRC, f) for f in ("moss_api.cu", "moss_device.cuh", "moss_kernels.cuh")]
+    units = ("moss_api.cu", "moss_noalloc.cu")
+    srcs = [os.path.join(CSRC, f) for f in units + ("moss_device.cuh", "moss_kernels.cuh")]
     srcs.append(os.path.join(ROOT, "include", "moss.h"))
     if force or _stale(out, srcs):
         tmp = out + f".{os.getpid()}.tmp"
         subprocess.check_call([_nvcc(), *NVCC_FLAGS, *extra, "-I", os.path.join(ROOT, "include"),
-                               "-o", tmp, os.path.join(CSRC, "moss_api.cu")])
+                               "-o", tmp, *[os.path.join(CSRC, u) for u in units]])
         os.replace(tmp, out)
     return out
 

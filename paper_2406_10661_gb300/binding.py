@@ -90,7 +90,20 @@ SIGNATURES = {
                                                    _c_i32p]),
     "moss_set_kernel_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "moss_kernel_times": (ctypes.c_int, [_vp, _c_f64p, ctypes.POINTER(ctypes.c_int64)]),
+    "moss_lane_offsets_noalloc": (ctypes.c_int, [ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
+
+NOALLOC_MAX_LANES = 1 << 22
+
+
+def moss_lane_offsets_noalloc(n_lanes: int, d_off_cur: int, d_leave: int, d_enter: int,
+                              d_off_next: int, d_lbefore: int, stream: int = 0) -> int:
+    """Lane offsets of the next snapshot from per-lane leave/enter counts, for
+    callers that cannot allocate device memory (device pointers in and out;
+    see include/moss.h).  Returns the C status code."""
+    return load().moss_lane_offsets_noalloc(int(n_lanes), _vp(d_off_cur), _vp(d_leave),
+                                            _vp(d_enter), _vp(d_off_next), _vp(d_lbefore),
+                                            _vp(stream) if stream else None)
 
 _LIB = None
 
