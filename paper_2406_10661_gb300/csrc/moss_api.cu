@@ -20,10 +20,12 @@ using namespace moss;
 namespace {
 
 struct SnapBufs {
-    int32_t *lane, *id, *rptr, *rlast, *nl, *off;
-    void *s, *v;
-    float* v0f;
+    void* a;     // RecA<Real>[cap]
+    RecB* b;     // [cap]
+    int32_t* off;
 };
+
+constexpr int N_STEP_KERNELS = 3;  // decide, lanescan, place
 
 }  // namespace
 
@@ -39,49 +41,47 @@ struct MossHandle {
 
     // ---- host copies of the (union) inputs
     int n_lanes = 0, n_junctions = 0, n_veh = 0, n_phases = 0;
-    std::vector<int32_t> lane_scen, lane_lo, lane_hi, jl_b, jl_e, lane_road, lane_src_road;
-    std::vector<float> L, vmax;
+    std::vector<LaneInfo> lanes;
+    std::vector<int32_t> lane_src_road;  // junction lanes: the road they leave
     std::vector<int32_t> junc_scen, junc_phase_off;
     std::vector<int32_t> route_off, routes, dep, start_lane, veh_scen;
     std::vector<float> v0f;
-    std::vector<int32_t> q_off, q_ids;
+    std::vector<int32_t> q_off, q_ids, start_lanes;
     std::vector<int32_t> scen_veh_off, scen_lane_off, scen_junc_off;
     std::vector<uint32_t> key0, key1;
 
     // ---- device
     std::vector<void*> allocs;
     size_t bytes = 0;
-    float *d_L = nullptr, *d_vmax = nullptr, *d_v0f = nullptr;
-    int32_t *d_lane_scen = nullptr, *d_lane_road = nullptr;
-    int2 *d_lohi = nullptr, *d_jl = nullptr;
+    LaneInfo* d_lane = nullptr;
+    float* d_v0f = nullptr;
     int32_t *d_junc_offset = nullptr, *d_junc_phase_off = nullptr, *d_phase_green = nullptr,
             *d_phase_amber = nullptr, *d_junc_scen = nullptr, *d_junc_policy = nullptr,
             *d_junc_manual = nullptr, *d_junc_state = nullptr;
     int32_t *d_route_off = nullptr, *d_routes = nullptr, *d_dep = nullptr, *d_vstatus = nullptr,
             *d_vflags = nullptr;
-    int32_t *d_q_off = nullptr, *d_q_ids = nullptr, *d_q_head = nullptr;
+    int32_t *d_q_off = nullptr, *d_q_ids = nullptr, *d_q_head = nullptr, *d_start_lanes = nullptr;
     uint32_t *d_key0 = nullptr, *d_key1 = nullptr;
     int32_t* d_veh_base = nullptr;
     long long *d_step = nullptr, *d_metrics = nullptr;
     SnapBufs snap[2]{};
     int8_t* d_code = nullptr;
-    void *d_rs = nullptr, *d_rv = nullptr, *d_es = nullptr, *d_ev = nullptr;
-    int32_t *d_elane = nullptr, *d_eid = nullptr, *d_erptr = nullptr, *d_erlast = nullptr,
-            *d_enl = nullptr, *d_enext = nullptr, *d_head = nullptr, *d_enter = nullptr,
-            *d_leave = nullptr, *d_lbefore = nullptr;
-    float* d_ev0f = nullptr;
-    unsigned long long *d_lane_tiles = nullptr, *d_place_tiles = nullptr;
-    int n_lane_tiles = 0, max_place_tiles = 0;
+    void* d_stay = nullptr;  // SV<Real>[cap]
+    void* d_ea = nullptr;    // RecA<Real>[cap]
+    RecB* d_eb = nullptr;
+    int32_t *d_enext = nullptr, *d_enter = nullptr, *d_leave = nullptr, *d_lbefore = nullptr,
+            *d_tile_leave = nullptr, *d_tile_prefix = nullptr;
+    unsigned long long *d_head = nullptr, *d_lane_tiles = nullptr;
+    int n_lane_tiles = 0, max_slot_tiles = 0, n_junc_chunks = 0;
     Counters* d_cnt = nullptr;
-    int32_t *d_stage_a = nullptr, *d_stage_b = nullptr;  // setter staging (n_junctions)
+    int32_t* d_stage = nullptr;          // setter staging (2 * n_junctions)
     int32_t* h_stage = nullptr;          // pinned host staging of setter arguments (2 * n_junctions)
     cudaEvent_t stage_free = nullptr;    // recorded after the last copy out of h_stage
 
     int parity = 0;  // snapshot buffer holding the current step
     cudaGraphExec_t g2[2] = {nullptr, nullptr}, g1[2] = {nullptr, nullptr};
-    bool graphs_ready = false;
     bool timing = false;
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[N_STEP_KERNELS + 1] = {};
     double kms[4] = {0, 0, 0, 0};
     long long ksteps = 0;
 };
@@ -235,33 +235,35 @@ bool same_model(const MossParams& a, const MossParams& b) {
            a.p_lo == b.p_lo && a.flag_band == b.flag_band && a.precision == b.precision;
 }
 
+size_t reca_size(int precision) { return precision == 64 ? sizeof(RecA<double>) : sizeof(RecA<float>); }
+size_t sv_size(int precision) { return precision == 64 ? sizeof(SV<double>) : sizeof(SV<float>); }
+
 template <typename Real>
 Ctx<Real> make_ctx(MossHandle* h, int cur) {
     Ctx<Real> c;
     std::memset(&c, 0, sizeof(c));
     c.n_lanes = h->n_lanes; c.n_junctions = h->n_junctions; c.n_scen = h->n_scen; c.n_veh = h->n_veh;
-    c.L = h->d_L; c.vmax = h->d_vmax; c.lane_scen = h->d_lane_scen; c.lohi = h->d_lohi; c.jl = h->d_jl;
-    c.lane_road = h->d_lane_road;
+    c.lane = h->d_lane;
     c.junc_offset = h->d_junc_offset; c.junc_phase_off = h->d_junc_phase_off;
     c.phase_green = h->d_phase_green; c.phase_amber = h->d_phase_amber; c.junc_scen = h->d_junc_scen;
     c.junc_policy = h->d_junc_policy; c.junc_manual = h->d_junc_manual; c.junc_state = h->d_junc_state;
     c.route_off = h->d_route_off; c.routes = h->d_routes; c.dep = h->d_dep; c.v0f = h->d_v0f;
     c.vstatus = h->d_vstatus; c.vflags = h->d_vflags;
     c.q_off = h->d_q_off; c.q_ids = h->d_q_ids; c.q_head = h->d_q_head;
+    c.start_lanes = h->d_start_lanes; c.n_start = (int)h->start_lanes.size();
     c.key0 = h->d_key0; c.key1 = h->d_key1; c.veh_base = h->d_veh_base; c.scen_step = h->d_step;
     c.metrics = h->d_metrics;
     for (int k = 0; k < 2; ++k) {
         const SnapBufs& b = h->snap[k == 0 ? cur : 1 - cur];
         Snap<Real>& s = k == 0 ? c.cur : c.nxt;
-        s.lane = b.lane; s.s = (Real*)b.s; s.v = (Real*)b.v; s.id = b.id; s.v0f = b.v0f;
-        s.rptr = b.rptr; s.rlast = b.rlast; s.nl = b.nl; s.off = b.off;
+        s.a = (RecA<Real>*)b.a; s.b = b.b; s.off = b.off;
     }
-    c.code = h->d_code; c.rs = (Real*)h->d_rs; c.rv = (Real*)h->d_rv;
-    c.es = (Real*)h->d_es; c.ev = (Real*)h->d_ev; c.elane = h->d_elane; c.eid = h->d_eid;
-    c.ev0f = h->d_ev0f; c.erptr = h->d_erptr; c.erlast = h->d_erlast; c.enl = h->d_enl;
-    c.enext = h->d_enext; c.head = h->d_head; c.enter = h->d_enter; c.leave = h->d_leave;
-    c.lbefore = h->d_lbefore; c.lane_tiles = h->d_lane_tiles; c.place_tiles = h->d_place_tiles;
-    c.n_lane_tiles = h->n_lane_tiles; c.max_place_tiles = h->max_place_tiles; c.cnt = h->d_cnt;
+    c.code = h->d_code; c.stay = (SV<Real>*)h->d_stay;
+    c.ea = (RecA<Real>*)h->d_ea; c.eb = h->d_eb; c.enext = h->d_enext; c.head = h->d_head;
+    c.enter = h->d_enter; c.leave = h->d_leave; c.lbefore = h->d_lbefore;
+    c.tile_leave = h->d_tile_leave; c.tile_prefix = h->d_tile_prefix; c.lane_tiles = h->d_lane_tiles;
+    c.n_lane_tiles = h->n_lane_tiles; c.max_slot_tiles = h->max_slot_tiles;
+    c.n_junc_chunks = h->n_junc_chunks; c.cnt = h->d_cnt;
     const MossParams& p = h->prm;
     c.dt = Real(p.dt); c.a_max = Real(p.a_max); c.b_comf = Real(p.b_comf); c.T = Real(p.T);
     c.s0 = Real(p.s0); c.len = Real(p.veh_len); c.pol = Real(p.politeness); c.a_th = Real(p.a_th);
@@ -272,18 +274,17 @@ Ctx<Real> make_ctx(MossHandle* h, int cur) {
 }
 
 struct Grids {
-    int prep, decide, lanescan, place;
+    int decide_work, decide_ins, lanescan, place;
 };
 
 Grids grids(const MossHandle* h) {
     Grids g;
-    const int cap = h->sm_count * 8;
-    const long long work = std::max<long long>(std::max(h->n_lanes, h->n_junctions),
-                                               std::max(h->n_lane_tiles, h->max_place_tiles));
-    g.prep = (int)std::max<long long>(1, std::min<long long>((work + PREP_THREADS - 1) / PREP_THREADS, cap));
-    g.decide = (int)std::max<long long>(1, std::min<long long>((h->n_veh + DECIDE_THREADS - 1) / DECIDE_THREADS, cap));
-    g.lanescan = std::max(1, std::min(h->n_lane_tiles, h->sm_count * 4));
-    g.place = (int)std::max<long long>(1, std::min<long long>(h->max_place_tiles, cap));
+    g.decide_work = std::max(1, std::min(h->max_slot_tiles, h->sm_count * 3));
+    const int ns = (int)h->start_lanes.size();
+    g.decide_ins = ns > 0 ? std::max(1, std::min((ns + TILE - 1) / TILE, h->sm_count)) : 0;
+    const int tickets = h->n_lane_tiles + 1 + h->n_junc_chunks;
+    g.lanescan = std::max(1, std::min(tickets, h->sm_count * 4));
+    g.place = std::max(1, std::min(2 * h->max_slot_tiles, h->sm_count * 8));
     return g;
 }
 
@@ -293,19 +294,38 @@ void enqueue_step(MossHandle* h, int cur, bool timed) {
     const Grids g = grids(h);
     cudaStream_t s = h->stream;
     if (timed) cudaEventRecord(h->ev[0], s);
-    k_prepare<Real><<<g.prep, PREP_THREADS, 0, s>>>(c);
+    k_decide<Real><<<g.decide_work + g.decide_ins, TILE, 0, s>>>(c, g.decide_work);
     if (timed) cudaEventRecord(h->ev[1], s);
-    k_decide<Real><<<g.decide, DECIDE_THREADS, 0, s>>>(c);
-    if (timed) cudaEventRecord(h->ev[2], s);
     k_lanescan<Real><<<g.lanescan, LANESCAN_THREADS, 0, s>>>(c);
+    if (timed) cudaEventRecord(h->ev[2], s);
+    k_place<Real><<<g.place, TILE, 0, s>>>(c);
     if (timed) cudaEventRecord(h->ev[3], s);
-    k_place<Real><<<g.place, PLACE_THREADS, 0, s>>>(c);
-    if (timed) cudaEventRecord(h->ev[4], s);
 }
 
 void enqueue(MossHandle* h, int cur, bool timed) {
     if (h->precision == 64) enqueue_step<double>(h, cur, timed);
     else enqueue_step<float>(h, cur, timed);
+}
+
+template <typename Real>
+void enqueue_junction_init(MossHandle* h) {
+    Ctx<Real> c = make_ctx<Real>(h, h->parity);
+    const int nb = std::max(1, std::min((h->n_junctions + 255) / 256, h->sm_count * 4));
+    k_junction_init<Real><<<nb, 256, 0, h->stream>>>(c);
+}
+
+int junction_init(MossHandle* h) {
+    if (h->n_junctions == 0) return MOSS_OK;
+    if (h->precision == 64) enqueue_junction_init<double>(h);
+    else enqueue_junction_init<float>(h);
+    CK(cudaGetLastError());
+    return MOSS_OK;
+}
+
+template <typename Real>
+void enqueue_set_signal(MossHandle* h, int n, int policy) {
+    Ctx<Real> c = make_ctx<Real>(h, h->parity);
+    k_set_signal<Real><<<(n + 255) / 256, 256, 0, h->stream>>>(c, n, h->d_stage, h->d_stage + n, policy);
 }
 
 void destroy_graphs(MossHandle* h) {
@@ -314,7 +334,6 @@ void destroy_graphs(MossHandle* h) {
         if (h->g1[k]) cudaGraphExecDestroy(h->g1[k]);
         h->g2[k] = h->g1[k] = nullptr;
     }
-    h->graphs_ready = false;
 }
 
 int build_graphs(MossHandle* h) {
@@ -331,24 +350,16 @@ int build_graphs(MossHandle* h) {
             (nsteps == 2 ? h->g2[p] : h->g1[p]) = ex;
         }
     }
-    h->graphs_ready = true;
     return MOSS_OK;
 }
 
-__global__ void k_set_signal(int n, const int32_t* ids, const int32_t* phases, int policy,
-                             int32_t* junc_policy, int32_t* junc_manual) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    junc_policy[ids[k]] = policy;
-    if (policy == POL_MANUAL) junc_manual[ids[k]] = phases[k];
-}
-
-// read back and clear the device error word
+// read back the device error word; recoverable reports are cleared once read,
+// a poisoning error stays (every later step of the handle is skipped)
 int check_device(MossHandle* h) {
     int err = 0;
     CK(cudaMemcpy(&err, &h->d_cnt->err, sizeof(int), cudaMemcpyDeviceToHost));
     if (err == 0) return MOSS_OK;
-    if (!(err & ERR_POISON)) {  // recoverable reports are cleared once read
+    if (!(err & ERR_POISON)) {
         const int zero = 0;
         CK(cudaMemcpy(&h->d_cnt->err, &zero, sizeof(int), cudaMemcpyHostToDevice));
     }
@@ -356,7 +367,7 @@ int check_device(MossHandle* h) {
     std::string m = "device reported:";
     if (err & ERR_ROUTE) m += " undrivable route;";
     if (err & ERR_TRANSFER) m += " transfer overflow;";
-    if (err & ERR_RANGE) m += " list overflow;";
+    if (err & ERR_RANGE) m += " index out of range;";
     return fail(h, MOSS_EDEVICE, m);
 }
 
@@ -385,9 +396,8 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
     h->n_lanes = (int)tot_lanes; h->n_junctions = (int)tot_j; h->n_veh = (int)tot_v;
     h->n_phases = (int)tot_ph;
     const int NL = h->n_lanes, NJ = h->n_junctions, NV = h->n_veh;
-    h->lane_scen.resize(NL); h->lane_lo.resize(NL); h->lane_hi.resize(NL); h->jl_b.resize(NL);
-    h->jl_e.resize(NL); h->lane_road.resize(NL); h->lane_src_road.resize(NL); h->L.resize(NL);
-    h->vmax.resize(NL);
+    h->lanes.resize(NL);
+    h->lane_src_road.assign(NL, -1);
     h->junc_scen.resize(NJ); h->junc_phase_off.resize(NJ + 1);
     std::vector<int32_t> junc_offset(NJ), phase_green(tot_ph), phase_amber(tot_ph);
     h->route_off.resize(NV + 1); h->routes.resize(tot_routes); h->dep.resize(NV);
@@ -404,25 +414,24 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
         for (int r = 0; r < nt.n_roads; ++r)
             for (int l = nt.road_lane_off[r]; l < nt.road_lane_off[r + 1]; ++l) road_of[l] = r;
         for (int l = 0; l < nt.n_lanes; ++l) {
-            const int g = LO + l;
-            h->lane_scen[g] = k;
-            h->L[g] = nt.lane_length[l];
-            h->vmax[g] = nt.lane_vmax[l];
+            LaneInfo& li = h->lanes[LO + l];
+            li.scen = k;
+            li.L = nt.lane_length[l];
+            li.vmax = nt.lane_vmax[l];
             if (l < NRL) {
                 const int r = road_of[l];
-                h->lane_lo[g] = LO + nt.road_lane_off[r];
-                h->lane_hi[g] = LO + nt.road_lane_off[r + 1];
-                h->jl_b[g] = LO + nt.jl_off[l];
-                h->jl_e[g] = LO + nt.jl_off[l + 1];
-                h->lane_road[g] = RO + r;
-                h->lane_src_road[g] = RO + r;
+                li.lo = LO + nt.road_lane_off[r];
+                li.hi = LO + nt.road_lane_off[r + 1];
+                li.jb = LO + nt.jl_off[l];
+                li.je = LO + nt.jl_off[l + 1];
+                li.road = RO + r;
             } else {
                 const int q = l - NRL;
-                h->lane_lo[g] = -1;
-                h->lane_hi[g] = LO + nt.jl_target[q];
-                h->jl_b[g] = JO + nt.jl_junction[q];
-                h->jl_e[g] = nt.jl_mask[q];
-                h->lane_road[g] = RO + road_of[nt.jl_target[q]];
+                li.lo = -1;
+                li.hi = LO + nt.jl_target[q];
+                li.jb = JO + nt.jl_junction[q];
+                li.je = nt.jl_mask[q];
+                li.road = RO + road_of[nt.jl_target[q]];
             }
         }
         for (int l = 0; l < NRL; ++l)
@@ -466,6 +475,9 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
             std::stable_sort(h->q_ids.begin() + h->q_off[l], h->q_ids.begin() + h->q_off[l + 1],
                              [&](int a, int b) { return h->dep[a] < h->dep[b]; });
     }
+    h->start_lanes.clear();
+    for (int l = 0; l < NL; ++l)
+        if (h->q_off[l + 1] > h->q_off[l]) h->start_lanes.push_back(l);
 
     // ---- device
     if (stream) {
@@ -476,18 +488,7 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
     }
     CK(cudaGetDevice(&h->device));
     CK(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device));
-    const size_t rs = h->precision == 64 ? 8 : 4;
-    std::vector<int2> lohi(NL), jl(NL);
-    for (int l = 0; l < NL; ++l) {
-        lohi[l] = make_int2(h->lane_lo[l], h->lane_hi[l]);
-        jl[l] = make_int2(h->jl_b[l], h->jl_e[l]);
-    }
-    TRY(upload(h, &h->d_L, h->L));
-    TRY(upload(h, &h->d_vmax, h->vmax));
-    TRY(upload(h, &h->d_lane_scen, h->lane_scen));
-    TRY(upload(h, &h->d_lane_road, h->lane_road));
-    TRY(upload(h, &h->d_lohi, lohi));
-    TRY(upload(h, &h->d_jl, jl));
+    TRY(upload(h, &h->d_lane, h->lanes));
     TRY(upload(h, &h->d_junc_offset, junc_offset));
     TRY(upload(h, &h->d_junc_phase_off, h->junc_phase_off));
     TRY(upload(h, &h->d_phase_green, phase_green));
@@ -505,39 +506,44 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
     TRY(upload(h, &h->d_q_off, h->q_off));
     TRY(upload(h, &h->d_q_ids, h->q_ids));
     TRY(upload(h, &h->d_q_head, std::vector<int32_t>(h->q_off.begin(), h->q_off.end() - 1)));
+    TRY(upload(h, &h->d_start_lanes, h->start_lanes));
     TRY(upload(h, &h->d_key0, h->key0));
     TRY(upload(h, &h->d_key1, h->key1));
     TRY(upload(h, &h->d_veh_base, std::vector<int32_t>(h->scen_veh_off.begin(), h->scen_veh_off.end() - 1)));
     TRY(upload(h, &h->d_step, std::vector<long long>(n, 0)));
     TRY(upload(h, &h->d_metrics, std::vector<long long>((size_t)n * M_NFIELDS, 0)));
     const size_t cap = std::max(NV, 1);
+    const size_t ra = reca_size(h->precision);
     for (int k = 0; k < 2; ++k) {
         SnapBufs& b = h->snap[k];
-        TRY(dalloc(h, &b.lane, cap)); TRY(dalloc(h, &b.id, cap)); TRY(dalloc(h, &b.rptr, cap));
-        TRY(dalloc(h, &b.rlast, cap)); TRY(dalloc(h, &b.nl, cap)); TRY(dalloc(h, &b.v0f, cap));
-        TRY(dalloc(h, (char**)&b.s, cap * rs)); TRY(dalloc(h, (char**)&b.v, cap * rs));
+        TRY(dalloc(h, (char**)&b.a, cap * ra));
+        TRY(dalloc(h, &b.b, cap));
         TRY(upload(h, &b.off, std::vector<int32_t>(NL + 1, 0)));
     }
     TRY(dalloc(h, &h->d_code, cap));
-    TRY(dalloc(h, (char**)&h->d_rs, cap * rs)); TRY(dalloc(h, (char**)&h->d_rv, cap * rs));
-    TRY(dalloc(h, (char**)&h->d_es, cap * rs)); TRY(dalloc(h, (char**)&h->d_ev, cap * rs));
-    TRY(dalloc(h, &h->d_elane, cap)); TRY(dalloc(h, &h->d_eid, cap)); TRY(dalloc(h, &h->d_erptr, cap));
-    TRY(dalloc(h, &h->d_erlast, cap)); TRY(dalloc(h, &h->d_enl, cap)); TRY(dalloc(h, &h->d_enext, cap));
-    TRY(dalloc(h, &h->d_ev0f, cap));
-    TRY(dalloc(h, &h->d_head, NL)); TRY(dalloc(h, &h->d_enter, NL)); TRY(dalloc(h, &h->d_leave, NL));
+    TRY(dalloc(h, (char**)&h->d_stay, cap * sv_size(h->precision)));
+    TRY(dalloc(h, (char**)&h->d_ea, cap * ra));
+    TRY(dalloc(h, &h->d_eb, cap));
+    TRY(dalloc(h, &h->d_enext, cap));
+    TRY(upload(h, &h->d_head, std::vector<unsigned long long>(NL, 0ull)));
+    TRY(upload(h, &h->d_enter, std::vector<int32_t>(NL, 0)));
+    TRY(upload(h, &h->d_leave, std::vector<int32_t>(NL, 0)));
     TRY(dalloc(h, &h->d_lbefore, NL));
     h->n_lane_tiles = (NL + LANESCAN_TILE - 1) / LANESCAN_TILE;
-    h->max_place_tiles = 2 * ((NV + PLACE_TILE - 1) / PLACE_TILE) + 2;
-    TRY(dalloc(h, &h->d_lane_tiles, h->n_lane_tiles));
-    TRY(dalloc(h, &h->d_place_tiles, h->max_place_tiles));
+    h->max_slot_tiles = (NV + TILE - 1) / TILE + 1;
+    h->n_junc_chunks = (NJ + JUNC_CHUNK - 1) / JUNC_CHUNK;
+    TRY(dalloc(h, &h->d_tile_leave, h->max_slot_tiles));
+    TRY(dalloc(h, &h->d_tile_prefix, h->max_slot_tiles));
+    TRY(upload(h, &h->d_lane_tiles, std::vector<unsigned long long>(h->n_lane_tiles, 0ull)));
     Counters c0{};
+    c0.tag = 1;
     TRY(upload(h, &h->d_cnt, std::vector<Counters>(1, c0)));
-    TRY(dalloc(h, &h->d_stage_a, 2 * std::max(NJ, 1)));
-    TRY(dalloc(h, &h->d_stage_b, std::max(NJ, 1)));
+    TRY(dalloc(h, &h->d_stage, 2 * std::max(NJ, 1)));
     CK(cudaHostAlloc((void**)&h->h_stage, sizeof(int32_t) * 2 * std::max(NJ, 1), cudaHostAllocDefault));
     CK(cudaEventCreateWithFlags(&h->stage_free, cudaEventDisableTiming));
     CK(cudaEventRecord(h->stage_free, h->stream));
-    for (int k = 0; k < 5; ++k) CK(cudaEventCreate(&h->ev[k]));
+    for (int k = 0; k <= N_STEP_KERNELS; ++k) CK(cudaEventCreate(&h->ev[k]));
+    TRY(junction_init(h));
     CK(cudaStreamSynchronize(h->stream));
     TRY(build_graphs(h));
     return MOSS_OK;
@@ -548,7 +554,7 @@ void free_all(MossHandle* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
-    for (int k = 0; k < 5; ++k)
+    for (int k = 0; k <= N_STEP_KERNELS; ++k)
         if (h->ev[k]) cudaEventDestroy(h->ev[k]);
     if (h->stage_free) cudaEventDestroy(h->stage_free);
     if (h->h_stage) cudaFreeHost(h->h_stage);
@@ -581,6 +587,15 @@ int scen_metrics(MossHandle* h, int s, MossMetrics* out) {
     return check_device(h);
 }
 
+template <typename Real>
+void unpack_a(const std::vector<char>& raw, int n, std::vector<int32_t>& lane, std::vector<int32_t>& id,
+              std::vector<double>& sv, std::vector<double>& vv) {
+    const RecA<Real>* a = (const RecA<Real>*)raw.data();
+    for (int k = 0; k < n; ++k) {
+        lane[k] = a[k].lane; id[k] = a[k].id; sv[k] = (double)a[k].s; vv[k] = (double)a[k].v;
+    }
+}
+
 int scen_state(MossHandle* h, int s, MossState* out) {
     if (!out || !out->status || !out->lane || !out->s || !out->v || !out->rc || !out->flags)
         return fail(h, MOSS_EINVAL, "null state array");
@@ -590,23 +605,18 @@ int scen_state(MossHandle* h, int s, MossState* out) {
     CK(cudaMemcpy(&c, h->d_cnt, sizeof(c), cudaMemcpyDeviceToHost));
     const int n = c.n_cur, NV = h->n_veh;
     const SnapBufs& b = h->snap[h->parity];
-    std::vector<int32_t> lane(n), id(n), rptr(n), status(NV), vflags(NV);
+    const size_t ra = reca_size(h->precision);
+    std::vector<char> raw((size_t)n * ra);
+    std::vector<RecB> rb(n);
+    std::vector<int32_t> lane(n), id(n), status(NV), vflags(NV);
     std::vector<double> sv(n), vv(n);
     long long step = 0;
     CK(cudaMemcpy(&step, h->d_step + s, sizeof(long long), cudaMemcpyDeviceToHost));
     if (n > 0) {
-        CK(cudaMemcpy(lane.data(), b.lane, n * 4, cudaMemcpyDeviceToHost));
-        CK(cudaMemcpy(id.data(), b.id, n * 4, cudaMemcpyDeviceToHost));
-        CK(cudaMemcpy(rptr.data(), b.rptr, n * 4, cudaMemcpyDeviceToHost));
-        if (h->precision == 64) {
-            CK(cudaMemcpy(sv.data(), b.s, n * 8, cudaMemcpyDeviceToHost));
-            CK(cudaMemcpy(vv.data(), b.v, n * 8, cudaMemcpyDeviceToHost));
-        } else {
-            std::vector<float> fs(n), fv(n);
-            CK(cudaMemcpy(fs.data(), b.s, n * 4, cudaMemcpyDeviceToHost));
-            CK(cudaMemcpy(fv.data(), b.v, n * 4, cudaMemcpyDeviceToHost));
-            for (int i = 0; i < n; ++i) { sv[i] = fs[i]; vv[i] = fv[i]; }
-        }
+        CK(cudaMemcpy(raw.data(), b.a, raw.size(), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(rb.data(), b.b, n * sizeof(RecB), cudaMemcpyDeviceToHost));
+        if (h->precision == 64) unpack_a<double>(raw, n, lane, id, sv, vv);
+        else unpack_a<float>(raw, n, lane, id, sv, vv);
     }
     CK(cudaMemcpy(status.data(), h->d_vstatus, NV * 4, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(vflags.data(), h->d_vflags, NV * 4, cudaMemcpyDeviceToHost));
@@ -626,14 +636,14 @@ int scen_state(MossHandle* h, int s, MossState* out) {
         out->lane[i] = lane[k] - lo;
         out->s[i] = sv[k];
         out->v[i] = vv[k];
-        out->rc[i] = rptr[k] - h->route_off[g];
+        out->rc[i] = rb[k].rptr - h->route_off[g];
     }
     return check_device(h);
 }
 
 int jl_toward_host(const MossHandle* h, int l, int out_road) {
-    for (int j = h->jl_b[l]; j < h->jl_e[l]; ++j)
-        if (h->lane_road[j] == out_road) return j;
+    for (int j = h->lanes[l].jb; j < h->lanes[l].je; ++j)
+        if (h->lanes[j].road == out_road) return j;
     return -1;
 }
 
@@ -641,33 +651,28 @@ template <typename Real>
 int upload_state(MossHandle* h, const std::vector<int>& order, const std::vector<double>& s,
                  const std::vector<double>& v, const std::vector<int>& lane_of, const std::vector<int>& rc) {
     const int n = (int)order.size();
-    std::vector<int32_t> lane(n), id(n), rptr(n), rlast(n), nl(n);
-    std::vector<float> v0f(n);
-    std::vector<Real> rs_(n), rv_(n);
+    std::vector<RecA<Real>> a(n);
+    std::vector<RecB> b(n);
     std::vector<int32_t> off(h->n_lanes + 1, 0);
     for (int k = 0; k < n; ++k) {
         const int g = order[k];
         const int l = lane_of[g];
-        lane[k] = l; id[k] = g; rs_[k] = Real(s[g]); rv_[k] = Real(v[g]); v0f[k] = h->v0f[g];
-        rptr[k] = h->route_off[g] + rc[g];
-        rlast[k] = h->route_off[g + 1] - 1;
-        if (h->lane_lo[l] < 0) nl[k] = h->lane_hi[l];
-        else nl[k] = rptr[k] < rlast[k] ? jl_toward_host(h, l, h->routes[rptr[k] + 1]) : -1;
+        std::memset(&a[k], 0, sizeof(a[k]));
+        a[k].s = Real(s[g]); a[k].v = Real(v[g]); a[k].id = g; a[k].lane = l;
+        b[k].v0f = h->v0f[g];
+        b[k].rptr = h->route_off[g] + rc[g];
+        b[k].rlast = h->route_off[g + 1] - 1;
+        if (h->lanes[l].lo < 0) b[k].nl = h->lanes[l].hi;
+        else b[k].nl = b[k].rptr < b[k].rlast ? jl_toward_host(h, l, h->routes[b[k].rptr + 1]) : -1;
         off[l + 1]++;
     }
     for (int l = 0; l < h->n_lanes; ++l) off[l + 1] += off[l];
-    const SnapBufs& b = h->snap[h->parity];
+    const SnapBufs& sb = h->snap[h->parity];
     if (n > 0) {
-        CK(cudaMemcpy(b.lane, lane.data(), n * 4, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(b.id, id.data(), n * 4, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(b.rptr, rptr.data(), n * 4, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(b.rlast, rlast.data(), n * 4, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(b.nl, nl.data(), n * 4, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(b.v0f, v0f.data(), n * 4, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(b.s, rs_.data(), n * sizeof(Real), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(b.v, rv_.data(), n * sizeof(Real), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(sb.a, a.data(), n * sizeof(RecA<Real>), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(sb.b, b.data(), n * sizeof(RecB), cudaMemcpyHostToDevice));
     }
-    CK(cudaMemcpy(b.off, off.data(), off.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(sb.off, off.data(), off.size() * 4, cudaMemcpyHostToDevice));
     return MOSS_OK;
 }
 
@@ -711,14 +716,11 @@ int moss_step(moss_t h, int n) {
         for (int k = 0; k < n; ++k) {
             enqueue(h, h->parity, true);
             h->parity ^= 1;
-            CK(cudaEventSynchronize(h->ev[4]));
-            for (int q = 0; q < 4; ++q) {
+            CK(cudaEventSynchronize(h->ev[N_STEP_KERNELS]));
+            for (int q = 0; q < N_STEP_KERNELS; ++q) {
                 float ms = 0;
                 CK(cudaEventElapsedTime(&ms, h->ev[q], h->ev[q + 1]));
-                // event pairs bracket prepare, decide, lanescan, place; report
-                // in the order decide, lanescan, place, prepare
-                const int slot = q == 0 ? 3 : q - 1;
-                h->kms[slot] += ms;
+                h->kms[q] += ms;  // decide, lanescan, place
             }
             h->ksteps++;
         }
@@ -755,16 +757,14 @@ int moss_batch_set_signal_phase(moss_t h, int scenario, int n, const int32_t* ju
     }
     // the pinned staging area is reused: wait until the previous copy out of it ran
     CK(cudaEventSynchronize(h->stage_free));
-    int32_t* ids = h->h_stage;
-    int32_t* ph = h->h_stage + n;
     for (int k = 0; k < n; ++k) {
-        ids[k] = j0 + junction_ids[k];
-        ph[k] = phase_idx[k];
+        h->h_stage[k] = j0 + junction_ids[k];
+        h->h_stage[n + k] = phase_idx[k];
     }
-    CK(cudaMemcpyAsync(h->d_stage_a, h->h_stage, 2 * n * 4, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->d_stage, h->h_stage, 2 * n * 4, cudaMemcpyHostToDevice, h->stream));
     CK(cudaEventRecord(h->stage_free, h->stream));
-    k_set_signal<<<(n + 255) / 256, 256, 0, h->stream>>>(n, h->d_stage_a, h->d_stage_a + n, POL_MANUAL,
-                                                          h->d_junc_policy, h->d_junc_manual);
+    if (h->precision == 64) enqueue_set_signal<double>(h, n, POL_MANUAL);
+    else enqueue_set_signal<float>(h, n, POL_MANUAL);
     CK(cudaGetLastError());
     return MOSS_OK;
 }
@@ -772,17 +772,20 @@ int moss_batch_set_signal_phase(moss_t h, int scenario, int n, const int32_t* ju
 int moss_set_signal_policy(moss_t h, int n, const int32_t* junction_ids, int32_t policy) {
     if (!h) return MOSS_EINVAL;
     if (policy < 0 || policy > 2) return fail(h, MOSS_EINVAL, "unknown policy");
-    if (n < 0 || (n > 0 && !junction_ids) || n > h->n_junctions) return fail(h, MOSS_EINVAL, "bad arrays");
-    if (n == 0) return MOSS_OK;
     const int nj = h->scen_junc_off[1];
+    if (n < 0 || (n > 0 && !junction_ids) || n > nj) return fail(h, MOSS_EINVAL, "bad arrays");
+    if (n == 0) return MOSS_OK;
     for (int k = 0; k < n; ++k)
         if (junction_ids[k] < 0 || junction_ids[k] >= nj) return fail(h, MOSS_EINVAL, "junction id out of range");
     CK(cudaEventSynchronize(h->stage_free));
-    for (int k = 0; k < n; ++k) h->h_stage[k] = junction_ids[k];
-    CK(cudaMemcpyAsync(h->d_stage_a, h->h_stage, n * 4, cudaMemcpyHostToDevice, h->stream));
+    for (int k = 0; k < n; ++k) {
+        h->h_stage[k] = junction_ids[k];
+        h->h_stage[n + k] = 0;
+    }
+    CK(cudaMemcpyAsync(h->d_stage, h->h_stage, 2 * n * 4, cudaMemcpyHostToDevice, h->stream));
     CK(cudaEventRecord(h->stage_free, h->stream));
-    k_set_signal<<<(n + 255) / 256, 256, 0, h->stream>>>(n, h->d_stage_a, h->d_stage_a, policy,
-                                                          h->d_junc_policy, h->d_junc_manual);
+    if (h->precision == 64) enqueue_set_signal<double>(h, n, policy);
+    else enqueue_set_signal<float>(h, n, policy);
     CK(cudaGetLastError());
     return MOSS_OK;
 }
@@ -832,14 +835,14 @@ int moss_set_state(moss_t h, const MossState* in, int64_t step) {
         if (l < 0 || l >= h->n_lanes) return fail(h, MOSS_EINVAL, "active vehicle on a bad lane");
         if (rc[i] < 0 || rc[i] >= nr) return fail(h, MOSS_EINVAL, "route cursor out of range");
         const int road = h->routes[h->route_off[i] + rc[i]];
-        if (h->lane_lo[l] >= 0) {
-            if (h->lane_road[l] != road) return fail(h, MOSS_EINVAL, "lane is not on the route's road");
+        if (h->lanes[l].lo >= 0) {
+            if (h->lanes[l].road != road) return fail(h, MOSS_EINVAL, "lane is not on the route's road");
         } else {
             if (rc[i] + 1 >= nr || h->lane_src_road[l] != road ||
-                h->lane_road[l] != h->routes[h->route_off[i] + rc[i] + 1])
+                h->lanes[l].road != h->routes[h->route_off[i] + rc[i] + 1])
                 return fail(h, MOSS_EINVAL, "junction lane does not join the route's roads");
         }
-        if (!(s[i] >= 0.0 && s[i] <= h->L[l]) || !(v[i] >= 0.0) || !std::isfinite(v[i]))
+        if (!(s[i] >= 0.0 && s[i] <= h->lanes[l].L) || !(v[i] >= 0.0) || !std::isfinite(v[i]))
             return fail(h, MOSS_EINVAL, "position or speed out of range");
         lane_of[i] = l;
         order.push_back(i);
@@ -873,8 +876,11 @@ int moss_set_state(moss_t h, const MossState* in, int64_t step) {
     long long cur[2] = {n_act, n_arr};
     CK(cudaMemcpy(h->d_metrics + M_CUR_ACTIVE, cur, sizeof(cur), cudaMemcpyHostToDevice));
     Counters c{};
-    c.n_cur = (int)n_act; c.n_next = (int)n_act;
+    CK(cudaMemcpy(&c, h->d_cnt, sizeof(c), cudaMemcpyDeviceToHost));
+    c.n_cur = (int)n_act; c.n_next = (int)n_act; c.n_ent = 0; c.ticket_lane = 0; c.done_place = 0;
     CK(cudaMemcpy(h->d_cnt, &c, sizeof(c), cudaMemcpyHostToDevice));
+    TRY(junction_init(h));
+    CK(cudaStreamSynchronize(h->stream));
     return MOSS_OK;
 }
 

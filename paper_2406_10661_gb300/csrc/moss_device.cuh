@@ -1,24 +1,26 @@
 // Device side of the per-timestep vehicle update (arxiv 2406.10661, §3.1,
 // App. B.2-B.3), written for sm_103a.
 //
-// Layout.  Active vehicles live in a lane-major snapshot: structure-of-arrays
-// sorted by (lane, s descending, id ascending); lane l occupies slots
-// [off[l], off[l+1]).  The snapshot of step t is read-only during step t
-// (§3.1 two-phase read/write separation); step t writes the snapshot of
-// step t+1 into the other buffer.  The paper's linked lists with side
-// pointers (§3.1) become O(1) neighbour slots (leader = slot-1, follower =
-// slot+1) and a binary search in the adjacent lane's segment.
+// Layout.  Active vehicles live in a lane-major snapshot sorted by (lane,
+// s descending, id ascending); lane l occupies slots [off[l], off[l+1]).
+// Each slot holds two 16-byte records: A = (s, v, id, lane) and B = (v0f,
+// route index of the current road, route index of the last road, next lane).
+// The snapshot of step t is read-only during step t (§3.1 two-phase
+// read/write separation); step t writes the snapshot of step t+1 into the
+// other buffer.  The paper's linked lists with side pointers (§3.1) become
+// O(1) neighbour slots (leader = slot-1, follower = slot+1) and a binary
+// search in the adjacent lane's segment (adjacent lanes of a road are
+// adjacent in memory).
 //
-// One step = four kernels:
-//   k_prepare   junction signal states for step t (§3.2 policies), departure
-//               insertion against the snapshot (App. B.2 update stream 3),
-//               reset of per-lane counters;
+// One step = three kernels:
 //   k_decide    per vehicle: sensing, IDM (App. B.3 eqs. (1)-(2)), randomized
 //               MOBIL (App. B.3) with deterministic conflict resolution,
 //               ballistic integration with clamps, transfer at lane ends and
-//               arrival (App. B.2 update stream 1);
+//               arrival (App. B.2 update stream 1); extra blocks run the
+//               departure insertion (App. B.2 update stream 3);
 //   k_lanescan  per-lane sizes of the next snapshot -> offsets (single-pass
-//               decoupled look-back scan);
+//               decoupled look-back scan), prefix of leavers per slot tile,
+//               signal states of the next step (§3.2 policies);
 //   k_place     writes the next snapshot: vehicles that kept their lane keep
 //               their relative order (no overtaking within a lane), vehicles
 //               that entered a lane are merged by (s, id).
@@ -50,49 +52,58 @@ enum : int { ERR_TIMEOUT = 1, ERR_ROUTE = 2, ERR_TRANSFER = 4, ERR_RANGE = 8 };
 // of the handle returns at once and the host reports the error
 constexpr int ERR_POISON = ERR_TIMEOUT | ERR_RANGE;
 
-constexpr int DECIDE_THREADS = 256;
+constexpr int TILE = 256;           // slots per tile of k_decide / k_place (= threads)
 constexpr int LANESCAN_THREADS = 256;
 constexpr int LANESCAN_ITEMS = 4;
 constexpr int LANESCAN_TILE = LANESCAN_THREADS * LANESCAN_ITEMS;
-constexpr int PLACE_THREADS = 256;
-constexpr int PLACE_TILE = PLACE_THREADS;  // one slot per thread
-constexpr int PREP_THREADS = 256;
+constexpr int JUNC_CHUNK = 1024;    // junctions per k_lanescan ticket
 constexpr long long SPIN_LIMIT = 1ll << 22;  // bounded waits (~0.5 s with backoff)
 
 struct Counters {
-    int n_cur;      // active vehicles in the current snapshot
-    int n_next;     // active vehicles in the next snapshot
-    int n_ent;      // entrants appended this step
-    int ticket_lane;
-    int ticket_place;
-    int done_place; // k_place blocks finished (the last one resets the step)
+    int n_cur;       // active vehicles in the current snapshot
+    int n_next;      // active vehicles in the next snapshot
+    int n_ent;       // entrants appended this step
+    int ticket_lane; // k_lanescan tickets
+    int done_place;  // k_place blocks finished (the last one closes the step)
     int err;
+    int tag;         // step tag of the per-lane entrant lists (never 0)
     int pad;
+};
+
+// snapshot records
+template <typename Real> struct RecA;
+template <> struct alignas(16) RecA<float> { float s, v; int id, lane; };
+template <> struct alignas(16) RecA<double> { double s, v; int id, lane; };
+struct alignas(16) RecB {
+    float v0f;
+    int rptr;   // index in routes[] of the current road (junction lane: the road just left)
+    int rlast;  // index in routes[] of the last road
+    int nl;     // next lane on the route (-1 on the last road)
+};
+template <typename Real> struct alignas(2 * sizeof(Real)) SV { Real s, v; };
+
+// One 32-byte record per lane.
+//   road lane:     lo, hi = lanes [lo, hi) of its road (left to right); jb, je =
+//                  junction lanes leaving it; road = its road; scen = scenario
+//   junction lane: lo = -1, hi = the road lane it feeds; jb = its junction;
+//                  je = phase mask; road = road of its target
+struct alignas(32) LaneInfo {
+    float L, vmax;
+    int lo, hi, jb, je, road, scen;
 };
 
 template <typename Real>
 struct Snap {
-    int32_t* lane;
-    Real* s;
-    Real* v;
-    int32_t* id;
-    float* v0f;
-    int32_t* rptr;   // absolute index (in routes[]) of the current road
-    int32_t* rlast;  // absolute index of the last road of the route
-    int32_t* nl;     // next lane on the route (-1 on the last road)
-    int32_t* off;    // [n_lanes+1] lane segments
+    RecA<Real>* a;
+    RecB* b;
+    int32_t* off;  // [n_lanes+1] lane segments
 };
 
 template <typename Real>
 struct Ctx {
     // ---- network (possibly a union of scenarios)
     int n_lanes, n_junctions, n_scen, n_veh;
-    const float* L;
-    const float* vmax;
-    const int32_t* lane_scen;  // scenario of the lane
-    const int2* lohi;          // road lane: its road's lanes [lo, hi); junction lane: (-1, target)
-    const int2* jl;            // road lane: leaving junction lanes [b, e); junction lane: (junction, mask)
-    const int32_t* lane_road;  // road lane: road id; junction lane: road id of its target
+    const LaneInfo* lane;
     const int32_t* junc_offset;
     const int32_t* junc_phase_off;
     const int32_t* phase_green;
@@ -100,18 +111,20 @@ struct Ctx {
     const int32_t* junc_scen;
     int32_t* junc_policy;
     int32_t* junc_manual;
-    int32_t* junc_state;  // per step: bits 0-3 phase, 4-7 n_phases, 8 amber, 9 all green
+    int32_t* junc_state;  // bits 0-3 phase, 4-7 n_phases, 8 amber, 9 all green
     // ---- vehicles (by global id)
     const int32_t* route_off;
     const int32_t* routes;
     const int32_t* dep;
     const float* v0f;
     int32_t* vstatus;
-    int32_t* vflags;  // (step & 0xFFFFFF) << 8 | flags
-    // ---- departure queues (by lane; junction lanes have none)
+    int32_t* vflags;  // (step & 0xFFFFFF) << 8 | flags, written when flags != 0
+    // ---- departure queues (by lane) and the lanes that have one
     const int32_t* q_off;
     const int32_t* q_ids;
     int32_t* q_head;
+    const int32_t* start_lanes;
+    int n_start;
     // ---- scenarios
     const uint32_t* key0;
     const uint32_t* key1;
@@ -121,26 +134,19 @@ struct Ctx {
     // ---- snapshots (current -> next)
     Snap<Real> cur, nxt;
     // ---- per-step scratch
-    int8_t* code;  // per current slot: C_STAY / C_MOVE / C_ARRIVE
-    Real* rs;      // stayer's new s
-    Real* rv;      // stayer's new v
-    // entrants of the next snapshot (lane changes, transfers, insertions)
-    Real* es;
-    Real* ev;
-    int32_t* elane;
-    int32_t* eid;
-    float* ev0f;
-    int32_t* erptr;
-    int32_t* erlast;
-    int32_t* enl;
-    int32_t* enext;  // per-lane singly linked list
-    int32_t* head;   // [n_lanes] list head or -1
-    int32_t* enter; // [n_lanes]
-    int32_t* leave; // [n_lanes]
-    int32_t* lbefore;  // [n_lanes] leavers in lanes before l
+    int8_t* code;         // per current slot: C_STAY / C_MOVE / C_ARRIVE
+    SV<Real>* stay;       // stayer's new (s, v)
+    RecA<Real>* ea;       // entrants of the next snapshot (lane changes, transfers, insertions)
+    RecB* eb;
+    int32_t* enext;       // per-lane singly linked list of entrants
+    unsigned long long* head;  // [n_lanes] (tag << 32 | entrant) or stale
+    int32_t* enter;       // [n_lanes], zeroed by k_lanescan after use
+    int32_t* leave;       // [n_lanes], zeroed by k_lanescan after use
+    int32_t* lbefore;     // [n_lanes] leavers in lanes before l
+    int32_t* tile_leave;  // [slot tiles] leavers per tile of the current snapshot
+    int32_t* tile_prefix; // [slot tiles] leavers before the tile
     unsigned long long* lane_tiles;
-    unsigned long long* place_tiles;
-    int n_lane_tiles, max_place_tiles;
+    int n_lane_tiles, max_slot_tiles, n_junc_chunks;
     Counters* cnt;
     // ---- parameters
     Real dt, a_max, b_comf, T, s0, len, pol, a_th, b_safe, p_att, p_hi, p_lo, band;
@@ -171,7 +177,6 @@ __device__ __forceinline__ Real unit24(uint32_t w) {
 }
 
 template <typename Real> __device__ __forceinline__ Real rabs(Real x) { return x < Real(0) ? -x : x; }
-template <typename Real> __device__ __forceinline__ Real rmax(Real a, Real b) { return a > b ? a : b; }
 
 // ---------------------------------------------------------------------------
 // IDM, App. B.3 eqs. (1)-(2), delta = 4 as ((v/v0)^2)^2.
@@ -198,25 +203,48 @@ __device__ __forceinline__ Real p_lc(const Ctx<Real>& c, Real uT) {
     return c.p_lo;
 }
 
-// light of junction lane jl from its junction's state for this step (§3.2; R19)
+// signal state of a junction at step t (§3.2 policies; reading R19)
+__device__ __forceinline__ int junction_state(int policy, int manual, int offset, const int32_t* green,
+                                              const int32_t* amber, int np, long long t) {
+    if (policy == POL_NONE || np <= 0) return 512;
+    if (policy == POL_MANUAL) return (manual & 15) | ((np & 15) << 4);
+    long long cyc = 0;
+    for (int p = 0; p < np; ++p) cyc += green[p] + amber[p];
+    if (cyc <= 0) return 512;
+    long long x = (t + offset) % cyc;
+    if (x < 0) x += cyc;
+    for (int p = 0; p < np; ++p) {
+        const long long g = green[p], a = amber[p];
+        if (x < g + a) return p | ((np & 15) << 4) | (x >= g ? 256 : 0);
+        x -= g + a;
+    }
+    return (np & 15) << 4;
+}
+
 template <typename Real>
-__device__ __forceinline__ int light_of(const Ctx<Real>& c, int jl) {
-    const int2 jm = c.jl[jl];
-    const int st = c.junc_state[jm.x];
+__device__ __forceinline__ int junction_state_at(const Ctx<Real>& c, int j, long long t) {
+    const int p0 = c.junc_phase_off[j];
+    return junction_state(c.junc_policy[j], c.junc_manual[j], c.junc_offset[j], c.phase_green + p0,
+                          c.phase_amber + p0, c.junc_phase_off[j + 1] - p0, t);
+}
+
+// light of a junction lane (its lane record ji) for this step
+template <typename Real>
+__device__ __forceinline__ int light_of(const Ctx<Real>& c, const LaneInfo& ji) {
+    const int st = c.junc_state[ji.jb];
     if (st & 512) return LIGHT_GREEN;
-    const int p = st & 15, np = (st >> 4) & 15, mask = jm.y;
+    const int p = st & 15, np = (st >> 4) & 15, mask = ji.je;
     if (!((mask >> p) & 1)) return LIGHT_RED;
     if (!(st & 256)) return LIGHT_GREEN;
     const int nx = (p + 1) % (np > 0 ? np : 1);
     return ((mask >> nx) & 1) ? LIGHT_GREEN : LIGHT_AMBER;
 }
 
-// junction lane leaving road lane l towards road out_road (-1 if none)
+// junction lane leaving road lane (record li) towards road out_road (-1 if none)
 template <typename Real>
-__device__ __forceinline__ int jl_toward(const Ctx<Real>& c, int l, int out_road) {
-    const int2 r = c.jl[l];
-    for (int j = r.x; j < r.y; ++j)
-        if (c.lane_road[j] == out_road) return j;
+__device__ __forceinline__ int jl_toward(const Ctx<Real>& c, const LaneInfo& li, int out_road) {
+    for (int j = li.jb; j < li.je; ++j)
+        if (c.lane[j].road == out_road) return j;
     return -1;
 }
 
@@ -232,7 +260,8 @@ __device__ __forceinline__ int partition_point(const Ctx<Real>& c, int b, int e,
     int lo = b, hi = e;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (ahead(c.cur.s[mid], c.cur.id[mid], s, id)) lo = mid + 1;
+        const RecA<Real> m = c.cur.a[mid];
+        if (ahead(m.s, m.id, s, id)) lo = mid + 1;
         else hi = mid;
     }
     return lo;
@@ -244,63 +273,70 @@ struct LaneAcc {
     int has_leader, stop, overlap, nl;  // nl: the next lane from this lane on the route
 };
 
-// Ego acceleration on `lane` at (s, v): min over the leader (slot ld in this
-// lane, else lookahead over at most two lanes, R11) and the stop line (R12).
-// nl: next lane from `lane` on the ego's route (-1 none); rptr/rlast: route.
+// Ego acceleration on a lane (record li) at (s, v): min over the leader (slot
+// ld in this lane, else lookahead over at most two lanes, R11) and the stop
+// line (R12).  nl: next lane from this lane on the ego's route (-1 none).
 template <typename Real>
-__device__ LaneAcc<Real> accel_on_lane(const Ctx<Real>& c, int lane, Real s, Real v, Real v0,
-                                       int ld, int nl, int rptr, int rlast) {
+__device__ __forceinline__ LaneAcc<Real> accel_on_lane(const Ctx<Real>& c, const LaneInfo& li, Real s,
+                                                       Real v, Real v0, int ld, int nl, int rptr,
+                                                       int rlast) {
     LaneAcc<Real> r;
     r.has_leader = 0; r.stop = 0; r.overlap = 0; r.gap = Real(0); r.stop_gap = Real(0); r.nl = nl;
     Real a = idm_free(c, v, v0);
-    const bool road = c.lohi[lane].x >= 0;
     if (ld >= 0) {
-        const Real gap = c.cur.s[ld] - c.len - s;
-        a = idm(c, v, v0, gap, v - c.cur.v[ld]);
+        const RecA<Real> L = c.cur.a[ld];
+        const Real gap = L.s - c.len - s;
+        a = idm(c, v, v0, gap, v - L.v);
         r.has_leader = 1; r.gap = gap; r.overlap = gap < Real(0);
-    } else if (nl >= 0) {
-        Real base = Real(c.L[lane]) - s;
-        int x = nl;
-        for (int k = 0; k < 2 && x >= 0; ++k) {
-            const int b = c.cur.off[x], e = c.cur.off[x + 1];
-            if (e > b) {
-                const int rr = e - 1;  // rearmost vehicle of lane x
-                const Real gap = base + c.cur.s[rr] - c.len;
-                a = idm(c, v, v0, gap, v - c.cur.v[rr]);
-                r.has_leader = 1; r.gap = gap;
-                break;
-            }
-            if (k == 1) break;
-            base += Real(c.L[x]);
-            // the lane after x on the route
-            if (c.lohi[x].x < 0) {
-                x = c.lohi[x].y;  // junction lane -> its target road lane
-            } else {
-                // x is a road lane (ego on a junction lane): route road after x's road
-                const int rp = rptr + 1;  // x is road routes[rptr+1]
-                x = (rp < rlast) ? jl_toward(c, x, c.routes[rp + 1]) : -1;
+    }
+    if (nl >= 0) {
+        const LaneInfo ni = c.lane[nl];
+        if (ld < 0) {
+            Real base = Real(li.L) - s;
+            int x = nl;
+            LaneInfo xi = ni;
+            for (int k = 0; k < 2; ++k) {
+                const int b = c.cur.off[x], e = c.cur.off[x + 1];
+                if (e > b) {
+                    const RecA<Real> R = c.cur.a[e - 1];  // rearmost vehicle of lane x
+                    const Real gap = base + R.s - c.len;
+                    a = idm(c, v, v0, gap, v - R.v);
+                    r.has_leader = 1; r.gap = gap;
+                    break;
+                }
+                if (k == 1) break;
+                base += Real(xi.L);
+                // the lane after x on the route
+                if (xi.lo < 0) {
+                    x = xi.hi;  // junction lane -> its target road lane
+                } else {
+                    // x is a road lane (ego on a junction lane): the road after x's road
+                    const int rp = rptr + 1;
+                    x = (rp < rlast) ? jl_toward(c, xi, c.routes[rp + 1]) : -1;
+                }
+                if (x < 0) break;
+                xi = c.lane[x];
             }
         }
-    }
-    if (road && nl >= 0 && light_of(c, nl) != LIGHT_GREEN) {
-        const Real gs = Real(c.L[lane]) - s;
-        const Real as = idm(c, v, v0, gs, v);
-        if (as < a) a = as;
-        r.stop = 1; r.stop_gap = gs;
+        if (li.lo >= 0 && light_of(c, ni) != LIGHT_GREEN) {
+            const Real gs = Real(li.L) - s;
+            const Real as = idm(c, v, v0, gs, v);
+            if (as < a) a = as;
+            r.stop = 1; r.stop_gap = gs;
+        }
     }
     r.a = a;
     return r;
 }
 
-// in-lane acceleration of follower slot f on lane fl towards a leader at
-// (s_ld, v_ld), or on free road (politeness terms, R2)
+// in-lane acceleration of a follower F (desired-speed factor f_v0f, lane limit
+// vmax) towards a leader at (s_ld, v_ld), or on free road (politeness terms, R2)
 template <typename Real>
-__device__ __forceinline__ Real acc_pair(const Ctx<Real>& c, int f, int fl, bool has_ld, Real s_ld,
-                                         Real v_ld) {
-    const Real v0 = Real(c.cur.v0f[f]) * Real(c.vmax[fl]);
-    const Real vf = c.cur.v[f];
-    if (!has_ld) return idm_free(c, vf, v0);
-    return idm(c, vf, v0, s_ld - c.len - c.cur.s[f], vf - v_ld);
+__device__ __forceinline__ Real acc_pair(const Ctx<Real>& c, const RecA<Real>& F, float f_v0f, float vmax,
+                                         bool has_ld, Real s_ld, Real v_ld) {
+    const Real v0 = Real(f_v0f) * Real(vmax);
+    if (!has_ld) return idm_free(c, F.v, v0);
+    return idm(c, F.v, v0, s_ld - c.len - F.s, F.v - v_ld);
 }
 
 template <typename Real>
@@ -312,69 +348,81 @@ struct Decision {
 
 // The full per-vehicle decision before conflict resolution (App. B.3).  A pure
 // function of the snapshot, so any thread can recompute any vehicle's
-// decision bit-for-bit (used to resolve conflicts, R9).
+// decision bit-for-bit (used to resolve conflicts, R9); it has one call site.
 template <typename Real>
-__device__ __noinline__ Decision<Real> decide(const Ctx<Real>& c, int i, long long t,
-                                              uint32_t k0, uint32_t k1, int vbase) {
+__device__ __forceinline__ Decision<Real> decide(const Ctx<Real>& c, int i, long long t, uint32_t k0,
+                                                 uint32_t k1, int vbase) {
     Decision<Real> D;
     D.cand = 0; D.dir = 0; D.tl = -1; D.TL = -1; D.TF = -1; D.flag = 0;
     D.u = Real(0); D.scale = Real(1);
-    const int lane = c.cur.lane[i];
-    const Real s = c.cur.s[i], v = c.cur.v[i];
-    const int id = c.cur.id[i];
-    const int rptr = c.cur.rptr[i], rlast = c.cur.rlast[i], nl = c.cur.nl[i];
-    const Real v0f = Real(c.cur.v0f[i]);
+    const RecA<Real> E = c.cur.a[i];
+    const RecB EB = c.cur.b[i];
+    const int lane = E.lane;
+    const LaneInfo li = c.lane[lane];
     const int b = c.cur.off[lane], e = c.cur.off[lane + 1];
     const int OL = (i > b) ? i - 1 : -1;
-    D.own = accel_on_lane(c, lane, s, v, v0f * Real(c.vmax[lane]), OL, nl, rptr, rlast);
+    const Real v0f = Real(EB.v0f);
+    D.own = accel_on_lane(c, li, E.s, E.v, v0f * Real(li.vmax), OL, EB.nl, EB.rptr, EB.rlast);
     D.tgt = D.own;
-    const int2 lh = c.lohi[lane];
-    if (lh.x < 0 || lh.y - lh.x < 2) return D;  // junction lane or single-lane road
+    if (li.lo < 0 || li.hi - li.lo < 2) return D;  // junction lane or single-lane road
     uint32_t w[4];
-    philox4x32_10(k0, k1, uint32_t(id - vbase), uint32_t(t), 0u, 0u, w);
-    const Real u_att = unit24<Real>(w[0]), u_lc = unit24<Real>(w[1]), u_dir = unit24<Real>(w[2]);
+    philox4x32_10(k0, k1, uint32_t(E.id - vbase), uint32_t(t), 0u, 0u, w);
+    const Real u_att = unit24<Real>(w[0]);
     if (!(u_att < c.p_att)) return D;
+    const Real u_lc = unit24<Real>(w[1]), u_dir = unit24<Real>(w[2]);
 
     const int OF = (i + 1 < e) ? i + 1 : -1;
     Real a_old = Real(0), at_old = Real(0);
     if (OF >= 0) {
-        a_old = acc_pair(c, OF, lane, true, s, v);
-        at_old = OL >= 0 ? acc_pair(c, OF, lane, true, c.cur.s[OL], c.cur.v[OL])
-                         : acc_pair(c, OF, lane, false, Real(0), Real(0));
+        const RecA<Real> F = c.cur.a[OF];
+        const float fv0f = c.cur.b[OF].v0f;
+        a_old = acc_pair(c, F, fv0f, li.vmax, true, E.s, E.v);
+        if (OL >= 0) {
+            const RecA<Real> L = c.cur.a[OL];
+            at_old = acc_pair(c, F, fv0f, li.vmax, true, L.s, L.v);
+        } else {
+            at_old = acc_pair(c, F, fv0f, li.vmax, false, Real(0), Real(0));
+        }
     }
     // next road of the route (for the target lane's junction lane)
-    const int next_road = (nl >= 0) ? c.lane_road[nl] : -1;
+    const int next_road = (EB.nl >= 0) ? c.lane[EB.nl].road : -1;
     Real u[2] = {Real(0), Real(0)}, scl[2] = {Real(0), Real(0)};
     int feas[2] = {0, 0}, TLs[2] = {-1, -1}, TFs[2] = {-1, -1};
     LaneAcc<Real> tg[2];
     tg[0] = D.own; tg[1] = D.own;
-    const Real pos_scale = s > Real(1) ? s : Real(1);
+    const Real pos_scale = E.s > Real(1) ? E.s : Real(1);
+#pragma unroll
     for (int side = 0; side < 2; ++side) {
         const int tl = side == 0 ? lane - 1 : lane + 1;
-        if (tl < lh.x || tl >= lh.y) continue;
+        if (tl < li.lo || tl >= li.hi) continue;
+        const LaneInfo ti = c.lane[tl];
         const int tb = c.cur.off[tl], te = c.cur.off[tl + 1];
-        const int p = partition_point(c, tb, te, s, id);
+        const int p = partition_point(c, tb, te, E.s, E.id);
         const int TL = (p > tb) ? p - 1 : -1, TF = (p < te) ? p : -1;
         TLs[side] = TL; TFs[side] = TF;
         int ok = 1;
+        RecA<Real> TLr, TFr;
+        TLr.s = Real(0); TLr.v = Real(0); TFr.s = Real(0); TFr.v = Real(0);
         if (TL >= 0) {
-            const Real g = c.cur.s[TL] - c.len - s;
+            TLr = c.cur.a[TL];
+            const Real g = TLr.s - c.len - E.s;
             if (!(g > Real(0))) ok = 0;
             if (rabs(g) < c.band * pos_scale) D.flag = 1;
         }
         if (TF >= 0) {
-            const Real g = s - c.len - c.cur.s[TF];
+            TFr = c.cur.a[TF];
+            const Real g = E.s - c.len - TFr.s;
             if (!(g > Real(0))) ok = 0;
             if (rabs(g) < c.band * pos_scale) D.flag = 1;
         }
-        const int nlt = (next_road >= 0) ? jl_toward(c, tl, next_road) : -1;
-        tg[side] = accel_on_lane(c, tl, s, v, v0f * Real(c.vmax[tl]), TL, nlt, rptr, rlast);
+        const int nlt = (next_road >= 0) ? jl_toward(c, ti, next_road) : -1;
+        tg[side] = accel_on_lane(c, ti, E.s, E.v, v0f * Real(ti.vmax), TL, nlt, EB.rptr, EB.rlast);
         const Real at_ego = tg[side].a;
         Real a_new = Real(0), at_new = Real(0);
         if (TF >= 0) {
-            a_new = TL >= 0 ? acc_pair(c, TF, tl, true, c.cur.s[TL], c.cur.v[TL])
-                            : acc_pair(c, TF, tl, false, Real(0), Real(0));
-            at_new = acc_pair(c, TF, tl, true, s, v);
+            const float fv0f = c.cur.b[TF].v0f;
+            a_new = acc_pair(c, TFr, fv0f, ti.vmax, TL >= 0, TLr.s, TLr.v);
+            at_new = acc_pair(c, TFr, fv0f, ti.vmax, true, E.s, E.v);
             if (!(at_new >= -c.b_safe)) ok = 0;
             const Real sc = rabs(at_new) > Real(1) ? rabs(at_new) : Real(1);
             if (rabs(at_new + c.b_safe) < c.band * sc) D.flag = 1;
@@ -418,7 +466,6 @@ __device__ __noinline__ Decision<Real> decide(const Ctx<Real>& c, int i, long lo
 }
 
 // ---------------------------------------------------------------------------
-// bounded acquire load of a look-back tile word
 __device__ __forceinline__ unsigned long long load_acquire(unsigned long long* p) {
     cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> a(*p);
     return a.load(cuda::memory_order_acquire);
@@ -428,12 +475,56 @@ __device__ __forceinline__ void store_release(unsigned long long* p, unsigned lo
     a.store(v, cuda::memory_order_release);
 }
 
+// Warp-cooperative look-back of a decoupled scan (all 32 lanes of one warp).
+// Tile words: flag (2 bits: 1 aggregate, 2 inclusive prefix) | 62-bit value.
+// Returns the exclusive prefix of `tile`; sets *timeout if a bounded wait gave up.
+__device__ __forceinline__ unsigned long long warp_lookback(unsigned long long* st, int tile, bool* timeout) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long prefix = 0;
+    int p = tile - 1;
+    long long spins = 0;
+    while (p >= 0) {
+        const int idx = p - lane;
+        const unsigned long long w = idx >= 0 ? load_acquire(&st[idx]) : (2ull << 62);
+        const unsigned f = (unsigned)(w >> 62);
+        const unsigned m2 = __ballot_sync(0xffffffffu, f == 2);
+        const unsigned m0 = __ballot_sync(0xffffffffu, f == 0);
+        const int first2 = m2 ? __ffs(m2) - 1 : 31;
+        const unsigned upto = first2 >= 31 ? 0xffffffffu : ((2u << first2) - 1u);
+        if (m0 & upto) {
+            if (++spins > SPIN_LIMIT) { *timeout = true; return prefix; }
+            if (spins > 16) __nanosleep(64);
+            continue;
+        }
+        unsigned long long val = (lane <= first2) ? (w & ((1ull << 62) - 1)) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+        prefix += val;
+        if (m2) break;
+        p -= 32;
+    }
+    return prefix;
+}
+
 // Per-scenario metric accumulation: register partials per thread, flushed
 // with one set of atomics per block when the whole block shares a scenario.
 struct MetricAcc {
     int scen;
     long long m[8];  // updates, arrived, tt_steps, speed_fx, lane_changes, flagged, overlaps, inserted
 };
+
+__device__ __forceinline__ int metric_field(int k) {
+    switch (k) {
+        case 0: return M_UPDATES;
+        case 1: return M_ARRIVED;
+        case 2: return M_TT_STEPS;
+        case 3: return M_SPEED_FX;
+        case 4: return M_LANE_CHANGES;
+        case 5: return M_FLAGGED;
+        case 6: return M_OVERLAPS;
+        default: return M_INSERTED;
+    }
+}
 
 __device__ __forceinline__ void macc_reset(MetricAcc& a, int scen) {
     a.scen = scen;
@@ -443,11 +534,9 @@ __device__ __forceinline__ void macc_reset(MetricAcc& a, int scen) {
 
 __device__ __forceinline__ void macc_flush_thread(MetricAcc& a, long long* metrics) {
     if (a.scen < 0) return;
-    static const int map[8] = {M_UPDATES, M_ARRIVED, M_TT_STEPS, M_SPEED_FX, M_LANE_CHANGES,
-                               M_FLAGGED, M_OVERLAPS, M_INSERTED};
 #pragma unroll
     for (int k = 0; k < 8; ++k)
-        if (a.m[k]) atomicAdd((unsigned long long*)&metrics[a.scen * M_NFIELDS + map[k]],
+        if (a.m[k]) atomicAdd((unsigned long long*)&metrics[a.scen * M_NFIELDS + metric_field(k)],
                               (unsigned long long)a.m[k]);
 }
 
@@ -477,9 +566,7 @@ __device__ void macc_flush_block(MetricAcc& a, long long* metrics) {
     if (tid < 8) {
         long long x = 0;
         for (int w = 0; w < THREADS / 32; ++w) x += red[tid][w];
-        static const int map[8] = {M_UPDATES, M_ARRIVED, M_TT_STEPS, M_SPEED_FX, M_LANE_CHANGES,
-                                   M_FLAGGED, M_OVERLAPS, M_INSERTED};
-        if (x) atomicAdd((unsigned long long*)&metrics[s0 * M_NFIELDS + map[tid]], (unsigned long long)x);
+        if (x) atomicAdd((unsigned long long*)&metrics[s0 * M_NFIELDS + metric_field(tid)], (unsigned long long)x);
     }
 }
 

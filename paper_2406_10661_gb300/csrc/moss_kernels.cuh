@@ -5,447 +5,435 @@
 
 namespace moss {
 
-// ---------------------------------------------------------------------------
-// k_prepare: one thread per lane and per junction.
-//   - junction signal state for step t (fixed time / manual / none, R19);
-//   - reset of the per-lane entrant lists and counters of this step;
-//   - departure insertion (R18): the head of a start lane's FIFO enters at
-//     s = 0, v = 0 when it is due and the snapshot's rearmost vehicle on the
-//     lane has s - len >= s0 (or the lane is empty).
-//   - clears the look-back tile words of this step.
-template <typename Real>
-__global__ void __launch_bounds__(PREP_THREADS) k_prepare(Ctx<Real> c) {
-    if (c.cnt->err & ERR_POISON) return;  // a failed step leaves the state frozen
-    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nthreads = gridDim.x * blockDim.x;
-    for (int k = gtid; k < c.n_lane_tiles; k += nthreads) c.lane_tiles[k] = 0ull;
-    for (int k = gtid; k < c.max_place_tiles; k += nthreads) c.place_tiles[k] = 0ull;
-    for (int j = gtid; j < c.n_junctions; j += nthreads) {
-        const int s = c.junc_scen[j];
-        const long long t = c.scen_step[s];
-        const int p0 = c.junc_phase_off[j], np = c.junc_phase_off[j + 1] - p0;
-        const int pol = c.junc_policy[j];
-        int st;
-        if (pol == POL_NONE || np <= 0) {
-            st = 512;
-        } else if (pol == POL_MANUAL) {
-            st = (c.junc_manual[j] & 15) | ((np & 15) << 4);
-        } else {
-            long long cyc = 0;
-            for (int p = 0; p < np; ++p) cyc += c.phase_green[p0 + p] + c.phase_amber[p0 + p];
-            if (cyc <= 0) {
-                st = 512;
-            } else {
-                long long x = (t + c.junc_offset[j]) % cyc;
-                if (x < 0) x += cyc;
-                st = 0;
-                for (int p = 0; p < np; ++p) {
-                    const long long g = c.phase_green[p0 + p], a = c.phase_amber[p0 + p];
-                    if (x < g + a) {
-                        st = p | ((np & 15) << 4) | (x >= g ? 256 : 0);
-                        break;
-                    }
-                    x -= g + a;
-                }
-            }
-        }
-        c.junc_state[j] = st;
-    }
-    for (int l = gtid; l < c.n_lanes; l += nthreads) {
-        c.head[l] = -1;
-        c.enter[l] = 0;
-        c.leave[l] = 0;
-    }
-    // the counters above must be visible before insertion appends; insertion
-    // for lane l is done by the same thread that reset lane l.
-    for (int l = gtid; l < c.n_lanes; l += nthreads) {
-        const int h = c.q_head[l];
-        if (h >= c.q_off[l + 1]) continue;
-        const int vid = c.q_ids[h];
-        const int sc = c.lane_scen[l];
-        const long long t = c.scen_step[sc];
-        if ((long long)c.dep[vid] > t) continue;
-        const int b = c.cur.off[l], e = c.cur.off[l + 1];
-        int fl = F_INSERTED;
-        if (e > b) {
-            const Real sr = c.cur.s[e - 1];
-            const Real g = sr - c.len - c.s0;
-            const Real scl = sr > Real(1) ? sr : Real(1);
-            if (rabs(g) < c.band * scl) fl |= F_FLAGGED;
-            if (!(g >= Real(0))) continue;
-        }
-        const int q = atomicAdd(&c.cnt->n_ent, 1);
-        const int r0 = c.route_off[vid], r1 = c.route_off[vid + 1] - 1;
-        int nl = -1;
-        if (r0 < r1) {
-            nl = jl_toward(c, l, c.routes[r0 + 1]);
-            if (nl < 0) atomicOr(&c.cnt->err, ERR_ROUTE);
-        }
-        c.es[q] = Real(0); c.ev[q] = Real(0); c.elane[q] = l; c.eid[q] = vid;
-        c.ev0f[q] = c.v0f[vid]; c.erptr[q] = r0; c.erlast[q] = r1; c.enl[q] = nl;
-        c.enext[q] = c.head[l];
-        c.head[l] = q;
-        c.enter[l] += 1;
-        c.q_head[l] = h + 1;
-        c.vstatus[vid] = 1;
-        c.vflags[vid] = int((t & 0xFFFFFF) << 8) | fl;
-        long long* M = c.metrics + (long long)sc * M_NFIELDS;
-        atomicAdd((unsigned long long*)&M[M_INSERTED], 1ull);
-        atomicAdd((unsigned long long*)&M[M_CUR_ACTIVE], 1ull);
-        if (fl & F_FLAGGED) atomicAdd((unsigned long long*)&M[M_FLAGGED], 1ull);
-    }
+// entrant list of a lane for this step's tag (-1 if empty or stale)
+__device__ __forceinline__ int list_head(const unsigned long long* head, int lane, int tag) {
+    const unsigned long long h = head[lane];
+    return (int)(h >> 32) == tag ? (int)(unsigned)(h & 0xffffffffull) : -1;
+}
+
+// append entrant q to the list of `lane`
+__device__ __forceinline__ void list_push(unsigned long long* head, int32_t* enext, int lane, int q, int tag) {
+    const unsigned long long prev =
+        atomicExch(&head[lane], ((unsigned long long)(unsigned)tag << 32) | (unsigned)q);
+    enext[q] = (int)(prev >> 32) == tag ? (int)(unsigned)(prev & 0xffffffffull) : -1;
 }
 
 // ---------------------------------------------------------------------------
-// k_decide: one thread per vehicle of the current snapshot.
+// Departure insertion (R18) for start lane l: the head of its FIFO enters at
+// s = 0, v = 0 when due and the snapshot's rearmost vehicle on the lane has
+// s - len >= s0 (or the lane is empty).
 template <typename Real>
-__global__ void __launch_bounds__(DECIDE_THREADS) k_decide(Ctx<Real> c) {
+__device__ void insert_departure(const Ctx<Real>& c, int l, int tag) {
+    const int h = c.q_head[l];
+    if (h >= c.q_off[l + 1]) return;
+    const int vid = c.q_ids[h];
+    const int sc = c.lane[l].scen;
+    const long long t = c.scen_step[sc];
+    if ((long long)c.dep[vid] > t) return;
+    const int b = c.cur.off[l], e = c.cur.off[l + 1];
+    int fl = F_INSERTED;
+    if (e > b) {
+        const Real sr = c.cur.a[e - 1].s;
+        const Real g = sr - c.len - c.s0;
+        const Real scl = sr > Real(1) ? sr : Real(1);
+        if (rabs(g) < c.band * scl) fl |= F_FLAGGED;
+        if (!(g >= Real(0))) return;
+    }
+    const int q = atomicAdd(&c.cnt->n_ent, 1);
+    const int r0 = c.route_off[vid], r1 = c.route_off[vid + 1] - 1;
+    int nl = -1;
+    if (r0 < r1) {
+        nl = jl_toward(c, c.lane[l], c.routes[r0 + 1]);
+        if (nl < 0) atomicOr(&c.cnt->err, ERR_ROUTE);
+    }
+    RecA<Real> A;
+    A.s = Real(0); A.v = Real(0); A.id = vid; A.lane = l;
+    RecB B;
+    B.v0f = c.v0f[vid]; B.rptr = r0; B.rlast = r1; B.nl = nl;
+    c.ea[q] = A;
+    c.eb[q] = B;
+    atomicAdd(&c.enter[l], 1);
+    list_push(c.head, c.enext, l, q, tag);
+    c.q_head[l] = h + 1;
+    c.vstatus[vid] = 1;
+    c.vflags[vid] = int((t & 0xFFFFFF) << 8) | fl;
+    long long* M = c.metrics + (long long)sc * M_NFIELDS;
+    atomicAdd((unsigned long long*)&M[M_INSERTED], 1ull);
+    atomicAdd((unsigned long long*)&M[M_CUR_ACTIVE], 1ull);
+    if (fl & F_FLAGGED) atomicAdd((unsigned long long*)&M[M_FLAGGED], 1ull);
+}
+
+// ---------------------------------------------------------------------------
+// k_decide: blocks [0, n_work) take 256-slot tiles of the current snapshot
+// (one vehicle per thread); blocks [n_work, gridDim) run the insertion.
+template <typename Real>
+__global__ void __launch_bounds__(TILE, 3) k_decide(Ctx<Real> c, int n_work) {
     if (c.cnt->err & ERR_POISON) return;
+    const int tag = c.cnt->tag;
+    if ((int)blockIdx.x >= n_work) {
+        const int stride = (gridDim.x - n_work) * TILE;
+        for (int k = (blockIdx.x - n_work) * TILE + threadIdx.x; k < c.n_start; k += stride)
+            insert_departure(c, c.start_lanes[k], tag);
+        return;
+    }
     const int n = c.cnt->n_cur;
-    const int per_block = (n + gridDim.x - 1) / gridDim.x;
-    const int beg = blockIdx.x * per_block;
-    const int end = min(n, beg + per_block);
+    const int n_tiles = (n + TILE - 1) / TILE;
     MetricAcc acc;
     macc_reset(acc, -1);
-    for (int i = beg + threadIdx.x; i < end; i += blockDim.x) {
-        const int lane = c.cur.lane[i];
-        const int nl0 = c.cur.nl[i];
-        if ((unsigned)lane >= (unsigned)c.n_lanes || nl0 < -1 || nl0 >= c.n_lanes) {
-            atomicOr(&c.cnt->err, ERR_RANGE);
-            continue;
-        }
-        const int sc = c.lane_scen[lane];
-        if (sc != acc.scen) {
-            macc_flush_thread(acc, c.metrics);
-            macc_reset(acc, sc);
-        }
-        const long long t = c.scen_step[sc];
-        const uint32_t k0 = c.key0[sc], k1 = c.key1[sc];
-        const int vbase = c.veh_base[sc];
-        Decision<Real> D = decide(c, i, t, k0, k1, vbase);
-        int fl = D.flag ? F_FLAGGED : 0;
-        bool granted = false;
-        if (D.cand) {
-            fl |= F_CANDIDATE;
-            granted = true;
-            // rivals: candidates of the lane beyond the target lane that fall
-            // into the same target-lane gap (TL ahead of them, them ahead of TF)
-            const int ol = D.tl + D.dir;  // lane of potential rivals
-            const int2 lh = c.lohi[lane];
-            if (ol >= lh.x && ol < lh.y) {
-                const int ob = c.cur.off[ol], oe = c.cur.off[ol + 1];
-                int ra = ob, rb = oe;
-                // first slot behind TL, first slot not ahead of TF
-                if (D.TL >= 0) ra = partition_point(c, ob, oe, c.cur.s[D.TL], c.cur.id[D.TL]);
-                if (D.TF >= 0) rb = partition_point(c, ob, oe, c.cur.s[D.TF], c.cur.id[D.TF]);
-                const int my_id = c.cur.id[i];
-                for (int r = ra; r < rb; ++r) {
-                    const Decision<Real> R = decide(c, r, t, k0, k1, vbase);
-                    if (!R.cand || R.tl != D.tl) continue;
-                    const Real sc2 = D.scale > R.scale ? D.scale : R.scale;
-                    if (rabs(D.u - R.u) < c.band * sc2) fl |= F_FLAGGED;
-                    const int rid = c.cur.id[r];
-                    const bool win = D.u > R.u || (D.u == R.u && my_id < rid);
-                    if (!win) granted = false;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += n_work) {
+        const int i = tile * TILE + threadIdx.x;
+        int leaver = 0;
+        if (i < n) {
+            const RecA<Real> E = c.cur.a[i];
+            const int lane = E.lane;
+            if ((unsigned)lane >= (unsigned)c.n_lanes) {
+                atomicOr(&c.cnt->err, ERR_RANGE);
+            } else {
+                const int sc = c.lane[lane].scen;
+                if (sc != acc.scen) {
+                    macc_flush_thread(acc, c.metrics);
+                    macc_reset(acc, sc);
+                }
+                const long long t = c.scen_step[sc];
+                const uint32_t k0 = c.key0[sc], k1 = c.key1[sc];
+                const int vbase = c.veh_base[sc];
+                // job 0 is this vehicle; jobs 1.. are the rivals of a lane-change
+                // candidate (R9): vehicles of the lane beyond the target lane that
+                // fall into the same target-lane gap.  One call site of decide()
+                // makes every recomputation bit-identical to the rival's own.
+                Decision<Real> D;
+                int fl = 0;
+                bool granted = false;
+                int r = 0, rend = 0;
+                for (int job = 0;; ++job) {
+                    const int slot = job == 0 ? i : r;
+                    const Decision<Real> X = decide(c, slot, t, k0, k1, vbase);
+                    if (job == 0) {
+                        D = X;
+                        fl = D.flag ? F_FLAGGED : 0;
+                        if (!D.cand) break;
+                        fl |= F_CANDIDATE;
+                        granted = true;
+                        const LaneInfo li = c.lane[lane];
+                        const int ol = D.tl + D.dir;
+                        if (ol < li.lo || ol >= li.hi) break;
+                        const int ob = c.cur.off[ol], oe = c.cur.off[ol + 1];
+                        r = ob; rend = oe;
+                        if (D.TL >= 0) {
+                            const RecA<Real> T = c.cur.a[D.TL];
+                            r = partition_point(c, ob, oe, T.s, T.id);
+                        }
+                        if (D.TF >= 0) {
+                            const RecA<Real> T = c.cur.a[D.TF];
+                            rend = partition_point(c, ob, oe, T.s, T.id);
+                        }
+                        if (r >= rend) break;
+                    } else {
+                        if (X.cand && X.tl == D.tl) {
+                            const Real sc2 = D.scale > X.scale ? D.scale : X.scale;
+                            if (rabs(D.u - X.u) < c.band * sc2) fl |= F_FLAGGED;
+                            const int rid = c.cur.a[r].id;
+                            if (!(D.u > X.u || (D.u == X.u && E.id < rid))) granted = false;
+                        }
+                        if (++r >= rend) break;
+                    }
+                }
+                if (D.cand && !granted) fl |= F_CONFLICT_LOST;
+                // ---- integration (R12, R13)
+                const LaneAcc<Real>& la = granted ? D.tgt : D.own;
+                int nlane = granted ? D.tl : lane;
+                if (granted) fl |= F_CHANGED;
+                const Real s = E.s, v = E.v, a = la.a, dt = c.dt;
+                Real vn = v + a * dt, disp;
+                if (vn >= Real(0)) {
+                    disp = v * dt + Real(0.5) * a * dt * dt;
+                } else {
+                    disp = -v * v / (Real(2) * a);
+                    vn = Real(0);
+                }
+                if (la.has_leader) { const Real cl = la.gap > Real(0) ? la.gap : Real(0); if (disp > cl) disp = cl; }
+                if (la.stop) { const Real cl = la.stop_gap > Real(0) ? la.stop_gap : Real(0); if (disp > cl) disp = cl; }
+                LaneInfo ni = c.lane[nlane];
+                Real sn = s + disp;
+                if (la.stop && sn > Real(ni.L)) sn = Real(ni.L);
+                // ---- transfer and arrival (R17).  The overshoot past the lane end is
+                // taken as disp - (L - s): L - s is exact for s >= L/2 (Sterbenz), so
+                // the position on the next lane does not lose the bits of L.
+                const RecB EB = c.cur.b[i];
+                int rptr = EB.rptr;
+                const int rlast = EB.rlast;
+                int nl = la.nl;
+                bool arrived = false;
+                Real ex = disp - (Real(ni.L) - s);  // distance beyond the end of nlane
+                if (!la.stop) {
+                    for (int iter = 0;;) {
+                        const Real Ll = Real(ni.L);
+                        const Real scl = Ll > Real(1) ? Ll : Real(1);
+                        const bool road = ni.lo >= 0;
+                        if (rabs(ex) < c.band * scl) fl |= F_FLAGGED;
+                        if (road && rptr == rlast) {
+                            if (ex >= Real(0)) arrived = true;
+                            break;
+                        }
+                        if (!(ex > Real(0))) break;
+                        if (++iter > 4 || nl < 0) { atomicOr(&c.cnt->err, ERR_TRANSFER); sn = Ll; break; }
+                        sn = ex;
+                        fl |= F_TRANSFER;
+                        nlane = nl;
+                        ni = c.lane[nlane];
+                        if (road) {
+                            nl = ni.hi;  // entered a junction lane: next is its target road lane
+                        } else {
+                            rptr += 1;  // entered the next road
+                            nl = (rptr < rlast) ? jl_toward(c, ni, c.routes[rptr + 1]) : -1;
+                            if (rptr < rlast && nl < 0) atomicOr(&c.cnt->err, ERR_ROUTE);
+                        }
+                        ex = sn - Real(ni.L);
+                    }
+                }
+                // ---- outputs
+                if (arrived) fl |= F_ARRIVED;
+                acc.m[0] += 1;
+                acc.m[3] += (long long)llrint(double(vn) * SPEED_FX);
+                if (fl & F_FLAGGED) acc.m[5] += 1;
+                if (fl & F_CHANGED) acc.m[4] += 1;
+                if (D.own.overlap) acc.m[6] += 1;
+                if (fl) c.vflags[E.id] = int((t & 0xFFFFFF) << 8) | fl;
+                if (arrived) {
+                    c.code[i] = C_ARRIVE;
+                    leaver = 1;
+                    c.vstatus[E.id] = 2;
+                    acc.m[1] += 1;
+                    acc.m[2] += (t + 1) - (long long)c.dep[E.id];
+                    atomicAdd(&c.leave[lane], 1);
+                    long long* M = c.metrics + (long long)sc * M_NFIELDS;
+                    atomicAdd((unsigned long long*)&M[M_CUR_ACTIVE], (unsigned long long)(-1ll));
+                    atomicAdd((unsigned long long*)&M[M_CUR_ARRIVED], 1ull);
+                } else if (nlane == lane) {
+                    c.code[i] = C_STAY;
+                    SV<Real> w;
+                    w.s = sn; w.v = vn;
+                    c.stay[i] = w;
+                } else {
+                    c.code[i] = C_MOVE;
+                    leaver = 1;
+                    atomicAdd(&c.leave[lane], 1);
+                    const int q = atomicAdd(&c.cnt->n_ent, 1);
+                    RecA<Real> A;
+                    A.s = sn; A.v = vn; A.id = E.id; A.lane = nlane;
+                    RecB B;
+                    B.v0f = EB.v0f; B.rptr = rptr; B.rlast = rlast; B.nl = nl;
+                    c.ea[q] = A;
+                    c.eb[q] = B;
+                    atomicAdd(&c.enter[nlane], 1);
+                    list_push(c.head, c.enext, nlane, q, tag);
                 }
             }
-            if (!granted) fl |= F_CONFLICT_LOST;
         }
-        // ---- integration (R12, R13)
-        const LaneAcc<Real>& la = granted ? D.tgt : D.own;
-        int nlane = granted ? D.tl : lane;
-        if (granted) fl |= F_CHANGED;
-        const Real s = c.cur.s[i], v = c.cur.v[i], a = la.a, dt = c.dt;
-        Real vn = v + a * dt, disp;
-        if (vn >= Real(0)) {
-            disp = v * dt + Real(0.5) * a * dt * dt;
-        } else {
-            disp = -v * v / (Real(2) * a);
-            vn = Real(0);
-        }
-        if (la.has_leader) { const Real cl = la.gap > Real(0) ? la.gap : Real(0); if (disp > cl) disp = cl; }
-        if (la.stop) { const Real cl = la.stop_gap > Real(0) ? la.stop_gap : Real(0); if (disp > cl) disp = cl; }
-        Real sn = s + disp;
-        if (la.stop && sn > Real(c.L[nlane])) sn = Real(c.L[nlane]);
-        // ---- transfer and arrival (R17).  The overshoot past the lane end is
-        // taken as disp - (L - s): L - s is exact for s >= L/2 (Sterbenz), so
-        // the position on the next lane does not lose the bits of L.
-        int rptr = c.cur.rptr[i];
-        const int rlast = c.cur.rlast[i];
-        int nl = la.nl;
-        bool arrived = false;
-        Real ex = disp - (Real(c.L[nlane]) - s);  // distance beyond the end of nlane
-        for (int iter = 0;; ) {
-            const Real Ll = Real(c.L[nlane]);
-            const Real scl = Ll > Real(1) ? Ll : Real(1);
-            if (la.stop && iter == 0) break;
-            const bool road = c.lohi[nlane].x >= 0;
-            if (road && rptr == rlast) {
-                if (rabs(ex) < c.band * scl) fl |= F_FLAGGED;
-                if (ex >= Real(0)) arrived = true;
-                break;
-            }
-            if (rabs(ex) < c.band * scl) fl |= F_FLAGGED;
-            if (!(ex > Real(0))) break;
-            if (++iter > 4 || nl < 0) { atomicOr(&c.cnt->err, ERR_TRANSFER); sn = Ll; break; }
-            sn = ex;
-            fl |= F_TRANSFER;
-            if (road) {
-                nlane = nl;                 // into the junction lane
-                nl = c.lohi[nlane].y;       // its target road lane
-            } else {
-                nlane = nl;                 // onto the next road
-                rptr += 1;
-                nl = (rptr < rlast) ? jl_toward(c, nlane, c.routes[rptr + 1]) : -1;
-                if (rptr < rlast && nl < 0) atomicOr(&c.cnt->err, ERR_ROUTE);
-            }
-            ex = sn - Real(c.L[nlane]);
-        }
-        // ---- outputs
-        if (arrived) fl |= F_ARRIVED;
-        const int id = c.cur.id[i];
-        acc.m[0] += 1;
-        acc.m[3] += (long long)llrint(double(vn) * SPEED_FX);
-        if (fl & F_FLAGGED) acc.m[5] += 1;
-        if (fl & F_CHANGED) acc.m[4] += 1;
-        if (D.own.overlap) acc.m[6] += 1;
-        c.vflags[id] = int((t & 0xFFFFFF) << 8) | fl;
-        if (arrived) {
-            c.code[i] = C_ARRIVE;
-            c.vstatus[id] = 2;
-            acc.m[1] += 1;
-            acc.m[2] += (t + 1) - (long long)c.dep[id];
-            atomicAdd(&c.leave[lane], 1);
-            long long* M = c.metrics + (long long)sc * M_NFIELDS;
-            atomicAdd((unsigned long long*)&M[M_CUR_ACTIVE], (unsigned long long)(-1ll));
-            atomicAdd((unsigned long long*)&M[M_CUR_ARRIVED], 1ull);
-        } else if (nlane == lane) {
-            c.code[i] = C_STAY;
-            c.rs[i] = sn;
-            c.rv[i] = vn;
-        } else {
-            c.code[i] = C_MOVE;
-            atomicAdd(&c.leave[lane], 1);
-            const int q = atomicAdd(&c.cnt->n_ent, 1);
-            c.es[q] = sn; c.ev[q] = vn; c.elane[q] = nlane; c.eid[q] = id;
-            c.ev0f[q] = c.cur.v0f[i]; c.erptr[q] = rptr; c.erlast[q] = rlast; c.enl[q] = nl;
-            atomicAdd(&c.enter[nlane], 1);
-            c.enext[q] = atomicExch(&c.head[nlane], q);
-        }
+        const int tot = __syncthreads_count(leaver);
+        if (threadIdx.x == 0) c.tile_leave[tile] = tot;
     }
-    macc_flush_block<DECIDE_THREADS>(acc, c.metrics);
+    macc_flush_block<TILE>(acc, c.metrics);
 }
 
 // ---------------------------------------------------------------------------
-// k_lanescan: next-snapshot lane offsets.  newsize(l) = size(l) - leave(l) +
-// enter(l).  Two exclusive prefix sums (new sizes, leavers) over lanes in one
-// decoupled look-back pass; tile words pack (flag:2 | leavers:31 | sizes:31).
+// block-wide exclusive scan of one 64-bit value per thread (256 threads)
+__device__ __forceinline__ long long block_exclusive_scan(long long x, long long* total) {
+    __shared__ long long warp_sum[LANESCAN_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_sum[warp] = incl;
+    __syncthreads();
+    long long base = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < LANESCAN_THREADS / 32; ++w) {
+        const long long ws = warp_sum[w];
+        if (w < warp) base += ws;
+        tot += ws;
+    }
+    __syncthreads();
+    *total = tot;
+    return base + incl - x;
+}
+
+// k_lanescan.  Tickets [0, n_lane_tiles): next-snapshot lane offsets.
+// newsize(l) = size(l) - leave(l) + enter(l); two exclusive prefix sums (new
+// sizes, leavers) over lanes in one decoupled look-back pass; tile words pack
+// (flag:2 | leavers:31 | sizes:31).  Ticket n_lane_tiles: exclusive prefix of
+// the leavers per slot tile.  Remaining tickets: signal states of the next
+// step for chunks of junctions.
 template <typename Real>
 __global__ void __launch_bounds__(LANESCAN_THREADS) k_lanescan(Ctx<Real> c) {
     if (c.cnt->err & ERR_POISON) return;
     __shared__ int s_tile;
-    __shared__ long long s_sum[LANESCAN_THREADS];
     __shared__ unsigned long long s_prefix;
+    const int n_tickets = c.n_lane_tiles + 1 + c.n_junc_chunks;
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(&c.cnt->ticket_lane, 1);
         __syncthreads();
         const int tile = s_tile;
-        if (tile >= c.n_lane_tiles) return;
-        const int base = tile * LANESCAN_TILE + threadIdx.x * LANESCAN_ITEMS;
-        int ns[LANESCAN_ITEMS], lv[LANESCAN_ITEMS];
-        long long tn = 0, tl = 0;
-#pragma unroll
-        for (int k = 0; k < LANESCAN_ITEMS; ++k) {
-            const int l = base + k;
-            if (l < c.n_lanes) {
-                const int sz = c.cur.off[l + 1] - c.cur.off[l];
-                lv[k] = c.leave[l];
-                ns[k] = sz - lv[k] + c.enter[l];
-            } else {
-                ns[k] = 0; lv[k] = 0;
-            }
-            tn += ns[k]; tl += lv[k];
-        }
-        // block-wide inclusive scan of (tn, tl) packed in one 64-bit value
-        long long packed = (tl << 31) | tn;
-        s_sum[threadIdx.x] = packed;
         __syncthreads();
-        for (int o = 1; o < LANESCAN_THREADS; o <<= 1) {
-            const long long x = threadIdx.x >= o ? s_sum[threadIdx.x - o] : 0;
-            __syncthreads();
-            s_sum[threadIdx.x] += x;
-            __syncthreads();
-        }
-        const long long incl = s_sum[threadIdx.x];
-        const long long total = s_sum[LANESCAN_THREADS - 1];
-        if (threadIdx.x == 0) {
-            unsigned long long prefix = 0;
-            unsigned long long* st = c.lane_tiles;
-            if (tile == 0) {
-                store_release(&st[0], (2ull << 62) | (unsigned long long)total);
-            } else {
-                store_release(&st[tile], (1ull << 62) | (unsigned long long)total);
-                int p = tile - 1;
-                long long spins = 0;
-                while (p >= 0) {
-                    const unsigned long long w = load_acquire(&st[p]);
-                    const unsigned long long f = w >> 62;
-                    if (f == 0) {
-                        if (++spins > SPIN_LIMIT) { atomicOr(&c.cnt->err, ERR_TIMEOUT); break; }
-                        if (spins > 64) __nanosleep(100);
-                        continue;
-                    }
-                    prefix += w & ((1ull << 62) - 1);
-                    if (f == 2) break;
-                    --p;
+        if (tile >= n_tickets) return;
+        if (tile < c.n_lane_tiles) {
+            const int base = tile * LANESCAN_TILE + threadIdx.x * LANESCAN_ITEMS;
+            int ns[LANESCAN_ITEMS], lv[LANESCAN_ITEMS];
+            long long tn = 0, tl = 0;
+#pragma unroll
+            for (int k = 0; k < LANESCAN_ITEMS; ++k) {
+                const int l = base + k;
+                if (l < c.n_lanes) {
+                    const int sz = c.cur.off[l + 1] - c.cur.off[l];
+                    lv[k] = c.leave[l];
+                    ns[k] = sz - lv[k] + c.enter[l];
+                    c.leave[l] = 0;
+                    c.enter[l] = 0;
+                } else {
+                    ns[k] = 0; lv[k] = 0;
                 }
-                store_release(&st[tile], (2ull << 62) | (prefix + (unsigned long long)total));
+                tn += ns[k]; tl += lv[k];
             }
-            s_prefix = prefix;
-        }
-        __syncthreads();
-        const unsigned long long pre = s_prefix;
-        long long excl = (long long)pre + incl - packed;
-        long long en = excl & ((1ll << 31) - 1), el = excl >> 31;
+            const long long packed = (tl << 31) | tn;
+            long long total;
+            const long long excl_in = block_exclusive_scan(packed, &total);
+            if (threadIdx.x < 32) {
+                bool timeout = false;
+                unsigned long long prefix = 0;
+                if (tile == 0) {
+                    if (threadIdx.x == 0) store_release(&c.lane_tiles[0], (2ull << 62) | (unsigned long long)total);
+                } else {
+                    if (threadIdx.x == 0) store_release(&c.lane_tiles[tile], (1ull << 62) | (unsigned long long)total);
+                    prefix = warp_lookback(c.lane_tiles, tile, &timeout);
+                    if (threadIdx.x == 0) {
+                        store_release(&c.lane_tiles[tile], (2ull << 62) | (prefix + (unsigned long long)total));
+                        if (timeout) atomicOr(&c.cnt->err, ERR_TIMEOUT);
+                    }
+                }
+                if (threadIdx.x == 0) s_prefix = prefix;
+            }
+            __syncthreads();
+            long long excl = (long long)s_prefix + excl_in;
+            long long en = excl & ((1ll << 31) - 1), el = excl >> 31;
 #pragma unroll
-        for (int k = 0; k < LANESCAN_ITEMS; ++k) {
-            const int l = base + k;
-            if (l < c.n_lanes) {
-                c.nxt.off[l] = (int)en;
-                c.lbefore[l] = (int)el;
+            for (int k = 0; k < LANESCAN_ITEMS; ++k) {
+                const int l = base + k;
+                if (l < c.n_lanes) {
+                    c.nxt.off[l] = (int)en;
+                    c.lbefore[l] = (int)el;
+                }
+                en += ns[k]; el += lv[k];
             }
-            en += ns[k]; el += lv[k];
-        }
-        if (tile == c.n_lane_tiles - 1 && threadIdx.x == LANESCAN_THREADS - 1) {
-            c.nxt.off[c.n_lanes] = (int)en;
-            c.cnt->n_next = (int)en;
+            if (tile == c.n_lane_tiles - 1 && threadIdx.x == LANESCAN_THREADS - 1) {
+                c.nxt.off[c.n_lanes] = (int)en;
+                c.cnt->n_next = (int)en;
+            }
+        } else if (tile == c.n_lane_tiles) {
+            // leavers before each slot tile of the current snapshot
+            const int nt = (c.cnt->n_cur + TILE - 1) / TILE;
+            long long carry = 0;
+            for (int b0 = 0; b0 < nt; b0 += LANESCAN_THREADS) {
+                const int k = b0 + threadIdx.x;
+                const long long x = k < nt ? c.tile_leave[k] : 0;
+                long long tot;
+                const long long ex = block_exclusive_scan(x, &tot);
+                if (k < nt) c.tile_prefix[k] = (int)(carry + ex);
+                carry += tot;
+            }
+        } else {
+            // signal states of the next step
+            const int j0 = (tile - c.n_lane_tiles - 1) * JUNC_CHUNK;
+            for (int j = j0 + threadIdx.x; j < j0 + JUNC_CHUNK && j < c.n_junctions; j += LANESCAN_THREADS)
+                c.junc_state[j] = junction_state_at(c, j, c.scen_step[c.junc_scen[j]] + 1);
         }
         __syncthreads();
     }
 }
 
 // ---------------------------------------------------------------------------
-// k_place: writes the next snapshot.  Tiles [0, n_stay_tiles) cover the
-// current slots (vehicles that kept their lane keep their relative order;
-// their rank = stayers ahead in the lane + entrants ahead of them); the
-// remaining tiles cover the entrants (rank = stayers ahead + entrants ahead).
+// k_place: writes the next snapshot.  Stayer tiles (one per block iteration):
+// a vehicle that kept its lane goes to off'[lane] + (stayers ahead of it in
+// the lane) + (entrants ahead of it); stayers ahead = its slot rank in the
+// lane minus the leavers before it in the lane.  Then the entrants: rank =
+// stayers ahead + entrants ahead.  The last block to finish closes the step.
 template <typename Real>
-__device__ __forceinline__ int entrants_ahead(const Ctx<Real>& c, int lane, Real s, int id) {
+__device__ __forceinline__ int entrants_ahead(const Ctx<Real>& c, int lane, Real s, int id, int tag) {
     int cnt = 0, guard = 0;
-    for (int q = c.head[lane]; q >= 0; q = c.enext[q]) {
-        if (q != -1 && ahead(c.es[q], c.eid[q], s, id)) ++cnt;
-        if (++guard > (1 << 24)) { atomicOr(&c.cnt->err, ERR_RANGE); break; }
+    for (int q = list_head(c.head, lane, tag); q >= 0; q = c.enext[q]) {
+        const RecA<Real> Q = c.ea[q];
+        if (ahead(Q.s, Q.id, s, id)) ++cnt;
+        if (++guard > c.n_veh) { atomicOr(&c.cnt->err, ERR_RANGE); break; }
     }
     return cnt;
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(PLACE_THREADS) k_place(Ctx<Real> c) {
+__global__ void __launch_bounds__(TILE) k_place(Ctx<Real> c) {
     if (c.cnt->err & ERR_POISON) return;
-    __shared__ int s_tile;
-    __shared__ int s_warp[PLACE_THREADS / 32];
-    __shared__ unsigned long long s_prefix;
+    __shared__ int s_warp[TILE / 32];
     const int n = c.cnt->n_cur;
     const int n_ent = c.cnt->n_ent;
-    const int n_stay_tiles = (n + PLACE_TILE - 1) / PLACE_TILE;
-    const int n_ent_tiles = (n_ent + PLACE_TILE - 1) / PLACE_TILE;
-    for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(&c.cnt->ticket_place, 1);
+    const int tag = c.cnt->tag;
+    const int n_tiles = (n + TILE - 1) / TILE;
+    const int lane_id = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int i = tile * TILE + threadIdx.x;
+        const bool valid = i < n;
+        const int8_t code = valid ? c.code[i] : C_STAY;
+        const int leaver = (valid && code != C_STAY) ? 1 : 0;
+        const unsigned ball = __ballot_sync(0xffffffffu, leaver);
+        const int wpre = __popc(ball & ((1u << lane_id) - 1));
+        if (lane_id == 0) s_warp[warp] = __popc(ball);
         __syncthreads();
-        const int tile = s_tile;
-        if (tile >= n_stay_tiles + n_ent_tiles) break;
-        if (tile < n_stay_tiles) {
-            const int i = tile * PLACE_TILE + threadIdx.x;
-            const bool valid = i < n;
-            const int8_t code = valid ? c.code[i] : C_STAY;
-            const int leaver = (valid && code != C_STAY) ? 1 : 0;
-            // block exclusive scan of leaver flags
-            const unsigned ball = __ballot_sync(0xffffffffu, leaver);
-            const int lane_id = threadIdx.x & 31, warp = threadIdx.x >> 5;
-            const int wpre = __popc(ball & ((1u << lane_id) - 1));
-            if (lane_id == 0) s_warp[warp] = __popc(ball);
-            __syncthreads();
-            int wbase = 0, total = 0;
-            for (int w = 0; w < PLACE_THREADS / 32; ++w) {
-                if (w < warp) wbase += s_warp[w];
-                total += s_warp[w];
-            }
-            if (threadIdx.x == 0) {
-                unsigned long long prefix = 0;
-                unsigned long long* st = c.place_tiles;
-                if (tile == 0) {
-                    store_release(&st[0], (2ull << 62) | (unsigned long long)total);
-                } else {
-                    store_release(&st[tile], (1ull << 62) | (unsigned long long)total);
-                    int p = tile - 1;
-                    long long spins = 0;
-                    while (p >= 0) {
-                        const unsigned long long w = load_acquire(&st[p]);
-                        const unsigned long long f = w >> 62;
-                        if (f == 0) {
-                            if (++spins > SPIN_LIMIT) { atomicOr(&c.cnt->err, ERR_TIMEOUT); break; }
-                            if (spins > 64) __nanosleep(100);
-                            continue;
-                        }
-                        prefix += w & ((1ull << 62) - 1);
-                        if (f == 2) break;
-                        --p;
-                    }
-                    store_release(&st[tile], (2ull << 62) | (prefix + (unsigned long long)total));
-                }
-                s_prefix = prefix;
-            }
-            __syncthreads();
-            if (valid && code == C_STAY) {
-                const long long leavers_before = (long long)s_prefix + wbase + wpre;
-                const int lane = c.cur.lane[i];
-                const int stay_rank = (i - c.cur.off[lane]) - (int)(leavers_before - c.lbefore[lane]);
-                const Real sn = c.rs[i];
-                const int id = c.cur.id[i];
-                const int pos = c.nxt.off[lane] + stay_rank + entrants_ahead(c, lane, sn, id);
-                if (pos < c.nxt.off[lane] || pos >= c.nxt.off[lane + 1]) {
-                    atomicOr(&c.cnt->err, ERR_RANGE);
-                } else {
-                c.nxt.lane[pos] = lane;
-                c.nxt.s[pos] = sn;
-                c.nxt.v[pos] = c.rv[i];
-                c.nxt.id[pos] = id;
-                c.nxt.v0f[pos] = c.cur.v0f[i];
-                c.nxt.rptr[pos] = c.cur.rptr[i];
-                c.nxt.rlast[pos] = c.cur.rlast[i];
-                c.nxt.nl[pos] = c.cur.nl[i];
-                }
-            }
-        } else {
-            const int q = (tile - n_stay_tiles) * PLACE_TILE + threadIdx.x;
-            if (q < n_ent) {
-                const int lane = c.elane[q];
-                const Real sn = c.es[q];
-                const int id = c.eid[q];
-                int rank = entrants_ahead(c, lane, sn, id);
-                // stayers of this lane ahead of the entrant (old segment of the lane)
-                const int b = c.cur.off[lane], e = c.cur.off[lane + 1];
-                for (int k = b; k < e; ++k)
-                    if (c.code[k] == C_STAY && ahead(c.rs[k], c.cur.id[k], sn, id)) ++rank;
-                const int pos = c.nxt.off[lane] + rank;
-                if (pos < c.nxt.off[lane] || pos >= c.nxt.off[lane + 1]) {
-                    atomicOr(&c.cnt->err, ERR_RANGE);
-                } else {
-                c.nxt.lane[pos] = lane;
-                c.nxt.s[pos] = sn;
-                c.nxt.v[pos] = c.ev[q];
-                c.nxt.id[pos] = id;
-                c.nxt.v0f[pos] = c.ev0f[q];
-                c.nxt.rptr[pos] = c.erptr[q];
-                c.nxt.rlast[pos] = c.erlast[q];
-                c.nxt.nl[pos] = c.enl[q];
-                }
+        int wbase = 0;
+        for (int w = 0; w < warp; ++w) wbase += s_warp[w];
+        __syncthreads();
+        if (valid && code == C_STAY) {
+            const RecA<Real> A = c.cur.a[i];
+            const RecB B = c.cur.b[i];
+            const SV<Real> w = c.stay[i];
+            const int lane = A.lane;
+            const int leavers_before = c.tile_prefix[tile] + wbase + wpre;
+            const int stay_rank = (i - c.cur.off[lane]) - (leavers_before - c.lbefore[lane]);
+            const int pos = c.nxt.off[lane] + stay_rank + entrants_ahead(c, lane, w.s, A.id, tag);
+            if (pos < c.nxt.off[lane] || pos >= c.nxt.off[lane + 1]) {
+                atomicOr(&c.cnt->err, ERR_RANGE);
+            } else {
+                RecA<Real> O;
+                O.s = w.s; O.v = w.v; O.id = A.id; O.lane = lane;
+                c.nxt.a[pos] = O;
+                c.nxt.b[pos] = B;
             }
         }
-        __syncthreads();
     }
+    for (int q = blockIdx.x * TILE + threadIdx.x; q < n_ent; q += gridDim.x * TILE) {
+        const RecA<Real> Q = c.ea[q];
+        const int lane = Q.lane;
+        int rank = entrants_ahead(c, lane, Q.s, Q.id, tag);
+        // stayers of this lane ahead of the entrant (old segment of the lane)
+        const int b = c.cur.off[lane], e = c.cur.off[lane + 1];
+        for (int k = b; k < e; ++k) {
+            if (c.code[k] != C_STAY) continue;
+            if (ahead(c.stay[k].s, c.cur.a[k].id, Q.s, Q.id)) ++rank;
+        }
+        const int pos = c.nxt.off[lane] + rank;
+        if (pos < c.nxt.off[lane] || pos >= c.nxt.off[lane + 1]) {
+            atomicOr(&c.cnt->err, ERR_RANGE);
+        } else {
+            c.nxt.a[pos] = Q;
+            c.nxt.b[pos] = c.eb[q];
+        }
+    }
+    // clear the lane look-back words for the next step (k_lanescan is done)
+    for (int k = blockIdx.x * TILE + threadIdx.x; k < c.n_lane_tiles; k += gridDim.x * TILE)
+        c.lane_tiles[k] = 0ull;
     // the last block to finish closes the step: publish the next snapshot
-    // size, reset the step counters and advance every scenario's clock
+    // size, reset the step counters, advance the list tag and every
+    // scenario's clock
+    __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         const int done = atomicAdd(&c.cnt->done_place, 1);
@@ -454,12 +442,33 @@ __global__ void __launch_bounds__(PLACE_THREADS) k_place(Ctx<Real> c) {
             c.cnt->n_cur = c.cnt->n_next;
             c.cnt->n_ent = 0;
             c.cnt->ticket_lane = 0;
-            c.cnt->ticket_place = 0;
             c.cnt->done_place = 0;
+            int tg = c.cnt->tag + 1;
+            c.cnt->tag = tg > 0x3fffffff ? 1 : tg;
             for (int s = 0; s < c.n_scen; ++s) c.scen_step[s] += 1;
             __threadfence();
         }
     }
+}
+
+// signal states for the current step of every junction (after creation or
+// a state reset)
+template <typename Real>
+__global__ void k_junction_init(Ctx<Real> c) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < c.n_junctions; j += gridDim.x * blockDim.x)
+        c.junc_state[j] = junction_state_at(c, j, c.scen_step[c.junc_scen[j]]);
+}
+
+// setter: policy (and manual phase) of n junctions, effective from the
+// current step (the state of the step is recomputed)
+template <typename Real>
+__global__ void k_set_signal(Ctx<Real> c, int n, const int32_t* ids, const int32_t* phases, int policy) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int j = ids[k];
+    c.junc_policy[j] = policy;
+    if (policy == POL_MANUAL) c.junc_manual[j] = phases[k];
+    c.junc_state[j] = junction_state_at(c, j, c.scen_step[c.junc_scen[j]]);
 }
 
 }  // namespace moss
