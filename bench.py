@@ -300,7 +300,7 @@ def run_ours(args):
         "e2e": {"value": e2e_val, "unit": "vehicle-updates/s", "h2d_bytes_per_step": 8 * J,
                 "d2h_bytes_per_step": 8 * 12 + 4, "steps": e2e_steps,
                 "api": "moss_set_signal_phase + moss_step(1) + moss_get_metrics per step"},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": 3 * args.steps,
         "wall_s_timed_region": wall,
         "cpu_baseline": cpu,
     }

@@ -279,7 +279,7 @@ struct Grids {
 
 Grids grids(const MossHandle* h) {
     Grids g;
-    g.decide_work = std::max(1, std::min(h->max_slot_tiles, h->sm_count * 3));
+    g.decide_work = std::max(1, std::min(h->max_slot_tiles, h->sm_count * MOSS_DECIDE_MIN_BLOCKS));
     const int ns = (int)h->start_lanes.size();
     g.decide_ins = ns > 0 ? std::max(1, std::min((ns + TILE - 1) / TILE, h->sm_count)) : 0;
     const int tickets = h->n_lane_tiles + 1 + h->n_junc_chunks;

@@ -66,8 +66,12 @@ __device__ void insert_departure(const Ctx<Real>& c, int l, int tag) {
 // ---------------------------------------------------------------------------
 // k_decide: blocks [0, n_work) take 256-slot tiles of the current snapshot
 // (one vehicle per thread); blocks [n_work, gridDim) run the insertion.
+// MOSS_DECIDE_MIN_BLOCKS: resident blocks per SM the register budget targets.
+#ifndef MOSS_DECIDE_MIN_BLOCKS
+#define MOSS_DECIDE_MIN_BLOCKS 3
+#endif
 template <typename Real>
-__global__ void __launch_bounds__(TILE, 3) k_decide(Ctx<Real> c, int n_work) {
+__global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Real> c, int n_work) {
     if (c.cnt->err & ERR_POISON) return;
     const int tag = c.cnt->tag;
     if ((int)blockIdx.x >= n_work) {
