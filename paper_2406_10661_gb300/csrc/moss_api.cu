@@ -532,7 +532,7 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
     h->n_lane_tiles = (NL + LANESCAN_TILE - 1) / LANESCAN_TILE;
     h->max_slot_tiles = (NV + TILE - 1) / TILE + 1;
     h->n_junc_chunks = (NJ + JUNC_CHUNK - 1) / JUNC_CHUNK;
-    TRY(dalloc(h, &h->d_tile_leave, h->max_slot_tiles));
+    TRY(upload(h, &h->d_tile_leave, std::vector<int32_t>(h->max_slot_tiles, 0)));
     TRY(dalloc(h, &h->d_tile_prefix, h->max_slot_tiles));
     TRY(upload(h, &h->d_lane_tiles, std::vector<unsigned long long>(h->n_lane_tiles, 0ull)));
     Counters c0{};

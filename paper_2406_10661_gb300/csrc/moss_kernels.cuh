@@ -68,7 +68,7 @@ __device__ void insert_departure(const Ctx<Real>& c, int l, int tag) {
 // (one vehicle per thread); blocks [n_work, gridDim) run the insertion.
 // MOSS_DECIDE_MIN_BLOCKS: resident blocks per SM the register budget targets.
 #ifndef MOSS_DECIDE_MIN_BLOCKS
-#define MOSS_DECIDE_MIN_BLOCKS 3
+#define MOSS_DECIDE_MIN_BLOCKS 4
 #endif
 template <typename Real>
 __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Real> c, int n_work) {
@@ -234,8 +234,9 @@ __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Rea
                 }
             }
         }
-        const int tot = __syncthreads_count(leaver);
-        if (threadIdx.x == 0) c.tile_leave[tile] = tot;
+        // leavers of this tile (k_lanescan zeroes the counters after reading them)
+        const unsigned lb = __ballot_sync(0xffffffffu, leaver);
+        if ((threadIdx.x & 31) == 0 && lb) atomicAdd(&c.tile_leave[tile], __popc(lb));
     }
     macc_flush_block<TILE>(acc, c.metrics);
 }
@@ -287,20 +288,36 @@ __global__ void __launch_bounds__(LANESCAN_THREADS) k_lanescan(Ctx<Real> c) {
             const int base = tile * LANESCAN_TILE + threadIdx.x * LANESCAN_ITEMS;
             int ns[LANESCAN_ITEMS], lv[LANESCAN_ITEMS];
             long long tn = 0, tl = 0;
+            if (base + LANESCAN_ITEMS <= c.n_lanes) {
+                // four lanes with 16-byte loads (base is a multiple of 4)
+                const int4 o = *reinterpret_cast<const int4*>(c.cur.off + base);
+                const int o4 = c.cur.off[base + 4];
+                const int4 lvv = *reinterpret_cast<const int4*>(c.leave + base);
+                const int4 env = *reinterpret_cast<const int4*>(c.enter + base);
+                *reinterpret_cast<int4*>(c.leave + base) = make_int4(0, 0, 0, 0);
+                *reinterpret_cast<int4*>(c.enter + base) = make_int4(0, 0, 0, 0);
+                lv[0] = lvv.x; lv[1] = lvv.y; lv[2] = lvv.z; lv[3] = lvv.w;
+                ns[0] = o.y - o.x - lvv.x + env.x;
+                ns[1] = o.z - o.y - lvv.y + env.y;
+                ns[2] = o.w - o.z - lvv.z + env.z;
+                ns[3] = o4 - o.w - lvv.w + env.w;
+            } else {
 #pragma unroll
-            for (int k = 0; k < LANESCAN_ITEMS; ++k) {
-                const int l = base + k;
-                if (l < c.n_lanes) {
-                    const int sz = c.cur.off[l + 1] - c.cur.off[l];
-                    lv[k] = c.leave[l];
-                    ns[k] = sz - lv[k] + c.enter[l];
-                    c.leave[l] = 0;
-                    c.enter[l] = 0;
-                } else {
-                    ns[k] = 0; lv[k] = 0;
+                for (int k = 0; k < LANESCAN_ITEMS; ++k) {
+                    const int l = base + k;
+                    if (l < c.n_lanes) {
+                        const int sz = c.cur.off[l + 1] - c.cur.off[l];
+                        lv[k] = c.leave[l];
+                        ns[k] = sz - lv[k] + c.enter[l];
+                        c.leave[l] = 0;
+                        c.enter[l] = 0;
+                    } else {
+                        ns[k] = 0; lv[k] = 0;
+                    }
                 }
-                tn += ns[k]; tl += lv[k];
             }
+#pragma unroll
+            for (int k = 0; k < LANESCAN_ITEMS; ++k) { tn += ns[k]; tl += lv[k]; }
             const long long packed = (tl << 31) | tn;
             long long total;
             const long long excl_in = block_exclusive_scan(packed, &total);
@@ -336,16 +353,22 @@ __global__ void __launch_bounds__(LANESCAN_THREADS) k_lanescan(Ctx<Real> c) {
                 c.cnt->n_next = (int)en;
             }
         } else if (tile == c.n_lane_tiles) {
-            // leavers before each slot tile of the current snapshot
+            // leavers before each slot tile of the current snapshot: every
+            // thread sums a contiguous run of tiles (loads issued together),
+            // one block scan, then the runs are written out; the counters are
+            // zeroed for the next step
             const int nt = (c.cnt->n_cur + TILE - 1) / TILE;
-            long long carry = 0;
-            for (int b0 = 0; b0 < nt; b0 += LANESCAN_THREADS) {
-                const int k = b0 + threadIdx.x;
-                const long long x = k < nt ? c.tile_leave[k] : 0;
-                long long tot;
-                const long long ex = block_exclusive_scan(x, &tot);
-                if (k < nt) c.tile_prefix[k] = (int)(carry + ex);
-                carry += tot;
+            const int per = (nt + LANESCAN_THREADS - 1) / LANESCAN_THREADS;
+            const int k0 = threadIdx.x * per, k1 = min(nt, k0 + per);
+            long long run = 0;
+            for (int k = k0; k < k1; ++k) run += c.tile_leave[k];
+            long long tot;
+            long long acc = block_exclusive_scan(run, &tot);
+            for (int k = k0; k < k1; ++k) {
+                const int x = c.tile_leave[k];
+                c.tile_prefix[k] = (int)acc;
+                c.tile_leave[k] = 0;
+                acc += x;
             }
         } else {
             // signal states of the next step
@@ -387,6 +410,14 @@ __global__ void __launch_bounds__(TILE) k_place(Ctx<Real> c) {
         const int i = tile * TILE + threadIdx.x;
         const bool valid = i < n;
         const int8_t code = valid ? c.code[i] : C_STAY;
+        RecA<Real> A;
+        RecB B;
+        SV<Real> w;
+        if (valid) {  // issued before the tile's leaver scan
+            A = c.cur.a[i];
+            B = c.cur.b[i];
+            w = c.stay[i];
+        }
         const int leaver = (valid && code != C_STAY) ? 1 : 0;
         const unsigned ball = __ballot_sync(0xffffffffu, leaver);
         const int wpre = __popc(ball & ((1u << lane_id) - 1));
@@ -396,9 +427,6 @@ __global__ void __launch_bounds__(TILE) k_place(Ctx<Real> c) {
         for (int w = 0; w < warp; ++w) wbase += s_warp[w];
         __syncthreads();
         if (valid && code == C_STAY) {
-            const RecA<Real> A = c.cur.a[i];
-            const RecB B = c.cur.b[i];
-            const SV<Real> w = c.stay[i];
             const int lane = A.lane;
             const int leavers_before = c.tile_prefix[tile] + wbase + wpre;
             const int stay_rank = (i - c.cur.off[lane]) - (leavers_before - c.lbefore[lane]);
@@ -419,10 +447,14 @@ __global__ void __launch_bounds__(TILE) k_place(Ctx<Real> c) {
         int rank = entrants_ahead(c, lane, Q.s, Q.id, tag);
         // stayers of this lane ahead of the entrant (old segment of the lane)
         const int b = c.cur.off[lane], e = c.cur.off[lane + 1];
-        for (int k = b; k < e; ++k) {
-            if (c.code[k] != C_STAY) continue;
-            if (ahead(c.stay[k].s, c.cur.a[k].id, Q.s, Q.id)) ++rank;
+        int k = b;
+        for (; k + 4 <= e; k += 4) {  // four independent probes per round trip
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (c.code[k + u] == C_STAY && ahead(c.stay[k + u].s, c.cur.a[k + u].id, Q.s, Q.id)) ++rank;
         }
+        for (; k < e; ++k)
+            if (c.code[k] == C_STAY && ahead(c.stay[k].s, c.cur.a[k].id, Q.s, Q.id)) ++rank;
         const int pos = c.nxt.off[lane] + rank;
         if (pos < c.nxt.off[lane] || pos >= c.nxt.off[lane + 1]) {
             atomicOr(&c.cnt->err, ERR_RANGE);
