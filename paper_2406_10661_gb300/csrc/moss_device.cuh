@@ -54,7 +54,7 @@ constexpr int ERR_POISON = ERR_TIMEOUT | ERR_RANGE;
 
 constexpr int TILE = 256;           // slots per tile of k_decide / k_place (= threads)
 constexpr int LANESCAN_THREADS = 256;
-constexpr int LANESCAN_ITEMS = 4;
+constexpr int LANESCAN_ITEMS = 16;
 constexpr int LANESCAN_TILE = LANESCAN_THREADS * LANESCAN_ITEMS;
 constexpr int JUNC_CHUNK = 1024;    // junctions per k_lanescan ticket
 constexpr long long SPIN_LIMIT = 1ll << 22;  // bounded waits (~0.5 s with backoff)
@@ -178,21 +178,28 @@ __device__ __forceinline__ Real unit24(uint32_t w) {
 
 template <typename Real> __device__ __forceinline__ Real rabs(Real x) { return x < Real(0) ? -x : x; }
 
+// x / y: IEEE division in FP64; the hardware's fast approximate division in
+// FP32 (about 2 ulp, far inside the 1e-5 tolerance and the 1e-4 flag bands).
+// Denominators here are desired speeds and gaps >= 1e-3 m, far from the
+// range where the approximation degrades.
+template <typename Real> __device__ __forceinline__ Real qdiv(Real x, Real y) { return x / y; }
+template <> __device__ __forceinline__ float qdiv<float>(float x, float y) { return __fdividef(x, y); }
+
 // ---------------------------------------------------------------------------
 // IDM, App. B.3 eqs. (1)-(2), delta = 4 as ((v/v0)^2)^2.
 template <typename Real>
 __device__ __forceinline__ Real idm_free(const Ctx<Real>& c, Real v, Real v0) {
-    const Real r = v / v0, r2 = r * r;
+    const Real r = qdiv(v, v0), r2 = r * r;
     return c.a_max * (Real(1) - r2 * r2);
 }
 
 template <typename Real>
 __device__ __forceinline__ Real idm(const Ctx<Real>& c, Real v, Real v0, Real gap, Real dv) {
-    const Real r = v / v0, r2 = r * r;
+    const Real r = qdiv(v, v0), r2 = r * r;
     const Real dyn = v * c.T + v * dv * c.inv_2sqrt_ab;
     const Real sstar = c.s0 + (dyn > Real(0) ? dyn : Real(0));
     const Real g = gap > Real(1e-3) ? gap : Real(1e-3);
-    const Real q = sstar / g;
+    const Real q = qdiv(sstar, g);
     return c.a_max * (Real(1) - r2 * r2 - q * q);
 }
 
@@ -341,9 +348,10 @@ __device__ __forceinline__ Real acc_pair(const Ctx<Real>& c, const RecA<Real>& F
 
 template <typename Real>
 struct Decision {
-    LaneAcc<Real> own, tgt;
+    LaneAcc<Real> own;
     Real u, scale;
     int cand, dir, tl, TL, TF, flag;  // TL/TF: slots in the target lane or -1
+    int nlt;                          // next lane on the route from the target lane
 };
 
 // The full per-vehicle decision before conflict resolution (App. B.3).  A pure
@@ -353,7 +361,7 @@ template <typename Real>
 __device__ __forceinline__ Decision<Real> decide(const Ctx<Real>& c, int i, long long t, uint32_t k0,
                                                  uint32_t k1, int vbase) {
     Decision<Real> D;
-    D.cand = 0; D.dir = 0; D.tl = -1; D.TL = -1; D.TF = -1; D.flag = 0;
+    D.cand = 0; D.dir = 0; D.tl = -1; D.TL = -1; D.TF = -1; D.flag = 0; D.nlt = -1;
     D.u = Real(0); D.scale = Real(1);
     const RecA<Real> E = c.cur.a[i];
     const RecB EB = c.cur.b[i];
@@ -363,7 +371,6 @@ __device__ __forceinline__ Decision<Real> decide(const Ctx<Real>& c, int i, long
     const int OL = (i > b) ? i - 1 : -1;
     const Real v0f = Real(EB.v0f);
     D.own = accel_on_lane(c, li, E.s, E.v, v0f * Real(li.vmax), OL, EB.nl, EB.rptr, EB.rlast);
-    D.tgt = D.own;
     if (li.lo < 0 || li.hi - li.lo < 2) return D;  // junction lane or single-lane road
     uint32_t w[4];
     philox4x32_10(k0, k1, uint32_t(E.id - vbase), uint32_t(t), 0u, 0u, w);
@@ -387,9 +394,7 @@ __device__ __forceinline__ Decision<Real> decide(const Ctx<Real>& c, int i, long
     // next road of the route (for the target lane's junction lane)
     const int next_road = (EB.nl >= 0) ? c.lane[EB.nl].road : -1;
     Real u[2] = {Real(0), Real(0)}, scl[2] = {Real(0), Real(0)};
-    int feas[2] = {0, 0}, TLs[2] = {-1, -1}, TFs[2] = {-1, -1};
-    LaneAcc<Real> tg[2];
-    tg[0] = D.own; tg[1] = D.own;
+    int feas[2] = {0, 0}, TLs[2] = {-1, -1}, TFs[2] = {-1, -1}, NLs[2] = {-1, -1};
     const Real pos_scale = E.s > Real(1) ? E.s : Real(1);
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
@@ -416,8 +421,8 @@ __device__ __forceinline__ Decision<Real> decide(const Ctx<Real>& c, int i, long
             if (rabs(g) < c.band * pos_scale) D.flag = 1;
         }
         const int nlt = (next_road >= 0) ? jl_toward(c, ti, next_road) : -1;
-        tg[side] = accel_on_lane(c, ti, E.s, E.v, v0f * Real(ti.vmax), TL, nlt, EB.rptr, EB.rlast);
-        const Real at_ego = tg[side].a;
+        NLs[side] = nlt;
+        const Real at_ego = accel_on_lane(c, ti, E.s, E.v, v0f * Real(ti.vmax), TL, nlt, EB.rptr, EB.rlast).a;
         Real a_new = Real(0), at_new = Real(0);
         if (TF >= 0) {
             const float fv0f = c.cur.b[TF].v0f;
@@ -459,9 +464,8 @@ __device__ __forceinline__ Decision<Real> decide(const Ctx<Real>& c, int i, long
     D.cand = 1;
     D.dir = side == 0 ? -1 : 1;
     D.tl = side == 0 ? lane - 1 : lane + 1;
-    D.TL = TLs[side]; D.TF = TFs[side];
+    D.TL = TLs[side]; D.TF = TFs[side]; D.nlt = NLs[side];
     D.u = u[side];
-    D.tgt = tg[side];
     return D;
 }
 

@@ -143,10 +143,18 @@ __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Rea
                     }
                 }
                 if (D.cand && !granted) fl |= F_CONFLICT_LOST;
-                // ---- integration (R12, R13)
-                const LaneAcc<Real>& la = granted ? D.tgt : D.own;
-                int nlane = granted ? D.tl : lane;
-                if (granted) fl |= F_CHANGED;
+                // ---- integration (R12, R13); a granted change drives on the
+                // target lane (its kinematics recomputed from the same inputs)
+                LaneAcc<Real> la = D.own;
+                int nlane = lane;
+                if (granted) {
+                    fl |= F_CHANGED;
+                    nlane = D.tl;
+                    const LaneInfo ti = c.lane[nlane];
+                    const RecB EB0 = c.cur.b[i];
+                    la = accel_on_lane(c, ti, E.s, E.v, Real(EB0.v0f) * Real(ti.vmax), D.TL, D.nlt,
+                                       EB0.rptr, EB0.rlast);
+                }
                 const Real s = E.s, v = E.v, a = la.a, dt = c.dt;
                 Real vn = v + a * dt, disp;
                 if (vn >= Real(0)) {
@@ -289,18 +297,22 @@ __global__ void __launch_bounds__(LANESCAN_THREADS) k_lanescan(Ctx<Real> c) {
             int ns[LANESCAN_ITEMS], lv[LANESCAN_ITEMS];
             long long tn = 0, tl = 0;
             if (base + LANESCAN_ITEMS <= c.n_lanes) {
-                // four lanes with 16-byte loads (base is a multiple of 4)
-                const int4 o = *reinterpret_cast<const int4*>(c.cur.off + base);
-                const int o4 = c.cur.off[base + 4];
-                const int4 lvv = *reinterpret_cast<const int4*>(c.leave + base);
-                const int4 env = *reinterpret_cast<const int4*>(c.enter + base);
-                *reinterpret_cast<int4*>(c.leave + base) = make_int4(0, 0, 0, 0);
-                *reinterpret_cast<int4*>(c.enter + base) = make_int4(0, 0, 0, 0);
-                lv[0] = lvv.x; lv[1] = lvv.y; lv[2] = lvv.z; lv[3] = lvv.w;
-                ns[0] = o.y - o.x - lvv.x + env.x;
-                ns[1] = o.z - o.y - lvv.y + env.y;
-                ns[2] = o.w - o.z - lvv.z + env.z;
-                ns[3] = o4 - o.w - lvv.w + env.w;
+                // 16-byte loads (base is a multiple of 4)
+                int o[LANESCAN_ITEMS + 1];
+#pragma unroll
+                for (int k = 0; k < LANESCAN_ITEMS; k += 4) {
+                    const int4 ov = *reinterpret_cast<const int4*>(c.cur.off + base + k);
+                    const int4 lvv = *reinterpret_cast<const int4*>(c.leave + base + k);
+                    const int4 env = *reinterpret_cast<const int4*>(c.enter + base + k);
+                    o[k] = ov.x; o[k + 1] = ov.y; o[k + 2] = ov.z; o[k + 3] = ov.w;
+                    lv[k] = lvv.x; lv[k + 1] = lvv.y; lv[k + 2] = lvv.z; lv[k + 3] = lvv.w;
+                    ns[k] = env.x; ns[k + 1] = env.y; ns[k + 2] = env.z; ns[k + 3] = env.w;
+                    *reinterpret_cast<int4*>(c.leave + base + k) = make_int4(0, 0, 0, 0);
+                    *reinterpret_cast<int4*>(c.enter + base + k) = make_int4(0, 0, 0, 0);
+                }
+                o[LANESCAN_ITEMS] = c.cur.off[base + LANESCAN_ITEMS];
+#pragma unroll
+                for (int k = 0; k < LANESCAN_ITEMS; ++k) ns[k] += o[k + 1] - o[k] - lv[k];
             } else {
 #pragma unroll
                 for (int k = 0; k < LANESCAN_ITEMS; ++k) {
@@ -441,26 +453,27 @@ __global__ void __launch_bounds__(TILE) k_place(Ctx<Real> c) {
             }
         }
     }
-    for (int q = blockIdx.x * TILE + threadIdx.x; q < n_ent; q += gridDim.x * TILE) {
+    // entrants: one warp per entrant; the warp counts the stayers of the
+    // lane's old segment that are ahead of it, 32 slots per round
+    const int gwarp = blockIdx.x * (TILE / 32) + warp, nwarps = gridDim.x * (TILE / 32);
+    for (int q = gwarp; q < n_ent; q += nwarps) {
         const RecA<Real> Q = c.ea[q];
         const int lane = Q.lane;
-        int rank = entrants_ahead(c, lane, Q.s, Q.id, tag);
-        // stayers of this lane ahead of the entrant (old segment of the lane)
         const int b = c.cur.off[lane], e = c.cur.off[lane + 1];
-        int k = b;
-        for (; k + 4 <= e; k += 4) {  // four independent probes per round trip
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (c.code[k + u] == C_STAY && ahead(c.stay[k + u].s, c.cur.a[k + u].id, Q.s, Q.id)) ++rank;
+        int rank = 0;
+        for (int k = b + lane_id; k - lane_id < e; k += 32) {
+            const bool p = k < e && c.code[k] == C_STAY && ahead(c.stay[k].s, c.cur.a[k].id, Q.s, Q.id);
+            rank += __popc(__ballot_sync(0xffffffffu, p));
         }
-        for (; k < e; ++k)
-            if (c.code[k] == C_STAY && ahead(c.stay[k].s, c.cur.a[k].id, Q.s, Q.id)) ++rank;
-        const int pos = c.nxt.off[lane] + rank;
-        if (pos < c.nxt.off[lane] || pos >= c.nxt.off[lane + 1]) {
-            atomicOr(&c.cnt->err, ERR_RANGE);
-        } else {
-            c.nxt.a[pos] = Q;
-            c.nxt.b[pos] = c.eb[q];
+        if (lane_id == 0) {
+            rank += entrants_ahead(c, lane, Q.s, Q.id, tag);
+            const int pos = c.nxt.off[lane] + rank;
+            if (pos < c.nxt.off[lane] || pos >= c.nxt.off[lane + 1]) {
+                atomicOr(&c.cnt->err, ERR_RANGE);
+            } else {
+                c.nxt.a[pos] = Q;
+                c.nxt.b[pos] = c.eb[q];
+            }
         }
     }
     // clear the lane look-back words for the next step (k_lanescan is done)
