@@ -55,8 +55,8 @@ struct MossHandle {
     size_t bytes = 0;
     LaneInfo* d_lane = nullptr;
     float* d_v0f = nullptr;
-    int32_t *d_junc_offset = nullptr, *d_junc_phase_off = nullptr, *d_phase_green = nullptr,
-            *d_phase_amber = nullptr, *d_junc_scen = nullptr, *d_junc_policy = nullptr,
+    JuncInfo* d_junc = nullptr;
+    int32_t *d_phase_green = nullptr, *d_phase_amber = nullptr, *d_junc_policy = nullptr,
             *d_junc_manual = nullptr, *d_junc_state = nullptr;
     int32_t *d_route_off = nullptr, *d_routes = nullptr, *d_dep = nullptr, *d_vstatus = nullptr,
             *d_vflags = nullptr;
@@ -244,8 +244,8 @@ Ctx<Real> make_ctx(MossHandle* h, int cur) {
     std::memset(&c, 0, sizeof(c));
     c.n_lanes = h->n_lanes; c.n_junctions = h->n_junctions; c.n_scen = h->n_scen; c.n_veh = h->n_veh;
     c.lane = h->d_lane;
-    c.junc_offset = h->d_junc_offset; c.junc_phase_off = h->d_junc_phase_off;
-    c.phase_green = h->d_phase_green; c.phase_amber = h->d_phase_amber; c.junc_scen = h->d_junc_scen;
+    c.junc = h->d_junc;
+    c.phase_green = h->d_phase_green; c.phase_amber = h->d_phase_amber;
     c.junc_policy = h->d_junc_policy; c.junc_manual = h->d_junc_manual; c.junc_state = h->d_junc_state;
     c.route_off = h->d_route_off; c.routes = h->d_routes; c.dep = h->d_dep; c.v0f = h->d_v0f;
     c.vstatus = h->d_vstatus; c.vflags = h->d_vflags;
@@ -489,11 +489,16 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
     CK(cudaGetDevice(&h->device));
     CK(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device));
     TRY(upload(h, &h->d_lane, h->lanes));
-    TRY(upload(h, &h->d_junc_offset, junc_offset));
-    TRY(upload(h, &h->d_junc_phase_off, h->junc_phase_off));
+    std::vector<JuncInfo> junc(NJ);
+    for (int j = 0; j < NJ; ++j) {
+        junc[j].offset = junc_offset[j];
+        junc[j].phase_off = h->junc_phase_off[j];
+        junc[j].np = h->junc_phase_off[j + 1] - h->junc_phase_off[j];
+        junc[j].scen = h->junc_scen[j];
+    }
+    TRY(upload(h, &h->d_junc, junc));
     TRY(upload(h, &h->d_phase_green, phase_green));
     TRY(upload(h, &h->d_phase_amber, phase_amber));
-    TRY(upload(h, &h->d_junc_scen, h->junc_scen));
     TRY(upload(h, &h->d_junc_policy, std::vector<int32_t>(NJ, POL_FIXED)));
     TRY(upload(h, &h->d_junc_manual, std::vector<int32_t>(NJ, 0)));
     TRY(dalloc(h, &h->d_junc_state, NJ));

@@ -56,7 +56,7 @@ constexpr int TILE = 256;           // slots per tile of k_decide / k_place (= t
 constexpr int LANESCAN_THREADS = 256;
 constexpr int LANESCAN_ITEMS = 16;
 constexpr int LANESCAN_TILE = LANESCAN_THREADS * LANESCAN_ITEMS;
-constexpr int JUNC_CHUNK = 1024;    // junctions per k_lanescan ticket
+constexpr int JUNC_CHUNK = 256;     // junctions per k_lanescan ticket (one per thread)
 constexpr long long SPIN_LIMIT = 1ll << 22;  // bounded waits (~0.5 s with backoff)
 
 struct Counters {
@@ -92,6 +92,15 @@ struct alignas(32) LaneInfo {
     int lo, hi, jb, je, road, scen;
 };
 
+// One 16-byte record per junction (signal program; policy and manual phase
+// are mutable and kept apart)
+struct alignas(16) JuncInfo {
+    int offset;    // program shift in steps
+    int phase_off; // first phase in phase_green / phase_amber
+    int np;        // number of phases (0 = no signal)
+    int scen;      // scenario
+};
+
 template <typename Real>
 struct Snap {
     RecA<Real>* a;
@@ -104,11 +113,9 @@ struct Ctx {
     // ---- network (possibly a union of scenarios)
     int n_lanes, n_junctions, n_scen, n_veh;
     const LaneInfo* lane;
-    const int32_t* junc_offset;
-    const int32_t* junc_phase_off;
+    const JuncInfo* junc;
     const int32_t* phase_green;
     const int32_t* phase_amber;
-    const int32_t* junc_scen;
     int32_t* junc_policy;
     int32_t* junc_manual;
     int32_t* junc_state;  // bits 0-3 phase, 4-7 n_phases, 8 amber, 9 all green
@@ -228,11 +235,14 @@ __device__ __forceinline__ int junction_state(int policy, int manual, int offset
     return (np & 15) << 4;
 }
 
+// signal state of junction j, `ahead` steps after its scenario's current step
 template <typename Real>
-__device__ __forceinline__ int junction_state_at(const Ctx<Real>& c, int j, long long t) {
-    const int p0 = c.junc_phase_off[j];
-    return junction_state(c.junc_policy[j], c.junc_manual[j], c.junc_offset[j], c.phase_green + p0,
-                          c.phase_amber + p0, c.junc_phase_off[j + 1] - p0, t);
+__device__ __forceinline__ int junction_state_at(const Ctx<Real>& c, int j, int ahead) {
+    const JuncInfo J = c.junc[j];
+    const int pol = c.junc_policy[j], man = c.junc_manual[j];
+    const long long t = c.scen_step[J.scen] + ahead;
+    return junction_state(pol, man, J.offset, c.phase_green + J.phase_off, c.phase_amber + J.phase_off,
+                          J.np, t);
 }
 
 // light of a junction lane (its lane record ji) for this step

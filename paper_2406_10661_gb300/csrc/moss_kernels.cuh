@@ -385,8 +385,8 @@ __global__ void __launch_bounds__(LANESCAN_THREADS) k_lanescan(Ctx<Real> c) {
         } else {
             // signal states of the next step
             const int j0 = (tile - c.n_lane_tiles - 1) * JUNC_CHUNK;
-            for (int j = j0 + threadIdx.x; j < j0 + JUNC_CHUNK && j < c.n_junctions; j += LANESCAN_THREADS)
-                c.junc_state[j] = junction_state_at(c, j, c.scen_step[c.junc_scen[j]] + 1);
+            const int j = j0 + threadIdx.x;
+            if (j < c.n_junctions) c.junc_state[j] = junction_state_at(c, j, 1);
         }
         __syncthreads();
     }
@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(TILE) k_place(Ctx<Real> c) {
 template <typename Real>
 __global__ void k_junction_init(Ctx<Real> c) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < c.n_junctions; j += gridDim.x * blockDim.x)
-        c.junc_state[j] = junction_state_at(c, j, c.scen_step[c.junc_scen[j]]);
+        c.junc_state[j] = junction_state_at(c, j, 0);
 }
 
 // setter: policy (and manual phase) of n junctions, effective from the
@@ -517,7 +517,7 @@ __global__ void k_set_signal(Ctx<Real> c, int n, const int32_t* ids, const int32
     const int j = ids[k];
     c.junc_policy[j] = policy;
     if (policy == POL_MANUAL) c.junc_manual[j] = phases[k];
-    c.junc_state[j] = junction_state_at(c, j, c.scen_step[c.junc_scen[j]]);
+    c.junc_state[j] = junction_state_at(c, j, 0);
 }
 
 }  // namespace moss
