@@ -42,7 +42,7 @@ def build_route_walk(force=False):
     src = os.path.join(CSRC, "route_walk.c")
     if force or _stale(out, [src]):
         tmp = out + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-shared", "-fPIC", "-o", tmp, src])
+        subprocess.check_call(["gcc", "-O2", "-shared", "-fPIC", "-pthread", "-o", tmp, src])
         os.replace(tmp, out)
     return out
 

@@ -392,6 +392,7 @@ def _walk_lib():
             try:
                 lib = ctypes.CDLL(path)
                 lib.moss_gen_walk.restype = ctypes.c_int
+                lib.moss_gen_succ.restype = ctypes.c_int
                 _WALK_LIB = lib
             except OSError:
                 _WALK_LIB = False
@@ -441,28 +442,55 @@ def _walk(pred, ds, sel, origins, row_all, lengths=None, routes=None, route_off=
         k += 1
 
 
-def shortest_routes(net: Network, origins: np.ndarray, dests: np.ndarray,
-                    chunk: int = 256) -> Tuple[np.ndarray, np.ndarray]:
-    """Free-flow-time shortest routes (road sequences, origin..destination)
-    on the road graph without U-turns.  Returns CSR (route_off, routes)."""
+def _successors(A, ds: np.ndarray) -> np.ndarray:
+    """Rows of next-road pointers towards each destination in ds (reversed
+    graph A): the compiled multithreaded Dijkstra when built, else scipy."""
+    lib = _walk_lib()
+    if lib:
+        import ctypes
+        import os
+        P = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        indptr = np.ascontiguousarray(A.indptr, dtype=np.int64)
+        indices = np.ascontiguousarray(A.indices, dtype=np.int32)
+        w = np.ascontiguousarray(A.data, dtype=np.float64)
+        d = np.ascontiguousarray(ds, dtype=np.int64)
+        succ = np.empty((len(d), A.shape[0]), dtype=np.int32)
+        rc = lib.moss_gen_succ(ctypes.c_int(A.shape[0]), P(indptr), P(indices), P(w),
+                               ctypes.c_int(len(d)), P(d), P(succ),
+                               ctypes.c_int(max(1, min(32, os.cpu_count() or 1))))
+        assert rc == 0, "route generation failed"
+        return succ
     import scipy.sparse.csgraph as cg
+    _, pred = cg.dijkstra(A, indices=ds, return_predecessors=True)
+    return pred
+
+
+def shortest_routes(net: Network, origins: np.ndarray, dests: np.ndarray,
+                    chunk: int = 1024, keep_max: int = 4096) -> Tuple[np.ndarray, np.ndarray]:
+    """Free-flow-time shortest routes (road sequences, origin..destination)
+    on the road graph without U-turns.  Returns CSR (route_off, routes).
+    Successor rows of up to ``keep_max`` destinations are kept between the
+    length pass and the fill pass; beyond that they are recomputed."""
     A = _line_graph(net)
     n = len(origins)
     uniq, inv = np.unique(dests, return_inverse=True)
     order = np.argsort(inv, kind="stable")
     bounds = np.searchsorted(inv[order], np.arange(0, len(uniq) + chunk, chunk))
+    keep = len(uniq) <= keep_max
     lengths = np.zeros(n, dtype=np.int64)
     chunks = []
     for ci, c0 in enumerate(range(0, len(uniq), chunk)):
         ds = uniq[c0:c0 + chunk].astype(np.int64)
-        _, pred = cg.dijkstra(A, indices=ds, return_predecessors=True)
+        pred = _successors(A, ds)
         sel = order[bounds[ci]:bounds[ci + 1]]
-        chunks.append((ds, pred, sel, c0))
         _walk(pred, ds, sel, origins, inv - c0, lengths=lengths)
+        chunks.append((ds, pred if keep else None, sel, c0))
     route_off = np.zeros(n + 1, dtype=np.int64)
     route_off[1:] = np.cumsum(lengths)
     routes = np.empty(int(route_off[-1]), dtype=np.int32)
     for ds, pred, sel, c0 in chunks:
+        if pred is None:
+            pred = _successors(A, ds)
         _walk(pred, ds, sel, origins, inv - c0, routes=routes, route_off=route_off)
     return _i32(route_off), routes
 
@@ -515,10 +543,11 @@ def medium_scenario(seed: int = 0, n: int = 100_000) -> Scenario:
 
 
 def city_scenario(seed: int = 0, n: int = 2_464_950, G: int = 100,
-                  dest_pool: int = 1024, dep_horizon: int = 3600) -> Scenario:
+                  dest_pool: Optional[int] = 1024, dep_horizon: int = 3600) -> Scenario:
     """Perturbed 100x100 grid (39,600 roads, 1-4 lanes, log-normal lengths) with
-    2,464,950 trips departing uniformly over 3,600 s; destinations from a pool
-    of 1,024 roads so that route building stays within seconds."""
+    2,464,950 trips departing uniformly over 3,600 s; origins uniform over all
+    roads, destinations uniform over a pool of 1,024 roads (trip attractors;
+    it also bounds the shortest-path work to 1,024 Dijkstra runs)."""
     net = perturbed_grid_network(G, seed=seed)
     veh = random_demand(net, n, dep_horizon, seed=seed, dest_pool=dest_pool)
     return Scenario(net, veh, Params(seed=seed), f"city{G}x{G}_{n}")
