@@ -36,10 +36,10 @@ sys.path.insert(0, ROOT)
 
 T_WARM = 3600   # the timed steps start at this step
 SPEC_BYTES = {  # algorithmic bytes per unit, FP32 state
-    "decide": 41.0,    # per active vehicle: read 8x4 B state record, write code + s' + v'
-    "place": 65.0,     # per active vehicle: read code, s', v', 6x4 B fields; write 8x4 B record
+    "own": 41.0,       # per active vehicle: read its 32 B record, write code + s' + v' (9 B)
+    "mobil": 41.0,     # per MOBIL evaluation: read the 32 B record, write code + s' + v'
     "lanescan": 20.0,  # per lane: read 2 offsets + leave + enter, write offset + leavers-before
-    "prepare": 20.0,   # per lane: reset 3 counters, read queue head + bound
+    "place": 73.0,     # per active vehicle: read code, s', v' and the 32 B record, write 32 B
 }
 STEP_BYTES = 64.0      # whole step: read and write one 8x4 B state record per vehicle update
 
@@ -239,10 +239,11 @@ def run_ours(args):
         m3 = sim.metrics()
         sim.set_kernel_timing(False)
         upd_k = (m3["vehicle_updates"] - m2["vehicle_updates"]) / max(kn, 1)
+        mob_k = (m3["mobil_evals"] - m2["mobil_evals"]) / max(kn, 1)
         avg_ms = {k: v / max(kn, 1) for k, v in kt.items()}
         dom = max(avg_ms, key=avg_ms.get)
         n_lanes = int(scen.net.n_lanes)
-        units = {"decide": upd_k, "place": upd_k, "lanescan": n_lanes, "prepare": n_lanes}
+        units = {"own": upd_k, "mobil": mob_k, "lanescan": n_lanes, "place": upd_k}
         peak, peak_kind = _peaks()
         achieved = SPEC_BYTES[dom] * units[dom] / (avg_ms[dom] * 1e-3) / 1e9
         step_ms_k = sum(avg_ms.values())
@@ -306,7 +307,7 @@ def run_ours(args):
         "e2e": {"value": e2e_val, "unit": "vehicle-updates/s", "h2d_bytes_per_step": 8 * J,
                 "d2h_bytes_per_step": 8 * 12 + 4, "steps": e2e_steps,
                 "api": "moss_set_signal_phase + moss_step(1) + moss_get_metrics per step"},
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": 4 * args.steps,
         "wall_s_timed_region": wall,
         "cpu_baseline": cpu,
     }

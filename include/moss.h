@@ -137,11 +137,13 @@ typedef struct MossParams {
 } MossParams;
 
 /* Cumulative metrics (§3.3): throughput = n_arrived; ATT = tt_sum / n_arrived;
- * network speed = speed_sum / vehicle_updates (speed after each update). */
+ * network speed = speed_sum / vehicle_updates (speed after each update).
+ * mobil_evals: vehicle updates that evaluated the MOBIL utilities (the
+ * attempt draw passed on an eligible road lane). */
 typedef struct MossMetrics {
     int64_t step, n_active, n_waiting, n_arrived;
     double tt_sum, speed_sum;
-    int64_t vehicle_updates, lane_changes, flagged, overlaps, inserted, errors;
+    int64_t vehicle_updates, lane_changes, flagged, overlaps, inserted, errors, mobil_evals;
 } MossMetrics;
 
 /* Per-vehicle state by vehicle id (host arrays of MossVehicles.n entries,
@@ -225,8 +227,8 @@ int moss_batch_set_signal_phase(moss_t h, int scenario, int n, const int32_t* ju
  * Kernel timing for measurement: when enabled, every step records CUDA
  * events around each kernel on the handle's stream (graphs are not used
  * while enabled).  moss_kernel_times returns the summed milliseconds per
- * kernel since enabling, in the order decide, lanescan, place, prepare,
- * and the number of timed steps.
+ * kernel since enabling, in launch order (own, mobil, lanescan, place), and
+ * the number of timed steps.
  */
 int moss_set_kernel_timing(moss_t h, int enable);
 int moss_kernel_times(moss_t h, double* ms4, int64_t* steps);

@@ -25,7 +25,8 @@ _LIB_PATH = os.path.join(_HERE, "_moss_oracle.so")
 _LIB = None
 
 METRIC_NAMES = ("step", "n_active", "n_waiting", "n_arrived", "tt_sum", "speed_sum",
-                "vehicle_updates", "lane_changes", "flagged", "overlaps", "inserted", "errors")
+                "vehicle_updates", "lane_changes", "flagged", "overlaps", "inserted", "errors",
+                "mobil_evals")
 
 DECISION_NAMES = ("a_own", "eligible", "attempted", "cand", "dir", "u", "uL", "uR", "feasL",
                   "feasR", "uT", "pLC", "u_att", "u_lc", "u_dir", "at_ego_L", "at_ego_R",

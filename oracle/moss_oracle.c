@@ -131,6 +131,7 @@ typedef struct {
     /* metrics */
     double m_speed_sum, m_tt_sum;
     long m_updates, m_arrived, m_lane_changes, m_flagged, m_overlaps, m_inserted, m_errors;
+    long m_mobil;
 } Oracle;
 
 /* Snapshot of the public state at the start of a step (§3.1). */
@@ -608,6 +609,7 @@ static void step_once(Oracle* O) {
         if (!S.active[i]) continue;
         D[i] = decide(O, &S, i, t);
         if (D[i].own.overlap) O->m_overlaps++;
+        if (D[i].attempted) O->m_mobil++;
     }
     /* conflict resolution among candidates, bucketed by target lane (R9) */
     int* tcnt = (int*)xcalloc(O->n_lanes + 1, sizeof(int));
@@ -740,7 +742,7 @@ void mo_step(void* h, int n) {
 void mo_set_reverse_order(void* h, int rev) { ((Oracle*)h)->reverse_order = rev; }
 
 /* metrics: [step, n_active, n_waiting, n_arrived, tt_sum, speed_sum, updates,
- *           lane_changes, flagged, overlaps, inserted, errors] */
+ *           lane_changes, flagged, overlaps, inserted, errors, mobil_evals] */
 void mo_get_metrics(void* h, double* out) {
     Oracle* O = (Oracle*)h;
     long act = 0, wait = 0;
@@ -753,6 +755,7 @@ void mo_get_metrics(void* h, double* out) {
     out[6] = (double)O->m_updates; out[7] = (double)O->m_lane_changes;
     out[8] = (double)O->m_flagged; out[9] = (double)O->m_overlaps;
     out[10] = (double)O->m_inserted; out[11] = (double)O->m_errors;
+    out[12] = (double)O->m_mobil;
 }
 
 void mo_get_state(void* h, int* status, int* lane, double* s, double* v, int* rc, int* flags) {

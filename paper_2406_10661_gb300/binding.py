@@ -54,7 +54,8 @@ class MossMetrics(ctypes.Structure):
                 ("tt_sum", ctypes.c_double), ("speed_sum", ctypes.c_double),
                 ("vehicle_updates", ctypes.c_int64), ("lane_changes", ctypes.c_int64),
                 ("flagged", ctypes.c_int64), ("overlaps", ctypes.c_int64),
-                ("inserted", ctypes.c_int64), ("errors", ctypes.c_int64)]
+                ("inserted", ctypes.c_int64), ("errors", ctypes.c_int64),
+                ("mobil_evals", ctypes.c_int64)]
 
     def as_dict(self) -> Dict[str, float]:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -204,7 +205,7 @@ class _Handle:
         ms = np.zeros(4, dtype=np.float64)
         n = ctypes.c_int64(0)
         _check(self.lib.moss_kernel_times(self.h, _ptr(ms, ctypes.c_double), ctypes.byref(n)), self.h)
-        return dict(zip(("decide", "lanescan", "place", "prepare"), ms.tolist())), int(n.value)
+        return dict(zip(("own", "mobil", "lanescan", "place"), ms.tolist())), int(n.value)
 
 
 def _state_arrays(n: int):

@@ -12,12 +12,15 @@
 // search in the adjacent lane's segment (adjacent lanes of a road are
 // adjacent in memory).
 //
-// One step = three kernels:
-//   k_decide    per vehicle: sensing, IDM (App. B.3 eqs. (1)-(2)), randomized
-//               MOBIL (App. B.3) with deterministic conflict resolution,
-//               ballistic integration with clamps, transfer at lane ends and
-//               arrival (App. B.2 update stream 1); extra blocks run the
-//               departure insertion (App. B.2 update stream 3);
+// One step = four kernels:
+//   k_own       per vehicle: sensing, IDM (App. B.3 eqs. (1)-(2)), the MOBIL
+//               attempt draw; vehicles that do not attempt a lane change are
+//               integrated (ballistic update with clamps), transferred at lane
+//               ends or arrive (App. B.2 update stream 1); the others go to
+//               a work list; extra blocks run the departure insertion (App.
+//               B.2 update stream 3);
+//   k_mobil     the work list in dense warps: randomized MOBIL (App. B.3) with
+//               deterministic conflict resolution, then the same update;
 //   k_lanescan  per-lane sizes of the next snapshot -> offsets (single-pass
 //               decoupled look-back scan), prefix of leavers per slot tile,
 //               signal states of the next step (§3.2 policies);
@@ -42,7 +45,7 @@ enum : int8_t { C_STAY = 0, C_MOVE = 1, C_ARRIVE = 2 };
 // per-scenario metric accumulators (int64, deterministic integer sums)
 enum : int {
     M_UPDATES = 0, M_ARRIVED, M_TT_STEPS, M_SPEED_FX, M_LANE_CHANGES, M_FLAGGED,
-    M_OVERLAPS, M_INSERTED, M_ERRORS, M_CUR_ACTIVE, M_CUR_ARRIVED, M_NFIELDS
+    M_OVERLAPS, M_INSERTED, M_ERRORS, M_CUR_ACTIVE, M_CUR_ARRIVED, M_MOBIL, M_NFIELDS
 };
 constexpr double SPEED_FX = 16777216.0;  // speed sums in units of 2^-24 m/s
 
@@ -67,7 +70,7 @@ struct Counters {
     int done_place;  // k_place blocks finished (the last one closes the step)
     int err;
     int tag;         // step tag of the per-lane entrant lists (never 0)
-    int pad;
+    int n_mobil;     // vehicles that evaluate MOBIL this step (k_mobil's work list)
 };
 
 // snapshot records
@@ -152,6 +155,7 @@ struct Ctx {
     int32_t* lbefore;     // [n_lanes] leavers in lanes before l
     int32_t* tile_leave;  // [slot tiles] leavers per tile of the current snapshot
     int32_t* tile_prefix; // [slot tiles] leavers before the tile
+    int32_t* mlist;       // [n_veh] slots of the vehicles that evaluate MOBIL this step
     unsigned long long* lane_tiles;
     int n_lane_tiles, max_slot_tiles, n_junc_chunks;
     Counters* cnt;
@@ -484,6 +488,12 @@ __device__ __forceinline__ unsigned long long load_acquire(unsigned long long* p
     cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> a(*p);
     return a.load(cuda::memory_order_acquire);
 }
+// look-back words carry flag and value in one 64-bit word, so a relaxed
+// (single-copy atomic) load that sees the flag also sees the value
+__device__ __forceinline__ unsigned long long load_relaxed(unsigned long long* p) {
+    cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> a(*p);
+    return a.load(cuda::memory_order_relaxed);
+}
 __device__ __forceinline__ void store_release(unsigned long long* p, unsigned long long v) {
     cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> a(*p);
     a.store(v, cuda::memory_order_release);
@@ -499,7 +509,7 @@ __device__ __forceinline__ unsigned long long warp_lookback(unsigned long long* 
     long long spins = 0;
     while (p >= 0) {
         const int idx = p - lane;
-        const unsigned long long w = idx >= 0 ? load_acquire(&st[idx]) : (2ull << 62);
+        const unsigned long long w = idx >= 0 ? load_relaxed(&st[idx]) : (2ull << 62);
         const unsigned f = (unsigned)(w >> 62);
         const unsigned m2 = __ballot_sync(0xffffffffu, f == 2);
         const unsigned m0 = __ballot_sync(0xffffffffu, f == 0);
@@ -524,7 +534,7 @@ __device__ __forceinline__ unsigned long long warp_lookback(unsigned long long* 
 // with one set of atomics per block when the whole block shares a scenario.
 struct MetricAcc {
     int scen;
-    long long m[8];  // updates, arrived, tt_steps, speed_fx, lane_changes, flagged, overlaps, inserted
+    long long m[9];  // updates, arrived, tt_steps, speed_fx, lane_changes, flagged, overlaps, inserted, mobil
 };
 
 __device__ __forceinline__ int metric_field(int k) {
@@ -536,20 +546,21 @@ __device__ __forceinline__ int metric_field(int k) {
         case 4: return M_LANE_CHANGES;
         case 5: return M_FLAGGED;
         case 6: return M_OVERLAPS;
-        default: return M_INSERTED;
+        case 7: return M_INSERTED;
+        default: return M_MOBIL;
     }
 }
 
 __device__ __forceinline__ void macc_reset(MetricAcc& a, int scen) {
     a.scen = scen;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) a.m[k] = 0;
+    for (int k = 0; k < 9; ++k) a.m[k] = 0;
 }
 
 __device__ __forceinline__ void macc_flush_thread(MetricAcc& a, long long* metrics) {
     if (a.scen < 0) return;
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < 9; ++k)
         if (a.m[k]) atomicAdd((unsigned long long*)&metrics[a.scen * M_NFIELDS + metric_field(k)],
                               (unsigned long long)a.m[k]);
 }
@@ -558,7 +569,7 @@ __device__ __forceinline__ void macc_flush_thread(MetricAcc& a, long long* metri
 // same scenario (or nothing), else fall back to per-thread atomics.
 template <int THREADS>
 __device__ void macc_flush_block(MetricAcc& a, long long* metrics) {
-    __shared__ long long red[8][THREADS / 32];
+    __shared__ long long red[9][THREADS / 32];
     __shared__ int scen0;
     const int tid = threadIdx.x;
     if (tid == 0) scen0 = -1;
@@ -571,13 +582,13 @@ __device__ void macc_flush_block(MetricAcc& a, long long* metrics) {
     if (s0 < 0) return;
     const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < 9; ++k) {
         long long x = a.scen < 0 ? 0 : a.m[k];
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
         if (lane == 0) red[k][warp] = x;
     }
     __syncthreads();
-    if (tid < 8) {
+    if (tid < 9) {
         long long x = 0;
         for (int w = 0; w < THREADS / 32; ++w) x += red[tid][w];
         if (x) atomicAdd((unsigned long long*)&metrics[s0 * M_NFIELDS + metric_field(tid)], (unsigned long long)x);

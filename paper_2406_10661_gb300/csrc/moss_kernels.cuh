@@ -64,14 +64,107 @@ __device__ void insert_departure(const Ctx<Real>& c, int l, int tag) {
 }
 
 // ---------------------------------------------------------------------------
-// k_decide: blocks [0, n_work) take 256-slot tiles of the current snapshot
-// (one vehicle per thread); blocks [n_work, gridDim) run the insertion.
-// MOSS_DECIDE_MIN_BLOCKS: resident blocks per SM the register budget targets.
-#ifndef MOSS_DECIDE_MIN_BLOCKS
-#define MOSS_DECIDE_MIN_BLOCKS 4
-#endif
+// Ballistic update with clamps (R12, R13), transfer and arrival (R17), and the
+// outputs of one vehicle (slot i) driving on lane `nlane` (record ni) with
+// lane kinematics la.  Returns 1 if the vehicle leaves its lane's segment.
 template <typename Real>
-__global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Real> c, int n_work) {
+__device__ __forceinline__ int integrate_emit(const Ctx<Real>& c, MetricAcc& acc, int i, const RecA<Real>& E,
+                                              const RecB& EB, const LaneAcc<Real>& la, int nlane, int fl,
+                                              bool own_overlap, long long t, int sc, int tag) {
+    const int lane = E.lane;
+    const Real s = E.s, v = E.v, a = la.a, dt = c.dt;
+    Real vn = v + a * dt, disp;
+    if (vn >= Real(0)) {
+        disp = v * dt + Real(0.5) * a * dt * dt;
+    } else {
+        disp = -v * v / (Real(2) * a);
+        vn = Real(0);
+    }
+    if (la.has_leader) { const Real cl = la.gap > Real(0) ? la.gap : Real(0); if (disp > cl) disp = cl; }
+    if (la.stop) { const Real cl = la.stop_gap > Real(0) ? la.stop_gap : Real(0); if (disp > cl) disp = cl; }
+    LaneInfo ni = c.lane[nlane];
+    Real sn = s + disp;
+    if (la.stop && sn > Real(ni.L)) sn = Real(ni.L);
+    // The overshoot past the lane end is taken as disp - (L - s): L - s is
+    // exact for s >= L/2 (Sterbenz), so the position on the next lane does
+    // not lose the bits of L.
+    int rptr = EB.rptr;
+    const int rlast = EB.rlast;
+    int nl = la.nl;
+    bool arrived = false;
+    Real ex = disp - (Real(ni.L) - s);  // distance beyond the end of nlane
+    if (!la.stop) {
+        for (int iter = 0;;) {
+            const Real Ll = Real(ni.L);
+            const Real scl = Ll > Real(1) ? Ll : Real(1);
+            const bool road = ni.lo >= 0;
+            if (rabs(ex) < c.band * scl) fl |= F_FLAGGED;
+            if (road && rptr == rlast) {
+                if (ex >= Real(0)) arrived = true;
+                break;
+            }
+            if (!(ex > Real(0))) break;
+            if (++iter > 4 || nl < 0) { atomicOr(&c.cnt->err, ERR_TRANSFER); sn = Ll; break; }
+            sn = ex;
+            fl |= F_TRANSFER;
+            nlane = nl;
+            ni = c.lane[nlane];
+            if (road) {
+                nl = ni.hi;  // entered a junction lane: next is its target road lane
+            } else {
+                rptr += 1;  // entered the next road
+                nl = (rptr < rlast) ? jl_toward(c, ni, c.routes[rptr + 1]) : -1;
+                if (rptr < rlast && nl < 0) atomicOr(&c.cnt->err, ERR_ROUTE);
+            }
+            ex = sn - Real(ni.L);
+        }
+    }
+    if (arrived) fl |= F_ARRIVED;
+    acc.m[0] += 1;
+    acc.m[3] += (long long)llrint(double(vn) * SPEED_FX);
+    if (fl & F_FLAGGED) acc.m[5] += 1;
+    if (fl & F_CHANGED) acc.m[4] += 1;
+    if (own_overlap) acc.m[6] += 1;
+    if (fl) c.vflags[E.id] = int((t & 0xFFFFFF) << 8) | fl;
+    if (arrived) {
+        c.code[i] = C_ARRIVE;
+        c.vstatus[E.id] = 2;
+        acc.m[1] += 1;
+        acc.m[2] += (t + 1) - (long long)c.dep[E.id];
+        atomicAdd(&c.leave[lane], 1);
+        long long* M = c.metrics + (long long)sc * M_NFIELDS;
+        atomicAdd((unsigned long long*)&M[M_CUR_ACTIVE], (unsigned long long)(-1ll));
+        atomicAdd((unsigned long long*)&M[M_CUR_ARRIVED], 1ull);
+        return 1;
+    }
+    if (nlane == lane) {
+        c.code[i] = C_STAY;
+        SV<Real> w;
+        w.s = sn; w.v = vn;
+        c.stay[i] = w;
+        return 0;
+    }
+    c.code[i] = C_MOVE;
+    atomicAdd(&c.leave[lane], 1);
+    const int q = atomicAdd(&c.cnt->n_ent, 1);
+    RecA<Real> A;
+    A.s = sn; A.v = vn; A.id = E.id; A.lane = nlane;
+    RecB B;
+    B.v0f = EB.v0f; B.rptr = rptr; B.rlast = rlast; B.nl = nl;
+    c.ea[q] = A;
+    c.eb[q] = B;
+    atomicAdd(&c.enter[nlane], 1);
+    list_push(c.head, c.enext, nlane, q, tag);
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// k_own: blocks [0, n_work) take 256-slot tiles of the current snapshot (one
+// vehicle per thread): own-lane kinematics and the MOBIL attempt draw (R4);
+// vehicles that do not attempt are updated here, the others are appended to
+// k_mobil's work list.  Blocks [n_work, gridDim) run the insertion.
+template <typename Real>
+__global__ void __launch_bounds__(TILE) k_own(Ctx<Real> c, int n_work) {
     if (c.cnt->err & ERR_POISON) return;
     const int tag = c.cnt->tag;
     if ((int)blockIdx.x >= n_work) {
@@ -82,169 +175,139 @@ __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Rea
     }
     const int n = c.cnt->n_cur;
     const int n_tiles = (n + TILE - 1) / TILE;
+    const int lane_id = threadIdx.x & 31;
     MetricAcc acc;
     macc_reset(acc, -1);
     for (int tile = blockIdx.x; tile < n_tiles; tile += n_work) {
         const int i = tile * TILE + threadIdx.x;
-        int leaver = 0;
+        int leaver = 0, attempt = 0;
         if (i < n) {
             const RecA<Real> E = c.cur.a[i];
+            const RecB EB = c.cur.b[i];
             const int lane = E.lane;
-            if ((unsigned)lane >= (unsigned)c.n_lanes) {
+            if ((unsigned)lane >= (unsigned)c.n_lanes || EB.nl < -1 || EB.nl >= c.n_lanes) {
                 atomicOr(&c.cnt->err, ERR_RANGE);
             } else {
-                const int sc = c.lane[lane].scen;
+                const LaneInfo li = c.lane[lane];
+                const int sc = li.scen;
                 if (sc != acc.scen) {
                     macc_flush_thread(acc, c.metrics);
                     macc_reset(acc, sc);
                 }
                 const long long t = c.scen_step[sc];
-                const uint32_t k0 = c.key0[sc], k1 = c.key1[sc];
-                const int vbase = c.veh_base[sc];
-                // job 0 is this vehicle; jobs 1.. are the rivals of a lane-change
-                // candidate (R9): vehicles of the lane beyond the target lane that
-                // fall into the same target-lane gap.  One call site of decide()
-                // makes every recomputation bit-identical to the rival's own.
-                Decision<Real> D;
-                int fl = 0;
-                bool granted = false;
-                int r = 0, rend = 0;
-                for (int job = 0;; ++job) {
-                    const int slot = job == 0 ? i : r;
-                    const Decision<Real> X = decide(c, slot, t, k0, k1, vbase);
-                    if (job == 0) {
-                        D = X;
-                        fl = D.flag ? F_FLAGGED : 0;
-                        if (!D.cand) break;
-                        fl |= F_CANDIDATE;
-                        granted = true;
-                        const LaneInfo li = c.lane[lane];
-                        const int ol = D.tl + D.dir;
-                        if (ol < li.lo || ol >= li.hi) break;
-                        const int ob = c.cur.off[ol], oe = c.cur.off[ol + 1];
-                        r = ob; rend = oe;
-                        if (D.TL >= 0) {
-                            const RecA<Real> T = c.cur.a[D.TL];
-                            r = partition_point(c, ob, oe, T.s, T.id);
-                        }
-                        if (D.TF >= 0) {
-                            const RecA<Real> T = c.cur.a[D.TF];
-                            rend = partition_point(c, ob, oe, T.s, T.id);
-                        }
-                        if (r >= rend) break;
-                    } else {
-                        if (X.cand && X.tl == D.tl) {
-                            const Real sc2 = D.scale > X.scale ? D.scale : X.scale;
-                            if (rabs(D.u - X.u) < c.band * sc2) fl |= F_FLAGGED;
-                            const int rid = c.cur.a[r].id;
-                            if (!(D.u > X.u || (D.u == X.u && E.id < rid))) granted = false;
-                        }
-                        if (++r >= rend) break;
-                    }
+                if (li.lo >= 0 && li.hi - li.lo >= 2) {  // eligible for MOBIL (R7)
+                    uint32_t w[4];
+                    philox4x32_10(c.key0[sc], c.key1[sc], uint32_t(E.id - c.veh_base[sc]), uint32_t(t), 0u,
+                                  0u, w);
+                    attempt = unit24<Real>(w[0]) < c.p_att;
                 }
-                if (D.cand && !granted) fl |= F_CONFLICT_LOST;
-                // ---- integration (R12, R13); a granted change drives on the
-                // target lane (its kinematics recomputed from the same inputs)
-                LaneAcc<Real> la = D.own;
-                int nlane = lane;
-                if (granted) {
-                    fl |= F_CHANGED;
-                    nlane = D.tl;
-                    const LaneInfo ti = c.lane[nlane];
-                    const RecB EB0 = c.cur.b[i];
-                    la = accel_on_lane(c, ti, E.s, E.v, Real(EB0.v0f) * Real(ti.vmax), D.TL, D.nlt,
-                                       EB0.rptr, EB0.rlast);
-                }
-                const Real s = E.s, v = E.v, a = la.a, dt = c.dt;
-                Real vn = v + a * dt, disp;
-                if (vn >= Real(0)) {
-                    disp = v * dt + Real(0.5) * a * dt * dt;
-                } else {
-                    disp = -v * v / (Real(2) * a);
-                    vn = Real(0);
-                }
-                if (la.has_leader) { const Real cl = la.gap > Real(0) ? la.gap : Real(0); if (disp > cl) disp = cl; }
-                if (la.stop) { const Real cl = la.stop_gap > Real(0) ? la.stop_gap : Real(0); if (disp > cl) disp = cl; }
-                LaneInfo ni = c.lane[nlane];
-                Real sn = s + disp;
-                if (la.stop && sn > Real(ni.L)) sn = Real(ni.L);
-                // ---- transfer and arrival (R17).  The overshoot past the lane end is
-                // taken as disp - (L - s): L - s is exact for s >= L/2 (Sterbenz), so
-                // the position on the next lane does not lose the bits of L.
-                const RecB EB = c.cur.b[i];
-                int rptr = EB.rptr;
-                const int rlast = EB.rlast;
-                int nl = la.nl;
-                bool arrived = false;
-                Real ex = disp - (Real(ni.L) - s);  // distance beyond the end of nlane
-                if (!la.stop) {
-                    for (int iter = 0;;) {
-                        const Real Ll = Real(ni.L);
-                        const Real scl = Ll > Real(1) ? Ll : Real(1);
-                        const bool road = ni.lo >= 0;
-                        if (rabs(ex) < c.band * scl) fl |= F_FLAGGED;
-                        if (road && rptr == rlast) {
-                            if (ex >= Real(0)) arrived = true;
-                            break;
-                        }
-                        if (!(ex > Real(0))) break;
-                        if (++iter > 4 || nl < 0) { atomicOr(&c.cnt->err, ERR_TRANSFER); sn = Ll; break; }
-                        sn = ex;
-                        fl |= F_TRANSFER;
-                        nlane = nl;
-                        ni = c.lane[nlane];
-                        if (road) {
-                            nl = ni.hi;  // entered a junction lane: next is its target road lane
-                        } else {
-                            rptr += 1;  // entered the next road
-                            nl = (rptr < rlast) ? jl_toward(c, ni, c.routes[rptr + 1]) : -1;
-                            if (rptr < rlast && nl < 0) atomicOr(&c.cnt->err, ERR_ROUTE);
-                        }
-                        ex = sn - Real(ni.L);
-                    }
-                }
-                // ---- outputs
-                if (arrived) fl |= F_ARRIVED;
-                acc.m[0] += 1;
-                acc.m[3] += (long long)llrint(double(vn) * SPEED_FX);
-                if (fl & F_FLAGGED) acc.m[5] += 1;
-                if (fl & F_CHANGED) acc.m[4] += 1;
-                if (D.own.overlap) acc.m[6] += 1;
-                if (fl) c.vflags[E.id] = int((t & 0xFFFFFF) << 8) | fl;
-                if (arrived) {
-                    c.code[i] = C_ARRIVE;
-                    leaver = 1;
-                    c.vstatus[E.id] = 2;
-                    acc.m[1] += 1;
-                    acc.m[2] += (t + 1) - (long long)c.dep[E.id];
-                    atomicAdd(&c.leave[lane], 1);
-                    long long* M = c.metrics + (long long)sc * M_NFIELDS;
-                    atomicAdd((unsigned long long*)&M[M_CUR_ACTIVE], (unsigned long long)(-1ll));
-                    atomicAdd((unsigned long long*)&M[M_CUR_ARRIVED], 1ull);
-                } else if (nlane == lane) {
-                    c.code[i] = C_STAY;
-                    SV<Real> w;
-                    w.s = sn; w.v = vn;
-                    c.stay[i] = w;
-                } else {
-                    c.code[i] = C_MOVE;
-                    leaver = 1;
-                    atomicAdd(&c.leave[lane], 1);
-                    const int q = atomicAdd(&c.cnt->n_ent, 1);
-                    RecA<Real> A;
-                    A.s = sn; A.v = vn; A.id = E.id; A.lane = nlane;
-                    RecB B;
-                    B.v0f = EB.v0f; B.rptr = rptr; B.rlast = rlast; B.nl = nl;
-                    c.ea[q] = A;
-                    c.eb[q] = B;
-                    atomicAdd(&c.enter[nlane], 1);
-                    list_push(c.head, c.enext, nlane, q, tag);
+                if (!attempt) {
+                    const int b = c.cur.off[lane];
+                    const int OL = (i > b) ? i - 1 : -1;
+                    const LaneAcc<Real> own = accel_on_lane(c, li, E.s, E.v, Real(EB.v0f) * Real(li.vmax),
+                                                            OL, EB.nl, EB.rptr, EB.rlast);
+                    leaver = integrate_emit(c, acc, i, E, EB, own, lane, 0, own.overlap != 0, t, sc, tag);
                 }
             }
         }
+        // MOBIL work list: one atomic per warp
+        const unsigned am = __ballot_sync(0xffffffffu, attempt);
+        if (am) {
+            int base = 0;
+            if (lane_id == 0) base = atomicAdd(&c.cnt->n_mobil, __popc(am));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (attempt) c.mlist[base + __popc(am & ((1u << lane_id) - 1))] = i;
+        }
         // leavers of this tile (k_lanescan zeroes the counters after reading them)
         const unsigned lb = __ballot_sync(0xffffffffu, leaver);
-        if ((threadIdx.x & 31) == 0 && lb) atomicAdd(&c.tile_leave[tile], __popc(lb));
+        if (lane_id == 0 && lb) atomicAdd(&c.tile_leave[tile], __popc(lb));
+    }
+    macc_flush_block<TILE>(acc, c.metrics);
+}
+
+// ---------------------------------------------------------------------------
+// k_mobil: the vehicles that attempt a lane change, one per thread over the
+// dense work list: MOBIL decision (App. B.3), conflict resolution (R9), then
+// the update on the own or the target lane.
+// MOSS_MOBIL_MIN_BLOCKS: resident blocks per SM the register budget targets.
+#ifndef MOSS_MOBIL_MIN_BLOCKS
+#define MOSS_MOBIL_MIN_BLOCKS 4
+#endif
+template <typename Real>
+__global__ void __launch_bounds__(TILE, MOSS_MOBIL_MIN_BLOCKS) k_mobil(Ctx<Real> c) {
+    if (c.cnt->err & ERR_POISON) return;
+    const int tag = c.cnt->tag;
+    const int nm = c.cnt->n_mobil;
+    MetricAcc acc;
+    macc_reset(acc, -1);
+    for (int k = blockIdx.x * TILE + threadIdx.x; k < nm; k += gridDim.x * TILE) {
+        const int i = c.mlist[k];
+        const RecA<Real> E = c.cur.a[i];
+        const int lane = E.lane;
+        const int sc = c.lane[lane].scen;
+        if (sc != acc.scen) {
+            macc_flush_thread(acc, c.metrics);
+            macc_reset(acc, sc);
+        }
+        const long long t = c.scen_step[sc];
+        const uint32_t k0 = c.key0[sc], k1 = c.key1[sc];
+        const int vbase = c.veh_base[sc];
+        acc.m[8] += 1;
+        // job 0 is this vehicle; jobs 1.. are the rivals of a lane-change
+        // candidate (R9): vehicles of the lane beyond the target lane that
+        // fall into the same target-lane gap.  One call site of decide()
+        // makes every recomputation bit-identical to the rival's own.
+        Decision<Real> D;
+        int fl = 0;
+        bool granted = false;
+        int r = 0, rend = 0;
+        for (int job = 0;; ++job) {
+            const int slot = job == 0 ? i : r;
+            const Decision<Real> X = decide(c, slot, t, k0, k1, vbase);
+            if (job == 0) {
+                D = X;
+                fl = D.flag ? F_FLAGGED : 0;
+                if (!D.cand) break;
+                fl |= F_CANDIDATE;
+                granted = true;
+                const LaneInfo li = c.lane[lane];
+                const int ol = D.tl + D.dir;
+                if (ol < li.lo || ol >= li.hi) break;
+                const int ob = c.cur.off[ol], oe = c.cur.off[ol + 1];
+                r = ob; rend = oe;
+                if (D.TL >= 0) {
+                    const RecA<Real> T = c.cur.a[D.TL];
+                    r = partition_point(c, ob, oe, T.s, T.id);
+                }
+                if (D.TF >= 0) {
+                    const RecA<Real> T = c.cur.a[D.TF];
+                    rend = partition_point(c, ob, oe, T.s, T.id);
+                }
+                if (r >= rend) break;
+            } else {
+                if (X.cand && X.tl == D.tl) {
+                    const Real sc2 = D.scale > X.scale ? D.scale : X.scale;
+                    if (rabs(D.u - X.u) < c.band * sc2) fl |= F_FLAGGED;
+                    const int rid = c.cur.a[r].id;
+                    if (!(D.u > X.u || (D.u == X.u && E.id < rid))) granted = false;
+                }
+                if (++r >= rend) break;
+            }
+        }
+        if (D.cand && !granted) fl |= F_CONFLICT_LOST;
+        // a granted change drives on the target lane (its kinematics
+        // recomputed from the same inputs)
+        const RecB EB = c.cur.b[i];
+        LaneAcc<Real> la = D.own;
+        int nlane = lane;
+        if (granted) {
+            fl |= F_CHANGED;
+            nlane = D.tl;
+            const LaneInfo ti = c.lane[nlane];
+            la = accel_on_lane(c, ti, E.s, E.v, Real(EB.v0f) * Real(ti.vmax), D.TL, D.nlt, EB.rptr, EB.rlast);
+        }
+        if (integrate_emit(c, acc, i, E, EB, la, nlane, fl, D.own.overlap != 0, t, sc, tag))
+            atomicAdd(&c.tile_leave[i / TILE], 1);
     }
     macc_flush_block<TILE>(acc, c.metrics);
 }
@@ -490,6 +553,7 @@ __global__ void __launch_bounds__(TILE) k_place(Ctx<Real> c) {
             __threadfence();
             c.cnt->n_cur = c.cnt->n_next;
             c.cnt->n_ent = 0;
+            c.cnt->n_mobil = 0;
             c.cnt->ticket_lane = 0;
             c.cnt->done_place = 0;
             int tg = c.cnt->tag + 1;

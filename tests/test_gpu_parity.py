@@ -82,7 +82,7 @@ def test_fp64_rollout_matches_oracle_small():
         assert np.array_equal(g["flags"], r["flags"])
     gm, rm = sim.metrics(), ora.metrics()
     for k in ("step", "n_active", "n_waiting", "n_arrived", "vehicle_updates", "lane_changes",
-              "flagged", "overlaps", "inserted"):
+              "flagged", "overlaps", "inserted", "mobil_evals"):
         assert gm[k] == rm[k], (k, gm[k], rm[k])
     assert abs(gm["tt_sum"] - rm["tt_sum"]) < 1e-9
     assert abs(gm["speed_sum"] - rm["speed_sum"]) <= 1e-6 * rm["speed_sum"]
@@ -208,7 +208,7 @@ def test_batch_equals_alone():
         for k in ("s", "v"):
             assert np.array_equal(a[k], b[k]), (i, k)
         ma, mb = alone.metrics(), batch.metrics(i)
-        assert ma == mb
+        assert ma == mb, (i, ma, mb)
 
 
 def test_medium_one_step_parity_fp32():
