@@ -36,8 +36,7 @@ sys.path.insert(0, ROOT)
 
 T_WARM = 3600   # the timed steps start at this step
 SPEC_BYTES = {  # algorithmic bytes per unit, FP32 state
-    "own": 41.0,       # per active vehicle: read its 32 B record, write code + s' + v' (9 B)
-    "mobil": 41.0,     # per MOBIL evaluation: read the 32 B record, write code + s' + v'
+    "decide": 41.0,    # per active vehicle: read its 32 B record, write code + s' + v' (9 B)
     "lanescan": 20.0,  # per lane: read 2 offsets + leave + enter, write offset + leavers-before
     "place": 73.0,     # per active vehicle: read code, s', v' and the 32 B record, write 32 B
 }
@@ -243,7 +242,7 @@ def run_ours(args):
         avg_ms = {k: v / max(kn, 1) for k, v in kt.items()}
         dom = max(avg_ms, key=avg_ms.get)
         n_lanes = int(scen.net.n_lanes)
-        units = {"own": upd_k, "mobil": mob_k, "lanescan": n_lanes, "place": upd_k}
+        units = {"decide": upd_k, "lanescan": n_lanes, "place": upd_k}
         peak, peak_kind = _peaks()
         achieved = SPEC_BYTES[dom] * units[dom] / (avg_ms[dom] * 1e-3) / 1e9
         step_ms_k = sum(avg_ms.values())
@@ -307,7 +306,7 @@ def run_ours(args):
         "e2e": {"value": e2e_val, "unit": "vehicle-updates/s", "h2d_bytes_per_step": 8 * J,
                 "d2h_bytes_per_step": 8 * 12 + 4, "steps": e2e_steps,
                 "api": "moss_set_signal_phase + moss_step(1) + moss_get_metrics per step"},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": 3 * args.steps,
         "wall_s_timed_region": wall,
         "cpu_baseline": cpu,
     }

@@ -25,7 +25,7 @@ struct SnapBufs {
     int32_t* off;
 };
 
-constexpr int N_STEP_KERNELS = 4;  // own, mobil, lanescan, place
+constexpr int N_STEP_KERNELS = 3;  // decide, lanescan, place
 
 }  // namespace
 
@@ -70,7 +70,7 @@ struct MossHandle {
     void* d_ea = nullptr;    // RecA<Real>[cap]
     RecB* d_eb = nullptr;
     int32_t *d_enext = nullptr, *d_enter = nullptr, *d_leave = nullptr, *d_lbefore = nullptr,
-            *d_tile_leave = nullptr, *d_tile_prefix = nullptr, *d_mlist = nullptr;
+            *d_tile_leave = nullptr, *d_tile_prefix = nullptr;
     unsigned long long *d_head = nullptr, *d_lane_tiles = nullptr;
     int n_lane_tiles = 0, max_slot_tiles = 0, n_junc_chunks = 0;
     Counters* d_cnt = nullptr;
@@ -262,7 +262,6 @@ Ctx<Real> make_ctx(MossHandle* h, int cur) {
     c.ea = (RecA<Real>*)h->d_ea; c.eb = h->d_eb; c.enext = h->d_enext; c.head = h->d_head;
     c.enter = h->d_enter; c.leave = h->d_leave; c.lbefore = h->d_lbefore;
     c.tile_leave = h->d_tile_leave; c.tile_prefix = h->d_tile_prefix; c.lane_tiles = h->d_lane_tiles;
-    c.mlist = h->d_mlist;
     c.n_lane_tiles = h->n_lane_tiles; c.max_slot_tiles = h->max_slot_tiles;
     c.n_junc_chunks = h->n_junc_chunks; c.cnt = h->d_cnt;
     const MossParams& p = h->prm;
@@ -275,13 +274,12 @@ Ctx<Real> make_ctx(MossHandle* h, int cur) {
 }
 
 struct Grids {
-    int decide_work, decide_ins, mobil, lanescan, place;
+    int decide_work, decide_ins, lanescan, place;
 };
 
 Grids grids(const MossHandle* h) {
     Grids g;
-    g.decide_work = std::max(1, std::min(h->max_slot_tiles, h->sm_count * 8));
-    g.mobil = std::max(1, std::min(h->max_slot_tiles, h->sm_count * MOSS_MOBIL_MIN_BLOCKS));
+    g.decide_work = std::max(1, std::min(h->max_slot_tiles, h->sm_count * MOSS_DECIDE_MIN_BLOCKS));
     const int ns = (int)h->start_lanes.size();
     g.decide_ins = ns > 0 ? std::max(1, std::min((ns + TILE - 1) / TILE, h->sm_count)) : 0;
     const int tickets = h->n_lane_tiles + 1 + h->n_junc_chunks;
@@ -296,14 +294,12 @@ void enqueue_step(MossHandle* h, int cur, bool timed) {
     const Grids g = grids(h);
     cudaStream_t s = h->stream;
     if (timed) cudaEventRecord(h->ev[0], s);
-    k_own<Real><<<g.decide_work + g.decide_ins, TILE, 0, s>>>(c, g.decide_work);
+    k_decide<Real><<<g.decide_work + g.decide_ins, TILE, 0, s>>>(c, g.decide_work);
     if (timed) cudaEventRecord(h->ev[1], s);
-    k_mobil<Real><<<g.mobil, TILE, 0, s>>>(c);
-    if (timed) cudaEventRecord(h->ev[2], s);
     k_lanescan<Real><<<g.lanescan, LANESCAN_THREADS, 0, s>>>(c);
-    if (timed) cudaEventRecord(h->ev[3], s);
+    if (timed) cudaEventRecord(h->ev[2], s);
     k_place<Real><<<g.place, TILE, 0, s>>>(c);
-    if (timed) cudaEventRecord(h->ev[4], s);
+    if (timed) cudaEventRecord(h->ev[3], s);
 }
 
 void enqueue(MossHandle* h, int cur, bool timed) {
@@ -543,7 +539,6 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
     h->n_junc_chunks = (NJ + JUNC_CHUNK - 1) / JUNC_CHUNK;
     TRY(upload(h, &h->d_tile_leave, std::vector<int32_t>(h->max_slot_tiles, 0)));
     TRY(dalloc(h, &h->d_tile_prefix, h->max_slot_tiles));
-    TRY(dalloc(h, &h->d_mlist, cap));
     TRY(upload(h, &h->d_lane_tiles, std::vector<unsigned long long>(h->n_lane_tiles, 0ull)));
     Counters c0{};
     c0.tag = 1;
@@ -731,7 +726,7 @@ int moss_step(moss_t h, int n) {
             for (int q = 0; q < N_STEP_KERNELS; ++q) {
                 float ms = 0;
                 CK(cudaEventElapsedTime(&ms, h->ev[q], h->ev[q + 1]));
-                h->kms[q] += ms;  // own, mobil, lanescan, place
+                h->kms[q] += ms;  // decide, lanescan, place
             }
             h->ksteps++;
         }

@@ -12,15 +12,13 @@
 // search in the adjacent lane's segment (adjacent lanes of a road are
 // adjacent in memory).
 //
-// One step = four kernels:
-//   k_own       per vehicle: sensing, IDM (App. B.3 eqs. (1)-(2)), the MOBIL
-//               attempt draw; vehicles that do not attempt a lane change are
-//               integrated (ballistic update with clamps), transferred at lane
-//               ends or arrive (App. B.2 update stream 1); the others go to
-//               a work list; extra blocks run the departure insertion (App.
-//               B.2 update stream 3);
-//   k_mobil     the work list in dense warps: randomized MOBIL (App. B.3) with
-//               deterministic conflict resolution, then the same update;
+// One step = three kernels:
+//   k_decide    per vehicle: sensing, IDM (App. B.3 eqs. (1)-(2)), randomized
+//               MOBIL (App. B.3) with deterministic conflict resolution (the
+//               MOBIL jobs of a tile packed onto full warps), ballistic
+//               integration with clamps, transfer at lane ends and arrival
+//               (App. B.2 update stream 1); extra blocks run the departure
+//               insertion (App. B.2 update stream 3);
 //   k_lanescan  per-lane sizes of the next snapshot -> offsets (single-pass
 //               decoupled look-back scan), prefix of leavers per slot tile,
 //               signal states of the next step (§3.2 policies);
@@ -70,7 +68,7 @@ struct Counters {
     int done_place;  // k_place blocks finished (the last one closes the step)
     int err;
     int tag;         // step tag of the per-lane entrant lists (never 0)
-    int n_mobil;     // vehicles that evaluate MOBIL this step (k_mobil's work list)
+    int pad;
 };
 
 // snapshot records
@@ -155,7 +153,6 @@ struct Ctx {
     int32_t* lbefore;     // [n_lanes] leavers in lanes before l
     int32_t* tile_leave;  // [slot tiles] leavers per tile of the current snapshot
     int32_t* tile_prefix; // [slot tiles] leavers before the tile
-    int32_t* mlist;       // [n_veh] slots of the vehicles that evaluate MOBIL this step
     unsigned long long* lane_tiles;
     int n_lane_tiles, max_slot_tiles, n_junc_chunks;
     Counters* cnt;
@@ -188,6 +185,14 @@ __device__ __forceinline__ Real unit24(uint32_t w) {
 }
 
 template <typename Real> __device__ __forceinline__ Real rabs(Real x) { return x < Real(0) ? -x : x; }
+
+// speed in units of 2^-24 m/s, rounded to nearest (for the speed metric).  In
+// FP32 the product by 2^24 is exact and fits a 32-bit integer below 128 m/s,
+// so no FP64 instruction is needed (FP64 throughput is low on this part).
+__device__ __forceinline__ long long speed_fixed(float v) {
+    return v < 128.0f ? (long long)__float2int_rn(v * 16777216.0f) : (long long)llrintf(v * 16777216.0f);
+}
+__device__ __forceinline__ long long speed_fixed(double v) { return (long long)llrint(v * 16777216.0); }
 
 // x / y: IEEE division in FP64; the hardware's fast approximate division in
 // FP32 (about 2 ulp, far inside the 1e-5 tolerance and the 1e-4 flag bands).
@@ -261,9 +266,12 @@ __device__ __forceinline__ int light_of(const Ctx<Real>& c, const LaneInfo& ji) 
     return ((mask >> nx) & 1) ? LIGHT_GREEN : LIGHT_AMBER;
 }
 
-// junction lane leaving road lane (record li) towards road out_road (-1 if none)
+// junction lane leaving road lane (record li) towards road out_road (-1 if
+// none); `hint` is tried first (the position of the matching junction lane of
+// a neighbouring lane of the same road, usually the same)
 template <typename Real>
-__device__ __forceinline__ int jl_toward(const Ctx<Real>& c, const LaneInfo& li, int out_road) {
+__device__ __forceinline__ int jl_toward(const Ctx<Real>& c, const LaneInfo& li, int out_road, int hint = -1) {
+    if (hint >= 0 && li.jb + hint < li.je && c.lane[li.jb + hint].road == out_road) return li.jb + hint;
     for (int j = li.jb; j < li.je; ++j)
         if (c.lane[j].road == out_road) return j;
     return -1;
@@ -434,7 +442,7 @@ __device__ __forceinline__ Decision<Real> decide(const Ctx<Real>& c, int i, long
             if (!(g > Real(0))) ok = 0;
             if (rabs(g) < c.band * pos_scale) D.flag = 1;
         }
-        const int nlt = (next_road >= 0) ? jl_toward(c, ti, next_road) : -1;
+        const int nlt = (next_road >= 0) ? jl_toward(c, ti, next_road, EB.nl - li.jb) : -1;
         NLs[side] = nlt;
         const Real at_ego = accel_on_lane(c, ti, E.s, E.v, v0f * Real(ti.vmax), TL, nlt, EB.rptr, EB.rlast).a;
         Real a_new = Real(0), at_new = Real(0);
