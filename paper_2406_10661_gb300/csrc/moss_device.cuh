@@ -14,11 +14,10 @@
 //
 // One step = three kernels:
 //   k_decide    per vehicle: sensing, IDM (App. B.3 eqs. (1)-(2)), randomized
-//               MOBIL (App. B.3) with deterministic conflict resolution (the
-//               MOBIL jobs of a tile packed onto full warps), ballistic
-//               integration with clamps, transfer at lane ends and arrival
-//               (App. B.2 update stream 1); extra blocks run the departure
-//               insertion (App. B.2 update stream 3);
+//               MOBIL (App. B.3) with deterministic conflict resolution,
+//               ballistic integration with clamps, transfer at lane ends and
+//               arrival (App. B.2 update stream 1); extra blocks run the
+//               departure insertion (App. B.2 update stream 3);
 //   k_lanescan  per-lane sizes of the next snapshot -> offsets (single-pass
 //               decoupled look-back scan), prefix of leavers per slot tile,
 //               signal states of the next step (§3.2 policies);
@@ -374,6 +373,7 @@ struct Decision {
     Real u, scale;
     int cand, dir, tl, TL, TF, flag;  // TL/TF: slots in the target lane or -1
     int nlt;                          // next lane on the route from the target lane
+    int att;                          // MOBIL was evaluated (the attempt draw passed)
 };
 
 // The full per-vehicle decision before conflict resolution (App. B.3).  A pure
@@ -383,7 +383,7 @@ template <typename Real>
 __device__ __forceinline__ Decision<Real> decide(const Ctx<Real>& c, int i, long long t, uint32_t k0,
                                                  uint32_t k1, int vbase) {
     Decision<Real> D;
-    D.cand = 0; D.dir = 0; D.tl = -1; D.TL = -1; D.TF = -1; D.flag = 0; D.nlt = -1;
+    D.cand = 0; D.dir = 0; D.tl = -1; D.TL = -1; D.TF = -1; D.flag = 0; D.nlt = -1; D.att = 0;
     D.u = Real(0); D.scale = Real(1);
     const RecA<Real> E = c.cur.a[i];
     const RecB EB = c.cur.b[i];
@@ -398,6 +398,7 @@ __device__ __forceinline__ Decision<Real> decide(const Ctx<Real>& c, int i, long
     philox4x32_10(k0, k1, uint32_t(E.id - vbase), uint32_t(t), 0u, 0u, w);
     const Real u_att = unit24<Real>(w[0]);
     if (!(u_att < c.p_att)) return D;
+    D.att = 1;
     const Real u_lc = unit24<Real>(w[1]), u_dir = unit24<Real>(w[2]);
 
     const int OF = (i + 1 < e) ? i + 1 : -1;

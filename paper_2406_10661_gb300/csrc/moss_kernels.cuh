@@ -159,22 +159,12 @@ __device__ __forceinline__ int integrate_emit(const Ctx<Real>& c, MetricAcc& acc
 }
 
 // ---------------------------------------------------------------------------
-// k_decide: blocks [0, n_work) take 256-slot tiles of the current snapshot.
-// Per tile: every thread loads its vehicle and draws the MOBIL attempt (R4);
-// the attempting vehicles' MOBIL jobs are packed onto the first threads of
-// the block (full warps instead of a divergent share of every warp) and
-// their outcome goes through shared memory; then every thread updates its
-// own vehicle.  Blocks [n_work, gridDim) run the departure insertion.
+// k_decide: blocks [0, n_work) take 256-slot tiles of the current snapshot
+// (one vehicle per thread); blocks [n_work, gridDim) run the insertion.
 // MOSS_DECIDE_MIN_BLOCKS: resident blocks per SM the register budget targets.
 #ifndef MOSS_DECIDE_MIN_BLOCKS
 #define MOSS_DECIDE_MIN_BLOCKS 4
 #endif
-template <typename Real>
-struct JobOut {
-    LaneAcc<Real> la;  // kinematics on the lane the vehicle drives on
-    int nlane, fl, overlap;
-};
-
 template <typename Real>
 __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Real> c, int n_work) {
     if (c.cnt->err & ERR_POISON) return;
@@ -185,147 +175,88 @@ __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Rea
             insert_departure(c, c.start_lanes[k], tag);
         return;
     }
-    __shared__ int s_job[TILE];
-    __shared__ int s_wcount[TILE / 32];
-    __shared__ JobOut<Real> s_out[TILE];
     const int n = c.cnt->n_cur;
     const int n_tiles = (n + TILE - 1) / TILE;
-    const int lane_id = threadIdx.x & 31, warp = threadIdx.x >> 5;
     MetricAcc acc;
     macc_reset(acc, -1);
     for (int tile = blockIdx.x; tile < n_tiles; tile += n_work) {
         const int i = tile * TILE + threadIdx.x;
-        bool valid = i < n, attempt = false;
-        RecA<Real> E;
-        RecB EB;
-        LaneInfo li;
-        int sc = 0;
-        long long t = 0;
-        if (valid) {
-            E = c.cur.a[i];
-            EB = c.cur.b[i];
-            if ((unsigned)E.lane >= (unsigned)c.n_lanes || EB.nl < -1 || EB.nl >= c.n_lanes) {
+        int leaver = 0;
+        if (i < n) {
+            const RecA<Real> E = c.cur.a[i];
+            const int lane = E.lane;
+            if ((unsigned)lane >= (unsigned)c.n_lanes) {
                 atomicOr(&c.cnt->err, ERR_RANGE);
-                valid = false;
             } else {
-                li = c.lane[E.lane];
-                sc = li.scen;
-                t = c.scen_step[sc];
-                if (li.lo >= 0 && li.hi - li.lo >= 2) {  // eligible for MOBIL (R7)
-                    uint32_t w[4];
-                    philox4x32_10(c.key0[sc], c.key1[sc], uint32_t(E.id - c.veh_base[sc]), uint32_t(t), 0u,
-                                  0u, w);
-                    attempt = unit24<Real>(w[0]) < c.p_att;
+                const int sc = c.lane[lane].scen;
+                if (sc != acc.scen) {
+                    macc_flush_thread(acc, c.metrics);
+                    macc_reset(acc, sc);
                 }
-            }
-        }
-        // pack the MOBIL jobs of the tile
-        const unsigned am = __ballot_sync(0xffffffffu, attempt);
-        if (lane_id == 0) s_wcount[warp] = __popc(am);
-        __syncthreads();
-        int wbase = 0, m = 0;
-#pragma unroll
-        for (int w2 = 0; w2 < TILE / 32; ++w2) {
-            const int x = s_wcount[w2];
-            if (w2 < warp) wbase += x;
-            m += x;
-        }
-        if (attempt) s_job[wbase + __popc(am & ((1u << lane_id) - 1))] = threadIdx.x;
-        __syncthreads();
-        if ((int)threadIdx.x < m) {
-            const int j = s_job[threadIdx.x];
-            const int slot = tile * TILE + j;
-            const RecA<Real> JE = c.cur.a[slot];
-            const int jlane = JE.lane;
-            const LaneInfo jli = c.lane[jlane];
-            const int jsc = jli.scen;
-            if (jsc != acc.scen) {
-                macc_flush_thread(acc, c.metrics);
-                macc_reset(acc, jsc);
-            }
-            acc.m[8] += 1;
-            const long long jt = c.scen_step[jsc];
-            const uint32_t k0 = c.key0[jsc], k1 = c.key1[jsc];
-            const int vbase = c.veh_base[jsc];
-            // job 0 is this vehicle; jobs 1.. are the rivals of a lane-change
-            // candidate (R9): vehicles of the lane beyond the target lane that
-            // fall into the same target-lane gap.  One call site of decide()
-            // makes every recomputation bit-identical to the rival's own.
-            Decision<Real> D;
-            int fl = 0;
-            bool granted = false;
-            int r = 0, rend = 0;
-            for (int job = 0;; ++job) {
-                const int sl = job == 0 ? slot : r;
-                const Decision<Real> X = decide(c, sl, jt, k0, k1, vbase);
-                if (job == 0) {
-                    D = X;
-                    fl = D.flag ? F_FLAGGED : 0;
-                    if (!D.cand) break;
-                    fl |= F_CANDIDATE;
-                    granted = true;
-                    const int ol = D.tl + D.dir;
-                    if (ol < jli.lo || ol >= jli.hi) break;
-                    const int ob = c.cur.off[ol], oe = c.cur.off[ol + 1];
-                    r = ob; rend = oe;
-                    if (D.TL >= 0) {
-                        const RecA<Real> T = c.cur.a[D.TL];
-                        r = partition_point(c, ob, oe, T.s, T.id);
+                const long long t = c.scen_step[sc];
+                const uint32_t k0 = c.key0[sc], k1 = c.key1[sc];
+                const int vbase = c.veh_base[sc];
+                // job 0 is this vehicle; jobs 1.. are the rivals of a lane-change
+                // candidate (R9): vehicles of the lane beyond the target lane that
+                // fall into the same target-lane gap.  One call site of decide()
+                // makes every recomputation bit-identical to the rival's own.
+                Decision<Real> D;
+                int fl = 0;
+                bool granted = false;
+                int r = 0, rend = 0;
+                for (int job = 0;; ++job) {
+                    const int slot = job == 0 ? i : r;
+                    const Decision<Real> X = decide(c, slot, t, k0, k1, vbase);
+                    if (job == 0) {
+                        D = X;
+                        fl = D.flag ? F_FLAGGED : 0;
+                        if (!D.cand) break;
+                        fl |= F_CANDIDATE;
+                        granted = true;
+                        const LaneInfo li = c.lane[lane];
+                        const int ol = D.tl + D.dir;
+                        if (ol < li.lo || ol >= li.hi) break;
+                        const int ob = c.cur.off[ol], oe = c.cur.off[ol + 1];
+                        r = ob; rend = oe;
+                        if (D.TL >= 0) {
+                            const RecA<Real> T = c.cur.a[D.TL];
+                            r = partition_point(c, ob, oe, T.s, T.id);
+                        }
+                        if (D.TF >= 0) {
+                            const RecA<Real> T = c.cur.a[D.TF];
+                            rend = partition_point(c, ob, oe, T.s, T.id);
+                        }
+                        if (r >= rend) break;
+                    } else {
+                        if (X.cand && X.tl == D.tl) {
+                            const Real sc2 = D.scale > X.scale ? D.scale : X.scale;
+                            if (rabs(D.u - X.u) < c.band * sc2) fl |= F_FLAGGED;
+                            const int rid = c.cur.a[r].id;
+                            if (!(D.u > X.u || (D.u == X.u && E.id < rid))) granted = false;
+                        }
+                        if (++r >= rend) break;
                     }
-                    if (D.TF >= 0) {
-                        const RecA<Real> T = c.cur.a[D.TF];
-                        rend = partition_point(c, ob, oe, T.s, T.id);
-                    }
-                    if (r >= rend) break;
-                } else {
-                    if (X.cand && X.tl == D.tl) {
-                        const Real sc2 = D.scale > X.scale ? D.scale : X.scale;
-                        if (rabs(D.u - X.u) < c.band * sc2) fl |= F_FLAGGED;
-                        const int rid = c.cur.a[r].id;
-                        if (!(D.u > X.u || (D.u == X.u && JE.id < rid))) granted = false;
-                    }
-                    if (++r >= rend) break;
                 }
-            }
-            if (D.cand && !granted) fl |= F_CONFLICT_LOST;
-            JobOut<Real> o;
-            o.la = D.own;
-            o.nlane = jlane;
-            o.overlap = D.own.overlap;
-            if (granted) {
+                if (D.att) acc.m[8] += 1;
+                if (D.cand && !granted) fl |= F_CONFLICT_LOST;
                 // a granted change drives on the target lane (its kinematics
                 // recomputed from the same inputs)
-                fl |= F_CHANGED;
-                o.nlane = D.tl;
-                const LaneInfo ti = c.lane[D.tl];
-                const RecB JB = c.cur.b[slot];
-                o.la = accel_on_lane(c, ti, JE.s, JE.v, Real(JB.v0f) * Real(ti.vmax), D.TL, D.nlt, JB.rptr,
-                                     JB.rlast);
-            }
-            o.fl = fl;
-            s_out[j] = o;
-        }
-        __syncthreads();
-        int leaver = 0;
-        if (valid) {
-            if (sc != acc.scen) {
-                macc_flush_thread(acc, c.metrics);
-                macc_reset(acc, sc);
-            }
-            if (attempt) {
-                const JobOut<Real> o = s_out[threadIdx.x];
-                leaver = integrate_emit(c, acc, i, E, EB, o.la, o.nlane, o.fl, o.overlap != 0, t, sc, tag);
-            } else {
-                const int b = c.cur.off[E.lane];
-                const int OL = (i > b) ? i - 1 : -1;
-                const LaneAcc<Real> own = accel_on_lane(c, li, E.s, E.v, Real(EB.v0f) * Real(li.vmax), OL,
-                                                        EB.nl, EB.rptr, EB.rlast);
-                leaver = integrate_emit(c, acc, i, E, EB, own, E.lane, 0, own.overlap != 0, t, sc, tag);
+                const RecB EB = c.cur.b[i];
+                LaneAcc<Real> la = D.own;
+                int nlane = lane;
+                if (granted) {
+                    fl |= F_CHANGED;
+                    nlane = D.tl;
+                    const LaneInfo ti = c.lane[nlane];
+                    la = accel_on_lane(c, ti, E.s, E.v, Real(EB.v0f) * Real(ti.vmax), D.TL, D.nlt, EB.rptr,
+                                       EB.rlast);
+                }
+                leaver = integrate_emit(c, acc, i, E, EB, la, nlane, fl, D.own.overlap != 0, t, sc, tag);
             }
         }
         // leavers of this tile (k_lanescan zeroes the counters after reading them)
         const unsigned lb = __ballot_sync(0xffffffffu, leaver);
-        if (lane_id == 0 && lb) atomicAdd(&c.tile_leave[tile], __popc(lb));
+        if ((threadIdx.x & 31) == 0 && lb) atomicAdd(&c.tile_leave[tile], __popc(lb));
     }
     macc_flush_block<TILE>(acc, c.metrics);
 }
