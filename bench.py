@@ -315,6 +315,96 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batched(args):
+    """64 uneven scenarios advanced together (one set of launches per step,
+    replayed from a CUDA graph, autotuned schedule) against stepping the same
+    scenarios one at a time; both from the step-900 state the simulation
+    reaches, K timed steps each."""
+    import torch
+    from paper_2406_10661_gb300 import binding, scenario as sc
+    binding.load()
+    t0 = time.perf_counter()
+    scens = sc.batched_scenarios(args.scenarios, seed=args.seed)
+    gen_s = time.perf_counter() - t0
+    pre = 900
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        batch = binding.Batch(scens, precision=32, stream=stream.cuda_stream)
+        batch.step(pre)
+        tuned = batch.autotune(1)
+        batch.step(args.warmup)
+        batch.synchronize()
+        u0 = sum(batch.metrics(i)["vehicle_updates"] for i in range(len(scens)))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        b_ms = e0.elapsed_time(e1)
+        u1 = sum(batch.metrics(i)["vehicle_updates"] for i in range(len(scens)))
+        batch.close()
+        seq_ms, seq_upd = 0.0, 0
+        for s_ in scens:
+            sim = binding.Simulation(s_.net, s_.veh, s_.params, precision=32, stream=stream.cuda_stream)
+            sim.step(pre + 9 + args.warmup)  # the batch's autotune advanced it by 9 steps
+            sim.synchronize()
+            m0 = sim.metrics()["vehicle_updates"]
+            e0.record(stream)
+            sim.step(args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            seq_ms += e0.elapsed_time(e1)
+            seq_upd += sim.metrics()["vehicle_updates"] - m0
+            sim.close()
+    b_val = (u1 - u0) / (b_ms / 1e3)
+    s_val = seq_upd / (seq_ms / 1e3)
+    line = {"metric": "vehicle-updates/s (batched)", "value": b_val, "unit": "vehicle-updates/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": b_ms / args.steps,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batched{len(scens)}", "scenarios": len(scens),
+                       "vehicles": int(sum(x.veh.n for x in scens)),
+                       "vehicles_min_max": [int(min(x.veh.n for x in scens)), int(max(x.veh.n for x in scens))],
+                       "start": f"each scenario's own step-{pre} state", "schedule": tuned,
+                       "generation_s": gen_s},
+            "sequential": {"value": s_val, "ms_per_step": seq_ms / args.steps,
+                           "how": "the same scenarios, one handle each, stepped one scenario at a time"},
+            "batched_over_sequential": b_val / s_val,
+            "same_updates": int(u1 - u0) == int(seq_upd)}
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args):
+    """Poisson stream of rollout requests served with continuous admission by
+    device-memory budget; p50/p99 step latency and aggregate vehicle-updates/s,
+    against serving the same requests one at a time."""
+    import torch
+    from paper_2406_10661_gb300 import binding, serving
+    binding.load()
+    t0 = time.perf_counter()
+    reqs = serving.poisson_requests(args.requests, rate_hz=20.0, seed=args.seed)
+    gen_s = time.perf_counter() - t0
+    free, total = torch.cuda.mem_get_info()
+    budget = int(min(args.budget_gb * 2 ** 30, 0.8 * free))
+    stats = serving.Server(budget, max_slots=args.slots).run(reqs, realtime=True)
+    seq_reqs = serving.poisson_requests(args.requests, rate_hz=20.0, seed=args.seed)
+    seq = serving.Server(budget, max_slots=1).run(seq_reqs, realtime=False)
+    same = all(a.metrics == b.metrics for a, b in zip(reqs, seq_reqs))
+    line = {"metric": "vehicle-updates/s (served)", "value": stats["vehicle_updates_per_s"],
+            "unit": "vehicle-updates/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"serving{args.requests}", "arrivals": "Poisson 20/s",
+                       "vehicles": "log-uniform 5k-500k", "horizon": "uniform 300-3600 steps",
+                       "actions": "signal phases of every junction every 10 steps",
+                       "budget_bytes": budget, "max_slots": args.slots, "generation_s": gen_s},
+            "p50_step_ms": stats["p50_step_ms"], "p99_step_ms": stats["p99_step_ms"],
+            "wall_s": stats["wall_s"], "peak_slots": stats["peak_slots"], "peak_bytes": stats["peak_bytes"],
+            "sequential": {"value": seq["vehicle_updates_per_s"], "p50_step_ms": seq["p50_step_ms"],
+                           "p99_step_ms": seq["p99_step_ms"], "wall_s": seq["wall_s"]},
+            "served_over_sequential": stats["vehicle_updates_per_s"] / max(seq["vehicle_updates_per_s"], 1e-9),
+            "results_equal_alone_and_mixed": same}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -324,11 +414,20 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-roads", type=int, default=1000)
+    ap.add_argument("--workload", default="city", choices=["city", "batched", "serving"])
+    ap.add_argument("--scenarios", type=int, default=64)
+    ap.add_argument("--requests", type=int, default=100)
+    ap.add_argument("--slots", type=int, default=64)
+    ap.add_argument("--budget-gb", type=float, default=64.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

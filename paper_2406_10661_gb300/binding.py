@@ -92,6 +92,7 @@ SIGNATURES = {
     "moss_set_kernel_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "moss_kernel_times": (ctypes.c_int, [_vp, _c_f64p, ctypes.POINTER(ctypes.c_int64)]),
     "moss_lane_offsets_noalloc": (ctypes.c_int, [ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "moss_autotune": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p]),
 }
 
 NOALLOC_MAX_LANES = 1 << 22
@@ -200,6 +201,12 @@ class _Handle:
 
     def set_kernel_timing(self, on: bool) -> None:
         _check(self.lib.moss_set_kernel_timing(self.h, int(bool(on))), self.h)
+
+    def autotune(self, trial_steps: int = 3):
+        """Pick the fastest launch schedule on the next 9 * trial_steps steps."""
+        out = np.zeros(3, dtype=np.int32)
+        _check(self.lib.moss_autotune(self.h, int(trial_steps), _ptr(out, ctypes.c_int32)), self.h)
+        return dict(zip(("decide", "lanescan", "place"), out.tolist()))
 
     def kernel_times(self):
         ms = np.zeros(4, dtype=np.float64)

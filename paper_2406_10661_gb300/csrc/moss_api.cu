@@ -78,6 +78,9 @@ struct MossHandle {
     int32_t* h_stage = nullptr;          // pinned host staging of setter arguments (2 * n_junctions)
     cudaEvent_t stage_free = nullptr;    // recorded after the last copy out of h_stage
 
+    // launch configuration (blocks per SM) of the step kernels; moss_autotune picks them
+    int cfg_decide = MOSS_DECIDE_MIN_BLOCKS, cfg_lanescan = 4, cfg_place = 8;
+
     int parity = 0;  // snapshot buffer holding the current step
     cudaGraphExec_t g2[2] = {nullptr, nullptr}, g1[2] = {nullptr, nullptr};
     bool timing = false;
@@ -279,12 +282,12 @@ struct Grids {
 
 Grids grids(const MossHandle* h) {
     Grids g;
-    g.decide_work = std::max(1, std::min(h->max_slot_tiles, h->sm_count * MOSS_DECIDE_MIN_BLOCKS));
+    g.decide_work = std::max(1, std::min(h->max_slot_tiles, h->sm_count * h->cfg_decide));
     const int ns = (int)h->start_lanes.size();
     g.decide_ins = ns > 0 ? std::max(1, std::min((ns + TILE - 1) / TILE, h->sm_count)) : 0;
     const int tickets = h->n_lane_tiles + 1 + h->n_junc_chunks;
-    g.lanescan = std::max(1, std::min(tickets, h->sm_count * 4));
-    g.place = std::max(1, std::min(2 * h->max_slot_tiles, h->sm_count * 8));
+    g.lanescan = std::max(1, std::min(tickets, h->sm_count * h->cfg_lanescan));
+    g.place = std::max(1, std::min(2 * h->max_slot_tiles, h->sm_count * h->cfg_place));
     return g;
 }
 
@@ -926,6 +929,51 @@ int moss_set_kernel_timing(moss_t h, int enable) {
     for (double& x : h->kms) x = 0;
     h->ksteps = 0;
     return MOSS_OK;
+}
+
+// time `steps` steps (the simulation advances normally) with the current
+// launch configuration; returns the summed kernel milliseconds
+static int time_steps(MossHandle* h, int steps, double* ms) {
+    double tot = 0;
+    for (int k = 0; k < steps; ++k) {
+        enqueue(h, h->parity, true);
+        h->parity ^= 1;
+        CK(cudaEventSynchronize(h->ev[N_STEP_KERNELS]));
+        float x = 0;
+        CK(cudaEventElapsedTime(&x, h->ev[0], h->ev[N_STEP_KERNELS]));
+        tot += x;
+    }
+    CK(cudaGetLastError());
+    *ms = tot;
+    return MOSS_OK;
+}
+
+int moss_autotune(moss_t h, int trial_steps, int* chosen3) {
+    if (!h) return MOSS_EINVAL;
+    if (trial_steps < 1) return fail(h, MOSS_EINVAL, "trial_steps must be >= 1");
+    CK(cudaStreamSynchronize(h->stream));
+    // coordinate search over blocks per SM of each kernel; results do not
+    // depend on the launch configuration, only the time does
+    static const int cand_decide[] = {2, 3, 4};
+    static const int cand_lanescan[] = {1, 2, 4};
+    static const int cand_place[] = {4, 8, 16};
+    const int* cands[3] = {cand_decide, cand_lanescan, cand_place};
+    int* knobs[3] = {&h->cfg_decide, &h->cfg_lanescan, &h->cfg_place};
+    for (int d = 0; d < 3; ++d) {
+        int best = *knobs[d];
+        double best_ms = 1e300;
+        for (int k = 0; k < 3; ++k) {
+            *knobs[d] = cands[d][k];
+            double ms = 0;
+            TRY(time_steps(h, trial_steps, &ms));
+            if (ms < best_ms) { best_ms = ms; best = cands[d][k]; }
+        }
+        *knobs[d] = best;
+    }
+    destroy_graphs(h);
+    TRY(build_graphs(h));
+    if (chosen3) { chosen3[0] = h->cfg_decide; chosen3[1] = h->cfg_lanescan; chosen3[2] = h->cfg_place; }
+    return check_device(h);
 }
 
 int moss_kernel_times(moss_t h, double* ms4, int64_t* steps) {
