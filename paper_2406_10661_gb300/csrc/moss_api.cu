@@ -284,7 +284,7 @@ Grids grids(const MossHandle* h) {
     Grids g;
     g.decide_work = std::max(1, std::min(h->max_slot_tiles, h->sm_count * h->cfg_decide));
     const int ns = (int)h->start_lanes.size();
-    g.decide_ins = ns > 0 ? std::max(1, std::min((ns + TILE - 1) / TILE, h->sm_count)) : 0;
+    g.decide_ins = ns > 0 ? (ns + TILE - 1) / TILE : 0;  // one start lane per thread
     const int tickets = h->n_lane_tiles + 1 + h->n_junc_chunks;
     g.lanescan = std::max(1, std::min(tickets, h->sm_count * h->cfg_lanescan));
     g.place = std::max(1, std::min(2 * h->max_slot_tiles, h->sm_count * h->cfg_place));

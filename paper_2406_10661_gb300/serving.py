@@ -39,7 +39,7 @@ def estimate_device_bytes(scen: Scenario, precision: int = 32) -> int:
     per_lane = 32 + 2 * 4 + 8 + 3 * 4 + 2 * 4
     lanes = int(scen.net.n_lanes)
     return (n * per_vehicle + int(scen.veh.routes.size) * 4 + lanes * per_lane +
-            int(scen.net.n_junctions) * 48 + (1 << 20))
+            int(scen.net.n_junctions) * 48 + 64 * 1024)
 
 
 @dataclasses.dataclass
@@ -65,11 +65,12 @@ def actions_for(req: Request, step: int, n_junctions: int) -> np.ndarray:
 
 
 class _Active:
-    def __init__(self, req: Request, sim: binding.Simulation, stream, bytes_: int):
+    def __init__(self, req: Request, sim: binding.Simulation, stream, bytes_: int, actual: int):
         self.req = req
         self.sim = sim
         self.stream = stream
-        self.bytes = bytes_
+        self.bytes = bytes_      # admission accounting (the estimate, or more if larger)
+        self.actual = actual     # bytes the handle holds
         self.step = 0
         self.pending: List = []  # (start event, end event)
 
@@ -101,12 +102,14 @@ class Server:
         sc = req.scenario
         sim = binding.Simulation(sc.net, sc.veh, sc.params, precision=self.precision,
                                  stream=stream.cuda_stream)
-        b = sim.device_bytes()
-        self.active.append(_Active(req, sim, stream, b))
+        actual = sim.device_bytes()
+        b = max(actual, estimate_device_bytes(sc, self.precision))
+        self.active.append(_Active(req, sim, stream, b, actual))
         self.bytes_in_use += b
+        self.actual_in_use = getattr(self, "actual_in_use", 0) + actual
         req.admitted_at = now
         self.peak_slots = max(self.peak_slots, len(self.active))
-        self.peak_bytes = max(self.peak_bytes, self.bytes_in_use)
+        self.peak_bytes = max(self.peak_bytes, self.actual_in_use)
 
     def _launch_step(self, a: _Active) -> None:
         import torch
@@ -143,6 +146,7 @@ class Server:
         self.updates += int(m["vehicle_updates"])
         a.sim.close()
         self.bytes_in_use -= a.bytes
+        self.actual_in_use -= a.actual
         self.active.remove(a)
 
     def run(self, requests: List[Request], realtime: bool = True) -> Dict[str, float]:
