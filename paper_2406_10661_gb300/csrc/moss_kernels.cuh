@@ -177,9 +177,13 @@ __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Rea
     }
     const int n = c.cnt->n_cur;
     const int n_tiles = (n + TILE - 1) / TILE;
+    // each block takes a contiguous run of tiles: a thread's scenario (and so
+    // its metric partials) changes rarely, and neighbouring lanes stay close
+    const int per = (n_tiles + n_work - 1) / n_work;
+    const int t_beg = blockIdx.x * per, t_end = min(n_tiles, t_beg + per);
     MetricAcc acc;
     macc_reset(acc, -1);
-    for (int tile = blockIdx.x; tile < n_tiles; tile += n_work) {
+    for (int tile = t_beg; tile < t_end; ++tile) {
         const int i = tile * TILE + threadIdx.x;
         int leaver = 0;
         if (i < n) {
