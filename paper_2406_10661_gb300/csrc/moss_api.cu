@@ -539,9 +539,12 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
     TRY(dalloc(h, &h->d_lbefore, NL));
     h->n_lane_tiles = (NL + LANESCAN_TILE - 1) / LANESCAN_TILE;
     h->max_slot_tiles = (NV + TILE - 1) / TILE + 1;
+    // tile counter arrays padded for the 16-byte loads of the tile-prefix scan
+    const int tile_cap = ((h->max_slot_tiles + 4 * LANESCAN_THREADS - 1) / (4 * LANESCAN_THREADS)) *
+                         (4 * LANESCAN_THREADS);
     h->n_junc_chunks = (NJ + JUNC_CHUNK - 1) / JUNC_CHUNK;
-    TRY(upload(h, &h->d_tile_leave, std::vector<int32_t>(h->max_slot_tiles, 0)));
-    TRY(dalloc(h, &h->d_tile_prefix, h->max_slot_tiles));
+    TRY(upload(h, &h->d_tile_leave, std::vector<int32_t>(tile_cap, 0)));
+    TRY(upload(h, &h->d_tile_prefix, std::vector<int32_t>(tile_cap, 0)));
     TRY(upload(h, &h->d_lane_tiles, std::vector<unsigned long long>(h->n_lane_tiles, 0ull)));
     Counters c0{};
     c0.tag = 1;

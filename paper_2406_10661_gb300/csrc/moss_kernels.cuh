@@ -385,18 +385,28 @@ __global__ void __launch_bounds__(LANESCAN_THREADS) k_lanescan(Ctx<Real> c) {
             // thread sums a contiguous run of tiles (loads issued together),
             // one block scan, then the runs are written out; the counters are
             // zeroed for the next step
+            // (16-byte loads; the arrays are padded to a multiple of 4 * 256
+            // entries and hold zeros beyond the tiles in use)
             const int nt = (c.cnt->n_cur + TILE - 1) / TILE;
-            const int per = (nt + LANESCAN_THREADS - 1) / LANESCAN_THREADS;
-            const int k0 = threadIdx.x * per, k1 = min(nt, k0 + per);
+            const int per4 = (nt + 4 * LANESCAN_THREADS - 1) / (4 * LANESCAN_THREADS);
+            const int k0 = threadIdx.x * per4 * 4;
             long long run = 0;
-            for (int k = k0; k < k1; ++k) run += c.tile_leave[k];
+#pragma unroll 4
+            for (int q = 0; q < per4; ++q) {
+                const int4 x = *reinterpret_cast<const int4*>(c.tile_leave + k0 + 4 * q);
+                run += x.x + x.y + x.z + x.w;
+            }
             long long tot;
             long long acc = block_exclusive_scan(run, &tot);
-            for (int k = k0; k < k1; ++k) {
-                const int x = c.tile_leave[k];
-                c.tile_prefix[k] = (int)acc;
-                c.tile_leave[k] = 0;
-                acc += x;
+            for (int q = 0; q < per4; ++q) {
+                const int4 x = *reinterpret_cast<const int4*>(c.tile_leave + k0 + 4 * q);
+                int4 p;
+                p.x = (int)acc; acc += x.x;
+                p.y = (int)acc; acc += x.y;
+                p.z = (int)acc; acc += x.z;
+                p.w = (int)acc; acc += x.w;
+                *reinterpret_cast<int4*>(c.tile_prefix + k0 + 4 * q) = p;
+                *reinterpret_cast<int4*>(c.tile_leave + k0 + 4 * q) = make_int4(0, 0, 0, 0);
             }
         } else {
             // signal states of the next step
