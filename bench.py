@@ -135,6 +135,17 @@ def cpu_oracle_rate(scen, state, budget_s=15.0, max_road=4000, steps_cap=60):
                       f"single thread, {dt:.1f} s"}
 
 
+def reduce_ranks(dist, dev_s: float, updates: float, device=None):
+    """Replicas: the job's time is the slowest rank's, its work the sum of all
+    ranks' vehicle updates.  Returns (max seconds, summed updates)."""
+    import torch
+    t = torch.tensor([dev_s], dtype=torch.float64, device=device)
+    u = torch.tensor([updates], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -217,10 +228,7 @@ def run_ours(args):
         upd = m1["vehicle_updates"] - m0["vehicle_updates"]
         dev_s = sum(step_ms) / 1e3
         if dist:
-            t = torch.tensor([dev_s, float(upd)], dtype=torch.float64, device="cuda")
-            tmax = t.clone(); dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-            tsum = t.clone(); dist.all_reduce(tsum[1:], op=dist.ReduceOp.SUM)
-            dev_s_all, upd_all = float(tmax[0]), float(tsum[1])
+            dev_s_all, upd_all = reduce_ranks(dist, dev_s, float(upd), device="cuda")
         else:
             dev_s_all, upd_all = dev_s, float(upd)
         value = upd_all / dev_s_all
@@ -269,10 +277,8 @@ def run_ours(args):
         e2e_upd = mk["vehicle_updates"] - me0["vehicle_updates"]
         e2e_val = e2e_upd / e2e_s
         if dist:
-            t = torch.tensor([e2e_s, float(e2e_upd)], dtype=torch.float64, device="cuda")
-            a = t.clone(); dist.all_reduce(a[:1], op=dist.ReduceOp.MAX)
-            b = t.clone(); dist.all_reduce(b[1:], op=dist.ReduceOp.SUM)
-            e2e_val = float(b[1]) / float(a[0])
+            e2e_s_all, e2e_upd_all = reduce_ranks(dist, e2e_s, float(e2e_upd), device="cuda")
+            e2e_val = e2e_upd_all / e2e_s_all
 
     if rank != 0:
         if dist:
@@ -304,7 +310,7 @@ def run_ours(args):
         "step_roofline": {"achieved": step_ach, "frac": step_ach / peak, "bytes_per_update": STEP_BYTES},
         "clocks": clk.summary(),
         "e2e": {"value": e2e_val, "unit": "vehicle-updates/s", "h2d_bytes_per_step": 8 * J,
-                "d2h_bytes_per_step": 8 * 12 + 4, "steps": e2e_steps,
+                "d2h_bytes_per_step": 12 * 8 + 8 + 4,  # metric fields, step, error word "steps": e2e_steps,
                 "api": "moss_set_signal_phase + moss_step(1) + moss_get_metrics per step"},
         "gpu_launches": 3 * args.steps,
         "wall_s_timed_region": wall,

@@ -244,6 +244,19 @@ int moss_kernel_times(moss_t h, double* ms4, int64_t* steps);
 int moss_autotune(moss_t h, int trial_steps, int* chosen3);
 
 /*
+ * Failure-detection self-test (no counterpart in the paper).  Launches one
+ * warp that runs the step's look-back wait (the decoupled scan of the lane
+ * offsets) against a tile word that nothing ever publishes, so the bounded
+ * wait must give up after its iteration limit (about a second) instead of
+ * hanging.  Uses a 64-byte device buffer it allocates and frees itself, on
+ * cuda_stream (NULL = legacy default stream), and waits for the stream.
+ * Returns MOSS_ETIMEOUT when the wait gave up and the kernel reported it
+ * (the expected result; the CUDA context stays usable), MOSS_EDEVICE if the
+ * wait returned without reporting, MOSS_ECUDA if a CUDA call failed.
+ */
+int moss_selftest_bounded_wait(void* cuda_stream);
+
+/*
  * Lane offsets without allocating (no counterpart in the paper: an addition
  * for callers that cannot call cudaMalloc, such as code running inside a
  * framework whose caching allocator owns the device memory, or a process

@@ -93,6 +93,7 @@ SIGNATURES = {
     "moss_kernel_times": (ctypes.c_int, [_vp, _c_f64p, ctypes.POINTER(ctypes.c_int64)]),
     "moss_lane_offsets_noalloc": (ctypes.c_int, [ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "moss_autotune": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p]),
+    "moss_selftest_bounded_wait": (ctypes.c_int, [_vp]),
 }
 
 NOALLOC_MAX_LANES = 1 << 22
@@ -106,6 +107,14 @@ def moss_lane_offsets_noalloc(n_lanes: int, d_off_cur: int, d_leave: int, d_ente
     return load().moss_lane_offsets_noalloc(int(n_lanes), _vp(d_off_cur), _vp(d_leave),
                                             _vp(d_enter), _vp(d_off_next), _vp(d_lbefore),
                                             _vp(stream) if stream else None)
+
+
+def moss_selftest_bounded_wait(stream: int = 0) -> int:
+    """Run the bounded-wait self-test (a look-back wait on a word nothing
+    publishes); returns the C status, MOSS_ETIMEOUT when the wait gave up and
+    reported it as designed."""
+    return load().moss_selftest_bounded_wait(_vp(stream) if stream else None)
+
 
 _LIB = None
 

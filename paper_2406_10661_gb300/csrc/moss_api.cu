@@ -979,6 +979,25 @@ int moss_autotune(moss_t h, int trial_steps, int* chosen3) {
     return check_device(h);
 }
 
+int moss_selftest_bounded_wait(void* cuda_stream) {
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    void* buf = nullptr;
+    if (cudaMalloc(&buf, 64) != cudaSuccess) { cudaGetLastError(); return MOSS_ECUDA; }
+    int rc = MOSS_OK;
+    int err = 0;
+    if (cudaMemsetAsync(buf, 0, 64, st) != cudaSuccess) rc = MOSS_ECUDA;
+    if (rc == MOSS_OK) {
+        k_selftest_wait<<<1, 32, 0, st>>>((unsigned long long*)buf, (int*)((char*)buf + 32));
+        if (cudaGetLastError() != cudaSuccess) rc = MOSS_ECUDA;
+    }
+    if (rc == MOSS_OK && cudaMemcpyAsync(&err, (char*)buf + 32, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        rc = MOSS_ECUDA;
+    if (rc == MOSS_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = MOSS_ECUDA;
+    cudaFree(buf);
+    if (rc != MOSS_OK) return rc;
+    return (err & ERR_TIMEOUT) ? MOSS_ETIMEOUT : MOSS_EDEVICE;
+}
+
 int moss_kernel_times(moss_t h, double* ms4, int64_t* steps) {
     if (!h || !ms4 || !steps) return MOSS_EINVAL;
     for (int k = 0; k < 4; ++k) ms4[k] = h->kms[k];

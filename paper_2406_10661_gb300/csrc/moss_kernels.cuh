@@ -546,4 +546,12 @@ __global__ void k_set_signal(Ctx<Real> c, int n, const int32_t* ids, const int32
     c.junc_state[j] = junction_state_at(c, j, 0);
 }
 
+// Failure-detection self-test: the look-back of tile 1 waits on tile word 0,
+// which nothing publishes, so the bounded wait must give up and report.
+__global__ void k_selftest_wait(unsigned long long* words, int* err) {
+    bool timeout = false;
+    warp_lookback(words, 1, &timeout);
+    if (threadIdx.x == 0 && timeout) atomicOr(err, ERR_TIMEOUT);
+}
+
 }  // namespace moss

@@ -222,3 +222,20 @@ def test_medium_one_step_parity_fp32():
     sim.step(1); ora.step(1)
     n, excused = compare_one_step(sim.state(), ora.state())
     assert n > 10_000 and excused <= n // 1000
+
+
+def test_city_one_step_parity_fp32():
+    """Full size, in the launch configuration the benchmark times: the city
+    workload (39,600 roads, 2,464,950 trips) simulated on the GPU to step
+    3600 (about two million vehicles on the network), then one step on both
+    sides from that state; every vehicle compared."""
+    scen = sc.city_scenario()
+    sim = _sim(scen, 32)
+    sim.step(3600)
+    st = sim.state()
+    assert (st["status"] == 1).sum() > 1_000_000
+    ora = _ora(scen)
+    ora.set_state(st["status"], st["lane"], st["s"], st["v"], st["rc"], 3600)
+    sim.step(1); ora.step(1)
+    n, excused = compare_one_step(sim.state(), ora.state())
+    assert n > 1_000_000 and excused <= n // 1000
