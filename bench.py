@@ -310,7 +310,8 @@ def run_ours(args):
         "step_roofline": {"achieved": step_ach, "frac": step_ach / peak, "bytes_per_update": STEP_BYTES},
         "clocks": clk.summary(),
         "e2e": {"value": e2e_val, "unit": "vehicle-updates/s", "h2d_bytes_per_step": 8 * J,
-                "d2h_bytes_per_step": 12 * 8 + 8 + 4,  # metric fields, step, error word "steps": e2e_steps,
+                "d2h_bytes_per_step": 12 * 8 + 8 + 4,  # metric fields, step counter, error word
+                "steps": e2e_steps,
                 "api": "moss_set_signal_phase + moss_step(1) + moss_get_metrics per step"},
         "gpu_launches": 3 * args.steps,
         "wall_s_timed_region": wall,
