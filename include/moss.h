@@ -227,8 +227,9 @@ int moss_batch_set_signal_phase(moss_t h, int scenario, int n, const int32_t* ju
  * Kernel timing for measurement: when enabled, every step records CUDA
  * events around each kernel on the handle's stream (graphs are not used
  * while enabled).  moss_kernel_times returns the summed milliseconds per
- * kernel since enabling, in launch order (decide, lanescan, place, and a
- * fourth slot that is 0), and the number of timed steps.
+ * kernel since enabling, in the order (decide, lanescan, place, resolve) —
+ * the launch order is decide, resolve, lanescan, place; resolve finishes the
+ * lane-change candidates — and the number of timed steps.
  */
 int moss_set_kernel_timing(moss_t h, int enable);
 int moss_kernel_times(moss_t h, double* ms4, int64_t* steps);

@@ -221,7 +221,7 @@ class _Handle:
         ms = np.zeros(4, dtype=np.float64)
         n = ctypes.c_int64(0)
         _check(self.lib.moss_kernel_times(self.h, _ptr(ms, ctypes.c_double), ctypes.byref(n)), self.h)
-        return dict(zip(("decide", "lanescan", "place"), ms.tolist()[:3])), int(n.value)
+        return dict(zip(("decide", "lanescan", "place", "resolve"), ms.tolist())), int(n.value)
 
 
 def _state_arrays(n: int):

@@ -25,7 +25,7 @@ struct SnapBufs {
     int32_t* off;
 };
 
-constexpr int N_STEP_KERNELS = 3;  // decide, lanescan, place
+constexpr int N_STEP_KERNELS = 4;  // decide, resolve, lanescan, place (launch order)
 
 }  // namespace
 
@@ -72,6 +72,8 @@ struct MossHandle {
     int32_t *d_enext = nullptr, *d_enter = nullptr, *d_leave = nullptr, *d_lbefore = nullptr,
             *d_tile_leave = nullptr, *d_tile_prefix = nullptr;
     unsigned long long *d_head = nullptr, *d_lane_tiles = nullptr;
+    void* d_cands = nullptr;  // Cand<Real>[cap]
+    unsigned long long* d_gap_head = nullptr;
     int n_lane_tiles = 0, max_slot_tiles = 0, n_junc_chunks = 0;
     Counters* d_cnt = nullptr;
     int32_t* d_stage = nullptr;          // setter staging (2 * n_junctions)
@@ -265,6 +267,7 @@ Ctx<Real> make_ctx(MossHandle* h, int cur) {
     c.ea = (RecA<Real>*)h->d_ea; c.eb = h->d_eb; c.enext = h->d_enext; c.head = h->d_head;
     c.enter = h->d_enter; c.leave = h->d_leave; c.lbefore = h->d_lbefore;
     c.tile_leave = h->d_tile_leave; c.tile_prefix = h->d_tile_prefix; c.lane_tiles = h->d_lane_tiles;
+    c.cands = (Cand<Real>*)h->d_cands; c.gap_head = h->d_gap_head;
     c.n_lane_tiles = h->n_lane_tiles; c.max_slot_tiles = h->max_slot_tiles;
     c.n_junc_chunks = h->n_junc_chunks; c.cnt = h->d_cnt;
     const MossParams& p = h->prm;
@@ -277,7 +280,7 @@ Ctx<Real> make_ctx(MossHandle* h, int cur) {
 }
 
 struct Grids {
-    int decide_work, decide_ins, lanescan, place;
+    int decide_work, decide_ins, resolve, lanescan, place;
 };
 
 Grids grids(const MossHandle* h) {
@@ -285,6 +288,8 @@ Grids grids(const MossHandle* h) {
     g.decide_work = std::max(1, std::min(h->max_slot_tiles, h->sm_count * h->cfg_decide));
     const int ns = (int)h->start_lanes.size();
     g.decide_ins = ns > 0 ? (ns + TILE - 1) / TILE : 0;  // one start lane per thread
+    // candidates are a few per cent of the vehicles; the kernel strides over them
+    g.resolve = std::max(1, std::min(h->max_slot_tiles, h->sm_count * 2));
     const int tickets = h->n_lane_tiles + 1 + h->n_junc_chunks;
     g.lanescan = std::max(1, std::min(tickets, h->sm_count * h->cfg_lanescan));
     g.place = std::max(1, std::min(2 * h->max_slot_tiles, h->sm_count * h->cfg_place));
@@ -299,10 +304,12 @@ void enqueue_step(MossHandle* h, int cur, bool timed) {
     if (timed) cudaEventRecord(h->ev[0], s);
     k_decide<Real><<<g.decide_work + g.decide_ins, TILE, 0, s>>>(c, g.decide_work);
     if (timed) cudaEventRecord(h->ev[1], s);
-    k_lanescan<Real><<<g.lanescan, LANESCAN_THREADS, 0, s>>>(c);
+    k_resolve<Real><<<g.resolve, TILE, 0, s>>>(c);
     if (timed) cudaEventRecord(h->ev[2], s);
-    k_place<Real><<<g.place, TILE, 0, s>>>(c);
+    k_lanescan<Real><<<g.lanescan, LANESCAN_THREADS, 0, s>>>(c);
     if (timed) cudaEventRecord(h->ev[3], s);
+    k_place<Real><<<g.place, TILE, 0, s>>>(c);
+    if (timed) cudaEventRecord(h->ev[4], s);
 }
 
 void enqueue(MossHandle* h, int cur, bool timed) {
@@ -533,6 +540,9 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
     TRY(dalloc(h, (char**)&h->d_ea, cap * ra));
     TRY(dalloc(h, &h->d_eb, cap));
     TRY(dalloc(h, &h->d_enext, cap));
+    TRY(dalloc(h, (char**)&h->d_cands,
+               cap * (h->precision == 64 ? sizeof(Cand<double>) : sizeof(Cand<float>))));
+    TRY(upload(h, &h->d_gap_head, std::vector<unsigned long long>(cap + NL + 1, 0ull)));
     TRY(upload(h, &h->d_head, std::vector<unsigned long long>(NL, 0ull)));
     TRY(upload(h, &h->d_enter, std::vector<int32_t>(NL, 0)));
     TRY(upload(h, &h->d_leave, std::vector<int32_t>(NL, 0)));
@@ -729,10 +739,12 @@ int moss_step(moss_t h, int n) {
             enqueue(h, h->parity, true);
             h->parity ^= 1;
             CK(cudaEventSynchronize(h->ev[N_STEP_KERNELS]));
+            // reported order: decide, lanescan, place, resolve
+            static const int slot_of[N_STEP_KERNELS] = {0, 3, 1, 2};
             for (int q = 0; q < N_STEP_KERNELS; ++q) {
                 float ms = 0;
                 CK(cudaEventElapsedTime(&ms, h->ev[q], h->ev[q + 1]));
-                h->kms[q] += ms;  // decide, lanescan, place
+                h->kms[slot_of[q]] += ms;
             }
             h->ksteps++;
         }
@@ -889,7 +901,8 @@ int moss_set_state(moss_t h, const MossState* in, int64_t step) {
     CK(cudaMemcpy(h->d_metrics + M_CUR_ACTIVE, cur, sizeof(cur), cudaMemcpyHostToDevice));
     Counters c{};
     CK(cudaMemcpy(&c, h->d_cnt, sizeof(c), cudaMemcpyDeviceToHost));
-    c.n_cur = (int)n_act; c.n_next = (int)n_act; c.n_ent = 0; c.ticket_lane = 0; c.done_place = 0;
+    c.n_cur = (int)n_act; c.n_next = (int)n_act; c.n_ent = 0; c.n_cand = 0; c.ticket_lane = 0;
+    c.done_place = 0;
     CK(cudaMemcpy(h->d_cnt, &c, sizeof(c), cudaMemcpyHostToDevice));
     TRY(junction_init(h));
     CK(cudaStreamSynchronize(h->stream));

@@ -67,7 +67,7 @@ struct Counters {
     int done_place;  // k_place blocks finished (the last one closes the step)
     int err;
     int tag;         // step tag of the per-lane entrant lists (never 0)
-    int pad;
+    int n_cand;      // lane-change candidates listed this step (for k_resolve)
 };
 
 // snapshot records
@@ -81,6 +81,21 @@ struct alignas(16) RecB {
     int nl;     // next lane on the route (-1 on the last road)
 };
 template <typename Real> struct alignas(2 * sizeof(Real)) SV { Real s, v; };
+
+// A lane-change candidate, finished by k_resolve.  gap = its insertion
+// position in the target lane's segment plus the target lane's index: equal
+// for two candidates exactly when they enter the same lane between the same
+// target leader and follower (unique over lanes: lane l's positions span
+// [off[l], off[l+1]], shifted by l).  Candidates of one gap form a list
+// (gap_head, next).  The own-lane kinematics are kept for a lost conflict.
+template <typename Real>
+struct alignas(16) Cand {
+    int slot, gap, TL, nlt;  // slot; gap key; target leader slot (-1 none); next lane from the target lane
+    int next, bits, id, nl;  // list link; CB_* bits; vehicle id; own next lane
+    Real u, scale;           // utility of the chosen side and its flag scale (R22)
+    Real a, lgap, sgap;      // own-lane acceleration, leader gap, stop-line gap
+};
+enum : int { CB_RIGHT = 1, CB_FLAG = 2, CB_LEADER = 4, CB_STOP = 8, CB_OVERLAP = 16 };
 
 // One 32-byte record per lane.
 //   road lane:     lo, hi = lanes [lo, hi) of its road (left to right); jb, je =
@@ -152,6 +167,8 @@ struct Ctx {
     int32_t* lbefore;     // [n_lanes] leavers in lanes before l
     int32_t* tile_leave;  // [slot tiles] leavers per tile of the current snapshot
     int32_t* tile_prefix; // [slot tiles] leavers before the tile
+    Cand<Real>* cands;    // this step's lane-change candidates (cnt->n_cand of them)
+    unsigned long long* gap_head;  // [n_veh + n_lanes + 1] (tag << 32 | candidate) or stale
     unsigned long long* lane_tiles;
     int n_lane_tiles, max_slot_tiles, n_junc_chunks;
     Counters* cnt;
@@ -376,30 +393,49 @@ struct Decision {
     int att;                          // MOBIL was evaluated (the attempt draw passed)
 };
 
-// The full per-vehicle decision before conflict resolution (App. B.3).  A pure
-// function of the snapshot, so any thread can recompute any vehicle's
-// decision bit-for-bit (used to resolve conflicts, R9); it has one call site.
+// The per-vehicle decision before conflict resolution (App. B.3), in two
+// parts.  decide_own: the acceleration on the own lane and, on a road with
+// two or more lanes, the MOBIL attempt draw (R4, R6).  decide_mobil: for a
+// vehicle whose attempt draw passed, the MOBIL utilities of the sides, p_LC
+// and the direction (R1-R5).  Both are pure functions of the snapshot.
 template <typename Real>
-__device__ __forceinline__ Decision<Real> decide(const Ctx<Real>& c, int i, long long t, uint32_t k0,
-                                                 uint32_t k1, int vbase) {
-    Decision<Real> D;
-    D.cand = 0; D.dir = 0; D.tl = -1; D.TL = -1; D.TF = -1; D.flag = 0; D.nlt = -1; D.att = 0;
-    D.u = Real(0); D.scale = Real(1);
-    const RecA<Real> E = c.cur.a[i];
-    const RecB EB = c.cur.b[i];
-    const int lane = E.lane;
-    const LaneInfo li = c.lane[lane];
-    const int b = c.cur.off[lane], e = c.cur.off[lane + 1];
+struct OwnPart {
+    LaneAcc<Real> own;
+    float u_lc, u_dir;  // the draws for p_LC and the direction (exact in FP32)
+    int att;            // the attempt draw passed: MOBIL is evaluated
+};
+
+template <typename Real>
+__device__ __forceinline__ OwnPart<Real> decide_own(const Ctx<Real>& c, int i, const RecA<Real>& E,
+                                                    const RecB& EB, const LaneInfo& li, int b, long long t,
+                                                    uint32_t k0, uint32_t k1, int vbase) {
+    OwnPart<Real> P;
+    P.att = 0; P.u_lc = 0.0f; P.u_dir = 0.0f;
     const int OL = (i > b) ? i - 1 : -1;
-    const Real v0f = Real(EB.v0f);
-    D.own = accel_on_lane(c, li, E.s, E.v, v0f * Real(li.vmax), OL, EB.nl, EB.rptr, EB.rlast);
-    if (li.lo < 0 || li.hi - li.lo < 2) return D;  // junction lane or single-lane road
+    P.own = accel_on_lane(c, li, E.s, E.v, Real(EB.v0f) * Real(li.vmax), OL, EB.nl, EB.rptr, EB.rlast);
+    if (li.lo < 0 || li.hi - li.lo < 2) return P;  // junction lane or single-lane road
     uint32_t w[4];
     philox4x32_10(k0, k1, uint32_t(E.id - vbase), uint32_t(t), 0u, 0u, w);
     const Real u_att = unit24<Real>(w[0]);
-    if (!(u_att < c.p_att)) return D;
-    D.att = 1;
-    const Real u_lc = unit24<Real>(w[1]), u_dir = unit24<Real>(w[2]);
+    if (!(u_att < c.p_att)) return P;
+    P.att = 1;
+    P.u_lc = unit24<float>(w[1]);
+    P.u_dir = unit24<float>(w[2]);
+    return P;
+}
+
+template <typename Real>
+__device__ __forceinline__ Decision<Real> decide_mobil(const Ctx<Real>& c, int i, const RecA<Real>& E,
+                                                       const RecB& EB, const LaneInfo& li, int b, int e,
+                                                       const LaneAcc<Real>& own, float f_lc, float f_dir) {
+    Decision<Real> D;
+    D.cand = 0; D.dir = 0; D.tl = -1; D.TL = -1; D.TF = -1; D.flag = 0; D.nlt = -1; D.att = 1;
+    D.u = Real(0); D.scale = Real(1);
+    D.own = own;
+    const int lane = E.lane;
+    const int OL = (i > b) ? i - 1 : -1;
+    const Real v0f = Real(EB.v0f);
+    const Real u_lc = Real(f_lc), u_dir = Real(f_dir);
 
     const int OF = (i + 1 < e) ? i + 1 : -1;
     Real a_old = Real(0), at_old = Real(0);
@@ -416,18 +452,24 @@ __device__ __forceinline__ Decision<Real> decide(const Ctx<Real>& c, int i, long
     }
     // next road of the route (for the target lane's junction lane)
     const int next_road = (EB.nl >= 0) ? c.lane[EB.nl].road : -1;
-    Real u[2] = {Real(0), Real(0)}, scl[2] = {Real(0), Real(0)};
-    int feas[2] = {0, 0}, TLs[2] = {-1, -1}, TFs[2] = {-1, -1}, NLs[2] = {-1, -1};
+    // The sides that exist are visited in order, so every vehicle with one
+    // side (an edge lane) runs the first pass together with its warp
+    // neighbours, whichever side that is; results go to the left/right
+    // variables by select.  Same arithmetic per side as a fixed left/right
+    // loop: the decision does not depend on the visiting order.
+    Real u0 = Real(0), u1 = Real(0), scl0 = Real(0), scl1 = Real(0);
+    int feas0 = 0, feas1 = 0, TL0 = -1, TL1 = -1, TF0 = -1, TF1 = -1, NL0 = -1, NL1 = -1;
     const Real pos_scale = E.s > Real(1) ? E.s : Real(1);
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
+    const int has_l = lane - 1 >= li.lo, has_r = lane + 1 < li.hi;
+    const int n_sides = has_l + has_r;
+#pragma unroll 1
+    for (int k = 0; k < n_sides; ++k) {
+        const int side = (k == 0 && has_l) ? 0 : 1;
         const int tl = side == 0 ? lane - 1 : lane + 1;
-        if (tl < li.lo || tl >= li.hi) continue;
         const LaneInfo ti = c.lane[tl];
         const int tb = c.cur.off[tl], te = c.cur.off[tl + 1];
         const int p = partition_point(c, tb, te, E.s, E.id);
         const int TL = (p > tb) ? p - 1 : -1, TF = (p < te) ? p : -1;
-        TLs[side] = TL; TFs[side] = TF;
         int ok = 1;
         RecA<Real> TLr, TFr;
         TLr.s = Real(0); TLr.v = Real(0); TFr.s = Real(0); TFr.v = Real(0);
@@ -444,7 +486,6 @@ __device__ __forceinline__ Decision<Real> decide(const Ctx<Real>& c, int i, long
             if (rabs(g) < c.band * pos_scale) D.flag = 1;
         }
         const int nlt = (next_road >= 0) ? jl_toward(c, ti, next_road, EB.nl - li.jb) : -1;
-        NLs[side] = nlt;
         const Real at_ego = accel_on_lane(c, ti, E.s, E.v, v0f * Real(ti.vmax), TL, nlt, EB.rptr, EB.rlast).a;
         Real a_new = Real(0), at_new = Real(0);
         if (TF >= 0) {
@@ -455,11 +496,14 @@ __device__ __forceinline__ Decision<Real> decide(const Ctx<Real>& c, int i, long
             const Real sc = rabs(at_new) > Real(1) ? rabs(at_new) : Real(1);
             if (rabs(at_new + c.b_safe) < c.band * sc) D.flag = 1;
         }
-        u[side] = (at_ego - D.own.a) + c.pol * ((at_new - a_new) + (at_old - a_old)) - c.a_th;
-        scl[side] = rabs(at_ego) + rabs(D.own.a) +
-                    c.pol * (rabs(at_new) + rabs(a_new) + rabs(at_old) + rabs(a_old)) + c.a_th;
-        feas[side] = ok;
+        const Real us = (at_ego - D.own.a) + c.pol * ((at_new - a_new) + (at_old - a_old)) - c.a_th;
+        const Real ss = rabs(at_ego) + rabs(D.own.a) +
+                        c.pol * (rabs(at_new) + rabs(a_new) + rabs(at_old) + rabs(a_old)) + c.a_th;
+        if (side == 0) { u0 = us; scl0 = ss; feas0 = ok; TL0 = TL; TF0 = TF; NL0 = nlt; }
+        else           { u1 = us; scl1 = ss; feas1 = ok; TL1 = TL; TF1 = TF; NL1 = nlt; }
     }
+    const Real u[2] = {u0, u1}, scl[2] = {scl0, scl1};
+    const int feas[2] = {feas0, feas1}, TLs[2] = {TL0, TL1}, TFs[2] = {TF0, TF1}, NLs[2] = {NL0, NL1};
     Real scale = Real(1);
     for (int sd = 0; sd < 2; ++sd)
         if (feas[sd] && scl[sd] > scale) scale = scl[sd];
@@ -508,6 +552,17 @@ __device__ __forceinline__ void store_release(unsigned long long* p, unsigned lo
     a.store(v, cuda::memory_order_release);
 }
 
+// Slot in an array shared through one counter: the threads of the warp that
+// are here together take consecutive slots with one atomic.
+__device__ __forceinline__ int warp_claim(int* counter) {
+    const unsigned m = __activemask();
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(counter, __popc(m));
+    base = __shfl_sync(m, base, leader);
+    return base + __popc(m & ((1u << lane) - 1u));
+}
+
 // Warp-cooperative look-back of a decoupled scan (all 32 lanes of one warp).
 // Tile words: flag (2 bits: 1 aggregate, 2 inclusive prefix) | 62-bit value.
 // Returns the exclusive prefix of `tile`; sets *timeout if a bounded wait gave up.
@@ -541,9 +596,13 @@ __device__ __forceinline__ unsigned long long warp_lookback(unsigned long long* 
 
 // Per-scenario metric accumulation: register partials per thread, flushed
 // with one set of atomics per block when the whole block shares a scenario.
+// Counts are 32-bit (each is at most the number of vehicles the thread
+// handles in one launch); travel-time and speed sums are 64-bit.
+constexpr int MACC_N = 8;
 struct MetricAcc {
     int scen;
-    long long m[9];  // updates, arrived, tt_steps, speed_fx, lane_changes, flagged, overlaps, inserted, mobil
+    int upd, arr, lc, flg, ovl, mob;  // updates, arrived, lane changes, flagged, overlaps, MOBIL evaluations
+    long long tt, spd;                // travel time in steps, speed in units of 2^-24 m/s
 };
 
 __device__ __forceinline__ int metric_field(int k) {
@@ -555,30 +614,43 @@ __device__ __forceinline__ int metric_field(int k) {
         case 4: return M_LANE_CHANGES;
         case 5: return M_FLAGGED;
         case 6: return M_OVERLAPS;
-        case 7: return M_INSERTED;
         default: return M_MOBIL;
+    }
+}
+
+__device__ __forceinline__ long long macc_value(const MetricAcc& a, int k) {
+    switch (k) {
+        case 0: return a.upd;
+        case 1: return a.arr;
+        case 2: return a.tt;
+        case 3: return a.spd;
+        case 4: return a.lc;
+        case 5: return a.flg;
+        case 6: return a.ovl;
+        default: return a.mob;
     }
 }
 
 __device__ __forceinline__ void macc_reset(MetricAcc& a, int scen) {
     a.scen = scen;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) a.m[k] = 0;
+    a.upd = a.arr = a.lc = a.flg = a.ovl = a.mob = 0;
+    a.tt = a.spd = 0;
 }
 
 __device__ __forceinline__ void macc_flush_thread(MetricAcc& a, long long* metrics) {
     if (a.scen < 0) return;
 #pragma unroll
-    for (int k = 0; k < 9; ++k)
-        if (a.m[k]) atomicAdd((unsigned long long*)&metrics[a.scen * M_NFIELDS + metric_field(k)],
-                              (unsigned long long)a.m[k]);
+    for (int k = 0; k < MACC_N; ++k) {
+        const long long x = macc_value(a, k);
+        if (x) atomicAdd((unsigned long long*)&metrics[a.scen * M_NFIELDS + metric_field(k)], (unsigned long long)x);
+    }
 }
 
 // Block-level flush: reduce in shared memory when every thread holds the
 // same scenario (or nothing), else fall back to per-thread atomics.
 template <int THREADS>
 __device__ void macc_flush_block(MetricAcc& a, long long* metrics) {
-    __shared__ long long red[9][THREADS / 32];
+    __shared__ long long red[MACC_N][THREADS / 32];
     __shared__ int scen0;
     const int tid = threadIdx.x;
     if (tid == 0) scen0 = -1;
@@ -591,13 +663,13 @@ __device__ void macc_flush_block(MetricAcc& a, long long* metrics) {
     if (s0 < 0) return;
     const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        long long x = a.scen < 0 ? 0 : a.m[k];
+    for (int k = 0; k < MACC_N; ++k) {
+        long long x = a.scen < 0 ? 0 : macc_value(a, k);
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
         if (lane == 0) red[k][warp] = x;
     }
     __syncthreads();
-    if (tid < 9) {
+    if (tid < MACC_N) {
         long long x = 0;
         for (int w = 0; w < THREADS / 32; ++w) x += red[tid][w];
         if (x) atomicAdd((unsigned long long*)&metrics[s0 * M_NFIELDS + metric_field(tid)], (unsigned long long)x);

@@ -39,7 +39,7 @@ __device__ void insert_departure(const Ctx<Real>& c, int l, int tag) {
         if (rabs(g) < c.band * scl) fl |= F_FLAGGED;
         if (!(g >= Real(0))) return;
     }
-    const int q = atomicAdd(&c.cnt->n_ent, 1);
+    const int q = warp_claim(&c.cnt->n_ent);
     const int r0 = c.route_off[vid], r1 = c.route_off[vid + 1] - 1;
     int nl = -1;
     if (r0 < r1) {
@@ -120,17 +120,17 @@ __device__ __forceinline__ int integrate_emit(const Ctx<Real>& c, MetricAcc& acc
         }
     }
     if (arrived) fl |= F_ARRIVED;
-    acc.m[0] += 1;
-    acc.m[3] += speed_fixed(vn);
-    if (fl & F_FLAGGED) acc.m[5] += 1;
-    if (fl & F_CHANGED) acc.m[4] += 1;
-    if (own_overlap) acc.m[6] += 1;
+    acc.upd += 1;
+    acc.spd += speed_fixed(vn);
+    if (fl & F_FLAGGED) acc.flg += 1;
+    if (fl & F_CHANGED) acc.lc += 1;
+    if (own_overlap) acc.ovl += 1;
     if (fl) c.vflags[E.id] = int((t & 0xFFFFFF) << 8) | fl;
     if (arrived) {
         c.code[i] = C_ARRIVE;
         c.vstatus[E.id] = 2;
-        acc.m[1] += 1;
-        acc.m[2] += (t + 1) - (long long)c.dep[E.id];
+        acc.arr += 1;
+        acc.tt += (t + 1) - (long long)c.dep[E.id];
         atomicAdd(&c.leave[lane], 1);
         long long* M = c.metrics + (long long)sc * M_NFIELDS;
         atomicAdd((unsigned long long*)&M[M_CUR_ACTIVE], (unsigned long long)(-1ll));
@@ -146,7 +146,7 @@ __device__ __forceinline__ int integrate_emit(const Ctx<Real>& c, MetricAcc& acc
     }
     c.code[i] = C_MOVE;
     atomicAdd(&c.leave[lane], 1);
-    const int q = atomicAdd(&c.cnt->n_ent, 1);
+    const int q = warp_claim(&c.cnt->n_ent);
     RecA<Real> A;
     A.s = sn; A.v = vn; A.id = E.id; A.lane = nlane;
     RecB B;
@@ -159,8 +159,35 @@ __device__ __forceinline__ int integrate_emit(const Ctx<Real>& c, MetricAcc& acc
 }
 
 // ---------------------------------------------------------------------------
+// A lane-change candidate leaves its decision for k_resolve: a record in the
+// candidate list, linked into the list of its target gap.
+template <typename Real>
+__device__ __forceinline__ void list_candidate(const Ctx<Real>& c, int i, const RecA<Real>& E,
+                                               const Decision<Real>& D, int tag) {
+    int gp;
+    if (D.TF >= 0) gp = D.TF;
+    else if (D.TL >= 0) gp = D.TL + 1;
+    else gp = c.cur.off[D.tl];
+    Cand<Real> C;
+    C.slot = i; C.gap = gp + D.tl; C.TL = D.TL; C.nlt = D.nlt;
+    C.bits = (D.dir > 0 ? CB_RIGHT : 0) | (D.flag ? CB_FLAG : 0) | (D.own.has_leader ? CB_LEADER : 0) |
+             (D.own.stop ? CB_STOP : 0) | (D.own.overlap ? CB_OVERLAP : 0);
+    C.id = E.id; C.nl = D.own.nl;
+    C.u = D.u; C.scale = D.scale;
+    C.a = D.own.a; C.lgap = D.own.gap; C.sgap = D.own.stop_gap;
+    const int k = warp_claim(&c.cnt->n_cand);
+    const unsigned long long prev =
+        atomicExch(&c.gap_head[C.gap], ((unsigned long long)(unsigned)tag << 32) | (unsigned)k);
+    C.next = (int)(prev >> 32) == tag ? (int)(unsigned)(prev & 0xffffffffull) : -1;
+    c.cands[k] = C;
+}
+
+// ---------------------------------------------------------------------------
 // k_decide: blocks [0, n_work) take 256-slot tiles of the current snapshot
 // (one vehicle per thread); blocks [n_work, gridDim) run the insertion.
+// Per vehicle: the own-lane acceleration and the attempt draw, MOBIL if the
+// draw passed, then the update; lane-change candidates are finished by
+// k_resolve.
 // MOSS_DECIDE_MIN_BLOCKS: resident blocks per SM the register budget targets.
 #ifndef MOSS_DECIDE_MIN_BLOCKS
 #define MOSS_DECIDE_MIN_BLOCKS 4
@@ -192,75 +219,97 @@ __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Rea
             if ((unsigned)lane >= (unsigned)c.n_lanes) {
                 atomicOr(&c.cnt->err, ERR_RANGE);
             } else {
-                const int sc = c.lane[lane].scen;
+                const LaneInfo li = c.lane[lane];
+                const int sc = li.scen;
                 if (sc != acc.scen) {
                     macc_flush_thread(acc, c.metrics);
                     macc_reset(acc, sc);
                 }
                 const long long t = c.scen_step[sc];
-                const uint32_t k0 = c.key0[sc], k1 = c.key1[sc];
-                const int vbase = c.veh_base[sc];
-                // job 0 is this vehicle; jobs 1.. are the rivals of a lane-change
-                // candidate (R9): vehicles of the lane beyond the target lane that
-                // fall into the same target-lane gap.  One call site of decide()
-                // makes every recomputation bit-identical to the rival's own.
-                Decision<Real> D;
-                int fl = 0;
-                bool granted = false;
-                int r = 0, rend = 0;
-                for (int job = 0;; ++job) {
-                    const int slot = job == 0 ? i : r;
-                    const Decision<Real> X = decide(c, slot, t, k0, k1, vbase);
-                    if (job == 0) {
-                        D = X;
-                        fl = D.flag ? F_FLAGGED : 0;
-                        if (!D.cand) break;
-                        fl |= F_CANDIDATE;
-                        granted = true;
-                        const LaneInfo li = c.lane[lane];
-                        const int ol = D.tl + D.dir;
-                        if (ol < li.lo || ol >= li.hi) break;
-                        const int ob = c.cur.off[ol], oe = c.cur.off[ol + 1];
-                        r = ob; rend = oe;
-                        if (D.TL >= 0) {
-                            const RecA<Real> T = c.cur.a[D.TL];
-                            r = partition_point(c, ob, oe, T.s, T.id);
-                        }
-                        if (D.TF >= 0) {
-                            const RecA<Real> T = c.cur.a[D.TF];
-                            rend = partition_point(c, ob, oe, T.s, T.id);
-                        }
-                        if (r >= rend) break;
-                    } else {
-                        if (X.cand && X.tl == D.tl) {
-                            const Real sc2 = D.scale > X.scale ? D.scale : X.scale;
-                            if (rabs(D.u - X.u) < c.band * sc2) fl |= F_FLAGGED;
-                            const int rid = c.cur.a[r].id;
-                            if (!(D.u > X.u || (D.u == X.u && E.id < rid))) granted = false;
-                        }
-                        if (++r >= rend) break;
-                    }
-                }
-                if (D.att) acc.m[8] += 1;
-                if (D.cand && !granted) fl |= F_CONFLICT_LOST;
-                // a granted change drives on the target lane (its kinematics
-                // recomputed from the same inputs)
                 const RecB EB = c.cur.b[i];
-                LaneAcc<Real> la = D.own;
-                int nlane = lane;
-                if (granted) {
-                    fl |= F_CHANGED;
-                    nlane = D.tl;
-                    const LaneInfo ti = c.lane[nlane];
-                    la = accel_on_lane(c, ti, E.s, E.v, Real(EB.v0f) * Real(ti.vmax), D.TL, D.nlt, EB.rptr,
-                                       EB.rlast);
+                const int b = c.cur.off[lane];
+                const OwnPart<Real> P = decide_own(c, i, E, EB, li, b, t, c.key0[sc], c.key1[sc], c.veh_base[sc]);
+                int fl = 0;
+                bool cand = false;
+                if (P.att) {
+                    acc.mob += 1;
+                    const Decision<Real> D = decide_mobil(c, i, E, EB, li, b, c.cur.off[lane + 1], P.own, P.u_lc,
+                                                          P.u_dir);
+                    if (D.cand) {
+                        list_candidate(c, i, E, D, tag);
+                        cand = true;
+                    }
+                    fl = D.flag ? F_FLAGGED : 0;
                 }
-                leaver = integrate_emit(c, acc, i, E, EB, la, nlane, fl, D.own.overlap != 0, t, sc, tag);
+                if (!cand) leaver = integrate_emit(c, acc, i, E, EB, P.own, lane, fl, P.own.overlap != 0, t, sc, tag);
             }
         }
         // leavers of this tile (k_lanescan zeroes the counters after reading them)
         const unsigned lb = __ballot_sync(0xffffffffu, leaver);
         if ((threadIdx.x & 31) == 0 && lb) atomicAdd(&c.tile_leave[tile], __popc(lb));
+    }
+    macc_flush_block<TILE>(acc, c.metrics);
+}
+
+// ---------------------------------------------------------------------------
+// k_resolve: the lane-change candidates of this step (grid-stride over the
+// list k_decide built).  Conflict rule R9: a candidate conflicts with the
+// candidates that enter the same lane from the other side into the same gap
+// (the other members of its gap list with the opposite direction); the
+// larger utility wins, ties to the smaller id.  Both sides compare the same
+// stored utilities, so the outcome is consistent.  Then the update on the
+// target lane (granted) or with the stored own-lane kinematics (lost).
+template <typename Real>
+__global__ void __launch_bounds__(TILE) k_resolve(Ctx<Real> c) {
+    if (c.cnt->err & ERR_POISON) return;
+    const int nc = c.cnt->n_cand;
+    const int tag = c.cnt->tag;
+    MetricAcc acc;
+    macc_reset(acc, -1);
+    for (int k = blockIdx.x * TILE + threadIdx.x; k < nc; k += gridDim.x * TILE) {
+        const Cand<Real> C = c.cands[k];
+        const int i = C.slot;
+        const RecA<Real> E = c.cur.a[i];
+        const RecB EB = c.cur.b[i];
+        const int lane = E.lane;
+        const int dir = (C.bits & CB_RIGHT) ? 1 : -1;
+        const int tl = lane + dir;
+        const int sc = c.lane[lane].scen;
+        if (sc != acc.scen) {
+            macc_flush_thread(acc, c.metrics);
+            macc_reset(acc, sc);
+        }
+        const long long t = c.scen_step[sc];
+        int fl = F_CANDIDATE | ((C.bits & CB_FLAG) ? F_FLAGGED : 0);
+        bool granted = true;
+        const unsigned long long h = c.gap_head[C.gap];
+        int q = (int)(h >> 32) == tag ? (int)(unsigned)(h & 0xffffffffull) : -1;
+        for (int guard = 0; q >= 0; q = c.cands[q].next) {
+            if (++guard > nc) { atomicOr(&c.cnt->err, ERR_RANGE); break; }
+            if (q == k) continue;
+            const int rbits = c.cands[q].bits;
+            if (((rbits & CB_RIGHT) ? 1 : -1) == dir) continue;  // same side: no conflict
+            const Real ru = c.cands[q].u, rs = c.cands[q].scale;
+            const Real sc2 = C.scale > rs ? C.scale : rs;
+            if (rabs(C.u - ru) < c.band * sc2) fl |= F_FLAGGED;
+            if (!(C.u > ru || (C.u == ru && C.id < c.cands[q].id))) granted = false;
+        }
+        LaneAcc<Real> la;
+        int nlane = lane;
+        if (granted) {
+            fl |= F_CHANGED;
+            nlane = tl;
+            const LaneInfo ti = c.lane[tl];
+            la = accel_on_lane(c, ti, E.s, E.v, Real(EB.v0f) * Real(ti.vmax), C.TL, C.nlt, EB.rptr, EB.rlast);
+        } else {
+            fl |= F_CONFLICT_LOST;
+            la.a = C.a; la.gap = C.lgap; la.stop_gap = C.sgap; la.nl = C.nl;
+            la.has_leader = (C.bits & CB_LEADER) != 0;
+            la.stop = (C.bits & CB_STOP) != 0;
+            la.overlap = (C.bits & CB_OVERLAP) != 0;
+        }
+        if (integrate_emit(c, acc, i, E, EB, la, nlane, fl, (C.bits & CB_OVERLAP) != 0, t, sc, tag))
+            atomicAdd(&c.tile_leave[i / TILE], 1);
     }
     macc_flush_block<TILE>(acc, c.metrics);
 }
@@ -290,17 +339,204 @@ __device__ __forceinline__ long long block_exclusive_scan(long long x, long long
     return base + incl - x;
 }
 
-// k_lanescan.  Tickets [0, n_lane_tiles): next-snapshot lane offsets.
-// newsize(l) = size(l) - leave(l) + enter(l); two exclusive prefix sums (new
-// sizes, leavers) over lanes in one decoupled look-back pass; tile words pack
-// (flag:2 | leavers:31 | sizes:31).  Ticket n_lane_tiles: exclusive prefix of
-// the leavers per slot tile.  Remaining tickets: signal states of the next
-// step for chunks of junctions.
+// One lane tile of k_lanescan (LANESCAN_TILE lanes).  newsize(l) = size(l) -
+// leave(l) + enter(l); two exclusive prefix sums (new sizes, leavers) over
+// lanes in one decoupled look-back pass; tile words pack (flag:2 |
+// leavers:31 | sizes:31).  Warp w takes 512 consecutive lanes of the tile in
+// 4 rounds of 128 (4 consecutive lanes per thread), so each 16-byte load and
+// store of a warp covers one contiguous 512-byte run.
+constexpr int LS_WARPS = LANESCAN_THREADS / 32;
+constexpr int LS_ROUNDS = LANESCAN_TILE / LS_WARPS / 128;
+static_assert(LS_ROUNDS * 128 * LS_WARPS == LANESCAN_TILE, "lane tile = warps x rounds x 128 lanes");
+static_assert(JUNC_CHUNK == LANESCAN_THREADS, "one junction per thread");
+
+template <typename Real>
+__device__ __forceinline__ void lanescan_tile(const Ctx<Real>& c, int tile) {
+    __shared__ long long s_wsum[LS_WARPS];
+    __shared__ unsigned long long s_prefix;
+    const int ln = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nl = c.n_lanes;
+    const int wbase = tile * LANESCAN_TILE + w * (LANESCAN_TILE / LS_WARPS);
+    int ns[LS_ROUNDS][4], lv[LS_ROUNDS][4];
+    long long wpre[LS_ROUNDS];
+    long long run = 0;
+    // every load of the tile is issued before any result is used (and before
+    // the zeroing stores), so the tile costs one memory round trip
+    int o[LS_ROUNDS][4], lvv[LS_ROUNDS][4], env[LS_ROUNDS][4], o4[LS_ROUNDS];
+#pragma unroll
+    for (int r = 0; r < LS_ROUNDS; ++r) {
+        const int l0 = wbase + r * 128 + 4 * ln;
+        if (l0 + 4 <= nl) {
+            const int4 ov = *reinterpret_cast<const int4*>(c.cur.off + l0);
+            const int4 lx = *reinterpret_cast<const int4*>(c.leave + l0);
+            const int4 ex = *reinterpret_cast<const int4*>(c.enter + l0);
+            o[r][0] = ov.x; o[r][1] = ov.y; o[r][2] = ov.z; o[r][3] = ov.w;
+            lvv[r][0] = lx.x; lvv[r][1] = lx.y; lvv[r][2] = lx.z; lvv[r][3] = lx.w;
+            env[r][0] = ex.x; env[r][1] = ex.y; env[r][2] = ex.z; env[r][3] = ex.w;
+            o4[r] = ln == 31 ? c.cur.off[l0 + 4] : 0;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int l = l0 + j;
+                const bool in = l < nl;
+                o[r][j] = in || l == nl ? c.cur.off[l] : 0;
+                lvv[r][j] = in ? c.leave[l] : 0;
+                env[r][j] = in ? c.enter[l] : 0;
+            }
+            o4[r] = 0;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < LS_ROUNDS; ++r) {
+        const int l0 = wbase + r * 128 + 4 * ln;
+        if (l0 + 4 <= nl) {
+            *reinterpret_cast<int4*>(c.leave + l0) = make_int4(0, 0, 0, 0);
+            *reinterpret_cast<int4*>(c.enter + l0) = make_int4(0, 0, 0, 0);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (l0 + j < nl) { c.leave[l0 + j] = 0; c.enter[l0 + j] = 0; }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < LS_ROUNDS; ++r) {
+        const int l0 = wbase + r * 128 + 4 * ln;
+        // offset after the thread's 4th lane: the next thread's first
+        int onx = __shfl_down_sync(0xffffffffu, o[r][0], 1);
+        if (ln == 31) onx = o4[r];
+        long long rs = 0, rl = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool valid = l0 + j < nl;
+            const int onext = j < 3 ? o[r][j + 1] : onx;
+            ns[r][j] = valid ? (onext - o[r][j]) - lvv[r][j] + env[r][j] : 0;
+            lv[r][j] = valid ? lvv[r][j] : 0;
+            rs += ns[r][j]; rl += lv[r][j];
+        }
+        const long long p = (rl << 31) | rs;
+        long long incl = p;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (ln >= d) incl += y;
+        }
+        wpre[r] = run + incl - p;
+        run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (ln == 0) s_wsum[w] = run;
+    __syncthreads();
+    long long wb = 0, total = 0;
+#pragma unroll
+    for (int k = 0; k < LS_WARPS; ++k) {
+        const long long x = s_wsum[k];
+        if (k < w) wb += x;
+        total += x;
+    }
+    if (threadIdx.x < 32) {
+        bool timeout = false;
+        unsigned long long prefix = 0;
+        if (tile == 0) {
+            if (threadIdx.x == 0) store_release(&c.lane_tiles[0], (2ull << 62) | (unsigned long long)total);
+        } else {
+            if (threadIdx.x == 0) store_release(&c.lane_tiles[tile], (1ull << 62) | (unsigned long long)total);
+            prefix = warp_lookback(c.lane_tiles, tile, &timeout);
+            if (threadIdx.x == 0) {
+                store_release(&c.lane_tiles[tile], (2ull << 62) | (prefix + (unsigned long long)total));
+                if (timeout) atomicOr(&c.cnt->err, ERR_TIMEOUT);
+            }
+        }
+        if (threadIdx.x == 0) s_prefix = prefix;
+    }
+    __syncthreads();
+    const long long base = (long long)s_prefix + wb;
+#pragma unroll
+    for (int r = 0; r < LS_ROUNDS; ++r) {
+        const int l0 = wbase + r * 128 + 4 * ln;
+        const long long ex = base + wpre[r];
+        long long en = ex & ((1ll << 31) - 1), el = ex >> 31;
+        int on[4], lb[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            on[j] = (int)en; lb[j] = (int)el;
+            en += ns[r][j]; el += lv[r][j];
+        }
+        if (l0 + 4 <= nl) {
+            *reinterpret_cast<int4*>(c.nxt.off + l0) = make_int4(on[0], on[1], on[2], on[3]);
+            *reinterpret_cast<int4*>(c.lbefore + l0) = make_int4(lb[0], lb[1], lb[2], lb[3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (l0 + j < nl) { c.nxt.off[l0 + j] = on[j]; c.lbefore[l0 + j] = lb[j]; }
+        }
+        if (l0 < nl && nl <= l0 + 4) {  // this thread holds the last lane
+            c.nxt.off[nl] = (int)en;
+            c.cnt->n_next = (int)en;
+        }
+    }
+}
+
+// Exclusive prefix of the leavers per slot tile of the current snapshot (one
+// block; the counters are zeroed for the next step).  Chunks of TP_CHUNK
+// counters go through shared memory: 16-byte coalesced loads in, each thread
+// scans a contiguous run (the padding of one word per 32 keeps the run reads
+// free of bank conflicts), 16-byte coalesced stores out.  The counter arrays
+// are padded to a multiple of 1024 entries and hold zeros past the tiles in
+// use.
+constexpr int TP_CHUNK = 8192;
+__device__ __forceinline__ int tp_pad(int k) { return k + (k >> 5); }
+
+template <typename Real>
+__device__ __forceinline__ void tile_prefix_scan(const Ctx<Real>& c) {
+    __shared__ int sm[TP_CHUNK + TP_CHUNK / 32];
+    const int nt = (c.cnt->n_cur + TILE - 1) / TILE;
+    const int nt4 = ((nt + 4 * LANESCAN_THREADS - 1) / (4 * LANESCAN_THREADS)) * (4 * LANESCAN_THREADS);
+    long long carry = 0;
+    for (int c0 = 0; c0 < nt4; c0 += TP_CHUNK) {
+        const int m = min(TP_CHUNK, nt4 - c0);  // a multiple of 4 * LANESCAN_THREADS
+        // all loads first (one memory round trip), then the zeroing stores
+        int4 x[TP_CHUNK / (4 * LANESCAN_THREADS)];
+#pragma unroll
+        for (int q = 0; q < TP_CHUNK / (4 * LANESCAN_THREADS); ++q) {
+            const int k = 4 * threadIdx.x + q * 4 * LANESCAN_THREADS;
+            x[q] = k < m ? *reinterpret_cast<const int4*>(c.tile_leave + c0 + k) : make_int4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int q = 0; q < TP_CHUNK / (4 * LANESCAN_THREADS); ++q) {
+            const int k = 4 * threadIdx.x + q * 4 * LANESCAN_THREADS;
+            if (k < m) {
+                *reinterpret_cast<int4*>(c.tile_leave + c0 + k) = make_int4(0, 0, 0, 0);
+                sm[tp_pad(k)] = x[q].x; sm[tp_pad(k + 1)] = x[q].y; sm[tp_pad(k + 2)] = x[q].z;
+                sm[tp_pad(k + 3)] = x[q].w;
+            }
+        }
+        __syncthreads();
+        const int per = m / LANESCAN_THREADS;
+        const int k0 = per * threadIdx.x;
+        long long sum = 0;
+        for (int j = 0; j < per; ++j) sum += sm[tp_pad(k0 + j)];
+        long long tot;
+        long long ex = block_exclusive_scan(sum, &tot) + carry;
+        for (int j = 0; j < per; ++j) {
+            const int x = sm[tp_pad(k0 + j)];
+            sm[tp_pad(k0 + j)] = (int)ex;
+            ex += x;
+        }
+        __syncthreads();
+        for (int k = 4 * threadIdx.x; k < m; k += 4 * LANESCAN_THREADS)
+            *reinterpret_cast<int4*>(c.tile_prefix + c0 + k) =
+                make_int4(sm[tp_pad(k)], sm[tp_pad(k + 1)], sm[tp_pad(k + 2)], sm[tp_pad(k + 3)]);
+        carry += tot;
+        __syncthreads();
+    }
+}
+
+// k_lanescan.  Tickets [0, n_lane_tiles): next-snapshot lane offsets (lane
+// tiles, above).  Ticket n_lane_tiles: the leaver prefix per slot tile.
+// Remaining tickets: signal states of the next step for chunks of junctions.
 template <typename Real>
 __global__ void __launch_bounds__(LANESCAN_THREADS) k_lanescan(Ctx<Real> c) {
     if (c.cnt->err & ERR_POISON) return;
     __shared__ int s_tile;
-    __shared__ unsigned long long s_prefix;
     const int n_tickets = c.n_lane_tiles + 1 + c.n_junc_chunks;
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(&c.cnt->ticket_lane, 1);
@@ -309,105 +545,9 @@ __global__ void __launch_bounds__(LANESCAN_THREADS) k_lanescan(Ctx<Real> c) {
         __syncthreads();
         if (tile >= n_tickets) return;
         if (tile < c.n_lane_tiles) {
-            const int base = tile * LANESCAN_TILE + threadIdx.x * LANESCAN_ITEMS;
-            int ns[LANESCAN_ITEMS], lv[LANESCAN_ITEMS];
-            long long tn = 0, tl = 0;
-            if (base + LANESCAN_ITEMS <= c.n_lanes) {
-                // 16-byte loads (base is a multiple of 4)
-                int o[LANESCAN_ITEMS + 1];
-#pragma unroll
-                for (int k = 0; k < LANESCAN_ITEMS; k += 4) {
-                    const int4 ov = *reinterpret_cast<const int4*>(c.cur.off + base + k);
-                    const int4 lvv = *reinterpret_cast<const int4*>(c.leave + base + k);
-                    const int4 env = *reinterpret_cast<const int4*>(c.enter + base + k);
-                    o[k] = ov.x; o[k + 1] = ov.y; o[k + 2] = ov.z; o[k + 3] = ov.w;
-                    lv[k] = lvv.x; lv[k + 1] = lvv.y; lv[k + 2] = lvv.z; lv[k + 3] = lvv.w;
-                    ns[k] = env.x; ns[k + 1] = env.y; ns[k + 2] = env.z; ns[k + 3] = env.w;
-                    *reinterpret_cast<int4*>(c.leave + base + k) = make_int4(0, 0, 0, 0);
-                    *reinterpret_cast<int4*>(c.enter + base + k) = make_int4(0, 0, 0, 0);
-                }
-                o[LANESCAN_ITEMS] = c.cur.off[base + LANESCAN_ITEMS];
-#pragma unroll
-                for (int k = 0; k < LANESCAN_ITEMS; ++k) ns[k] += o[k + 1] - o[k] - lv[k];
-            } else {
-#pragma unroll
-                for (int k = 0; k < LANESCAN_ITEMS; ++k) {
-                    const int l = base + k;
-                    if (l < c.n_lanes) {
-                        const int sz = c.cur.off[l + 1] - c.cur.off[l];
-                        lv[k] = c.leave[l];
-                        ns[k] = sz - lv[k] + c.enter[l];
-                        c.leave[l] = 0;
-                        c.enter[l] = 0;
-                    } else {
-                        ns[k] = 0; lv[k] = 0;
-                    }
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < LANESCAN_ITEMS; ++k) { tn += ns[k]; tl += lv[k]; }
-            const long long packed = (tl << 31) | tn;
-            long long total;
-            const long long excl_in = block_exclusive_scan(packed, &total);
-            if (threadIdx.x < 32) {
-                bool timeout = false;
-                unsigned long long prefix = 0;
-                if (tile == 0) {
-                    if (threadIdx.x == 0) store_release(&c.lane_tiles[0], (2ull << 62) | (unsigned long long)total);
-                } else {
-                    if (threadIdx.x == 0) store_release(&c.lane_tiles[tile], (1ull << 62) | (unsigned long long)total);
-                    prefix = warp_lookback(c.lane_tiles, tile, &timeout);
-                    if (threadIdx.x == 0) {
-                        store_release(&c.lane_tiles[tile], (2ull << 62) | (prefix + (unsigned long long)total));
-                        if (timeout) atomicOr(&c.cnt->err, ERR_TIMEOUT);
-                    }
-                }
-                if (threadIdx.x == 0) s_prefix = prefix;
-            }
-            __syncthreads();
-            long long excl = (long long)s_prefix + excl_in;
-            long long en = excl & ((1ll << 31) - 1), el = excl >> 31;
-#pragma unroll
-            for (int k = 0; k < LANESCAN_ITEMS; ++k) {
-                const int l = base + k;
-                if (l < c.n_lanes) {
-                    c.nxt.off[l] = (int)en;
-                    c.lbefore[l] = (int)el;
-                }
-                en += ns[k]; el += lv[k];
-            }
-            if (tile == c.n_lane_tiles - 1 && threadIdx.x == LANESCAN_THREADS - 1) {
-                c.nxt.off[c.n_lanes] = (int)en;
-                c.cnt->n_next = (int)en;
-            }
+            lanescan_tile(c, tile);
         } else if (tile == c.n_lane_tiles) {
-            // leavers before each slot tile of the current snapshot: every
-            // thread sums a contiguous run of tiles (loads issued together),
-            // one block scan, then the runs are written out; the counters are
-            // zeroed for the next step
-            // (16-byte loads; the arrays are padded to a multiple of 4 * 256
-            // entries and hold zeros beyond the tiles in use)
-            const int nt = (c.cnt->n_cur + TILE - 1) / TILE;
-            const int per4 = (nt + 4 * LANESCAN_THREADS - 1) / (4 * LANESCAN_THREADS);
-            const int k0 = threadIdx.x * per4 * 4;
-            long long run = 0;
-#pragma unroll 4
-            for (int q = 0; q < per4; ++q) {
-                const int4 x = *reinterpret_cast<const int4*>(c.tile_leave + k0 + 4 * q);
-                run += x.x + x.y + x.z + x.w;
-            }
-            long long tot;
-            long long acc = block_exclusive_scan(run, &tot);
-            for (int q = 0; q < per4; ++q) {
-                const int4 x = *reinterpret_cast<const int4*>(c.tile_leave + k0 + 4 * q);
-                int4 p;
-                p.x = (int)acc; acc += x.x;
-                p.y = (int)acc; acc += x.y;
-                p.z = (int)acc; acc += x.z;
-                p.w = (int)acc; acc += x.w;
-                *reinterpret_cast<int4*>(c.tile_prefix + k0 + 4 * q) = p;
-                *reinterpret_cast<int4*>(c.tile_leave + k0 + 4 * q) = make_int4(0, 0, 0, 0);
-            }
+            tile_prefix_scan(c);
         } else {
             // signal states of the next step
             const int j0 = (tile - c.n_lane_tiles - 1) * JUNC_CHUNK;
@@ -516,6 +656,7 @@ __global__ void __launch_bounds__(TILE) k_place(Ctx<Real> c) {
             __threadfence();
             c.cnt->n_cur = c.cnt->n_next;
             c.cnt->n_ent = 0;
+            c.cnt->n_cand = 0;
             c.cnt->ticket_lane = 0;
             c.cnt->done_place = 0;
             int tg = c.cnt->tag + 1;

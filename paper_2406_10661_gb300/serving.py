@@ -35,8 +35,12 @@ from .scenario import Scenario, Stream
 def estimate_device_bytes(scen: Scenario, precision: int = 32) -> int:
     n = int(scen.veh.n)
     r = 16 if precision == 32 else 32
-    per_vehicle = 2 * (r + 16) + 1 + (8 if precision == 32 else 16) + r + 16 + 4 + 4 * 7
-    per_lane = 32 + 2 * 4 + 8 + 3 * 4 + 2 * 4
+    real = 4 if precision == 32 else 8
+    # two snapshots, code, stayer (s, v), entrant records, entrant links,
+    # candidate records and gap heads, per-vehicle tables
+    cand = 64 if precision == 32 else 80
+    per_vehicle = 2 * (r + 16) + 1 + 2 * real + r + 16 + 4 + cand + 8 + 4 * 7
+    per_lane = 32 + 2 * 4 + 8 + 3 * 4 + 2 * 4 + 8
     lanes = int(scen.net.n_lanes)
     return (n * per_vehicle + int(scen.veh.routes.size) * 4 + lanes * per_lane +
             int(scen.net.n_junctions) * 48 + 64 * 1024)
