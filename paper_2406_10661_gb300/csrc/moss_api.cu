@@ -75,7 +75,7 @@ struct MossHandle {
     void* d_cands = nullptr;  // Cand<Real>[cap]
     unsigned long long* d_gap_head = nullptr;
     int n_lane_tiles = 0, max_slot_tiles = 0, n_junc_chunks = 0;
-    Counters* d_cnt = nullptr;
+    Counters* d_cnt = nullptr;  // [2]: per parity; d_cnt[0].err holds the device error bits
     int32_t* d_stage = nullptr;          // setter staging (2 * n_junctions)
     int32_t* h_stage = nullptr;          // pinned host staging of setter arguments (2 * n_junctions)
     cudaEvent_t stage_free = nullptr;    // recorded after the last copy out of h_stage
@@ -269,7 +269,8 @@ Ctx<Real> make_ctx(MossHandle* h, int cur) {
     c.tile_leave = h->d_tile_leave; c.tile_prefix = h->d_tile_prefix; c.lane_tiles = h->d_lane_tiles;
     c.cands = (Cand<Real>*)h->d_cands; c.gap_head = h->d_gap_head;
     c.n_lane_tiles = h->n_lane_tiles; c.max_slot_tiles = h->max_slot_tiles;
-    c.n_junc_chunks = h->n_junc_chunks; c.cnt = h->d_cnt;
+    c.n_junc_chunks = h->n_junc_chunks; c.cnt = h->d_cnt + cur;
+    c.cnt_next = h->d_cnt + (1 - cur); c.err = &h->d_cnt[0].err;
     const MossParams& p = h->prm;
     c.dt = Real(p.dt); c.a_max = Real(p.a_max); c.b_comf = Real(p.b_comf); c.T = Real(p.T);
     c.s0 = Real(p.s0); c.len = Real(p.veh_len); c.pol = Real(p.politeness); c.a_th = Real(p.a_th);
@@ -556,9 +557,9 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
     TRY(upload(h, &h->d_tile_leave, std::vector<int32_t>(tile_cap, 0)));
     TRY(upload(h, &h->d_tile_prefix, std::vector<int32_t>(tile_cap, 0)));
     TRY(upload(h, &h->d_lane_tiles, std::vector<unsigned long long>(h->n_lane_tiles, 0ull)));
-    Counters c0{};
-    c0.tag = 1;
-    TRY(upload(h, &h->d_cnt, std::vector<Counters>(1, c0)));
+    std::vector<Counters> c0(2, Counters{});
+    c0[0].tag = 1;
+    TRY(upload(h, &h->d_cnt, c0));
     TRY(dalloc(h, &h->d_stage, 2 * std::max(NJ, 1)));
     CK(cudaHostAlloc((void**)&h->h_stage, sizeof(int32_t) * 2 * std::max(NJ, 1), cudaHostAllocDefault));
     CK(cudaEventCreateWithFlags(&h->stage_free, cudaEventDisableTiming));
@@ -624,7 +625,7 @@ int scen_state(MossHandle* h, int s, MossState* out) {
     if (s < 0 || s >= h->n_scen) return fail(h, MOSS_EINVAL, "scenario index out of range");
     CK(cudaStreamSynchronize(h->stream));
     Counters c;
-    CK(cudaMemcpy(&c, h->d_cnt, sizeof(c), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&c, h->d_cnt + h->parity, sizeof(c), cudaMemcpyDeviceToHost));
     const int n = c.n_cur, NV = h->n_veh;
     const SnapBufs& b = h->snap[h->parity];
     const size_t ra = reca_size(h->precision);
@@ -900,10 +901,9 @@ int moss_set_state(moss_t h, const MossState* in, int64_t step) {
     long long cur[2] = {n_act, n_arr};
     CK(cudaMemcpy(h->d_metrics + M_CUR_ACTIVE, cur, sizeof(cur), cudaMemcpyHostToDevice));
     Counters c{};
-    CK(cudaMemcpy(&c, h->d_cnt, sizeof(c), cudaMemcpyDeviceToHost));
-    c.n_cur = (int)n_act; c.n_next = (int)n_act; c.n_ent = 0; c.n_cand = 0; c.ticket_lane = 0;
-    c.done_place = 0;
-    CK(cudaMemcpy(h->d_cnt, &c, sizeof(c), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(&c, h->d_cnt + h->parity, sizeof(c), cudaMemcpyDeviceToHost));
+    c.n_cur = (int)n_act; c.n_ent = 0; c.n_cand = 0; c.ticket_lane = 0;
+    CK(cudaMemcpy(h->d_cnt + h->parity, &c, sizeof(c), cudaMemcpyHostToDevice));
     TRY(junction_init(h));
     CK(cudaStreamSynchronize(h->stream));
     return MOSS_OK;

@@ -59,15 +59,17 @@ constexpr int LANESCAN_TILE = LANESCAN_THREADS * LANESCAN_ITEMS;
 constexpr int JUNC_CHUNK = 256;     // junctions per k_lanescan ticket (one per thread)
 constexpr long long SPIN_LIMIT = 1ll << 22;  // bounded waits (~0.5 s with backoff)
 
+// Step counters, one set per parity of the ping-pong snapshots: step t uses
+// the set of its parity and prepares the other one for step t + 1 (that set
+// was last used by step t - 1, which has finished).  err lives in set 0.
 struct Counters {
     int n_cur;       // active vehicles in the current snapshot
-    int n_next;      // active vehicles in the next snapshot
     int n_ent;       // entrants appended this step
-    int ticket_lane; // k_lanescan tickets
-    int done_place;  // k_place blocks finished (the last one closes the step)
-    int err;
-    int tag;         // step tag of the per-lane entrant lists (never 0)
     int n_cand;      // lane-change candidates listed this step (for k_resolve)
+    int ticket_lane; // k_lanescan tickets
+    int tag;         // step tag of the per-lane lists (never 0)
+    int err;         // device error bits (set 0 only)
+    int pad[2];
 };
 
 // snapshot records
@@ -171,7 +173,9 @@ struct Ctx {
     unsigned long long* gap_head;  // [n_veh + n_lanes + 1] (tag << 32 | candidate) or stale
     unsigned long long* lane_tiles;
     int n_lane_tiles, max_slot_tiles, n_junc_chunks;
-    Counters* cnt;
+    Counters* cnt;       // this step's counters
+    Counters* cnt_next;  // the next step's
+    int* err;            // device error bits
     // ---- parameters
     Real dt, a_max, b_comf, T, s0, len, pol, a_th, b_safe, p_att, p_hi, p_lo, band;
     Real inv_2sqrt_ab;  // 1 / (2 sqrt(a b)), computed in double on the host

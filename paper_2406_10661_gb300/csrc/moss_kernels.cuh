@@ -44,7 +44,7 @@ __device__ void insert_departure(const Ctx<Real>& c, int l, int tag) {
     int nl = -1;
     if (r0 < r1) {
         nl = jl_toward(c, c.lane[l], c.routes[r0 + 1]);
-        if (nl < 0) atomicOr(&c.cnt->err, ERR_ROUTE);
+        if (nl < 0) atomicOr(c.err, ERR_ROUTE);
     }
     RecA<Real> A;
     A.s = Real(0); A.v = Real(0); A.id = vid; A.lane = l;
@@ -104,7 +104,7 @@ __device__ __forceinline__ int integrate_emit(const Ctx<Real>& c, MetricAcc& acc
                 break;
             }
             if (!(ex > Real(0))) break;
-            if (++iter > 4 || nl < 0) { atomicOr(&c.cnt->err, ERR_TRANSFER); sn = Ll; break; }
+            if (++iter > 4 || nl < 0) { atomicOr(c.err, ERR_TRANSFER); sn = Ll; break; }
             sn = ex;
             fl |= F_TRANSFER;
             nlane = nl;
@@ -114,7 +114,7 @@ __device__ __forceinline__ int integrate_emit(const Ctx<Real>& c, MetricAcc& acc
             } else {
                 rptr += 1;  // entered the next road
                 nl = (rptr < rlast) ? jl_toward(c, ni, c.routes[rptr + 1]) : -1;
-                if (rptr < rlast && nl < 0) atomicOr(&c.cnt->err, ERR_ROUTE);
+                if (rptr < rlast && nl < 0) atomicOr(c.err, ERR_ROUTE);
             }
             ex = sn - Real(ni.L);
         }
@@ -194,7 +194,7 @@ __device__ __forceinline__ void list_candidate(const Ctx<Real>& c, int i, const 
 #endif
 template <typename Real>
 __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Real> c, int n_work) {
-    if (c.cnt->err & ERR_POISON) return;
+    if (*c.err & ERR_POISON) return;
     const int tag = c.cnt->tag;
     if ((int)blockIdx.x >= n_work) {
         const int stride = (gridDim.x - n_work) * TILE;
@@ -215,9 +215,10 @@ __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Rea
         int leaver = 0;
         if (i < n) {
             const RecA<Real> E = c.cur.a[i];
+            const RecB EB = c.cur.b[i];
             const int lane = E.lane;
             if ((unsigned)lane >= (unsigned)c.n_lanes) {
-                atomicOr(&c.cnt->err, ERR_RANGE);
+                atomicOr(c.err, ERR_RANGE);
             } else {
                 const LaneInfo li = c.lane[lane];
                 const int sc = li.scen;
@@ -226,7 +227,6 @@ __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Rea
                     macc_reset(acc, sc);
                 }
                 const long long t = c.scen_step[sc];
-                const RecB EB = c.cur.b[i];
                 const int b = c.cur.off[lane];
                 const OwnPart<Real> P = decide_own(c, i, E, EB, li, b, t, c.key0[sc], c.key1[sc], c.veh_base[sc]);
                 int fl = 0;
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Rea
 // target lane (granted) or with the stored own-lane kinematics (lost).
 template <typename Real>
 __global__ void __launch_bounds__(TILE) k_resolve(Ctx<Real> c) {
-    if (c.cnt->err & ERR_POISON) return;
+    if (*c.err & ERR_POISON) return;
     const int nc = c.cnt->n_cand;
     const int tag = c.cnt->tag;
     MetricAcc acc;
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(TILE) k_resolve(Ctx<Real> c) {
         const unsigned long long h = c.gap_head[C.gap];
         int q = (int)(h >> 32) == tag ? (int)(unsigned)(h & 0xffffffffull) : -1;
         for (int guard = 0; q >= 0; q = c.cands[q].next) {
-            if (++guard > nc) { atomicOr(&c.cnt->err, ERR_RANGE); break; }
+            if (++guard > nc) { atomicOr(c.err, ERR_RANGE); break; }
             if (q == k) continue;
             const int rbits = c.cands[q].bits;
             if (((rbits & CB_RIGHT) ? 1 : -1) == dir) continue;  // same side: no conflict
@@ -442,7 +442,7 @@ __device__ __forceinline__ void lanescan_tile(const Ctx<Real>& c, int tile) {
             prefix = warp_lookback(c.lane_tiles, tile, &timeout);
             if (threadIdx.x == 0) {
                 store_release(&c.lane_tiles[tile], (2ull << 62) | (prefix + (unsigned long long)total));
-                if (timeout) atomicOr(&c.cnt->err, ERR_TIMEOUT);
+                if (timeout) atomicOr(c.err, ERR_TIMEOUT);
             }
         }
         if (threadIdx.x == 0) s_prefix = prefix;
@@ -470,7 +470,7 @@ __device__ __forceinline__ void lanescan_tile(const Ctx<Real>& c, int tile) {
         }
         if (l0 < nl && nl <= l0 + 4) {  // this thread holds the last lane
             c.nxt.off[nl] = (int)en;
-            c.cnt->n_next = (int)en;
+            c.cnt_next->n_cur = (int)en;
         }
     }
 }
@@ -535,7 +535,7 @@ __device__ __forceinline__ void tile_prefix_scan(const Ctx<Real>& c) {
 // Remaining tickets: signal states of the next step for chunks of junctions.
 template <typename Real>
 __global__ void __launch_bounds__(LANESCAN_THREADS) k_lanescan(Ctx<Real> c) {
-    if (c.cnt->err & ERR_POISON) return;
+    if (*c.err & ERR_POISON) return;
     __shared__ int s_tile;
     const int n_tickets = c.n_lane_tiles + 1 + c.n_junc_chunks;
     for (;;) {
@@ -570,20 +570,32 @@ __device__ __forceinline__ int entrants_ahead(const Ctx<Real>& c, int lane, Real
     for (int q = list_head(c.head, lane, tag); q >= 0; q = c.enext[q]) {
         const RecA<Real> Q = c.ea[q];
         if (ahead(Q.s, Q.id, s, id)) ++cnt;
-        if (++guard > c.n_veh) { atomicOr(&c.cnt->err, ERR_RANGE); break; }
+        if (++guard > c.n_veh) { atomicOr(c.err, ERR_RANGE); break; }
     }
     return cnt;
 }
 
 template <typename Real>
 __global__ void __launch_bounds__(TILE) k_place(Ctx<Real> c) {
-    if (c.cnt->err & ERR_POISON) return;
+    if (*c.err & ERR_POISON) return;
     __shared__ int s_warp[TILE / 32];
     const int n = c.cnt->n_cur;
     const int n_ent = c.cnt->n_ent;
     const int tag = c.cnt->tag;
     const int n_tiles = (n + TILE - 1) / TILE;
     const int lane_id = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // closing the step: the next step's counters (k_lanescan already wrote
+    // its vehicle count) and every scenario's clock; no kernel of this step
+    // reads them after this point
+    if (blockIdx.x == 0) {
+        if (threadIdx.x == 0) {
+            c.cnt_next->n_ent = 0;
+            c.cnt_next->n_cand = 0;
+            c.cnt_next->ticket_lane = 0;
+            c.cnt_next->tag = tag >= 0x3fffffff ? 1 : tag + 1;
+        }
+        for (int s = threadIdx.x; s < c.n_scen; s += TILE) c.scen_step[s] += 1;
+    }
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int i = tile * TILE + threadIdx.x;
         const bool valid = i < n;
@@ -610,7 +622,7 @@ __global__ void __launch_bounds__(TILE) k_place(Ctx<Real> c) {
             const int stay_rank = (i - c.cur.off[lane]) - (leavers_before - c.lbefore[lane]);
             const int pos = c.nxt.off[lane] + stay_rank + entrants_ahead(c, lane, w.s, A.id, tag);
             if (pos < c.nxt.off[lane] || pos >= c.nxt.off[lane + 1]) {
-                atomicOr(&c.cnt->err, ERR_RANGE);
+                atomicOr(c.err, ERR_RANGE);
             } else {
                 RecA<Real> O;
                 O.s = w.s; O.v = w.v; O.id = A.id; O.lane = lane;
@@ -635,7 +647,7 @@ __global__ void __launch_bounds__(TILE) k_place(Ctx<Real> c) {
             rank += entrants_ahead(c, lane, Q.s, Q.id, tag);
             const int pos = c.nxt.off[lane] + rank;
             if (pos < c.nxt.off[lane] || pos >= c.nxt.off[lane + 1]) {
-                atomicOr(&c.cnt->err, ERR_RANGE);
+                atomicOr(c.err, ERR_RANGE);
             } else {
                 c.nxt.a[pos] = Q;
                 c.nxt.b[pos] = c.eb[q];
@@ -645,26 +657,6 @@ __global__ void __launch_bounds__(TILE) k_place(Ctx<Real> c) {
     // clear the lane look-back words for the next step (k_lanescan is done)
     for (int k = blockIdx.x * TILE + threadIdx.x; k < c.n_lane_tiles; k += gridDim.x * TILE)
         c.lane_tiles[k] = 0ull;
-    // the last block to finish closes the step: publish the next snapshot
-    // size, reset the step counters, advance the list tag and every
-    // scenario's clock
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const int done = atomicAdd(&c.cnt->done_place, 1);
-        if (done == (int)gridDim.x - 1) {
-            __threadfence();
-            c.cnt->n_cur = c.cnt->n_next;
-            c.cnt->n_ent = 0;
-            c.cnt->n_cand = 0;
-            c.cnt->ticket_lane = 0;
-            c.cnt->done_place = 0;
-            int tg = c.cnt->tag + 1;
-            c.cnt->tag = tg > 0x3fffffff ? 1 : tg;
-            for (int s = 0; s < c.n_scen; ++s) c.scen_step[s] += 1;
-            __threadfence();
-        }
-    }
 }
 
 // signal states for the current step of every junction (after creation or
