@@ -89,15 +89,23 @@ template <typename Real> struct alignas(2 * sizeof(Real)) SV { Real s, v; };
 // for two candidates exactly when they enter the same lane between the same
 // target leader and follower (unique over lanes: lane l's positions span
 // [off[l], off[l+1]], shifted by l).  Candidates of one gap form a list
-// (gap_head, next).  The own-lane kinematics are kept for a lost conflict.
+// (gap_head, next).  The record carries everything the update needs for
+// either outcome: the vehicle's records and its kinematics on the target
+// lane (granted) and on its own lane (lost a conflict).
 template <typename Real>
 struct alignas(16) Cand {
-    int slot, gap, TL, nlt;  // slot; gap key; target leader slot (-1 none); next lane from the target lane
-    int next, bits, id, nl;  // list link; CB_* bits; vehicle id; own next lane
-    Real u, scale;           // utility of the chosen side and its flag scale (R22)
-    Real a, lgap, sgap;      // own-lane acceleration, leader gap, stop-line gap
+    RecA<Real> E;            // the vehicle's snapshot records
+    RecB EB;
+    int slot, gap, next, bits;  // slot; gap key; list link; CB_* bits
+    int nl, tnl, scen, pad;     // next lane from the own / the target lane; scenario
+    Real u, scale;              // utility of the chosen side and its flag scale (R22)
+    Real a, lgap, sgap;         // own lane: acceleration, leader gap, stop-line gap
+    Real ta, tlgap, tsgap;      // target lane: the same
 };
-enum : int { CB_RIGHT = 1, CB_FLAG = 2, CB_LEADER = 4, CB_STOP = 8, CB_OVERLAP = 16 };
+enum : int {
+    CB_RIGHT = 1, CB_FLAG = 2, CB_LEADER = 4, CB_STOP = 8, CB_OVERLAP = 16, CB_TLEADER = 32, CB_TSTOP = 64,
+    CB_TOVERLAP = 128
+};
 
 // One 32-byte record per lane.
 //   road lane:     lo, hi = lanes [lo, hi) of its road (left to right); jb, je =

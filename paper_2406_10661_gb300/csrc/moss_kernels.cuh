@@ -162,19 +162,25 @@ __device__ __forceinline__ int integrate_emit(const Ctx<Real>& c, MetricAcc& acc
 // A lane-change candidate leaves its decision for k_resolve: a record in the
 // candidate list, linked into the list of its target gap.
 template <typename Real>
-__device__ __forceinline__ void list_candidate(const Ctx<Real>& c, int i, const RecA<Real>& E,
-                                               const Decision<Real>& D, int tag) {
+__device__ __forceinline__ void list_candidate(const Ctx<Real>& c, int i, const RecA<Real>& E, const RecB& EB,
+                                               int sc, const Decision<Real>& D, int tag) {
     int gp;
     if (D.TF >= 0) gp = D.TF;
     else if (D.TL >= 0) gp = D.TL + 1;
     else gp = c.cur.off[D.tl];
+    const LaneInfo ti = c.lane[D.tl];
+    const LaneAcc<Real> T =
+        accel_on_lane(c, ti, E.s, E.v, Real(EB.v0f) * Real(ti.vmax), D.TL, D.nlt, EB.rptr, EB.rlast);
     Cand<Real> C;
-    C.slot = i; C.gap = gp + D.tl; C.TL = D.TL; C.nlt = D.nlt;
+    C.E = E; C.EB = EB;
+    C.slot = i; C.gap = gp + D.tl;
     C.bits = (D.dir > 0 ? CB_RIGHT : 0) | (D.flag ? CB_FLAG : 0) | (D.own.has_leader ? CB_LEADER : 0) |
-             (D.own.stop ? CB_STOP : 0) | (D.own.overlap ? CB_OVERLAP : 0);
-    C.id = E.id; C.nl = D.own.nl;
+             (D.own.stop ? CB_STOP : 0) | (D.own.overlap ? CB_OVERLAP : 0) | (T.has_leader ? CB_TLEADER : 0) |
+             (T.stop ? CB_TSTOP : 0) | (T.overlap ? CB_TOVERLAP : 0);
+    C.nl = D.own.nl; C.tnl = T.nl; C.scen = sc; C.pad = 0;
     C.u = D.u; C.scale = D.scale;
     C.a = D.own.a; C.lgap = D.own.gap; C.sgap = D.own.stop_gap;
+    C.ta = T.a; C.tlgap = T.gap; C.tsgap = T.stop_gap;
     const int k = warp_claim(&c.cnt->n_cand);
     const unsigned long long prev =
         atomicExch(&c.gap_head[C.gap], ((unsigned long long)(unsigned)tag << 32) | (unsigned)k);
@@ -236,7 +242,7 @@ __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Rea
                     const Decision<Real> D = decide_mobil(c, i, E, EB, li, b, c.cur.off[lane + 1], P.own, P.u_lc,
                                                           P.u_dir);
                     if (D.cand) {
-                        list_candidate(c, i, E, D, tag);
+                        list_candidate(c, i, E, EB, sc, D, tag);
                         cand = true;
                     }
                     fl = D.flag ? F_FLAGGED : 0;
@@ -269,12 +275,11 @@ __global__ void __launch_bounds__(TILE) k_resolve(Ctx<Real> c) {
     for (int k = blockIdx.x * TILE + threadIdx.x; k < nc; k += gridDim.x * TILE) {
         const Cand<Real> C = c.cands[k];
         const int i = C.slot;
-        const RecA<Real> E = c.cur.a[i];
-        const RecB EB = c.cur.b[i];
+        const RecA<Real> E = C.E;
+        const RecB EB = C.EB;
         const int lane = E.lane;
         const int dir = (C.bits & CB_RIGHT) ? 1 : -1;
-        const int tl = lane + dir;
-        const int sc = c.lane[lane].scen;
+        const int sc = C.scen;
         if (sc != acc.scen) {
             macc_flush_thread(acc, c.metrics);
             macc_reset(acc, sc);
@@ -292,15 +297,17 @@ __global__ void __launch_bounds__(TILE) k_resolve(Ctx<Real> c) {
             const Real ru = c.cands[q].u, rs = c.cands[q].scale;
             const Real sc2 = C.scale > rs ? C.scale : rs;
             if (rabs(C.u - ru) < c.band * sc2) fl |= F_FLAGGED;
-            if (!(C.u > ru || (C.u == ru && C.id < c.cands[q].id))) granted = false;
+            if (!(C.u > ru || (C.u == ru && E.id < c.cands[q].E.id))) granted = false;
         }
         LaneAcc<Real> la;
         int nlane = lane;
         if (granted) {
             fl |= F_CHANGED;
-            nlane = tl;
-            const LaneInfo ti = c.lane[tl];
-            la = accel_on_lane(c, ti, E.s, E.v, Real(EB.v0f) * Real(ti.vmax), C.TL, C.nlt, EB.rptr, EB.rlast);
+            nlane = lane + dir;
+            la.a = C.ta; la.gap = C.tlgap; la.stop_gap = C.tsgap; la.nl = C.tnl;
+            la.has_leader = (C.bits & CB_TLEADER) != 0;
+            la.stop = (C.bits & CB_TSTOP) != 0;
+            la.overlap = (C.bits & CB_TOVERLAP) != 0;
         } else {
             fl |= F_CONFLICT_LOST;
             la.a = C.a; la.gap = C.lgap; la.stop_gap = C.sgap; la.nl = C.nl;

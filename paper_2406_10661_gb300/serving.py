@@ -38,7 +38,7 @@ def estimate_device_bytes(scen: Scenario, precision: int = 32) -> int:
     real = 4 if precision == 32 else 8
     # two snapshots, code, stayer (s, v), entrant records, entrant links,
     # candidate records and gap heads, per-vehicle tables
-    cand = 64 if precision == 32 else 80
+    cand = 96 if precision == 32 else 144
     per_vehicle = 2 * (r + 16) + 1 + 2 * real + r + 16 + 4 + cand + 8 + 4 * 7
     per_lane = 32 + 2 * 4 + 8 + 3 * 4 + 2 * 4 + 8
     lanes = int(scen.net.n_lanes)
