@@ -36,7 +36,7 @@ DECISION_NAMES = ("a_own", "eligible", "attempted", "cand", "dir", "u", "uL", "u
 
 F_FLAGGED, F_CHANGED, F_CANDIDATE, F_TRANSFER, F_ARRIVED, F_INSERTED, F_CONFLICT_LOST = (
     1, 2, 4, 8, 16, 32, 64)
-POLICY_FIXED, POLICY_MANUAL, POLICY_NONE = 0, 1, 2
+POLICY_FIXED, POLICY_MANUAL, POLICY_NONE, POLICY_MAX_PRESSURE = 0, 1, 2, 3
 LIGHT_GREEN, LIGHT_AMBER, LIGHT_RED = 0, 1, 2
 
 
@@ -73,6 +73,7 @@ def _setup(lib):
     lib.mo_set_signal.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, vp]
     lib.mo_light.argtypes = [vp, ctypes.c_int, ctypes.c_long]
     lib.mo_light.restype = ctypes.c_int
+    lib.mo_signal_state.argtypes = [vp, ctypes.c_int, vp]
     lib.mo_idm.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     lib.mo_idm.restype = ctypes.c_double
     lib.mo_idm_free.argtypes = [vp, ctypes.c_double, ctypes.c_double]
@@ -165,6 +166,13 @@ class Oracle:
         j = np.ascontiguousarray(junctions, dtype=np.int32)
         ph = np.ascontiguousarray(phases if phases is not None else np.zeros(len(j)), dtype=np.int32)
         self._lib.mo_set_signal(self.h, len(j), _p(j), int(policy), _p(ph))
+
+    def signal_state(self, j: int):
+        """Max-pressure state of junction j: (phase, steps in the current green
+        or amber interval, phase after the amber or -1)."""
+        out = np.zeros(3, dtype=np.int32)
+        self._lib.mo_signal_state(self.h, int(j), _p(out))
+        return int(out[0]), int(out[1]), int(out[2])
 
     def light(self, jl: int, t: int) -> int:
         return int(self._lib.mo_light(self.h, int(jl), ctypes.c_long(int(t))))

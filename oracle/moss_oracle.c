@@ -67,6 +67,18 @@
  *       departure time) over finished trips.
  *   R22 a decision whose deciding quantity is within flag_band (scaled) of
  *       its threshold is flagged.
+ *   R23 max pressure (§3.2 MAX_PRESSURE policy; App. B.2 prepare stream 1 /
+ *       update stream 2; Varaiya 2013): the pressure of a movement (a
+ *       junction lane) is the number of vehicles on the road lane it leaves
+ *       minus the number on the road lane it feeds, counted in the step's
+ *       snapshot; the pressure of a phase is the sum over the junction lanes
+ *       green in it.  A junction holds its phase for at least the phase's
+ *       programmed green time; from then on, at the end of every step it
+ *       takes the phase of maximal pressure (its current phase when that one
+ *       is maximal, else the smallest index among the maxima) for the next
+ *       step.  A change of phase goes through the current phase's programmed
+ *       amber (lanes green in both phases stay green, as in R19).  Setting
+ *       the policy starts the phase the junction shows at that step, green.
  */
 #include <math.h>
 #include <stdint.h>
@@ -98,7 +110,7 @@ static double unit24(uint32_t w) { return (double)(w >> 8) * (1.0 / 16777216.0);
 
 /* ------------------------------------------------------------------------ */
 enum { LIGHT_GREEN = 0, LIGHT_AMBER = 1, LIGHT_RED = 2 };
-enum { POLICY_FIXED = 0, POLICY_MANUAL = 1, POLICY_NONE = 2 };
+enum { POLICY_FIXED = 0, POLICY_MANUAL = 1, POLICY_NONE = 2, POLICY_MAXP = 3 };
 enum { ST_WAITING = 0, ST_ACTIVE = 1, ST_ARRIVED = 2 };
 enum {
     F_FLAGGED = 1, F_CHANGED = 2, F_CANDIDATE = 4, F_TRANSFER = 8,
@@ -114,6 +126,8 @@ typedef struct {
     int *jl_target, *jl_junction, *jl_mask; /* indexed by absolute lane id */
     int *junc_offset, *junc_phase_off, *phase_green, *phase_amber;
     int *junc_policy, *junc_manual;
+    int *jl_from;                      /* road lane a junction lane leaves (absolute ids) */
+    int *mp_phase, *mp_elapsed, *mp_pending; /* max-pressure state per junction (R23) */
     /* vehicles */
     int n_veh;
     int *route_off, *routes, *start_lane, *dep;
@@ -194,6 +208,13 @@ void* mo_create(int n_roads, const int* road_lane_off, int n_lanes, int n_road_l
     }
     for (int j = 0; j < n_junctions; ++j)
         O->junc_policy[j] = (junc_phase_off[j + 1] > junc_phase_off[j]) ? POLICY_FIXED : POLICY_NONE;
+    O->jl_from = (int*)xcalloc(n_lanes, sizeof(int));
+    for (int l = 0; l < n_lanes; ++l) O->jl_from[l] = -1;
+    for (int l = 0; l < n_road_lanes; ++l)
+        for (int jl = jl_off[l]; jl < jl_off[l + 1]; ++jl) O->jl_from[jl] = l;
+    O->mp_phase = (int*)xcalloc(n_junctions, sizeof(int));
+    O->mp_elapsed = (int*)xcalloc(n_junctions, sizeof(int));
+    O->mp_pending = (int*)xcalloc(n_junctions, sizeof(int));
 
     O->route_off = (int*)xcalloc(n_veh + 1, sizeof(int));
     memcpy(O->route_off, route_off, sizeof(int) * (n_veh + 1));
@@ -253,7 +274,7 @@ void mo_destroy(void* h) {
     void* ptrs[] = {O->road_lane_off, O->lane_road, O->L, O->vmax, O->jl_off, O->jl_target,
                     O->jl_junction, O->jl_mask, O->junc_offset, O->junc_phase_off,
                     O->phase_green, O->phase_amber, O->junc_policy, O->junc_manual,
-                    O->route_off, O->routes, O->start_lane, O->dep, O->v0f, O->status,
+                    O->jl_from, O->mp_phase, O->mp_elapsed, O->mp_pending, O->route_off, O->routes, O->start_lane, O->dep, O->v0f, O->status,
                     O->lane, O->rc, O->flags, O->s, O->v, O->q_off, O->q_ids, O->q_head};
     for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); ++i) free(ptrs[i]);
     free(O);
@@ -261,39 +282,123 @@ void mo_destroy(void* h) {
 
 /* ------------------------------------------------------------------------ */
 /* Signals (§3.2 policies; reading R19)                                       */
-int mo_light(void* h, int jl, long t) {
-    Oracle* O = (Oracle*)h;
-    int j = O->jl_junction[jl];
-    int mask = O->jl_mask[jl];
-    if (O->junc_policy[j] == POLICY_NONE) return LIGHT_GREEN;
-    if (O->junc_policy[j] == POLICY_MANUAL)
-        return ((mask >> O->junc_manual[j]) & 1) ? LIGHT_GREEN : LIGHT_RED;
+/* phase of junction j's fixed-time program at step t, and whether that step
+ * is in the phase's amber (R19); -1 if the junction has no phases */
+static int fixed_phase(const Oracle* O, int j, long t, int* in_amber) {
     int p0 = O->junc_phase_off[j], P = O->junc_phase_off[j + 1] - p0;
     long cycle = 0;
     for (int p = 0; p < P; ++p) cycle += O->phase_green[p0 + p] + O->phase_amber[p0 + p];
-    if (cycle <= 0) return LIGHT_GREEN;
+    *in_amber = 0;
+    if (P == 0 || cycle <= 0) return -1;
     long c = (t + O->junc_offset[j]) % cycle;
     if (c < 0) c += cycle;
     for (int p = 0; p < P; ++p) {
         long g = O->phase_green[p0 + p], a = O->phase_amber[p0 + p];
         if (c < g + a) {
-            if (!((mask >> p) & 1)) return LIGHT_RED;
-            if (c < g) return LIGHT_GREEN;
-            int nxt = (p + 1) % P;
-            return ((mask >> nxt) & 1) ? LIGHT_GREEN : LIGHT_AMBER;
+            *in_amber = c >= g;
+            return p;
         }
         c -= g + a;
     }
-    return LIGHT_RED; /* not reached */
+    return -1; /* not reached */
 }
 
-/* policy for n junctions; phases may be NULL unless policy == MANUAL */
+int mo_light(void* h, int jl, long t) {
+    Oracle* O = (Oracle*)h;
+    int j = O->jl_junction[jl];
+    int mask = O->jl_mask[jl];
+    int P = O->junc_phase_off[j + 1] - O->junc_phase_off[j];
+    if (O->junc_policy[j] == POLICY_NONE) return LIGHT_GREEN;
+    if (O->junc_policy[j] == POLICY_MANUAL)
+        return ((mask >> O->junc_manual[j]) & 1) ? LIGHT_GREEN : LIGHT_RED;
+    if (O->junc_policy[j] == POLICY_MAXP) {
+        if (P == 0) return LIGHT_GREEN;
+        int p = O->mp_phase[j], q = O->mp_pending[j];
+        if (!((mask >> p) & 1)) return LIGHT_RED;
+        if (q < 0) return LIGHT_GREEN;
+        return ((mask >> q) & 1) ? LIGHT_GREEN : LIGHT_AMBER;
+    }
+    int amber;
+    int p = fixed_phase(O, j, t, &amber);
+    if (p < 0) return LIGHT_GREEN;
+    if (!((mask >> p) & 1)) return LIGHT_RED;
+    if (!amber) return LIGHT_GREEN;
+    int nxt = (p + 1) % P;
+    return ((mask >> nxt) & 1) ? LIGHT_GREEN : LIGHT_AMBER;
+}
+
+/* policy for n junctions; phases may be NULL unless policy == MANUAL.  A
+ * junction switched to max pressure starts, green, the phase it shows at the
+ * current step (R23). */
 void mo_set_signal(void* h, int n, const int* junctions, int policy, const int* phases) {
     Oracle* O = (Oracle*)h;
     for (int k = 0; k < n; ++k) {
-        O->junc_policy[junctions[k]] = policy;
-        if (policy == POLICY_MANUAL) O->junc_manual[junctions[k]] = phases[k];
+        int j = junctions[k];
+        if (policy == POLICY_MAXP) {
+            int shown = 0;
+            if (O->junc_policy[j] == POLICY_FIXED) {
+                int amber;
+                int p = fixed_phase(O, j, O->step, &amber);
+                shown = p < 0 ? 0 : p;
+            } else if (O->junc_policy[j] == POLICY_MANUAL) {
+                shown = O->junc_manual[j];
+            } else if (O->junc_policy[j] == POLICY_MAXP) {
+                shown = O->mp_phase[j];
+            }
+            O->mp_phase[j] = shown;
+            O->mp_elapsed[j] = 1;
+            O->mp_pending[j] = -1;
+        }
+        O->junc_policy[j] = policy;
+        if (policy == POLICY_MANUAL) O->junc_manual[j] = phases[k];
     }
+}
+
+/* max-pressure state of junction j: out = [phase, steps in the current green
+ * or amber interval (counting the current step), phase after the amber or
+ * -1 while green] */
+void mo_signal_state(void* h, int j, int* out) {
+    Oracle* O = (Oracle*)h;
+    out[0] = O->mp_phase[j]; out[1] = O->mp_elapsed[j]; out[2] = O->mp_pending[j];
+}
+
+/* Advance every max-pressure junction from step t to t+1 using the lane
+ * counts of the step-t snapshot (R23). */
+static void maxp_advance(Oracle* O, const int* lane_cnt) {
+    long* press = (long*)xcalloc((size_t)O->n_junctions * 8, sizeof(long));
+    for (int jl = O->n_road_lanes; jl < O->n_lanes; ++jl) {
+        int j = O->jl_junction[jl];
+        if (O->junc_policy[j] != POLICY_MAXP) continue;
+        long d = (long)lane_cnt[O->jl_from[jl]] - (long)lane_cnt[O->jl_target[jl]];
+        for (int p = 0; p < 8; ++p)
+            if ((O->jl_mask[jl] >> p) & 1) press[(size_t)j * 8 + p] += d;
+    }
+    for (int j = 0; j < O->n_junctions; ++j) {
+        if (O->junc_policy[j] != POLICY_MAXP) continue;
+        int p0 = O->junc_phase_off[j], P = O->junc_phase_off[j + 1] - p0;
+        if (P == 0) continue;
+        int p = O->mp_phase[j], q = O->mp_pending[j], e = O->mp_elapsed[j];
+        if (q >= 0) {                               /* amber of p, towards q */
+            if (e >= O->phase_amber[p0 + p]) { p = q; q = -1; e = 1; }
+            else e += 1;
+        } else if (e >= O->phase_green[p0 + p]) {  /* minimum green served */
+            int best = p;
+            for (int k = 0; k < P; ++k) {
+                long pk = press[(size_t)j * 8 + k], pb = press[(size_t)j * 8 + best];
+                if (pk > pb || (pk == pb && best != p && k < best)) best = k;
+            }
+            if (best != p) {
+                if (O->phase_amber[p0 + p] > 0) { q = best; e = 1; }
+                else { p = best; e = 1; }
+            } else {
+                e += 1;
+            }
+        } else {
+            e += 1;
+        }
+        O->mp_phase[j] = p; O->mp_pending[j] = q; O->mp_elapsed[j] = e;
+    }
+    free(press);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -731,6 +836,7 @@ static void step_once(Oracle* O) {
         O->m_inserted++;
     }
     free(D); free(granted);
+    maxp_advance(O, S.lane_cnt);
     snap_free(&S);
     O->step = t + 1;
 }

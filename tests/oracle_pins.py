@@ -377,9 +377,132 @@ def check_permutation_invariance(libpath=None, steps=150):
     assert o1.metrics() == o2.metrics()
 
 
+# ---------------------------------------------------------------------------
+# Max pressure (reading R23), pinned to its definition written out here:
+# movement pressure = vehicles on the road lane a junction lane leaves minus
+# vehicles on the road lane it feeds (snapshot counts); phase pressure = sum
+# over the junction lanes green in the phase; the current phase is kept when
+# it is maximal, else the smallest index among the maxima.
+def _mp_definition(net, counts, j, current):
+    nrl = net.n_road_lanes
+    frm = np.full(net.n_lanes, -1, dtype=np.int64)
+    for l in range(nrl):
+        frm[net.jl_off[l]:net.jl_off[l + 1]] = l
+    P = int(net.junc_phase_off[j + 1] - net.junc_phase_off[j])
+    press = [0] * P
+    for jl in range(nrl, net.n_lanes):
+        k = jl - nrl
+        if net.jl_junction[k] != j:
+            continue
+        d = int(counts[frm[jl]]) - int(counts[net.jl_target[k]])
+        for p in range(P):
+            if (int(net.jl_mask[k]) >> p) & 1:
+                press[p] += d
+    m = max(press)
+    if press[current] == m:
+        return current
+    return press.index(m)
+
+
+def _parked(net, cars):
+    """Vehicles standing still on road lanes: cars = list of (lane, s); each
+    drives a one-road route on its lane's road.  Returns (vehicles, state)."""
+    lr = net.lane_road()
+    n = len(cars)
+    lanes = np.array([c[0] for c in cars], dtype=np.int32)
+    veh = sc.Vehicles(n=n, route_off=np.arange(n + 1, dtype=np.int32), routes=lr[lanes].astype(np.int32),
+                      start_lane=lanes, dep=np.zeros(n, dtype=np.int32), v0f=np.ones(n, dtype=np.float32))
+    st = dict(status=np.ones(n, dtype=np.int32), lane=lanes.copy(),
+              s=np.array([c[1] for c in cars], dtype=np.float64), v=np.zeros(n), rc=np.zeros(n, dtype=np.int32))
+    return veh, st
+
+
+def check_max_pressure_argmax(libpath=None):
+    """R23 with one-step phases (green 1, amber 0): after one step every
+    junction of a 3x3 grid shows the phase of maximal pressure of the
+    snapshot, for random vehicle counts (brute force against the definition)."""
+    net = sc.grid_network(3, length=200.0, lanes=2, green=1, amber=0)
+    rng = np.random.default_rng(5)
+    for trial in range(12):
+        n = int(rng.integers(5, 60))
+        lanes = rng.integers(0, net.n_road_lanes, n)
+        cars = [(int(l), float(rng.uniform(10.0, 190.0))) for l in lanes]
+        veh, st = _parked(net, cars)
+        scen = sc.Scenario(net, veh, sc.Params(), "mp")
+        t0 = int(rng.integers(0, 40))
+        o = _oracle(scen, st, libpath, step=t0)
+        o.set_signal(list(range(net.n_junctions)), oracle.POLICY_MAX_PRESSURE)
+        counts = np.bincount(lanes, minlength=net.n_lanes)
+        before = [o.signal_state(j) for j in range(net.n_junctions)]
+        o.step(1)
+        for j in range(net.n_junctions):
+            exp = _mp_definition(net, counts, j, before[j][0])
+            assert o.signal_state(j) == (exp, 1, -1) if exp != before[j][0] else o.signal_state(j) == (exp, 2, -1), \
+                (trial, j, o.signal_state(j), exp)
+
+
+def check_max_pressure_timing(libpath=None):
+    """R23 timing, worked by hand: the centre junction of a 3x3 grid (phases of
+    30 s green + 3 s amber) is switched to max pressure at step 66, while its
+    fixed program shows phase 2; five cars wait on one approach whose
+    movements are all red in phase 2.  The junction keeps phase 2 for its 30
+    green steps (steps 66-95), shows 3 amber steps (96-98) and turns to the
+    phase of maximal pressure at step 99."""
+    net = sc.grid_network(3, length=200.0, lanes=1, green=30, amber=3)
+    j = 4
+    nrl = net.n_road_lanes
+    # an approach of the centre junction that is red in phase 2
+    lr = net.lane_road()
+    lane_in = None
+    for l in range(nrl):
+        if net.road_to[lr[l]] != j:
+            continue
+        masks = net.jl_mask[net.jl_off[l] - nrl:net.jl_off[l + 1] - nrl]
+        if all(((int(m) >> 2) & 1) == 0 for m in masks):
+            lane_in = l
+            break
+    assert lane_in is not None
+    L = float(net.lane_length[lane_in])
+    counts = np.zeros(net.n_lanes, dtype=np.int64)
+    counts[lane_in] = 5
+    best = _mp_definition(net, counts, j, 2)
+    assert best != 2
+    jl_through = [jl for jl in range(net.jl_off[lane_in], net.jl_off[lane_in + 1])
+                  if (int(net.jl_mask[jl - nrl]) >> best) & 1][0]
+    # the five cars drive through that movement (a two-road route)
+    r_in, r_out = int(lr[lane_in]), int(lr[net.jl_target[jl_through - nrl]])
+    n = 5
+    veh = sc.Vehicles(n=n, route_off=np.arange(0, 2 * n + 1, 2, dtype=np.int32),
+                      routes=np.array([r_in, r_out] * n, dtype=np.int32),
+                      start_lane=np.full(n, lane_in, dtype=np.int32), dep=np.zeros(n, dtype=np.int32),
+                      v0f=np.ones(n, dtype=np.float32))
+    st = dict(status=np.ones(n, dtype=np.int32), lane=np.full(n, lane_in, dtype=np.int32),
+              s=np.array([L - 1.0 - 8.0 * k for k in range(n)]), v=np.zeros(n), rc=np.zeros(n, dtype=np.int32))
+    scen = sc.Scenario(net, veh, sc.Params(), "mp")
+    o = _oracle(scen, st, libpath, step=66)
+    o.set_signal([j], oracle.POLICY_MAX_PRESSURE)
+    for k in range(40):
+        st_k = o.signal_state(j)
+        if k <= 29:
+            assert st_k == (2, k + 1, -1), (k, st_k)
+            assert o.light(jl_through, 66 + k) == oracle.LIGHT_RED
+        elif k <= 32:
+            assert st_k == (2, k - 29, best), (k, st_k)
+            assert o.light(jl_through, 66 + k) == oracle.LIGHT_RED
+        elif k == 33:
+            assert st_k == (best, 1, -1), (k, st_k)
+            assert o.light(jl_through, 66 + k) == oracle.LIGHT_GREEN
+        if k <= 33:
+            assert (o.state()["lane"] == lane_in).all()  # the queue stays until the green
+        elif k == 39:
+            assert (o.state()["lane"] != lane_in).any()  # and moves on after it
+        o.step(1)
+
+
 ALL_CHECKS = [
     check_idm_free_road, check_idm_equilibrium, check_p_lc, check_mobil_case_A,
     check_mobil_case_B, check_mobil_case_C, check_mobil_case_D, check_mobil_mirror, check_neighbours_bruteforce,
     check_free_road_vs_rk4, check_platoon_equilibrium, check_red_light, check_signal_program,
-    check_arrival_and_travel_time, check_insertion, check_conflict,
+    check_arrival_and_travel_time, check_insertion, check_conflict, check_max_pressure_argmax,
+    check_max_pressure_timing,
 ]

@@ -31,6 +31,14 @@ MUTATIONS = [
     ("transfer_keeps_offset", "s_new -= Ll;\n", "\n"),
     ("conflict_smaller_wins", "return Dx->u > Dy->u ||", "return Dx->u < Dy->u ||"),
     ("ballistic_euler_position", "disp = v * dt + 0.5 * a * dt * dt;", "disp = v * dt;"),
+    ("maxp_pressure_sign", "long d = (long)lane_cnt[O->jl_from[jl]] - (long)lane_cnt[O->jl_target[jl]];",
+     "long d = (long)lane_cnt[O->jl_target[jl]] - (long)lane_cnt[O->jl_from[jl]];"),
+    ("maxp_upstream_only", "long d = (long)lane_cnt[O->jl_from[jl]] - (long)lane_cnt[O->jl_target[jl]];",
+     "long d = (long)lane_cnt[O->jl_from[jl]];"),
+    ("maxp_no_amber", "if (O->phase_amber[p0 + p] > 0) { q = best; e = 1; }", "if (0) { q = best; e = 1; }"),
+    ("maxp_min_green_off_by_one", "} else if (e >= O->phase_green[p0 + p]) {", "} else if (e > O->phase_green[p0 + p]) {"),
+    ("maxp_ties_to_smallest", "if (pk > pb || (pk == pb && best != p && k < best)) best = k;",
+     "if (pk > pb || (pk == pb && k < best)) best = k;"),
 ]
 
 BATTERY = r"""
