@@ -111,7 +111,7 @@ def city(args):
     return sc.city_scenario(seed=args.seed)
 
 
-def cpu_oracle_rate(scen, state, budget_s=15.0, max_road=4000, steps_cap=60):
+def cpu_oracle_rate(scen, state, budget_s=15.0, max_road=4000, steps_cap=60, max_pressure=False):
     """The FP64 oracle, as it stands, on the roads with id < max_road of the
     given state (a contiguous band of the grid at the same density)."""
     import oracle
@@ -119,6 +119,8 @@ def cpu_oracle_rate(scen, state, budget_s=15.0, max_road=4000, steps_cap=60):
     sample = sc.region_sample(state, scen.net, max_road)
     o = oracle.Oracle(scen.net, scen.veh, scen.params)
     o.set_state(sample["status"], sample["lane"], sample["s"], sample["v"], sample["rc"], T_WARM)
+    if max_pressure:
+        o.set_signal(list(range(scen.net.n_junctions)), oracle.POLICY_MAX_PRESSURE)
     o.step(1)  # untimed warm-up
     m0 = o.metrics()
     t0 = time.perf_counter()
@@ -201,6 +203,9 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     with torch.cuda.stream(stream):
         sim = binding.Simulation(scen.net, scen.veh, scen.params, precision=32, stream=stream.cuda_stream)
+        mp = args.policy == "max_pressure"
+        if mp:  # every junction under the adaptive max-pressure policy from step 0
+            sim.set_signal_policy(np.arange(scen.net.n_junctions, dtype=np.int32), binding.POLICY_MAX_PRESSURE)
         sim.step(T_WARM)  # set-up: the simulation reaches its own step-3600 state
         state0 = sim.state() if world == 1 else None
         for _ in range(args.warmup):
@@ -258,7 +263,8 @@ def run_ours(args):
 
         # end to end through the public API: every step the host writes the
         # signal actions of all junctions (pinned host arrays -> device), steps,
-        # and reads the metrics back (device -> host)
+        # and reads the metrics back (device -> host); under max pressure the
+        # junctions decide themselves and the host only steps and reads
         J = int(scen.net.n_junctions)
         jids = torch.arange(J, dtype=torch.int32).pin_memory().numpy()
         phases = torch.zeros(J, dtype=torch.int32).pin_memory().numpy()
@@ -269,8 +275,9 @@ def run_ours(args):
         t0 = time.perf_counter()
         for k in range(e2e_steps):
             t_now = T_WARM + args.warmup + args.steps + ksteps + k
-            phases[:] = ((t_now + offs) % 132) // 33
-            sim.set_signal_phase(jids, phases)
+            if not mp:
+                phases[:] = ((t_now + offs) % 132) // 33
+                sim.set_signal_phase(jids, phases)
             sim.step(1)
             mk = sim.metrics()
         e2e_s = time.perf_counter() - t0
@@ -284,7 +291,8 @@ def run_ours(args):
         if dist:
             dist.destroy_process_group()
         return
-    cpu = None if world > 1 else cpu_oracle_rate(scen, state0, budget_s=args.cpu_budget)
+    cpu = None if world > 1 else cpu_oracle_rate(scen, state0, budget_s=args.cpu_budget,
+                                                 max_pressure=args.policy == "max_pressure")
     n_total = int(scen.veh.n)
     line = {
         "metric": "vehicle-updates/s", "value": value, "unit": "vehicle-updates/s", "n_gpus": world,
@@ -296,7 +304,7 @@ def run_ours(args):
                    "start": f"the simulation's own state at step {T_WARM} (set-up, untimed)",
                    "active_per_step": upd / args.steps,
                    "l2": "flushed between timed steps by a 256 MiB write (outside the events)",
-                   "parallelism": f"replicas x{world}"},
+                   "signal_policy": args.policy, "parallelism": f"replicas x{world}"},
         "step_hz": 1e3 / ms_per_step,
         "nominal_vehicle_steps_per_s": n_total * 1e3 / ms_per_step,
         "paper_context": {"step_hz": 84.09, "vehicles": 2464950, "hardware": "RTX 4090 + Xeon 8462Y",
@@ -309,10 +317,11 @@ def run_ours(args):
         "kernel_ms": avg_ms,
         "step_roofline": {"achieved": step_ach, "frac": step_ach / peak, "bytes_per_update": STEP_BYTES},
         "clocks": clk.summary(),
-        "e2e": {"value": e2e_val, "unit": "vehicle-updates/s", "h2d_bytes_per_step": 8 * J,
+        "e2e": {"value": e2e_val, "unit": "vehicle-updates/s", "h2d_bytes_per_step": 0 if mp else 8 * J,
                 "d2h_bytes_per_step": 12 * 8 + 8 + 4,  # metric fields, step counter, error word
                 "steps": e2e_steps,
-                "api": "moss_set_signal_phase + moss_step(1) + moss_get_metrics per step"},
+                "api": ("moss_step(1) + moss_get_metrics per step" if mp else
+                        "moss_set_signal_phase + moss_step(1) + moss_get_metrics per step")},
         "gpu_launches": 4 * args.steps,
         "wall_s_timed_region": wall,
         "cpu_baseline": cpu,
@@ -326,12 +335,23 @@ def run_batched(args):
     """64 uneven scenarios advanced together (one set of launches per step,
     replayed from a CUDA graph, autotuned schedule) against stepping the same
     scenarios one at a time; both from the step-900 state the simulation
-    reaches, K timed steps each."""
+    reaches, K timed steps each.  Under torchrun every rank takes every
+    world-th scenario (no exchange between ranks); the job's rate is the
+    summed updates over the slowest rank's time."""
     import torch
-    from paper_2406_10661_gb300 import binding, scenario as sc
+    from paper_2406_10661_gb300 import binding, scenario as sc, serving
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
     binding.load()
     t0 = time.perf_counter()
-    scens = sc.batched_scenarios(args.scenarios, seed=args.seed)
+    mine = serving.shard(list(range(args.scenarios)), rank, world)
+    scens = sc.batched_scenarios(args.scenarios, seed=args.seed, only=mine)
     gen_s = time.perf_counter() - t0
     pre = 900
     stream = torch.cuda.Stream()
@@ -343,6 +363,9 @@ def run_batched(args):
         batch.synchronize()
         u0 = sum(batch.metrics(i)["vehicle_updates"] for i in range(len(scens)))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
         e0.record(stream)
         batch.step(args.steps)
         e1.record(stream)
@@ -350,33 +373,44 @@ def run_batched(args):
         b_ms = e0.elapsed_time(e1)
         u1 = sum(batch.metrics(i)["vehicle_updates"] for i in range(len(scens)))
         batch.close()
+        b_s, b_upd = b_ms / 1e3, float(u1 - u0)
+        if dist:
+            b_s, b_upd = reduce_ranks(dist, b_s, b_upd, device="cuda")
         seq_ms, seq_upd = 0.0, 0
-        for s_ in scens:
-            sim = binding.Simulation(s_.net, s_.veh, s_.params, precision=32, stream=stream.cuda_stream)
-            sim.step(pre + 9 + args.warmup)  # the batch's autotune advanced it by 9 steps
-            sim.synchronize()
-            m0 = sim.metrics()["vehicle_updates"]
-            e0.record(stream)
-            sim.step(args.steps)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            seq_ms += e0.elapsed_time(e1)
-            seq_upd += sim.metrics()["vehicle_updates"] - m0
-            sim.close()
-    b_val = (u1 - u0) / (b_ms / 1e3)
-    s_val = seq_upd / (seq_ms / 1e3)
+        if world == 1:
+            for s_ in scens:
+                sim = binding.Simulation(s_.net, s_.veh, s_.params, precision=32, stream=stream.cuda_stream)
+                sim.step(pre + 9 + args.warmup)  # the batch's autotune advanced it by 9 steps
+                sim.synchronize()
+                m0 = sim.metrics()["vehicle_updates"]
+                e0.record(stream)
+                sim.step(args.steps)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                seq_ms += e0.elapsed_time(e1)
+                seq_upd += sim.metrics()["vehicle_updates"] - m0
+                sim.close()
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    b_val = b_upd / b_s
     line = {"metric": "vehicle-updates/s (batched)", "value": b_val, "unit": "vehicle-updates/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": b_ms / args.steps,
-            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"batched{len(scens)}", "scenarios": len(scens),
-                       "vehicles": int(sum(x.veh.n for x in scens)),
-                       "vehicles_min_max": [int(min(x.veh.n for x in scens)), int(max(x.veh.n for x in scens))],
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * b_s / args.steps,
+            "higher_is_better": True, "scaling": "strong", "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"batched{args.scenarios}", "scenarios": args.scenarios,
+                       "scenarios_rank0": len(scens),
+                       "vehicles_rank0": int(sum(x.veh.n for x in scens)),
+                       "vehicles_min_max_rank0": [int(min(x.veh.n for x in scens)), int(max(x.veh.n for x in scens))],
                        "start": f"each scenario's own step-{pre} state", "schedule": tuned,
-                       "generation_s": gen_s},
-            "sequential": {"value": s_val, "ms_per_step": seq_ms / args.steps,
-                           "how": "the same scenarios, one handle each, stepped one scenario at a time"},
-            "batched_over_sequential": b_val / s_val,
-            "same_updates": int(u1 - u0) == int(seq_upd)}
+                       "sharding": f"every {world}-th scenario per rank", "generation_s": gen_s}}
+    if world == 1:
+        s_val = seq_upd / (seq_ms / 1e3)
+        line["sequential"] = {"value": s_val, "ms_per_step": seq_ms / args.steps,
+                              "how": "the same scenarios, one handle each, stepped one scenario at a time"}
+        line["batched_over_sequential"] = b_val / s_val
+        line["same_updates"] = int(b_upd) == int(seq_upd)
     print(json.dumps(line), flush=True)
 
 
@@ -422,6 +456,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-roads", type=int, default=1000)
     ap.add_argument("--workload", default="city", choices=["city", "batched", "serving"])
+    ap.add_argument("--policy", default="fixed", choices=["fixed", "max_pressure"],
+                    help="signal policy of every junction on the city workload")
     ap.add_argument("--scenarios", type=int, default=64)
     ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--slots", type=int, default=64)

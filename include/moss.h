@@ -57,6 +57,15 @@ extern "C" {
 #define MOSS_POLICY_FIXED_TIME 0 /* the network's built-in phase program */
 #define MOSS_POLICY_MANUAL 1     /* the phase set by moss_set_signal_phase */
 #define MOSS_POLICY_NONE 2       /* no signal: every junction lane is green */
+/* adaptive maximum pressure (§3.2): the pressure of a junction lane is the
+ * number of vehicles on the road lane it leaves minus the number on the road
+ * lane it feeds (this step's snapshot), the pressure of a phase the sum over
+ * its green junction lanes; the junction holds its phase for the phase's
+ * programmed green time, then takes the phase of maximal pressure (its
+ * current phase when that one is maximal, else the smallest index) for the
+ * next step, changing through the current phase's programmed amber.  Set on
+ * a junction, it starts the phase the junction shows at that step, green. */
+#define MOSS_POLICY_MAX_PRESSURE 3
 
 #define MOSS_ST_WAITING 0 /* not yet departed (or waiting for a safe entrance) */
 #define MOSS_ST_ACTIVE 1  /* on a lane */
@@ -179,6 +188,18 @@ int moss_set_signal_phase(moss_t h, int n, const int32_t* junction_ids, const in
 
 /* Set the signal policy of n junctions (§3.2 set_tl_policy). */
 int moss_set_signal_policy(moss_t h, int n, const int32_t* junction_ids, int32_t policy);
+
+/*
+ * Signal state of n junctions at the current step, into host arrays of n
+ * entries owned by the caller: the phase shown (-1 when every lane is green:
+ * no signal, or a junction without phases), the steps spent in the current
+ * green or amber interval (max-pressure junctions, counting the current step;
+ * 0 otherwise) and the phase that follows the current amber (-1 while
+ * green).  Single-scenario handles only (MOSS_EINVAL for a batch).  Waits for
+ * the handle's stream.
+ */
+int moss_get_signal_state(moss_t h, int n, const int32_t* junction_ids, int32_t* phase, int32_t* elapsed,
+                          int32_t* next_phase);
 
 /* Wait for the handle's stream and copy the cumulative metrics. */
 int moss_get_metrics(moss_t h, MossMetrics* out);

@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmoss.so")
 
 MOSS_OK, MOSS_EINVAL, MOSS_ENOMEM, MOSS_ECUDA, MOSS_ETIMEOUT, MOSS_EBUDGET, MOSS_EDEVICE = range(7)
-POLICY_FIXED_TIME, POLICY_MANUAL, POLICY_NONE = 0, 1, 2
+POLICY_FIXED_TIME, POLICY_MANUAL, POLICY_NONE, POLICY_MAX_PRESSURE = 0, 1, 2, 3
 F_FLAGGED, F_CHANGED, F_CANDIDATE, F_TRANSFER, F_ARRIVED, F_INSERTED, F_CONFLICT_LOST = (
     1, 2, 4, 8, 16, 32, 64)
 
@@ -74,6 +74,7 @@ SIGNATURES = {
     "moss_step": (ctypes.c_int, [_vp, ctypes.c_int]),
     "moss_set_signal_phase": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p, _c_i32p]),
     "moss_set_signal_policy": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p, ctypes.c_int32]),
+    "moss_get_signal_state": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p, _c_i32p, _c_i32p, _c_i32p]),
     "moss_get_metrics": (ctypes.c_int, [_vp, ctypes.POINTER(MossMetrics)]),
     "moss_get_state": (ctypes.c_int, [_vp, ctypes.POINTER(MossState)]),
     "moss_set_state": (ctypes.c_int, [_vp, ctypes.POINTER(MossState), ctypes.c_int64]),
@@ -280,6 +281,15 @@ class Simulation(_Handle):
         j = np.ascontiguousarray(junctions, dtype=np.int32)
         _check(self.lib.moss_set_signal_policy(self.h, len(j), _ptr(j, ctypes.c_int32),
                                                int(policy)), self.h)
+
+    def signal_state(self, junctions: Sequence[int]):
+        """(phase shown or -1, steps in the current interval, phase after the
+        amber or -1) per junction, at the current step."""
+        j = np.ascontiguousarray(junctions, dtype=np.int32)
+        ph, el, nx = (np.zeros(len(j), dtype=np.int32) for _ in range(3))
+        _check(self.lib.moss_get_signal_state(self.h, len(j), _ptr(j, ctypes.c_int32), _ptr(ph, ctypes.c_int32),
+                                              _ptr(el, ctypes.c_int32), _ptr(nx, ctypes.c_int32)), self.h)
+        return ph, el, nx
 
 
 class Batch(_Handle):

@@ -58,6 +58,9 @@ struct MossHandle {
     JuncInfo* d_junc = nullptr;
     int32_t *d_phase_green = nullptr, *d_phase_amber = nullptr, *d_junc_policy = nullptr,
             *d_junc_manual = nullptr, *d_junc_state = nullptr;
+    int4* d_mp = nullptr;  // max-pressure state per junction
+    int32_t *d_jj_off = nullptr, *d_jj_lane = nullptr, *d_jj_from = nullptr, *d_mp_press = nullptr;
+    int n_jj = 0;
     int32_t *d_route_off = nullptr, *d_routes = nullptr, *d_dep = nullptr, *d_vstatus = nullptr,
             *d_vflags = nullptr;
     int32_t *d_q_off = nullptr, *d_q_ids = nullptr, *d_q_head = nullptr, *d_start_lanes = nullptr;
@@ -252,6 +255,8 @@ Ctx<Real> make_ctx(MossHandle* h, int cur) {
     c.junc = h->d_junc;
     c.phase_green = h->d_phase_green; c.phase_amber = h->d_phase_amber;
     c.junc_policy = h->d_junc_policy; c.junc_manual = h->d_junc_manual; c.junc_state = h->d_junc_state;
+    c.mp = h->d_mp; c.jj_off = h->d_jj_off; c.jj_lane = h->d_jj_lane; c.jj_from = h->d_jj_from;
+    c.n_jj = h->n_jj; c.mp_press = h->d_mp_press; c.n_mp = &h->d_cnt[0].n_mp;
     c.route_off = h->d_route_off; c.routes = h->d_routes; c.dep = h->d_dep; c.v0f = h->d_v0f;
     c.vstatus = h->d_vstatus; c.vflags = h->d_vflags;
     c.q_off = h->d_q_off; c.q_ids = h->d_q_ids; c.q_head = h->d_q_head;
@@ -513,6 +518,31 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
     TRY(upload(h, &h->d_junc_policy, std::vector<int32_t>(NJ, POL_FIXED)));
     TRY(upload(h, &h->d_junc_manual, std::vector<int32_t>(NJ, 0)));
     TRY(dalloc(h, &h->d_junc_state, NJ));
+    {
+        // junction lanes of every junction with the road lane each one leaves
+        // (the pressures of the max-pressure policy)
+        std::vector<int32_t> from(NL, -1), jj_off(NJ + 1, 0);
+        for (int l = 0; l < NL; ++l)
+            if (h->lanes[l].lo >= 0)
+                for (int q = h->lanes[l].jb; q < h->lanes[l].je; ++q) from[q] = l;
+        for (int l = 0; l < NL; ++l)
+            if (h->lanes[l].lo < 0) jj_off[h->lanes[l].jb + 1]++;
+        for (int j = 0; j < NJ; ++j) jj_off[j + 1] += jj_off[j];
+        std::vector<int32_t> jj_lane(std::max(jj_off[NJ], 1)), jj_from(std::max(jj_off[NJ], 1));
+        std::vector<int32_t> fill(jj_off.begin(), jj_off.end() - 1);
+        for (int l = 0; l < NL; ++l)
+            if (h->lanes[l].lo < 0) {
+                const int q = fill[h->lanes[l].jb]++;
+                jj_lane[q] = l;
+                jj_from[q] = from[l];
+            }
+        TRY(upload(h, &h->d_jj_off, jj_off));
+        TRY(upload(h, &h->d_jj_lane, jj_lane));
+        TRY(upload(h, &h->d_jj_from, jj_from));
+        TRY(upload(h, &h->d_mp, std::vector<int4>(std::max(NJ, 1), make_int4(0, 1, -1, 0))));
+        TRY(upload(h, &h->d_mp_press, std::vector<int32_t>((size_t)std::max(NJ, 1) * 8, 0)));
+        h->n_jj = jj_off[NJ];
+    }
     TRY(upload(h, &h->d_route_off, h->route_off));
     TRY(upload(h, &h->d_routes, h->routes));
     TRY(upload(h, &h->d_dep, h->dep));
@@ -796,7 +826,7 @@ int moss_batch_set_signal_phase(moss_t h, int scenario, int n, const int32_t* ju
 
 int moss_set_signal_policy(moss_t h, int n, const int32_t* junction_ids, int32_t policy) {
     if (!h) return MOSS_EINVAL;
-    if (policy < 0 || policy > 2) return fail(h, MOSS_EINVAL, "unknown policy");
+    if (policy < 0 || policy > 3) return fail(h, MOSS_EINVAL, "unknown policy");
     const int nj = h->scen_junc_off[1];
     if (n < 0 || (n > 0 && !junction_ids) || n > nj) return fail(h, MOSS_EINVAL, "bad arrays");
     if (n == 0) return MOSS_OK;
@@ -813,6 +843,31 @@ int moss_set_signal_policy(moss_t h, int n, const int32_t* junction_ids, int32_t
     else enqueue_set_signal<float>(h, n, policy);
     CK(cudaGetLastError());
     return MOSS_OK;
+}
+
+int moss_get_signal_state(moss_t h, int n, const int32_t* junction_ids, int32_t* phase, int32_t* elapsed,
+                          int32_t* next_phase) {
+    if (!h) return MOSS_EINVAL;
+    if (h->n_scen != 1) return fail(h, MOSS_EINVAL, "signal state of batches is not available");
+    if (n < 0 || (n > 0 && (!junction_ids || !phase || !elapsed || !next_phase)))
+        return fail(h, MOSS_EINVAL, "bad arrays");
+    const int nj = h->n_junctions;
+    for (int k = 0; k < n; ++k)
+        if (junction_ids[k] < 0 || junction_ids[k] >= nj) return fail(h, MOSS_EINVAL, "junction id out of range");
+    if (n == 0) return MOSS_OK;
+    CK(cudaStreamSynchronize(h->stream));
+    std::vector<int32_t> st(nj), pol(nj);
+    std::vector<int4> mp(nj);
+    CK(cudaMemcpy(st.data(), h->d_junc_state, nj * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(pol.data(), h->d_junc_policy, nj * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(mp.data(), h->d_mp, nj * sizeof(int4), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < n; ++k) {
+        const int j = junction_ids[k], x = st[j];
+        phase[k] = (x & 512) ? -1 : (x & 15);
+        next_phase[k] = (x & 512) || !(x & 256) ? -1 : ((x >> 10) & 15);
+        elapsed[k] = pol[j] == POL_MAXP ? mp[j].y : 0;
+    }
+    return check_device(h);
 }
 
 int moss_get_metrics(moss_t h, MossMetrics* out) {

@@ -32,7 +32,7 @@
 namespace moss {
 
 enum : int { LIGHT_GREEN = 0, LIGHT_AMBER = 1, LIGHT_RED = 2 };
-enum : int { POL_FIXED = 0, POL_MANUAL = 1, POL_NONE = 2 };
+enum : int { POL_FIXED = 0, POL_MANUAL = 1, POL_NONE = 2, POL_MAXP = 3 };
 enum : int {
     F_FLAGGED = 1, F_CHANGED = 2, F_CANDIDATE = 4, F_TRANSFER = 8,
     F_ARRIVED = 16, F_INSERTED = 32, F_CONFLICT_LOST = 64
@@ -69,7 +69,8 @@ struct Counters {
     int ticket_lane; // k_lanescan tickets
     int tag;         // step tag of the per-lane lists (never 0)
     int err;         // device error bits (set 0 only)
-    int pad[2];
+    int n_mp;        // junctions under max pressure (set 0 only)
+    int pad;
 };
 
 // snapshot records
@@ -143,7 +144,14 @@ struct Ctx {
     const int32_t* phase_amber;
     int32_t* junc_policy;
     int32_t* junc_manual;
-    int32_t* junc_state;  // bits 0-3 phase, 4-7 n_phases, 8 amber, 9 all green
+    int32_t* junc_state;  // bits 0-3 phase, 4-7 n_phases, 8 amber, 9 all green, 10-13 phase after the amber
+    int4* mp;             // max-pressure state per junction: phase, steps in the interval, phase after the amber (-1)
+    const int32_t* jj_off;   // [n_junctions+1] junction lanes of each junction (CSR)
+    const int32_t* jj_lane;  // absolute lane ids
+    const int32_t* jj_from;  // the road lane each of them leaves
+    int n_jj;                // junction lanes in jj_lane
+    int32_t* mp_press;       // [n_junctions][8] phase pressures of this step, summed by k_resolve
+    int* n_mp;               // junctions under max pressure
     // ---- vehicles (by global id)
     const int32_t* route_off;
     const int32_t* routes;
@@ -266,20 +274,89 @@ __device__ __forceinline__ int junction_state(int policy, int manual, int offset
     if (x < 0) x += cyc;
     for (int p = 0; p < np; ++p) {
         const long long g = green[p], a = amber[p];
-        if (x < g + a) return p | ((np & 15) << 4) | (x >= g ? 256 : 0);
+        if (x < g + a) return p | ((np & 15) << 4) | (x >= g ? 256 | (((p + 1) % np) << 10) : 0);
         x -= g + a;
     }
     return (np & 15) << 4;
 }
 
+// encoded state of a max-pressure junction (R23)
+__device__ __forceinline__ int mp_encode(int4 m, int np) {
+    return (m.x & 15) | ((np & 15) << 4) | (m.z >= 0 ? 256 | ((m.z & 15) << 10) : 0);
+}
+
 // signal state of junction j, `ahead` steps after its scenario's current step
+// (a max-pressure junction: its current state)
 template <typename Real>
 __device__ __forceinline__ int junction_state_at(const Ctx<Real>& c, int j, int ahead) {
     const JuncInfo J = c.junc[j];
     const int pol = c.junc_policy[j], man = c.junc_manual[j];
+    if (pol == POL_MAXP) return J.np > 0 ? mp_encode(c.mp[j], J.np) : 512;
     const long long t = c.scen_step[J.scen] + ahead;
     return junction_state(pol, man, J.offset, c.phase_green + J.phase_off, c.phase_amber + J.phase_off,
                           J.np, t);
+}
+
+// Max pressure (R23), one junction lane: adds its movement pressure (vehicles
+// on the road lane it leaves minus vehicles on the road lane it feeds, in
+// this step's snapshot) to the phases it is green in.
+template <typename Real>
+__device__ __forceinline__ void mp_accumulate(const Ctx<Real>& c, int k) {
+    const int jl = c.jj_lane[k];
+    const LaneInfo ji = c.lane[jl];
+    if (c.junc_policy[ji.jb] != POL_MAXP) return;
+    const int from = c.jj_from[k], to = ji.hi;
+    const int d = (c.cur.off[from + 1] - c.cur.off[from]) - (c.cur.off[to + 1] - c.cur.off[to]);
+    if (d == 0) return;
+#pragma unroll
+    for (int ph = 0; ph < 8; ++ph)
+        if ((ji.je >> ph) & 1) atomicAdd(&c.mp_press[ji.jb * 8 + ph], d);
+}
+
+// Max pressure (R23): advances junction j from this step to the next with the
+// phase pressures of this step's snapshot (summed by mp_accumulate; cleared
+// here for the next step) and returns the next step's state.  The phase is
+// held for its programmed green; then the phase of maximal pressure is taken
+// (the current one when it is maximal, else the smallest index), through the
+// programmed amber.
+template <typename Real>
+__device__ __forceinline__ int mp_advance(const Ctx<Real>& c, int j) {
+    const JuncInfo J = c.junc[j];
+    int press[8];
+    {
+        int4* pp = reinterpret_cast<int4*>(c.mp_press + j * 8);
+        const int4 a = pp[0], b = pp[1];
+        pp[0] = make_int4(0, 0, 0, 0);
+        pp[1] = make_int4(0, 0, 0, 0);
+        press[0] = a.x; press[1] = a.y; press[2] = a.z; press[3] = a.w;
+        press[4] = b.x; press[5] = b.y; press[6] = b.z; press[7] = b.w;
+    }
+    if (J.np <= 0) return 512;
+    int4 m = c.mp[j];
+    int p = m.x, e = m.y, q = m.z;
+    if (q >= 0) {  // amber of p towards q
+        if (e >= c.phase_amber[J.phase_off + p]) { p = q; q = -1; e = 1; }
+        else e += 1;
+    } else if (e >= c.phase_green[J.phase_off + p]) {
+        int best = p, pb = press[0];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (k == p) pb = press[k];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (k < J.np && press[k] > pb) { best = k; pb = press[k]; }
+        if (best != p) {
+            if (c.phase_amber[J.phase_off + p] > 0) { q = best; e = 1; }
+            else { p = best; e = 1; }
+        } else {
+            e += 1;
+        }
+    } else {
+        e += 1;
+    }
+    m.x = p; m.y = e; m.z = q;
+    c.mp[j] = m;
+    return mp_encode(m, J.np);
 }
 
 // light of a junction lane (its lane record ji) for this step
@@ -287,10 +364,10 @@ template <typename Real>
 __device__ __forceinline__ int light_of(const Ctx<Real>& c, const LaneInfo& ji) {
     const int st = c.junc_state[ji.jb];
     if (st & 512) return LIGHT_GREEN;
-    const int p = st & 15, np = (st >> 4) & 15, mask = ji.je;
+    const int p = st & 15, mask = ji.je;
     if (!((mask >> p) & 1)) return LIGHT_RED;
     if (!(st & 256)) return LIGHT_GREEN;
-    const int nx = (p + 1) % (np > 0 ? np : 1);
+    const int nx = (st >> 10) & 15;  // the phase after the amber
     return ((mask >> nx) & 1) ? LIGHT_GREEN : LIGHT_AMBER;
 }
 

@@ -318,6 +318,9 @@ __global__ void __launch_bounds__(TILE) k_resolve(Ctx<Real> c) {
         if (integrate_emit(c, acc, i, E, EB, la, nlane, fl, (C.bits & CB_OVERLAP) != 0, t, sc, tag))
             atomicAdd(&c.tile_leave[i / TILE], 1);
     }
+    // the phase pressures of the max-pressure junctions (read by k_lanescan)
+    if (*c.n_mp > 0)
+        for (int k = blockIdx.x * TILE + threadIdx.x; k < c.n_jj; k += gridDim.x * TILE) mp_accumulate(c, k);
     macc_flush_block<TILE>(acc, c.metrics);
 }
 
@@ -559,7 +562,8 @@ __global__ void __launch_bounds__(LANESCAN_THREADS) k_lanescan(Ctx<Real> c) {
             // signal states of the next step
             const int j0 = (tile - c.n_lane_tiles - 1) * JUNC_CHUNK;
             const int j = j0 + threadIdx.x;
-            if (j < c.n_junctions) c.junc_state[j] = junction_state_at(c, j, 1);
+            if (j < c.n_junctions)
+                c.junc_state[j] = c.junc_policy[j] == POL_MAXP ? mp_advance(c, j) : junction_state_at(c, j, 1);
         }
         __syncthreads();
     }
@@ -681,6 +685,13 @@ __global__ void k_set_signal(Ctx<Real> c, int n, const int32_t* ids, const int32
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int j = ids[k];
+    if (policy == POL_MAXP) {
+        // starts, green, the phase the junction shows at this step (R23)
+        const int st = c.junc_state[j];
+        c.mp[j] = make_int4((st & 512) ? 0 : (st & 15), 1, -1, 0);
+    }
+    const int was = c.junc_policy[j] == POL_MAXP, now = policy == POL_MAXP;
+    if (was != now) atomicAdd(c.n_mp, now - was);
     c.junc_policy[j] = policy;
     if (policy == POL_MANUAL) c.junc_manual[j] = phases[k];
     c.junc_state[j] = junction_state_at(c, j, 0);

@@ -554,15 +554,19 @@ def city_scenario(seed: int = 0, n: int = 2_464_950, G: int = 100,
 
 
 def batched_scenarios(k: int = 64, seed: int = 0, n_lo: int = 2000, n_hi: int = 300_000,
-                      dep_horizon: int = 1800) -> List[Scenario]:
+                      dep_horizon: int = 1800, only=None) -> List[Scenario]:
     """k independent grid scenarios of uneven size: vehicles log-uniform in
     [n_lo, n_hi], grid side 5..40 grown with the vehicle count, medium-style
-    roads, own seed and signal offsets."""
+    roads, own seed and signal offsets.  `only` (indices) builds just those
+    scenarios of the set, identical to the ones of the full set."""
     st = Stream(seed, 404)
     u = st.uniform(k)
     ns = np.round(np.exp(np.log(n_lo) + u * (np.log(n_hi) - np.log(n_lo)))).astype(np.int64)
     out = []
+    keep = set(range(k)) if only is None else set(int(i) for i in only)
     for i, n in enumerate(ns):
+        if i not in keep:
+            continue
         G = int(np.clip(round(5 * 8 ** (math.log(n / 2000.0) / math.log(150.0))), 5, 40))
         s_i = seed * 1000 + i + 1
         net = grid_network(G, 300.0, 3, vmax_choices=(11.1, 13.89, 16.67), offsets=True,

@@ -192,6 +192,16 @@ class Server:
         }
 
 
+def shard(items, rank: int, world: int):
+    """The share of `items` (scenarios of a batch, or requests) that process
+    `rank` of `world` serves when each GPU has its own process and the items
+    are independent (no exchange between the processes): every world-th item,
+    starting at `rank`."""
+    if world < 1 or not (0 <= rank < world):
+        raise ValueError("need 0 <= rank < world")
+    return items[rank::world]
+
+
 def poisson_requests(n: int, rate_hz: float = 20.0, seed: int = 0, n_lo: int = 5000,
                      n_hi: int = 500_000, h_lo: int = 300, h_hi: int = 3600,
                      make=None) -> List[Request]:
