@@ -74,6 +74,10 @@ def _setup(lib):
     lib.mo_light.argtypes = [vp, ctypes.c_int, ctypes.c_long]
     lib.mo_light.restype = ctypes.c_int
     lib.mo_signal_state.argtypes = [vp, ctypes.c_int, vp]
+    lib.mo_set_lane_max_speed.argtypes = [vp, ctypes.c_int, vp, vp]
+    lib.mo_set_lane_restriction.argtypes = [vp, ctypes.c_int, vp, vp]
+    lib.mo_lane_queue.argtypes = [vp, vp]
+    lib.mo_road_speed.argtypes = [vp, vp]
     lib.mo_idm.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     lib.mo_idm.restype = ctypes.c_double
     lib.mo_idm_free.argtypes = [vp, ctypes.c_double, ctypes.c_double]
@@ -173,6 +177,26 @@ class Oracle:
         out = np.zeros(3, dtype=np.int32)
         self._lib.mo_signal_state(self.h, int(j), _p(out))
         return int(out[0]), int(out[1]), int(out[2])
+
+    def set_lane_max_speed(self, lanes, vmax) -> None:
+        l = np.ascontiguousarray(lanes, dtype=np.int32)
+        v = np.ascontiguousarray(vmax, dtype=np.float64)
+        self._lib.mo_set_lane_max_speed(self.h, len(l), _p(l), _p(v))
+
+    def set_lane_restriction(self, lanes, flags) -> None:
+        l = np.ascontiguousarray(lanes, dtype=np.int32)
+        f = np.ascontiguousarray(flags, dtype=np.int32)
+        self._lib.mo_set_lane_restriction(self.h, len(l), _p(l), _p(f))
+
+    def lane_queue(self) -> np.ndarray:
+        out = np.zeros(int(self.net.n_lanes), dtype=np.int32)
+        self._lib.mo_lane_queue(self.h, _p(out))
+        return out
+
+    def road_speed(self) -> np.ndarray:
+        out = np.zeros(int(self.net.n_roads), dtype=np.float64)
+        self._lib.mo_road_speed(self.h, _p(out))
+        return out
 
     def light(self, jl: int, t: int) -> int:
         return int(self._lib.mo_light(self.h, int(jl), ctypes.c_long(int(t))))

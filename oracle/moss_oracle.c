@@ -79,6 +79,16 @@
  *       step.  A change of phase goes through the current phase's programmed
  *       amber (lanes green in both phases stay green, as in R19).  Setting
  *       the policy starts the phase the junction shows at that step, green.
+ *   R24 metrics of §3.3: the queue length of a lane counts the vehicles with
+ *       v < 0.1 m/s whose distance to the lane end L - s is at most 50 m; the
+ *       average vehicle speed of a road is the mean speed of the vehicles on
+ *       its lanes, or the mean speed limit of its lanes when it is empty.
+ *   R25 lane setters (§3.2 "Lane"): a new maximum speed applies from the next
+ *       step (v0 = v0f x limit, R10).  A lane restricted from passing is not
+ *       entered: a vehicle whose next lane is restricted stops at the end of
+ *       its lane as before a red light (R12, R13); MOBIL treats a restricted
+ *       adjacent lane as absent; no departure is inserted onto it.  Vehicles
+ *       already on it drive on.
  */
 #include <math.h>
 #include <stdint.h>
@@ -128,6 +138,7 @@ typedef struct {
     int *junc_policy, *junc_manual;
     int *jl_from;                      /* road lane a junction lane leaves (absolute ids) */
     int *mp_phase, *mp_elapsed, *mp_pending; /* max-pressure state per junction (R23) */
+    int *restricted;                   /* per lane: restricted from passing (R25) */
     /* vehicles */
     int n_veh;
     int *route_off, *routes, *start_lane, *dep;
@@ -215,6 +226,7 @@ void* mo_create(int n_roads, const int* road_lane_off, int n_lanes, int n_road_l
     O->mp_phase = (int*)xcalloc(n_junctions, sizeof(int));
     O->mp_elapsed = (int*)xcalloc(n_junctions, sizeof(int));
     O->mp_pending = (int*)xcalloc(n_junctions, sizeof(int));
+    O->restricted = (int*)xcalloc(n_lanes, sizeof(int));
 
     O->route_off = (int*)xcalloc(n_veh + 1, sizeof(int));
     memcpy(O->route_off, route_off, sizeof(int) * (n_veh + 1));
@@ -274,7 +286,7 @@ void mo_destroy(void* h) {
     void* ptrs[] = {O->road_lane_off, O->lane_road, O->L, O->vmax, O->jl_off, O->jl_target,
                     O->jl_junction, O->jl_mask, O->junc_offset, O->junc_phase_off,
                     O->phase_green, O->phase_amber, O->junc_policy, O->junc_manual,
-                    O->jl_from, O->mp_phase, O->mp_elapsed, O->mp_pending, O->route_off, O->routes, O->start_lane, O->dep, O->v0f, O->status,
+                    O->jl_from, O->mp_phase, O->mp_elapsed, O->mp_pending, O->restricted, O->route_off, O->routes, O->start_lane, O->dep, O->v0f, O->status,
                     O->lane, O->rc, O->flags, O->s, O->v, O->q_off, O->q_ids, O->q_head};
     for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); ++i) free(ptrs[i]);
     free(O);
@@ -352,6 +364,53 @@ void mo_set_signal(void* h, int n, const int* junctions, int policy, const int* 
         O->junc_policy[j] = policy;
         if (policy == POLICY_MANUAL) O->junc_manual[j] = phases[k];
     }
+}
+
+/* R25 setters, effective from the next step */
+void mo_set_lane_max_speed(void* h, int n, const int* lanes, const double* vmax) {
+    Oracle* O = (Oracle*)h;
+    for (int k = 0; k < n; ++k) O->vmax[lanes[k]] = vmax[k];
+}
+
+void mo_set_lane_restriction(void* h, int n, const int* lanes, const int* flags) {
+    Oracle* O = (Oracle*)h;
+    for (int k = 0; k < n; ++k) O->restricted[lanes[k]] = flags[k] != 0;
+}
+
+/* R24 metrics of the current state: queue length per lane (out[n_lanes]) and
+ * average vehicle speed per road (out[n_roads]) */
+void mo_lane_queue(void* h, int* out) {
+    Oracle* O = (Oracle*)h;
+    for (int l = 0; l < O->n_lanes; ++l) out[l] = 0;
+    for (int i = 0; i < O->n_veh; ++i) {
+        if (O->status[i] != ST_ACTIVE) continue;
+        int l = O->lane[i];
+        if (O->v[i] < 0.1 && O->L[l] - O->s[i] <= 50.0) out[l]++;
+    }
+}
+
+void mo_road_speed(void* h, double* out) {
+    Oracle* O = (Oracle*)h;
+    double* sum = (double*)xcalloc(O->n_roads, sizeof(double));
+    long* cnt = (long*)xcalloc(O->n_roads, sizeof(long));
+    for (int i = 0; i < O->n_veh; ++i) {
+        if (O->status[i] != ST_ACTIVE) continue;
+        int r = O->lane_road[O->lane[i]];
+        if (r < 0) continue;  /* junction lanes belong to no road */
+        sum[r] += O->v[i];
+        cnt[r]++;
+    }
+    for (int r = 0; r < O->n_roads; ++r) {
+        if (cnt[r] > 0) {
+            out[r] = sum[r] / (double)cnt[r];
+        } else {
+            double m = 0.0;
+            int nl = O->road_lane_off[r + 1] - O->road_lane_off[r];
+            for (int l = O->road_lane_off[r]; l < O->road_lane_off[r + 1]; ++l) m += O->vmax[l];
+            out[r] = m / nl;
+        }
+    }
+    free(sum); free(cnt);
 }
 
 /* max-pressure state of junction j: out = [phase, steps in the current green
@@ -537,7 +596,8 @@ static LaneAcc accel_on_lane(const Oracle* O, const Snap* S, int vid, int lane, 
             rcn = rcm;
         }
     }
-    if (lane < O->n_road_lanes && nl1 >= O->n_road_lanes && S->light[nl1] != LIGHT_GREEN) {
+    if ((lane < O->n_road_lanes && nl1 >= O->n_road_lanes && S->light[nl1] != LIGHT_GREEN) ||
+        (nl1 >= 0 && O->restricted[nl1])) {
         double gs = O->L[lane] - s;
         double as = idm(O, v, v0, gs, v);
         if (as < a) a = as;
@@ -596,7 +656,7 @@ static Decision decide(const Oracle* O, const Snap* S, int vid, long t) {
     double pos_scale = s > 1.0 ? s : 1.0;
     for (int side = 0; side < 2; ++side) {         /* 0 = left (k-1), 1 = right (k+1) */
         int tl = side == 0 ? lane - 1 : lane + 1;
-        if (tl < lo || tl >= hi) continue;
+        if (tl < lo || tl >= hi || O->restricted[tl]) continue;
         int TL = leader_on(S, tl, s, vid), TF = follower_on(S, tl, s, vid);
         TLs[side] = TL; TFs[side] = TF;
         int ok = 1;
@@ -816,7 +876,7 @@ static void step_once(Oracle* O) {
     /* departure insertion against the snapshot (R18) */
     for (int l = 0; l < O->n_road_lanes; ++l) {
         int h = O->q_head[l];
-        if (h >= O->q_off[l + 1]) continue;
+        if (h >= O->q_off[l + 1] || O->restricted[l]) continue;
         int vid = O->q_ids[h];
         if (O->dep[vid] > t || O->status[vid] != ST_WAITING) continue;
         int r = rearmost_on(&S, l);

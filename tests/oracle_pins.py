@@ -499,10 +499,90 @@ def check_max_pressure_timing(libpath=None):
         o.step(1)
 
 
+# ---------------------------------------------------------------------------
+# Lane / road metrics (reading R24) and lane setters (reading R25)
+def check_lane_queue_and_road_speed(libpath=None):
+    """R24 worked by hand on one 300 m road of two lanes (and an empty road):
+    queued = v < 0.1 m/s within the last 50 m."""
+    cars = [(0, 295.0, 0.0),     # queued
+            (0, 260.0, 0.05),    # queued (40 m from the end)
+            (0, 240.0, 0.0),     # 60 m from the end: not counted
+            (0, 200.0, 0.2),     # moving: not counted
+            (1, 299.0, 0.0999),  # queued
+            (1, 251.0, 0.1)]     # v = 0.1 is not below the threshold
+    scen, st = one_road(2, 300.0, cars)
+    o = _oracle(scen, st, libpath)
+    q = o.lane_queue()
+    assert q.tolist() == [2, 1], q
+    sp = o.road_speed()
+    assert abs(sp[0] - (0.0 + 0.05 + 0.0 + 0.2 + 0.0999 + 0.1) / 6.0) < 1e-12, sp
+    # an empty road reports the mean speed limit of its lanes
+    scen2 = corridor((300.0, 300.0), [(0, 0)], n_lanes=2)
+    o2 = _oracle(scen2, None, libpath)
+    sp2 = o2.road_speed()
+    assert np.allclose(sp2, np.float32(13.89)), sp2
+
+
+def check_lane_max_speed(libpath=None):
+    """R25: a lane's new speed limit is the v0 of the next step (IDM free road,
+    App. B.3 eq. (1): a = a_max (1 - (v/v0)^4))."""
+    scen, st = one_road(1, 5000.0, [(0, 10.0, 4.0)])
+    o = _oracle(scen, st, libpath)
+    o.set_lane_max_speed([0], [5.0])
+    o.step(1)
+    a = 2.0 * (1.0 - (4.0 / 5.0) ** 4)
+    assert abs(o.state()["v"][0] - (4.0 + a)) < 1e-12
+    o.set_lane_max_speed([0], [4.0])  # v = v0: ... and a slower limit brakes the car
+    v1 = o.state()["v"][0]
+    o.step(1)
+    assert abs(o.state()["v"][0] - (v1 + 2.0 * (1.0 - (v1 / 4.0) ** 4))) < 1e-12
+    assert o.state()["v"][0] < v1
+
+
+def check_lane_restriction(libpath=None):
+    """R25: a restricted next lane stops the car at the end of its lane like a
+    red light; a restricted adjacent lane is never the target of a lane
+    change; no departure is inserted onto a restricted lane."""
+    # (a) stop before a restricted junction lane, go on once it is lifted
+    scen = corridor((300.0, 300.0), [(0, 0)])
+    o = _oracle(scen, None, libpath)
+    o.set_signal([0], oracle.POLICY_NONE)
+    jl = scen.net.n_road_lanes
+    o.set_lane_restriction([jl], [1])
+    L0 = float(scen.net.lane_length[0])
+    for t in range(150):
+        o.step(1)
+        stt = o.state()
+        if stt["status"][0] == 1:
+            assert stt["lane"][0] == 0 and L0 - stt["s"][0] >= -1e-12
+    assert o.state()["v"][0] < 1e-6
+    o.set_lane_restriction([jl], [0])
+    o.step(60)
+    assert o.state()["lane"][0] != 0
+    # (b) MOBIL case A wants lane 0; restricted, it never changes
+    scen, st = one_road(2, 1000.0, [(1, 100.0, 10.0), (1, 120.0, 5.0)], params=_mobil_params())
+    o = _oracle(scen, st, libpath)
+    o.set_lane_restriction([0], [1])
+    for t in range(20):
+        o.step(1)
+        assert o.state()["lane"][0] == 1
+    o2 = _oracle(scen, st, libpath)
+    o2.step(20)
+    assert (o2.state()["lane"] == 0).any()  # unrestricted, it does change
+    # (c) insertion onto a restricted start lane waits
+    scen = corridor((300.0, 300.0), [(0, 0), (1, 0)], n_lanes=2)
+    o = _oracle(scen, None, libpath)
+    o.set_lane_restriction([0], [1])
+    o.step(5)
+    stt = o.state()
+    assert stt["status"][0] == 0 and stt["status"][1] == 1
+
+
 ALL_CHECKS = [
     check_idm_free_road, check_idm_equilibrium, check_p_lc, check_mobil_case_A,
     check_mobil_case_B, check_mobil_case_C, check_mobil_case_D, check_mobil_mirror, check_neighbours_bruteforce,
     check_free_road_vs_rk4, check_platoon_equilibrium, check_red_light, check_signal_program,
     check_arrival_and_travel_time, check_insertion, check_conflict, check_max_pressure_argmax,
-    check_max_pressure_timing,
+    check_max_pressure_timing, check_lane_queue_and_road_speed, check_lane_max_speed,
+    check_lane_restriction,
 ]

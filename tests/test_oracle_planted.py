@@ -24,7 +24,7 @@ MUTATIONS = [
      "if (best < 0 || ahead_of(S, m, S->s[best], best)) best = m;\n    }\n    return best;\n}\n\n/* nearest vehicle behind"),
     ("p_lc_literal_branch", "return O->p_lo + (O->p_hi - O->p_lo) * uT;", "return (O->p_hi - O->p_lo) * uT;"),
     ("amber_as_green", "return ((mask >> nxt) & 1) ? LIGHT_GREEN : LIGHT_AMBER;", "return LIGHT_GREEN;"),
-    ("no_stop_line", "S->light[nl1] != LIGHT_GREEN) {", "S->light[nl1] == LIGHT_RED && 0) {"),
+    ("no_stop_line", "S->light[nl1] != LIGHT_GREEN) ||", "S->light[nl1] == LIGHT_RED && 0) ||"),
     ("snapshot_written_in_place", "O->lane[i] = lane; O->s[i] = s_new; O->v[i] = v_new; O->rc[i] = rc;",
      "O->lane[i] = lane; O->s[i] = s_new; O->v[i] = v_new; O->rc[i] = rc; S.s[i] = s_new;"),
     ("insertion_ignores_gap", "ok = g >= 0.0;", "ok = 1;"),
@@ -37,6 +37,12 @@ MUTATIONS = [
      "long d = (long)lane_cnt[O->jl_from[jl]];"),
     ("maxp_no_amber", "if (O->phase_amber[p0 + p] > 0) { q = best; e = 1; }", "if (0) { q = best; e = 1; }"),
     ("maxp_min_green_off_by_one", "} else if (e >= O->phase_green[p0 + p]) {", "} else if (e > O->phase_green[p0 + p]) {"),
+    ("queue_window_100m", "if (O->v[i] < 0.1 && O->L[l] - O->s[i] <= 50.0) out[l]++;",
+     "if (O->v[i] < 0.1 && O->L[l] - O->s[i] <= 100.0) out[l]++;"),
+    ("restriction_no_stop", "(nl1 >= 0 && O->restricted[nl1])) {", "(0)) {"),
+    ("restriction_ignored_by_mobil", "if (tl < lo || tl >= hi || O->restricted[tl]) continue;",
+     "if (tl < lo || tl >= hi) continue;"),
+    ("max_speed_setter_ignored", "for (int k = 0; k < n; ++k) O->vmax[lanes[k]] = vmax[k];", "(void)vmax;"),
     ("maxp_ties_to_smallest", "if (pk > pb || (pk == pb && best != p && k < best)) best = k;",
      "if (pk > pb || (pk == pb && k < best)) best = k;"),
 ]
