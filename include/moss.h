@@ -190,6 +190,39 @@ int moss_set_signal_phase(moss_t h, int n, const int32_t* junction_ids, const in
 int moss_set_signal_policy(moss_t h, int n, const int32_t* junction_ids, int32_t policy);
 
 /*
+ * Lane setters (§3.2 "Lane": set_lane_max_speed, set_lane_restriction), for
+ * the lanes of a single-scenario handle (scenario 0 of a batch), effective
+ * from the next step.  lane_ids and the values are host arrays of n entries.
+ *   - moss_set_lane_max_speed: new speed limits (m/s, > 0); desired speeds
+ *     are v0f x limit.
+ *   - moss_set_lane_restriction: flags != 0 restrict a lane from passing: it
+ *     is not entered — a vehicle whose next lane is restricted stops at the
+ *     end of its lane as before a red light, lane changes into it are not
+ *     considered, and no departure is inserted onto it; vehicles already on
+ *     it drive on.  0 lifts the restriction.
+ * Both wait for the handle's stream; MOSS_EINVAL for an id out of range or a
+ * limit that is not > 0 (nothing is changed).
+ */
+int moss_set_lane_max_speed(moss_t h, int n, const int32_t* lane_ids, const float* vmax);
+int moss_set_lane_restriction(moss_t h, int n, const int32_t* lane_ids, const int32_t* flags);
+
+/*
+ * Lane and road metrics of the current state (§3.3 "Lane Queue Length",
+ * "Road Traveling Time"), into caller-owned host arrays:
+ *   - moss_get_lane_queue: queue[l] for every lane l of the scenario = the
+ *     vehicles with v < 0.1 m/s within the last 50 m of the lane;
+ *   - moss_get_road_speed: speed[r] for every road r = the mean speed of the
+ *     vehicles on its lanes (m/s), or the mean speed limit of its lanes when
+ *     the road is empty.
+ * The batch forms take the scenario index (lane and road ids local to it).
+ * They wait for the handle's stream.
+ */
+int moss_get_lane_queue(moss_t h, int32_t* queue);
+int moss_get_road_speed(moss_t h, double* speed);
+int moss_batch_get_lane_queue(moss_t h, int scenario, int32_t* queue);
+int moss_batch_get_road_speed(moss_t h, int scenario, double* speed);
+
+/*
  * Signal state of n junctions at the current step, into host arrays of n
  * entries owned by the caller: the phase shown (-1 when every lane is green:
  * no signal, or a junction without phases), the steps spent in the current

@@ -75,6 +75,12 @@ SIGNATURES = {
     "moss_set_signal_phase": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p, _c_i32p]),
     "moss_set_signal_policy": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p, ctypes.c_int32]),
     "moss_get_signal_state": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p, _c_i32p, _c_i32p, _c_i32p]),
+    "moss_set_lane_max_speed": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p, ctypes.POINTER(ctypes.c_float)]),
+    "moss_set_lane_restriction": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p, _c_i32p]),
+    "moss_get_lane_queue": (ctypes.c_int, [_vp, _c_i32p]),
+    "moss_get_road_speed": (ctypes.c_int, [_vp, _c_f64p]),
+    "moss_batch_get_lane_queue": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p]),
+    "moss_batch_get_road_speed": (ctypes.c_int, [_vp, ctypes.c_int, _c_f64p]),
     "moss_get_metrics": (ctypes.c_int, [_vp, ctypes.POINTER(MossMetrics)]),
     "moss_get_state": (ctypes.c_int, [_vp, ctypes.POINTER(MossState)]),
     "moss_set_state": (ctypes.c_int, [_vp, ctypes.POINTER(MossState), ctypes.c_int64]),
@@ -250,6 +256,7 @@ class Simulation(_Handle):
         _check(rc)
         self.h = h
         self.n = int(veh.n)
+        self.net = net
         self.precision = precision
 
     def metrics(self) -> Dict[str, float]:
@@ -282,6 +289,30 @@ class Simulation(_Handle):
         _check(self.lib.moss_set_signal_policy(self.h, len(j), _ptr(j, ctypes.c_int32),
                                                int(policy)), self.h)
 
+    def set_lane_max_speed(self, lanes: Sequence[int], vmax) -> None:
+        l = np.ascontiguousarray(lanes, dtype=np.int32)
+        v = np.ascontiguousarray(vmax, dtype=np.float32)
+        _check(self.lib.moss_set_lane_max_speed(self.h, len(l), _ptr(l, ctypes.c_int32), _ptr(v, ctypes.c_float)),
+               self.h)
+
+    def set_lane_restriction(self, lanes: Sequence[int], flags) -> None:
+        l = np.ascontiguousarray(lanes, dtype=np.int32)
+        f = np.ascontiguousarray(flags, dtype=np.int32)
+        _check(self.lib.moss_set_lane_restriction(self.h, len(l), _ptr(l, ctypes.c_int32), _ptr(f, ctypes.c_int32)),
+               self.h)
+
+    def lane_queue(self) -> np.ndarray:
+        """Vehicles with v < 0.1 m/s within the last 50 m of every lane."""
+        out = np.zeros(int(self.net.n_lanes), dtype=np.int32)
+        _check(self.lib.moss_get_lane_queue(self.h, _ptr(out, ctypes.c_int32)), self.h)
+        return out
+
+    def road_speed(self) -> np.ndarray:
+        """Mean vehicle speed of every road (its lanes' mean limit when empty)."""
+        out = np.zeros(int(self.net.n_roads), dtype=np.float64)
+        _check(self.lib.moss_get_road_speed(self.h, _ptr(out, ctypes.c_double)), self.h)
+        return out
+
     def signal_state(self, junctions: Sequence[int]):
         """(phase shown or -1, steps in the current interval, phase after the
         amber or -1) per junction, at the current step."""
@@ -307,6 +338,7 @@ class Batch(_Handle):
                                           ctypes.byref(h)))
         self.h = h
         self.sizes = [int(s.veh.n) for s in scenarios]
+        self.nets = [s.net for s in scenarios]
         self.k = k
 
     def metrics(self, i: int) -> Dict[str, float]:
@@ -318,6 +350,16 @@ class Batch(_Handle):
         st, ms = _state_arrays(self.sizes[i])
         _check(self.lib.moss_batch_get_state(self.h, int(i), ctypes.byref(ms)), self.h)
         return st
+
+    def lane_queue(self, i: int) -> np.ndarray:
+        out = np.zeros(int(self.nets[i].n_lanes), dtype=np.int32)
+        _check(self.lib.moss_batch_get_lane_queue(self.h, int(i), _ptr(out, ctypes.c_int32)), self.h)
+        return out
+
+    def road_speed(self, i: int) -> np.ndarray:
+        out = np.zeros(int(self.nets[i].n_roads), dtype=np.float64)
+        _check(self.lib.moss_batch_get_road_speed(self.h, int(i), _ptr(out, ctypes.c_double)), self.h)
+        return out
 
     def set_signal_phase(self, i: int, junctions, phases) -> None:
         j = np.ascontiguousarray(junctions, dtype=np.int32)

@@ -61,6 +61,11 @@ struct MossHandle {
     int4* d_mp = nullptr;  // max-pressure state per junction
     int32_t *d_jj_off = nullptr, *d_jj_lane = nullptr, *d_jj_from = nullptr, *d_mp_press = nullptr;
     int n_jj = 0;
+    int2* d_road_span = nullptr;      // (first, end) road lanes per road
+    std::vector<int2> road_span;
+    std::vector<int> scen_road_off;   // [n_scen+1]
+    int32_t* d_lstage = nullptr;      // setter arguments for lanes (2 * n_lanes)
+    void* d_mbuf = nullptr;           // metric output (max(n_lanes, n_roads) doubles)
     int32_t *d_route_off = nullptr, *d_routes = nullptr, *d_dep = nullptr, *d_vstatus = nullptr,
             *d_vflags = nullptr;
     int32_t *d_q_off = nullptr, *d_q_ids = nullptr, *d_q_head = nullptr, *d_start_lanes = nullptr;
@@ -257,6 +262,7 @@ Ctx<Real> make_ctx(MossHandle* h, int cur) {
     c.junc_policy = h->d_junc_policy; c.junc_manual = h->d_junc_manual; c.junc_state = h->d_junc_state;
     c.mp = h->d_mp; c.jj_off = h->d_jj_off; c.jj_lane = h->d_jj_lane; c.jj_from = h->d_jj_from;
     c.n_jj = h->n_jj; c.mp_press = h->d_mp_press; c.n_mp = &h->d_cnt[0].n_mp;
+    c.road_span = h->d_road_span;
     c.route_off = h->d_route_off; c.routes = h->d_routes; c.dep = h->d_dep; c.v0f = h->d_v0f;
     c.vstatus = h->d_vstatus; c.vflags = h->d_vflags;
     c.q_off = h->d_q_off; c.q_ids = h->d_q_ids; c.q_head = h->d_q_head;
@@ -391,6 +397,7 @@ int check_device(MossHandle* h) {
 int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const MossParams* prms,
                 void* stream, MossHandle* h) {
     if (n < 1) return fail(h, MOSS_EINVAL, "need at least one scenario");
+    if (n > 65535) return fail(h, MOSS_EINVAL, "at most 65535 scenarios in a batch");
     h->prm = prms[0];
     h->precision = prms[0].precision;
     h->n_scen = n;
@@ -419,6 +426,8 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
     h->route_off.resize(NV + 1); h->routes.resize(tot_routes); h->dep.resize(NV);
     h->start_lane.resize(NV); h->v0f.resize(NV); h->veh_scen.resize(NV);
     h->scen_veh_off.assign(n + 1, 0); h->scen_lane_off.assign(n + 1, 0); h->scen_junc_off.assign(n + 1, 0);
+    h->scen_road_off.assign(n + 1, 0);
+    h->road_span.assign(tot_roads, make_int2(0, 0));
     h->key0.resize(n); h->key1.resize(n);
     int LO = 0, JO = 0, VO = 0, RO = 0, PO = 0, ROFF = 0;
     h->route_off[0] = 0;
@@ -452,6 +461,8 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
         }
         for (int l = 0; l < NRL; ++l)
             for (int j = nt.jl_off[l]; j < nt.jl_off[l + 1]; ++j) h->lane_src_road[LO + j] = RO + road_of[l];
+        for (int r = 0; r < nt.n_roads; ++r)
+            h->road_span[RO + r] = make_int2(LO + nt.road_lane_off[r], LO + nt.road_lane_off[r + 1]);
         for (int j = 0; j < nt.n_junctions; ++j) {
             h->junc_scen[JO + j] = k;
             junc_offset[JO + j] = nt.junc_offset[j];
@@ -477,6 +488,7 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
         ROFF += vh.n ? vh.route_off[vh.n] : 0;
         LO += nt.n_lanes; JO += nt.n_junctions; VO += vh.n; RO += nt.n_roads; PO += nph;
         h->scen_veh_off[k + 1] = VO; h->scen_lane_off[k + 1] = LO; h->scen_junc_off[k + 1] = JO;
+        h->scen_road_off[k + 1] = RO;
     }
     h->junc_phase_off[NJ] = PO;
     // departure queues per start lane ordered by (dep, id) (R18)
@@ -541,6 +553,11 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
         TRY(upload(h, &h->d_jj_from, jj_from));
         TRY(upload(h, &h->d_mp, std::vector<int4>(std::max(NJ, 1), make_int4(0, 1, -1, 0))));
         TRY(upload(h, &h->d_mp_press, std::vector<int32_t>((size_t)std::max(NJ, 1) * 8, 0)));
+        std::vector<int2> span(h->road_span);
+        if (span.empty()) span.push_back(make_int2(0, 0));
+        TRY(upload(h, &h->d_road_span, span));
+        TRY(dalloc(h, &h->d_lstage, 2 * (size_t)std::max(NL, 1)));
+        TRY(dalloc(h, (char**)&h->d_mbuf, sizeof(double) * (size_t)std::max(std::max(NL, (int)tot_roads), 1)));
         h->n_jj = jj_off[NJ];
     }
     TRY(upload(h, &h->d_route_off, h->route_off));
@@ -732,6 +749,68 @@ int upload_state(MossHandle* h, const std::vector<int>& order, const std::vector
 }  // namespace
 
 // ============================================================================
+namespace {
+
+// lane setters (R25) for the lanes of scenario 0
+template <typename Real>
+void enqueue_set_lane(MossHandle* h, int n, int mode) {
+    Ctx<Real> c = make_ctx<Real>(h, h->parity);
+    k_set_lane<Real><<<(n + 255) / 256, 256, 0, h->stream>>>(c, n, h->d_lstage, h->d_lstage + n, mode);
+}
+
+int set_lane(MossHandle* h, int n, const int32_t* lane_ids, const int32_t* vals, int mode) {
+    const int nl = h->scen_lane_off[1];
+    if (n < 0 || (n > 0 && (!lane_ids || !vals)) || n > nl) return fail(h, MOSS_EINVAL, "bad arrays");
+    for (int k = 0; k < n; ++k)
+        if (lane_ids[k] < 0 || lane_ids[k] >= nl) return fail(h, MOSS_EINVAL, "lane id out of range");
+    if (n == 0) return MOSS_OK;
+    std::vector<int32_t> buf(2 * (size_t)n);
+    for (int k = 0; k < n; ++k) { buf[k] = lane_ids[k]; buf[n + k] = vals[k]; }
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaMemcpy(h->d_lstage, buf.data(), buf.size() * 4, cudaMemcpyHostToDevice));
+    if (h->precision == 64) enqueue_set_lane<double>(h, n, mode);
+    else enqueue_set_lane<float>(h, n, mode);
+    CK(cudaGetLastError());
+    for (int k = 0; k < n; ++k) {
+        LaneInfo& li = h->lanes[lane_ids[k]];
+        if (mode == 0) std::memcpy(&li.vmax, &vals[k], 4);
+        else li.flags = vals[k] ? (li.flags | LF_RESTRICTED) : (li.flags & ~LF_RESTRICTED);
+    }
+    return MOSS_OK;
+}
+
+template <typename Real>
+int scen_lane_metrics(MossHandle* h, int s, int32_t* queue, double* speed) {
+    Ctx<Real> c = make_ctx<Real>(h, h->parity);
+    if (queue) {
+        const int l0 = h->scen_lane_off[s], l1 = h->scen_lane_off[s + 1];
+        if (l1 > l0) {
+            k_lane_queue<Real><<<(l1 - l0 + 255) / 256, 256, 0, h->stream>>>(c, l0, l1, (int32_t*)h->d_mbuf);
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(queue, h->d_mbuf, (size_t)(l1 - l0) * 4, cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+        }
+    }
+    if (speed) {
+        const int r0 = h->scen_road_off[s], r1 = h->scen_road_off[s + 1];
+        if (r1 > r0) {
+            k_road_speed<Real><<<(r1 - r0 + 255) / 256, 256, 0, h->stream>>>(c, r0, r1, (double*)h->d_mbuf);
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(speed, h->d_mbuf, (size_t)(r1 - r0) * 8, cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+        }
+    }
+    return check_device(h);
+}
+
+int lane_metrics(MossHandle* h, int s, int32_t* queue, double* speed) {
+    if (s < 0 || s >= h->n_scen) return fail(h, MOSS_EINVAL, "scenario index out of range");
+    return h->precision == 64 ? scen_lane_metrics<double>(h, s, queue, speed)
+                              : scen_lane_metrics<float>(h, s, queue, speed);
+}
+
+}  // namespace
+
 extern "C" {
 
 int moss_create(const MossNetwork* net, const MossVehicles* veh, const MossParams* prm,
@@ -843,6 +922,46 @@ int moss_set_signal_policy(moss_t h, int n, const int32_t* junction_ids, int32_t
     else enqueue_set_signal<float>(h, n, policy);
     CK(cudaGetLastError());
     return MOSS_OK;
+}
+
+int moss_set_lane_max_speed(moss_t h, int n, const int32_t* lane_ids, const float* vmax) {
+    if (!h) return MOSS_EINVAL;
+    if (n > 0 && !vmax) return fail(h, MOSS_EINVAL, "bad arrays");
+    std::vector<int32_t> bits(std::max(n, 0));
+    for (int k = 0; k < n; ++k) {
+        if (!(vmax[k] > 0.0f) || !std::isfinite(vmax[k])) return fail(h, MOSS_EINVAL, "speed limit must be > 0");
+        std::memcpy(&bits[k], &vmax[k], 4);
+    }
+    return set_lane(h, n, lane_ids, bits.data(), 0);
+}
+
+int moss_set_lane_restriction(moss_t h, int n, const int32_t* lane_ids, const int32_t* flags) {
+    if (!h) return MOSS_EINVAL;
+    return set_lane(h, n, lane_ids, flags, 1);
+}
+
+int moss_get_lane_queue(moss_t h, int32_t* queue) {
+    if (!h) return MOSS_EINVAL;
+    if (!queue) return fail(h, MOSS_EINVAL, "null output");
+    return lane_metrics(h, 0, queue, nullptr);
+}
+
+int moss_get_road_speed(moss_t h, double* speed) {
+    if (!h) return MOSS_EINVAL;
+    if (!speed) return fail(h, MOSS_EINVAL, "null output");
+    return lane_metrics(h, 0, nullptr, speed);
+}
+
+int moss_batch_get_lane_queue(moss_t h, int scenario, int32_t* queue) {
+    if (!h) return MOSS_EINVAL;
+    if (!queue) return fail(h, MOSS_EINVAL, "null output");
+    return lane_metrics(h, scenario, queue, nullptr);
+}
+
+int moss_batch_get_road_speed(moss_t h, int scenario, double* speed) {
+    if (!h) return MOSS_EINVAL;
+    if (!speed) return fail(h, MOSS_EINVAL, "null output");
+    return lane_metrics(h, scenario, nullptr, speed);
 }
 
 int moss_get_signal_state(moss_t h, int n, const int32_t* junction_ids, int32_t* phase, int32_t* elapsed,

@@ -113,10 +113,13 @@ enum : int {
 //                  junction lanes leaving it; road = its road; scen = scenario
 //   junction lane: lo = -1, hi = the road lane it feeds; jb = its junction;
 //                  je = phase mask; road = road of its target
+//   flags: LF_* bits set by the lane setters
 struct alignas(32) LaneInfo {
     float L, vmax;
-    int lo, hi, jb, je, road, scen;
+    int lo, hi, jb, je, road;
+    unsigned short scen, flags;
 };
+enum : int { LF_RESTRICTED = 1 };  // restricted from passing: not entered (R25)
 
 // One 16-byte record per junction (signal program; policy and manual phase
 // are mutable and kept apart)
@@ -149,6 +152,7 @@ struct Ctx {
     const int32_t* jj_off;   // [n_junctions+1] junction lanes of each junction (CSR)
     const int32_t* jj_lane;  // absolute lane ids
     const int32_t* jj_from;  // the road lane each of them leaves
+    const int2* road_span;   // [n_roads] (first, end) road lanes of every road (absolute ids)
     int n_jj;                // junction lanes in jj_lane
     int32_t* mp_press;       // [n_junctions][8] phase pressures of this step, summed by k_resolve
     int* n_mp;               // junctions under max pressure
@@ -452,7 +456,9 @@ __device__ __forceinline__ LaneAcc<Real> accel_on_lane(const Ctx<Real>& c, const
                 xi = c.lane[x];
             }
         }
-        if (li.lo >= 0 && light_of(c, ni) != LIGHT_GREEN) {
+        // stop line: a red or amber junction lane ahead (R12), or a next lane
+        // restricted from passing (R25)
+        if ((li.lo >= 0 && light_of(c, ni) != LIGHT_GREEN) || (ni.flags & LF_RESTRICTED)) {
             const Real gs = Real(li.L) - s;
             const Real as = idm(c, v, v0, gs, v);
             if (as < a) a = as;
@@ -549,7 +555,9 @@ __device__ __forceinline__ Decision<Real> decide_mobil(const Ctx<Real>& c, int i
     Real u0 = Real(0), u1 = Real(0), scl0 = Real(0), scl1 = Real(0);
     int feas0 = 0, feas1 = 0, TL0 = -1, TL1 = -1, TF0 = -1, TF1 = -1, NL0 = -1, NL1 = -1;
     const Real pos_scale = E.s > Real(1) ? E.s : Real(1);
-    const int has_l = lane - 1 >= li.lo, has_r = lane + 1 < li.hi;
+    // a side is a lane of the road that is not restricted from passing (R25)
+    const int has_l = lane - 1 >= li.lo && !(c.lane[lane - 1].flags & LF_RESTRICTED);
+    const int has_r = lane + 1 < li.hi && !(c.lane[lane + 1].flags & LF_RESTRICTED);
     const int n_sides = has_l + has_r;
 #pragma unroll 1
     for (int k = 0; k < n_sides; ++k) {

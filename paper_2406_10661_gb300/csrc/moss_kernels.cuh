@@ -27,7 +27,9 @@ __device__ void insert_departure(const Ctx<Real>& c, int l, int tag) {
     const int h = c.q_head[l];
     if (h >= c.q_off[l + 1]) return;
     const int vid = c.q_ids[h];
-    const int sc = c.lane[l].scen;
+    const LaneInfo ls = c.lane[l];
+    if (ls.flags & LF_RESTRICTED) return;  // no departure onto a restricted lane (R25)
+    const int sc = ls.scen;
     const long long t = c.scen_step[sc];
     if ((long long)c.dep[vid] > t) return;
     const int b = c.cur.off[l], e = c.cur.off[l + 1];
@@ -695,6 +697,51 @@ __global__ void k_set_signal(Ctx<Real> c, int n, const int32_t* ids, const int32
     c.junc_policy[j] = policy;
     if (policy == POL_MANUAL) c.junc_manual[j] = phases[k];
     c.junc_state[j] = junction_state_at(c, j, 0);
+}
+
+// lane setters (R25): speed limit (mode 0, value as float bits) or
+// restriction flag (mode 1) of n lanes, effective from the next step
+template <typename Real>
+__global__ void k_set_lane(Ctx<Real> c, int n, const int32_t* ids, const int32_t* vals, int mode) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    LaneInfo* li = const_cast<LaneInfo*>(c.lane) + ids[k];
+    if (mode == 0) li->vmax = __int_as_float(vals[k]);
+    else li->flags = vals[k] ? (li->flags | LF_RESTRICTED) : (li->flags & ~LF_RESTRICTED);
+}
+
+// metrics of the current snapshot (R24): queue length of lanes [l0, l1) —
+// vehicles with v < 0.1 m/s within the last 50 m (the lane's segment is
+// ordered from its end, so the scan stops at the first vehicle farther away)
+template <typename Real>
+__global__ void k_lane_queue(Ctx<Real> c, int l0, int l1, int32_t* out) {
+    const int l = l0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= l1) return;
+    const double L = (double)c.lane[l].L;
+    int q = 0;
+    for (int k = c.cur.off[l]; k < c.cur.off[l + 1]; ++k) {
+        const RecA<Real> a = c.cur.a[k];
+        if (L - (double)a.s > 50.0) break;
+        if ((double)a.v < 0.1) ++q;
+    }
+    out[l - l0] = q;
+}
+
+// average vehicle speed of roads [r0, r1) (R24): mean speed of the vehicles
+// on the road's lanes, the mean speed limit of its lanes when it is empty
+template <typename Real>
+__global__ void k_road_speed(Ctx<Real> c, int r0, int r1, double* out) {
+    const int r = r0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= r1) return;
+    const int2 sp = c.road_span[r];
+    double sum = 0.0, lim = 0.0;
+    int cnt = 0;
+    for (int l = sp.x; l < sp.y; ++l) {
+        lim += (double)c.lane[l].vmax;
+        for (int k = c.cur.off[l]; k < c.cur.off[l + 1]; ++k) sum += (double)c.cur.a[k].v;
+        cnt += c.cur.off[l + 1] - c.cur.off[l];
+    }
+    out[r - r0] = cnt > 0 ? sum / (double)cnt : lim / (double)(sp.y - sp.x);
 }
 
 // Failure-detection self-test: the look-back of tile 1 waits on tile word 0,
