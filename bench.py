@@ -282,6 +282,15 @@ def run_ours(args):
             mk = sim.metrics()
         e2e_s = time.perf_counter() - t0
         e2e_upd = mk["vehicle_updates"] - me0["vehicle_updates"]
+        # the lane / road metric calls of the public API on the same state
+        # (kernel + device-to-host copy of the per-lane / per-road arrays)
+        metric_ms = {}
+        for name, call in (("lane_queue", sim.lane_queue), ("road_speed", sim.road_speed)):
+            call()
+            t1 = time.perf_counter()
+            for _ in range(5):
+                call()
+            metric_ms[name] = (time.perf_counter() - t1) / 5 * 1e3
         e2e_val = e2e_upd / e2e_s
         if dist:
             e2e_s_all, e2e_upd_all = reduce_ranks(dist, e2e_s, float(e2e_upd), device="cuda")
@@ -323,6 +332,7 @@ def run_ours(args):
                 "api": ("moss_step(1) + moss_get_metrics per step" if mp else
                         "moss_set_signal_phase + moss_step(1) + moss_get_metrics per step")},
         "gpu_launches": 4 * args.steps,
+        "metric_calls_ms": metric_ms,
         "wall_s_timed_region": wall,
         "cpu_baseline": cpu,
     }
