@@ -77,6 +77,8 @@ def _setup(lib):
     lib.mo_set_lane_max_speed.argtypes = [vp, ctypes.c_int, vp, vp]
     lib.mo_set_lane_restriction.argtypes = [vp, ctypes.c_int, vp, vp]
     lib.mo_lane_queue.argtypes = [vp, vp]
+    lib.mo_set_vehicle_route.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
+    lib.mo_set_vehicle_route.restype = ctypes.c_int
     lib.mo_road_speed.argtypes = [vp, vp]
     lib.mo_idm.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     lib.mo_idm.restype = ctypes.c_double
@@ -187,6 +189,11 @@ class Oracle:
         l = np.ascontiguousarray(lanes, dtype=np.int32)
         f = np.ascontiguousarray(flags, dtype=np.int32)
         self._lib.mo_set_lane_restriction(self.h, len(l), _p(l), _p(f))
+
+    def set_vehicle_route(self, vid: int, roads) -> bool:
+        """Replace the route of vehicle vid (reading R26); False if refused."""
+        r = np.ascontiguousarray(roads, dtype=np.int32)
+        return self._lib.mo_set_vehicle_route(self.h, int(vid), len(r), _p(r)) == 0
 
     def lane_queue(self) -> np.ndarray:
         out = np.zeros(int(self.net.n_lanes), dtype=np.int32)

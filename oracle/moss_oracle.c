@@ -89,6 +89,12 @@
  *       its lane as before a red light (R12, R13); MOBIL treats a restricted
  *       adjacent lane as absent; no departure is inserted onto it.  Vehicles
  *       already on it drive on.
+ *   R26 re-routing (§3.2 "Vehicle", set_vehicle_route): the new route starts
+ *       with the road the vehicle is on (a waiting vehicle: the road of its
+ *       start lane; on a junction lane: the road it is entering, the road
+ *       just left is kept in front), consecutive roads must be joined by a
+ *       junction lane, and the vehicle arrives at the end of the new route's
+ *       last road as every trip does.
  */
 #include <math.h>
 #include <stdint.h>
@@ -141,7 +147,8 @@ typedef struct {
     int *restricted;                   /* per lane: restricted from passing (R25) */
     /* vehicles */
     int n_veh;
-    int *route_off, *routes, *start_lane, *dep;
+    int *route_beg, *route_len, *routes, *start_lane, *dep;  /* route of vid: routes[beg .. beg+len) */
+    long routes_used, routes_cap;
     double *v0f;
     /* runtime state */
     int *status, *lane, *rc, *flags;
@@ -228,9 +235,12 @@ void* mo_create(int n_roads, const int* road_lane_off, int n_lanes, int n_road_l
     O->mp_pending = (int*)xcalloc(n_junctions, sizeof(int));
     O->restricted = (int*)xcalloc(n_lanes, sizeof(int));
 
-    O->route_off = (int*)xcalloc(n_veh + 1, sizeof(int));
-    memcpy(O->route_off, route_off, sizeof(int) * (n_veh + 1));
-    O->routes = (int*)xcalloc(route_off[n_veh], sizeof(int));
+    O->route_beg = (int*)xcalloc(n_veh, sizeof(int));
+    O->route_len = (int*)xcalloc(n_veh, sizeof(int));
+    for (int i = 0; i < n_veh; ++i) { O->route_beg[i] = route_off[i]; O->route_len[i] = route_off[i + 1] - route_off[i]; }
+    O->routes_used = route_off[n_veh];
+    O->routes_cap = route_off[n_veh] > 0 ? route_off[n_veh] : 1;
+    O->routes = (int*)xcalloc(O->routes_cap, sizeof(int));
     memcpy(O->routes, routes, sizeof(int) * route_off[n_veh]);
     O->start_lane = (int*)xcalloc(n_veh, sizeof(int));
     O->dep = (int*)xcalloc(n_veh, sizeof(int));
@@ -286,7 +296,7 @@ void mo_destroy(void* h) {
     void* ptrs[] = {O->road_lane_off, O->lane_road, O->L, O->vmax, O->jl_off, O->jl_target,
                     O->jl_junction, O->jl_mask, O->junc_offset, O->junc_phase_off,
                     O->phase_green, O->phase_amber, O->junc_policy, O->junc_manual,
-                    O->jl_from, O->mp_phase, O->mp_elapsed, O->mp_pending, O->restricted, O->route_off, O->routes, O->start_lane, O->dep, O->v0f, O->status,
+                    O->jl_from, O->mp_phase, O->mp_elapsed, O->mp_pending, O->restricted, O->route_beg, O->route_len, O->routes, O->start_lane, O->dep, O->v0f, O->status,
                     O->lane, O->rc, O->flags, O->s, O->v, O->q_off, O->q_ids, O->q_head};
     for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); ++i) free(ptrs[i]);
     free(O);
@@ -375,6 +385,49 @@ void mo_set_lane_max_speed(void* h, int n, const int* lanes, const double* vmax)
 void mo_set_lane_restriction(void* h, int n, const int* lanes, const int* flags) {
     Oracle* O = (Oracle*)h;
     for (int k = 0; k < n; ++k) O->restricted[lanes[k]] = flags[k] != 0;
+}
+
+/* R26: replace the route of vehicle vid by roads[0..n); returns 0, or -1 if
+ * the vehicle has arrived, the route does not start with the vehicle's road,
+ * or two consecutive roads are not joined by a junction lane. */
+static int roads_joined(const Oracle* O, int a, int b) {
+    for (int l = O->road_lane_off[a]; l < O->road_lane_off[a + 1]; ++l)
+        for (int j = O->jl_off[l]; j < O->jl_off[l + 1]; ++j)
+            if (O->lane_road[O->jl_target[j]] == b) return 1;
+    return 0;
+}
+
+int mo_set_vehicle_route(void* h, int vid, int n, const int* roads) {
+    Oracle* O = (Oracle*)h;
+    if (vid < 0 || vid >= O->n_veh || n < 1 || O->status[vid] == ST_ARRIVED) return -1;
+    for (int k = 0; k < n; ++k)
+        if (roads[k] < 0 || roads[k] >= O->n_roads) return -1;
+    int prev = -1;  /* on a junction lane: the road just left stays in front */
+    if (O->status[vid] == ST_WAITING) {
+        if (roads[0] != O->lane_road[O->start_lane[vid]]) return -1;
+    } else if (O->lane[vid] < O->n_road_lanes) {
+        if (roads[0] != O->lane_road[O->lane[vid]]) return -1;
+    } else {
+        int jl = O->lane[vid];
+        if (roads[0] != O->lane_road[O->jl_target[jl]]) return -1;
+        prev = O->lane_road[O->jl_from[jl]];
+    }
+    for (int k = 0; k + 1 < n; ++k)
+        if (!roads_joined(O, roads[k], roads[k + 1])) return -1;
+    long need = O->routes_used + n + 1;
+    if (need > O->routes_cap) {
+        long cap = O->routes_cap * 2 > need ? O->routes_cap * 2 : need;
+        O->routes = (int*)realloc(O->routes, sizeof(int) * cap);
+        O->routes_cap = cap;
+    }
+    int beg = (int)O->routes_used, len = 0;
+    if (prev >= 0) O->routes[beg + len++] = prev;
+    for (int k = 0; k < n; ++k) O->routes[beg + len++] = roads[k];
+    O->routes_used += len;
+    O->route_beg[vid] = beg;
+    O->route_len[vid] = len;
+    if (O->status[vid] == ST_ACTIVE) O->rc[vid] = 0;
+    return 0;
 }
 
 /* R24 metrics of the current state: queue length per lane (out[n_lanes]) and
@@ -531,7 +584,7 @@ static int rearmost_on(const Snap* S, int lane) {
  * cursor is rc (index of the road just left when on a junction lane).
  * Writes the cursor that applies on the returned lane.  -1 if none. */
 static int next_lane(const Oracle* O, int vid, int lane, int rc, int* rc_next) {
-    int r0 = O->route_off[vid], last = O->route_off[vid + 1] - r0 - 1;
+    int r0 = O->route_beg[vid], last = O->route_len[vid] - 1;
     if (lane < O->n_road_lanes) {
         if (rc >= last) return -1;
         int out_road = O->routes[r0 + rc + 1];
@@ -827,7 +880,7 @@ static void step_once(Oracle* O) {
         /* a vehicle held by the stop line cannot leave its lane (R13) */
         if (la->stop && s_new > O->L[lane]) s_new = O->L[lane];
         int rc = S.rc[i];
-        int last = O->route_off[i + 1] - O->route_off[i] - 1;
+        int last = O->route_len[i] - 1;
         int arrived = 0, iter = 0;
         for (;;) {
             double Ll = O->L[lane];

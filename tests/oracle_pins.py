@@ -578,11 +578,56 @@ def check_lane_restriction(libpath=None):
     assert stt["status"][0] == 0 and stt["status"][1] == 1
 
 
+def check_reroute(libpath=None):
+    """R26 on a corridor of three 300 m roads (route 0-1-2): cut to 0-1 while
+    on road 0, or to 1 while on the junction lane into road 1, the car
+    arrives at the end of road 1 and never enters road 2; refused: a route not
+    starting with the car's road, roads not joined, an arrived car."""
+    L = 300.0
+    for when in ("road", "junction"):
+        scen = corridor((L, L, L), [(0, 0)], turn_len=10.0)
+        net = scen.net
+        o = _oracle(scen, None, libpath)
+        o.set_signal(list(range(net.n_junctions)), oracle.POLICY_NONE)
+        lr = net.lane_road()
+        t = 0
+        while True:
+            st = o.state()
+            lane = int(st["lane"][0])
+            if when == "road" and st["status"][0] == 1 and lane == 0:
+                assert not o.set_vehicle_route(0, [1, 2])      # must start with road 0
+                assert o.set_vehicle_route(0, [0, 1])
+                break
+            if when == "junction" and st["status"][0] == 1 and lane >= net.n_road_lanes:
+                assert not o.set_vehicle_route(0, [0, 1])      # the junction lane enters road 1
+                assert o.set_vehicle_route(0, [1])
+                break
+            o.step(1)
+            t += 1
+            assert t < 200
+        roads_seen = set()
+        for k in range(400):
+            o.step(1)
+            st = o.state()
+            if st["status"][0] == 2:
+                break
+            if st["lane"][0] < net.n_road_lanes:
+                roads_seen.add(int(lr[st["lane"][0]]))
+        assert st["status"][0] == 2 and 2 not in roads_seen, (when, roads_seen)
+        assert st["rc"][0] == (1 if when == "road" else 1)  # the last road of the stored route
+        assert not o.set_vehicle_route(0, [1])                # arrived
+    # roads that are not joined
+    scen = corridor((L, L, L), [(0, 50)])
+    o = _oracle(scen, None, libpath)
+    assert not o.set_vehicle_route(0, [0, 2])
+    assert o.set_vehicle_route(0, [0])                         # waiting: starts with its start road
+
+
 ALL_CHECKS = [
     check_idm_free_road, check_idm_equilibrium, check_p_lc, check_mobil_case_A,
     check_mobil_case_B, check_mobil_case_C, check_mobil_case_D, check_mobil_mirror, check_neighbours_bruteforce,
     check_free_road_vs_rk4, check_platoon_equilibrium, check_red_light, check_signal_program,
     check_arrival_and_travel_time, check_insertion, check_conflict, check_max_pressure_argmax,
     check_max_pressure_timing, check_lane_queue_and_road_speed, check_lane_max_speed,
-    check_lane_restriction,
+    check_lane_restriction, check_reroute,
 ]

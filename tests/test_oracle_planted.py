@@ -43,6 +43,8 @@ MUTATIONS = [
     ("restriction_ignored_by_mobil", "if (tl < lo || tl >= hi || O->restricted[tl]) continue;",
      "if (tl < lo || tl >= hi) continue;"),
     ("max_speed_setter_ignored", "for (int k = 0; k < n; ++k) O->vmax[lanes[k]] = vmax[k];", "(void)vmax;"),
+    ("reroute_drops_road_just_left", "    if (prev >= 0) O->routes[beg + len++] = prev;\n", "\n"),
+    ("reroute_start_unchecked", "        if (roads[0] != O->lane_road[O->lane[vid]]) return -1;\n", "\n"),
     ("maxp_ties_to_smallest", "if (pk > pb || (pk == pb && best != p && k < best)) best = k;",
      "if (pk > pb || (pk == pb && k < best)) best = k;"),
 ]
