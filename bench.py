@@ -43,6 +43,36 @@ SPEC_BYTES = {  # algorithmic bytes per unit, FP32 state
 STEP_BYTES = 64.0      # whole step: read and write one 8x4 B state record per vehicle update
 
 
+PROFILE = os.path.join(ROOT, "profiles", "step_kernels_city100x100_2464950.md")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2406_10661_gb300", "csrc", f)
+                  for f in ("moss_device.cuh", "moss_kernels.cuh")]
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def captured_traffic(kernel: str):
+    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu
+    summary, if that capture was taken from the current kernel sources (the
+    summary records their SHA-256); else None."""
+    try:
+        with open(PROFILE) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) == 4 and parts[0] == "traffic:" and parts[1] == kernel:
+                    if parts[3] == "sha256:" + kernel_source_hash():
+                        return float(parts[2])
+    except OSError:
+        pass
+    return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -319,7 +349,7 @@ def run_ours(args):
         "paper_context": {"step_hz": 84.09, "vehicles": 2464950, "hardware": "RTX 4090 + Xeon 8462Y",
                           "note": "different network (CBLab Roadnet-L); context only"},
         "roofline": {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": captured_traffic(f"k_{dom}"),
                      "peak_source": peak_kind,
                      "bytes_per_unit": SPEC_BYTES[dom], "units_per_launch": units[dom],
                      "avg_launch_ms": avg_ms[dom]},

@@ -207,6 +207,22 @@ int moss_set_lane_max_speed(moss_t h, int n, const int32_t* lane_ids, const floa
 int moss_set_lane_restriction(moss_t h, int n, const int32_t* lane_ids, const int32_t* flags);
 
 /*
+ * Re-routing (§3.2 "Vehicle", set_vehicle_route) of n vehicles of a
+ * single-scenario handle (scenario 0 of a batch): vehicle vehicle_ids[k]
+ * gets the route roads[route_off[k] .. route_off[k+1]) (host arrays; road
+ * ids).  The new route starts with the road the vehicle is on (a waiting
+ * vehicle: the road of its start lane; a vehicle on a junction lane: the
+ * road it is entering), every turn of it must be available from every lane,
+ * and the vehicle arrives at the end of its last road as every trip does
+ * (no destination inside a road).  All requests are checked before any is
+ * applied: MOSS_EINVAL (arrived vehicle, route not starting with the
+ * vehicle's road, roads not joined, duplicate or out-of-range ids) changes
+ * nothing.  Effective from the next step; waits for the handle's stream.
+ */
+int moss_set_vehicle_route(moss_t h, int n, const int32_t* vehicle_ids, const int32_t* route_off,
+                           const int32_t* roads);
+
+/*
  * Lane and road metrics of the current state (§3.3 "Lane Queue Length",
  * "Road Traveling Time"), into caller-owned host arrays:
  *   - moss_get_lane_queue: queue[l] for every lane l of the scenario = the

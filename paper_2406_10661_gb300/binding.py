@@ -75,6 +75,7 @@ SIGNATURES = {
     "moss_set_signal_phase": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p, _c_i32p]),
     "moss_set_signal_policy": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p, ctypes.c_int32]),
     "moss_get_signal_state": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p, _c_i32p, _c_i32p, _c_i32p]),
+    "moss_set_vehicle_route": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p, _c_i32p, _c_i32p]),
     "moss_set_lane_max_speed": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p, ctypes.POINTER(ctypes.c_float)]),
     "moss_set_lane_restriction": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p, _c_i32p]),
     "moss_get_lane_queue": (ctypes.c_int, [_vp, _c_i32p]),
@@ -288,6 +289,16 @@ class Simulation(_Handle):
         j = np.ascontiguousarray(junctions, dtype=np.int32)
         _check(self.lib.moss_set_signal_policy(self.h, len(j), _ptr(j, ctypes.c_int32),
                                                int(policy)), self.h)
+
+    def set_vehicle_route(self, vehicles: Sequence[int], routes) -> None:
+        """New routes (lists of road ids) for the given vehicles (all or nothing)."""
+        v = np.ascontiguousarray(vehicles, dtype=np.int32)
+        off = np.zeros(len(v) + 1, dtype=np.int32)
+        off[1:] = np.cumsum([len(r) for r in routes])
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(r, dtype=np.int32) for r in routes])
+                                    if len(routes) else np.zeros(0, dtype=np.int32), dtype=np.int32)
+        _check(self.lib.moss_set_vehicle_route(self.h, len(v), _ptr(v, ctypes.c_int32), _ptr(off, ctypes.c_int32),
+                                               _ptr(flat, ctypes.c_int32)), self.h)
 
     def set_lane_max_speed(self, lanes: Sequence[int], vmax) -> None:
         l = np.ascontiguousarray(lanes, dtype=np.int32)

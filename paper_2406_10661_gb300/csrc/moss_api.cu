@@ -44,7 +44,10 @@ struct MossHandle {
     std::vector<LaneInfo> lanes;
     std::vector<int32_t> lane_src_road;  // junction lanes: the road they leave
     std::vector<int32_t> junc_scen, junc_phase_off;
-    std::vector<int32_t> route_off, routes, dep, start_lane, veh_scen;
+    std::vector<int32_t> routes, dep, start_lane, veh_scen;
+    std::vector<int2> route_span;     // route of vehicle g: routes[span.x .. span.y)
+    size_t routes_cap = 0;            // capacity of d_routes (entries)
+    int32_t* d_req = nullptr;         // [n_veh] re-routing marks (-1)
     std::vector<float> v0f;
     std::vector<int32_t> q_off, q_ids, start_lanes;
     std::vector<int32_t> scen_veh_off, scen_lane_off, scen_junc_off;
@@ -66,7 +69,8 @@ struct MossHandle {
     std::vector<int> scen_road_off;   // [n_scen+1]
     int32_t* d_lstage = nullptr;      // setter arguments for lanes (2 * n_lanes)
     void* d_mbuf = nullptr;           // metric output (max(n_lanes, n_roads) doubles)
-    int32_t *d_route_off = nullptr, *d_routes = nullptr, *d_dep = nullptr, *d_vstatus = nullptr,
+    int2* d_route_span = nullptr;
+    int32_t *d_routes = nullptr, *d_dep = nullptr, *d_vstatus = nullptr,
             *d_vflags = nullptr;
     int32_t *d_q_off = nullptr, *d_q_ids = nullptr, *d_q_head = nullptr, *d_start_lanes = nullptr;
     uint32_t *d_key0 = nullptr, *d_key1 = nullptr;
@@ -263,7 +267,7 @@ Ctx<Real> make_ctx(MossHandle* h, int cur) {
     c.mp = h->d_mp; c.jj_off = h->d_jj_off; c.jj_lane = h->d_jj_lane; c.jj_from = h->d_jj_from;
     c.n_jj = h->n_jj; c.mp_press = h->d_mp_press; c.n_mp = &h->d_cnt[0].n_mp;
     c.road_span = h->d_road_span;
-    c.route_off = h->d_route_off; c.routes = h->d_routes; c.dep = h->d_dep; c.v0f = h->d_v0f;
+    c.route_span = h->d_route_span; c.routes = h->d_routes; c.dep = h->d_dep; c.v0f = h->d_v0f;
     c.vstatus = h->d_vstatus; c.vflags = h->d_vflags;
     c.q_off = h->d_q_off; c.q_ids = h->d_q_ids; c.q_head = h->d_q_head;
     c.start_lanes = h->d_start_lanes; c.n_start = (int)h->start_lanes.size();
@@ -423,14 +427,13 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
     h->lane_src_road.assign(NL, -1);
     h->junc_scen.resize(NJ); h->junc_phase_off.resize(NJ + 1);
     std::vector<int32_t> junc_offset(NJ), phase_green(tot_ph), phase_amber(tot_ph);
-    h->route_off.resize(NV + 1); h->routes.resize(tot_routes); h->dep.resize(NV);
+    h->route_span.resize(NV); h->routes.resize(tot_routes); h->dep.resize(NV);
     h->start_lane.resize(NV); h->v0f.resize(NV); h->veh_scen.resize(NV);
     h->scen_veh_off.assign(n + 1, 0); h->scen_lane_off.assign(n + 1, 0); h->scen_junc_off.assign(n + 1, 0);
     h->scen_road_off.assign(n + 1, 0);
     h->road_span.assign(tot_roads, make_int2(0, 0));
     h->key0.resize(n); h->key1.resize(n);
     int LO = 0, JO = 0, VO = 0, RO = 0, PO = 0, ROFF = 0;
-    h->route_off[0] = 0;
     for (int k = 0; k < n; ++k) {
         const MossNetwork& nt = nets[k];
         const MossVehicles& vh = vehs[k];
@@ -477,7 +480,7 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
             const int g = VO + i;
             const int a = vh.route_off[i], b = vh.route_off[i + 1];
             for (int q = a; q < b; ++q) h->routes[ROFF + q] = RO + vh.routes[q];
-            h->route_off[g + 1] = ROFF + b;
+            h->route_span[g] = make_int2(ROFF + a, ROFF + b);
             h->dep[g] = vh.dep[i];
             h->start_lane[g] = LO + vh.start_lane[i];
             h->v0f[g] = vh.v0f[i];
@@ -560,11 +563,20 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
         TRY(dalloc(h, (char**)&h->d_mbuf, sizeof(double) * (size_t)std::max(std::max(NL, (int)tot_roads), 1)));
         h->n_jj = jj_off[NJ];
     }
-    TRY(upload(h, &h->d_route_off, h->route_off));
-    TRY(upload(h, &h->d_routes, h->routes));
+    {
+        std::vector<int2> span(h->route_span);
+        if (span.empty()) span.push_back(make_int2(0, 0));
+        TRY(upload(h, &h->d_route_span, span));
+        // room for re-routed vehicles' routes (grown on demand)
+        h->routes_cap = h->routes.size() + std::max<size_t>(h->routes.size() / 4, 1 << 16);
+        TRY(dalloc(h, &h->d_routes, h->routes_cap));
+        if (!h->routes.empty())
+            CK(cudaMemcpy(h->d_routes, h->routes.data(), h->routes.size() * 4, cudaMemcpyHostToDevice));
+    }
     TRY(upload(h, &h->d_dep, h->dep));
     TRY(upload(h, &h->d_v0f, h->v0f));
     TRY(upload(h, &h->d_vstatus, std::vector<int32_t>(NV, MOSS_ST_WAITING)));
+    TRY(upload(h, &h->d_req, std::vector<int32_t>(std::max(NV, 1), -1)));
     TRY(upload(h, &h->d_vflags, std::vector<int32_t>(NV, 0)));
     TRY(upload(h, &h->d_q_off, h->q_off));
     TRY(upload(h, &h->d_q_ids, h->q_ids));
@@ -706,7 +718,7 @@ int scen_state(MossHandle* h, int s, MossState* out) {
         out->lane[i] = lane[k] - lo;
         out->s[i] = sv[k];
         out->v[i] = vv[k];
-        out->rc[i] = rb[k].rptr - h->route_off[g];
+        out->rc[i] = rb[k].rptr - h->route_span[g].x;
     }
     return check_device(h);
 }
@@ -730,8 +742,8 @@ int upload_state(MossHandle* h, const std::vector<int>& order, const std::vector
         std::memset(&a[k], 0, sizeof(a[k]));
         a[k].s = Real(s[g]); a[k].v = Real(v[g]); a[k].id = g; a[k].lane = l;
         b[k].v0f = h->v0f[g];
-        b[k].rptr = h->route_off[g] + rc[g];
-        b[k].rlast = h->route_off[g + 1] - 1;
+        b[k].rptr = h->route_span[g].x + rc[g];
+        b[k].rlast = h->route_span[g].y - 1;
         if (h->lanes[l].lo < 0) b[k].nl = h->lanes[l].hi;
         else b[k].nl = b[k].rptr < b[k].rlast ? jl_toward_host(h, l, h->routes[b[k].rptr + 1]) : -1;
         off[l + 1]++;
@@ -777,6 +789,134 @@ int set_lane(MossHandle* h, int n, const int32_t* lane_ids, const int32_t* vals,
         else li.flags = vals[k] ? (li.flags | LF_RESTRICTED) : (li.flags & ~LF_RESTRICTED);
     }
     return MOSS_OK;
+}
+
+// road b is reachable from every lane of road a (the rule routes obey)
+bool turn_from_every_lane(const MossHandle* h, int a, int b) {
+    const int2 sp = h->road_span[a];
+    for (int l = sp.x; l < sp.y; ++l) {
+        bool ok = false;
+        for (int j = h->lanes[l].jb; j < h->lanes[l].je && !ok; ++j) ok = h->lanes[j].road == b;
+        if (!ok) return false;
+    }
+    return true;
+}
+
+template <typename Real>
+int reroute_impl(MossHandle* h, int n, const int32_t* vids, const int32_t* route_off, const int32_t* roads) {
+    const int nv0 = h->scen_veh_off[1], nr0 = h->scen_road_off[1];
+    // device scratch for this call
+    int32_t *d_v = nullptr, *d_lane = nullptr;
+    int2* d_sp = nullptr;
+    auto cleanup = [&]() { cudaFree(d_v); cudaFree(d_lane); cudaFree(d_sp); };
+    if (cudaMalloc(&d_v, n * 4) != cudaSuccess || cudaMalloc(&d_lane, n * 4) != cudaSuccess ||
+        cudaMalloc(&d_sp, n * sizeof(int2)) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return fail(h, MOSS_ENOMEM, "re-routing scratch");
+    }
+    Ctx<Real> c = make_ctx<Real>(h, h->parity);
+    const int nb = (n + 255) / 256, grid = std::max(1, h->sm_count * 4);
+    std::vector<int32_t> lane(n, -1), status(nv0);
+    cudaError_t e = cudaMemcpy(d_v, vids, n * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_lane, lane.data(), n * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_mark_vehicles<<<nb, 256, 0, h->stream>>>(h->d_req, n, d_v, 1);
+        k_find_lanes<Real><<<grid, 256, 0, h->stream>>>(c, h->d_req, d_lane);
+        e = cudaStreamSynchronize(h->stream);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(lane.data(), d_lane, n * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(status.data(), h->d_vstatus, nv0 * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(h, MOSS_ECUDA, cudaGetErrorString(e));
+    }
+    // validate every request first (all or nothing)
+    std::string why;
+    std::vector<int> prev(n, -1);
+    for (int k = 0; k < n && why.empty(); ++k) {
+        const int g = vids[k], a = route_off[k], b = route_off[k + 1];
+        if (status[g] == MOSS_ST_ARRIVED) { why = "vehicle has arrived"; break; }
+        int first;
+        if (status[g] == MOSS_ST_WAITING) {
+            first = h->lanes[h->start_lane[g]].road;
+        } else {
+            const int l = lane[k];
+            if (l < 0) { why = "active vehicle not found"; break; }
+            first = h->lanes[l].road;  // a junction lane: the road it enters
+            if (h->lanes[l].lo < 0) prev[k] = h->lane_src_road[l];
+        }
+        if (roads[a] != first) { why = "the route must start with the vehicle's road"; break; }
+        for (int q = a; q + 1 < b; ++q)
+            if (!turn_from_every_lane(h, roads[q], roads[q + 1])) { why = "roads not joined"; break; }
+    }
+    if (!why.empty()) {
+        k_mark_vehicles<<<nb, 256, 0, h->stream>>>(h->d_req, n, d_v, 0);
+        cudaStreamSynchronize(h->stream);
+        cleanup();
+        return fail(h, MOSS_EINVAL, why);
+    }
+    // append the routes (the road just left stays in front for a vehicle on
+    // a junction lane)
+    const size_t old = h->routes.size();
+    std::vector<int2> sp(n);
+    for (int k = 0; k < n; ++k) {
+        const int beg = (int)h->routes.size();
+        if (prev[k] >= 0) h->routes.push_back(prev[k]);
+        for (int q = route_off[k]; q < route_off[k + 1]; ++q) h->routes.push_back(roads[q]);
+        sp[k] = make_int2(beg, (int)h->routes.size());
+    }
+    if (h->routes.size() > h->routes_cap) {  // grow the device route buffer
+        const size_t cap = std::max(h->routes.size(), 2 * h->routes_cap);
+        int32_t* nr = nullptr;
+        if (cudaMalloc(&nr, cap * 4) != cudaSuccess) {
+            cudaGetLastError();
+            h->routes.resize(old);
+            k_mark_vehicles<<<nb, 256, 0, h->stream>>>(h->d_req, n, d_v, 0);
+            cudaStreamSynchronize(h->stream);
+            cleanup();
+            return fail(h, MOSS_ENOMEM, "route buffer");
+        }
+        cudaMemcpy(nr, h->d_routes, old * 4, cudaMemcpyDeviceToDevice);
+        for (auto& p : h->allocs)
+            if (p == (void*)h->d_routes) p = (void*)nr;
+        cudaFree(h->d_routes);
+        h->d_routes = nr;
+        h->routes_cap = cap;
+        destroy_graphs(h);
+        TRY(build_graphs(h));
+        c = make_ctx<Real>(h, h->parity);
+    }
+    e = cudaMemcpy(h->d_routes + old, h->routes.data() + old, (h->routes.size() - old) * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_sp, sp.data(), n * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_apply_routes<Real><<<grid, 256, 0, h->stream>>>(c, h->d_req, n, d_v, d_sp);
+        k_mark_vehicles<<<nb, 256, 0, h->stream>>>(h->d_req, n, d_v, 0);
+        e = cudaStreamSynchronize(h->stream);
+    }
+    cleanup();
+    if (e != cudaSuccess) return fail(h, MOSS_ECUDA, cudaGetErrorString(e));
+    for (int k = 0; k < n; ++k) h->route_span[vids[k]] = sp[k];
+    (void)nr0;
+    return check_device(h);
+}
+
+int reroute(MossHandle* h, int n, const int32_t* vids, const int32_t* route_off, const int32_t* roads) {
+    const int nv0 = h->scen_veh_off[1], nr0 = h->scen_road_off[1];
+    if (n < 0 || (n > 0 && (!vids || !route_off || !roads))) return fail(h, MOSS_EINVAL, "bad arrays");
+    if (n == 0) return MOSS_OK;
+    if (route_off[0] != 0) return fail(h, MOSS_EINVAL, "route_off[0] != 0");
+    std::vector<char> seen(nv0, 0);
+    for (int k = 0; k < n; ++k) {
+        if (vids[k] < 0 || vids[k] >= nv0) return fail(h, MOSS_EINVAL, "vehicle id out of range");
+        if (seen[vids[k]]++) return fail(h, MOSS_EINVAL, "a vehicle appears twice");
+        if (route_off[k + 1] <= route_off[k]) return fail(h, MOSS_EINVAL, "every route needs a road");
+        for (int q = route_off[k]; q < route_off[k + 1]; ++q)
+            if (roads[q] < 0 || roads[q] >= nr0) return fail(h, MOSS_EINVAL, "road id out of range");
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return h->precision == 64 ? reroute_impl<double>(h, n, vids, route_off, roads)
+                              : reroute_impl<float>(h, n, vids, route_off, roads);
 }
 
 template <typename Real>
@@ -924,6 +1064,12 @@ int moss_set_signal_policy(moss_t h, int n, const int32_t* junction_ids, int32_t
     return MOSS_OK;
 }
 
+int moss_set_vehicle_route(moss_t h, int n, const int32_t* vehicle_ids, const int32_t* route_off,
+                           const int32_t* roads) {
+    if (!h) return MOSS_EINVAL;
+    return reroute(h, n, vehicle_ids, route_off, roads);
+}
+
 int moss_set_lane_max_speed(moss_t h, int n, const int32_t* lane_ids, const float* vmax) {
     if (!h) return MOSS_EINVAL;
     if (n > 0 && !vmax) return fail(h, MOSS_EINVAL, "bad arrays");
@@ -1030,15 +1176,15 @@ int moss_set_state(moss_t h, const MossState* in, int64_t step) {
         if (st != MOSS_ST_ACTIVE) continue;
         n_act++;
         const int l = in->lane[i];
-        const int nr = h->route_off[i + 1] - h->route_off[i];
+        const int nr = h->route_span[i].y - h->route_span[i].x;
         if (l < 0 || l >= h->n_lanes) return fail(h, MOSS_EINVAL, "active vehicle on a bad lane");
         if (rc[i] < 0 || rc[i] >= nr) return fail(h, MOSS_EINVAL, "route cursor out of range");
-        const int road = h->routes[h->route_off[i] + rc[i]];
+        const int road = h->routes[h->route_span[i].x + rc[i]];
         if (h->lanes[l].lo >= 0) {
             if (h->lanes[l].road != road) return fail(h, MOSS_EINVAL, "lane is not on the route's road");
         } else {
             if (rc[i] + 1 >= nr || h->lane_src_road[l] != road ||
-                h->lanes[l].road != h->routes[h->route_off[i] + rc[i] + 1])
+                h->lanes[l].road != h->routes[h->route_span[i].x + rc[i] + 1])
                 return fail(h, MOSS_EINVAL, "junction lane does not join the route's roads");
         }
         if (!(s[i] >= 0.0 && s[i] <= h->lanes[l].L) || !(v[i] >= 0.0) || !std::isfinite(v[i]))

@@ -157,7 +157,7 @@ struct Ctx {
     int32_t* mp_press;       // [n_junctions][8] phase pressures of this step, summed by k_resolve
     int* n_mp;               // junctions under max pressure
     // ---- vehicles (by global id)
-    const int32_t* route_off;
+    const int2* route_span;  // [n_veh] route of a vehicle: routes[x .. y)
     const int32_t* routes;
     const int32_t* dep;
     const float* v0f;

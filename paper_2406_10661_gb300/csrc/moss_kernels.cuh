@@ -42,7 +42,8 @@ __device__ void insert_departure(const Ctx<Real>& c, int l, int tag) {
         if (!(g >= Real(0))) return;
     }
     const int q = warp_claim(&c.cnt->n_ent);
-    const int r0 = c.route_off[vid], r1 = c.route_off[vid + 1] - 1;
+    const int2 rs = c.route_span[vid];
+    const int r0 = rs.x, r1 = rs.y - 1;
     int nl = -1;
     if (r0 < r1) {
         nl = jl_toward(c, c.lane[l], c.routes[r0 + 1]);
@@ -742,6 +743,43 @@ __global__ void k_road_speed(Ctx<Real> c, int r0, int r1, double* out) {
         cnt += c.cur.off[l + 1] - c.cur.off[l];
     }
     out[r - r0] = cnt > 0 ? sum / (double)cnt : lim / (double)(sp.y - sp.x);
+}
+
+// Re-routing (R26): mark the requested vehicles (req[vid] = their index in
+// the request, -1 otherwise), find the lanes of the active ones, and give
+// them their new routes (route spans; for the active ones the snapshot
+// record's route cursor, last road and next lane).
+__global__ void k_mark_vehicles(int32_t* req, int n, const int32_t* vids, int on) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) req[vids[k]] = on ? k : -1;
+}
+
+template <typename Real>
+__global__ void k_find_lanes(Ctx<Real> c, const int32_t* req, int32_t* lane_out) {
+    const int n = c.cnt->n_cur;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const RecA<Real> a = c.cur.a[i];
+        const int k = req[a.id];
+        if (k >= 0) lane_out[k] = a.lane;
+    }
+}
+
+template <typename Real>
+__global__ void k_apply_routes(Ctx<Real> c, const int32_t* req, int nv, const int32_t* vids, const int2* spans) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nv; k += gridDim.x * blockDim.x)
+        const_cast<int2*>(c.route_span)[vids[k]] = spans[k];
+    const int n = c.cnt->n_cur;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const RecA<Real> a = c.cur.a[i];
+        const int k = req[a.id];
+        if (k < 0) continue;
+        RecB b = c.cur.b[i];
+        b.rptr = spans[k].x;
+        b.rlast = spans[k].y - 1;
+        const LaneInfo li = c.lane[a.lane];
+        if (li.lo >= 0) b.nl = b.rptr < b.rlast ? jl_toward(c, li, c.routes[b.rptr + 1]) : -1;
+        c.cur.b[i] = b;
+    }
 }
 
 // Failure-detection self-test: the look-back of tile 1 waits on tile word 0,
