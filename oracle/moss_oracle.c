@@ -95,7 +95,20 @@
  *       just left is kept in front), consecutive roads must be joined by a
  *       junction lane, and the vehicle arrives at the end of the new route's
  *       last road as every trip does.
+ *   R27 lane groups (App. B.3: vehicles may not change lanes away from the
+ *       group of lanes that gives access to the next road): the group of a
+ *       vehicle is the set of lanes of its road with a junction lane to the
+ *       next road of its route.  Inside the group, MOBIL treats an adjacent
+ *       lane outside it as absent.  Outside the group (it entered the road
+ *       on a lane without access), the vehicle cannot leave the road from its
+ *       lane: it stops at the lane end as before a red light, and it changes
+ *       one lane towards the nearest lane of the group (ties: left) whenever
+ *       the safety part of R2 holds for that lane (gaps > 0, ã_new >=
+ *       -b_safe) — a mandatory change, without random draws, entered in the
+ *       conflict rule R9 with utility U_MAND (larger than any discretionary
+ *       utility).  On the last road of the route there is no group.
  */
+#define U_MAND 1e30
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -650,7 +663,7 @@ static LaneAcc accel_on_lane(const Oracle* O, const Snap* S, int vid, int lane, 
         }
     }
     if ((lane < O->n_road_lanes && nl1 >= O->n_road_lanes && S->light[nl1] != LIGHT_GREEN) ||
-        (nl1 >= 0 && O->restricted[nl1])) {
+        (nl1 >= 0 && O->restricted[nl1]) || (lane < O->n_road_lanes && nl1 == -2)) {
         double gs = O->L[lane] - s;
         double as = idm(O, v, v0, gs, v);
         if (as < a) a = as;
@@ -663,7 +676,7 @@ static LaneAcc accel_on_lane(const Oracle* O, const Snap* S, int vid, int lane, 
 /* Full per-vehicle decision (everything before conflict resolution). */
 typedef struct {
     LaneAcc own;
-    int eligible, attempted, cand, dir, tl, TL, TF;
+    int eligible, attempted, mandatory, cand, dir, tl, TL, TF;
     double u, scale;
     LaneAcc tgt;          /* ego on the chosen target lane */
     int flag;
@@ -673,6 +686,13 @@ typedef struct {
     double at_ego[2], a_new[2], at_new[2], a_old, at_old;
     int TLs[2], TFs[2], OF, OL;
 } Decision;
+
+/* road lane l has a junction lane to road r (R27) */
+static int has_access(const Oracle* O, int l, int r) {
+    for (int j = O->jl_off[l]; j < O->jl_off[l + 1]; ++j)
+        if (O->lane_road[O->jl_target[j]] == r) return 1;
+    return 0;
+}
 
 static Decision decide(const Oracle* O, const Snap* S, int vid, long t) {
     Decision D;
@@ -687,6 +707,41 @@ static Decision decide(const Oracle* O, const Snap* S, int vid, long t) {
     int lo = O->road_lane_off[road], hi = O->road_lane_off[road + 1];
     if (hi - lo < 2) return D;
     D.eligible = 1;
+    /* the next road of the route and the lane group giving access to it (R27) */
+    int rcv = S->rc[vid];
+    int next_road = rcv < O->route_len[vid] - 1 ? O->routes[O->route_beg[vid] + rcv + 1] : -1;
+    if (next_road >= 0 && !has_access(O, lane, next_road)) {
+        /* mandatory change towards the nearest lane of the group */
+        int best = -1;
+        for (int k = lo; k < hi; ++k)
+            if (has_access(O, k, next_road) && (best < 0 || abs(k - lane) < abs(best - lane))) best = k;
+        D.mandatory = 1;
+        if (best < 0) return D;
+        int dir = best < lane ? -1 : +1, tl = lane + dir;
+        if (O->restricted[tl]) return D;
+        int TL = leader_on(S, tl, s, vid), TF = follower_on(S, tl, s, vid);
+        double pos_scale = s > 1.0 ? s : 1.0;
+        int ok = 1;
+        if (TL >= 0) {
+            double g = S->s[TL] - O->len - s;
+            if (!(g > 0.0)) ok = 0;
+            if (fabs(g) < O->band * pos_scale) D.flag = 1;
+        }
+        if (TF >= 0) {
+            double g = s - O->len - S->s[TF];
+            if (!(g > 0.0)) ok = 0;
+            if (fabs(g) < O->band * pos_scale) D.flag = 1;
+            double at_new = acc_pair(O, S, TF, tl, vid, s, v);
+            if (!(at_new >= -O->b_safe)) ok = 0;
+            double sc = fabs(at_new) > 1.0 ? fabs(at_new) : 1.0;
+            if (fabs(at_new + O->b_safe) < O->band * sc) D.flag = 1;
+        }
+        if (!ok) return D;
+        D.cand = 1; D.dir = dir; D.tl = tl; D.TL = TL; D.TF = TF;
+        D.u = U_MAND; D.scale = 1.0;
+        D.tgt = accel_on_lane(O, S, vid, tl, s, v, rcv);
+        return D;
+    }
     uint32_t ctr[4] = {(uint32_t)vid, (uint32_t)t, 0u, 0u}, w[4];
     mo_philox4x32_10(O->key0, O->key1, ctr, w);
     D.u_att = unit24(w[0]); D.u_lc = unit24(w[1]); D.u_dir = unit24(w[2]);
@@ -710,6 +765,7 @@ static Decision decide(const Oracle* O, const Snap* S, int vid, long t) {
     for (int side = 0; side < 2; ++side) {         /* 0 = left (k-1), 1 = right (k+1) */
         int tl = side == 0 ? lane - 1 : lane + 1;
         if (tl < lo || tl >= hi || O->restricted[tl]) continue;
+        if (next_road >= 0 && !has_access(O, tl, next_road)) continue;  /* leaves the group (R27) */
         int TL = leader_on(S, tl, s, vid), TF = follower_on(S, tl, s, vid);
         TLs[side] = TL; TFs[side] = TF;
         int ok = 1;

@@ -220,7 +220,7 @@ def _f32(a) -> np.ndarray:
 def build_network(jxy: np.ndarray, links: np.ndarray, link_len: np.ndarray,
                   link_lanes: np.ndarray, link_vmax: np.ndarray,
                   junc_offset: np.ndarray, green: int = 30, amber: int = 3,
-                  lane_width: float = 3.5) -> Network:
+                  lane_width: float = 3.5, lane_groups: bool = False) -> Network:
     """Build a network from junction grid coordinates and undirected links.
 
     jxy: int [J,2] grid coordinates (headings are taken from them, so a
@@ -228,6 +228,9 @@ def build_network(jxy: np.ndarray, links: np.ndarray, link_len: np.ndarray,
     Each link gives two one-way roads with the link's length, lane count and
     speed limit.  Every road lane connects to every out-road of its end
     junction except the U-turn; in-lane i feeds out-lane min(i, n_out-1).
+    With ``lane_groups`` the lanes of a road with two or more lanes serve
+    turn groups instead: the leftmost lane left and straight, the rightmost
+    lane right and straight, the lanes between straight only.
     Junction lane lengths: box side W = 2 * lane_width * (max lanes of the
     junction's roads); straight W, right turn pi*W/8, left turn 3*pi*W/8.
     Signals: 4 phases (NS through+right, NS left, EW through+right, EW left),
@@ -276,6 +279,11 @@ def build_network(jxy: np.ndarray, links: np.ndarray, link_len: np.ndarray,
                     turn, length = 2, math.pi * W / 8.0
                 else:
                     turn, length = 0, W
+                if lane_groups and road_lanes[r] > 1:
+                    n_in = road_lanes[r]
+                    allowed = {0} | ({1} if i == 0 else set()) | ({2} if i == n_in - 1 else set())
+                    if turn not in allowed:
+                        continue
                 phase = (0 if ns else 2) + (1 if turn == 1 else 0)
                 tgt = road_lane_off[r2] + min(i, road_lanes[r2] - 1)
                 jl_src.append(src); jl_tgt.append(tgt); jl_len.append(length)
@@ -317,7 +325,7 @@ def _grid_links(G: int) -> Tuple[np.ndarray, np.ndarray]:
 
 def grid_network(G: int, length: float = 200.0, lanes: int = 2, vmax: float = 13.89,
                  vmax_choices=None, offsets: bool = False, seed: int = 0,
-                 green: int = 30, amber: int = 3) -> Network:
+                 green: int = 30, amber: int = 3, lane_groups: bool = False) -> Network:
     """Manhattan grid of G x G signalised junctions (configs "small"/"medium")."""
     jxy, links = _grid_links(G)
     E = len(links)
@@ -329,7 +337,7 @@ def grid_network(G: int, length: float = 200.0, lanes: int = 2, vmax: float = 13
     cycle = 4 * (green + amber)
     off = st.integers(0, cycle, G * G) if offsets else np.zeros(G * G, dtype=np.int64)
     return build_network(jxy, links, np.full(E, length), np.full(E, lanes), lv, off,
-                         green, amber)
+                         green, amber, lane_groups=lane_groups)
 
 
 def perturbed_grid_network(G: int = 100, seed: int = 0, median_len: float = 250.0,
@@ -531,6 +539,15 @@ def small_scenario(seed: int = 0) -> Scenario:
     net = grid_network(4, 200.0, 2, 13.89, offsets=False, seed=seed)
     veh = random_demand(net, 1000, 300, seed=seed)
     return Scenario(net, veh, Params(seed=seed), "grid4x4_1k")
+
+
+def small_groups_scenario(seed: int = 0) -> Scenario:
+    """4x4 grid of 200 m three-lane roads whose lanes serve turn groups (left
+    lane: left + straight, middle: straight, right lane: right + straight),
+    1,500 trips departing over the first 300 s."""
+    net = grid_network(4, 200.0, 3, 13.89, offsets=False, seed=seed, lane_groups=True)
+    veh = random_demand(net, 1500, 300, seed=seed)
+    return Scenario(net, veh, Params(seed=seed), "grid4x4_groups_1500")
 
 
 def medium_scenario(seed: int = 0, n: int = 100_000) -> Scenario:

@@ -623,11 +623,99 @@ def check_reroute(libpath=None):
     assert o.set_vehicle_route(0, [0])                         # waiting: starts with its start road
 
 
+# ---------------------------------------------------------------------------
+# Lane groups (reading R27)
+def _groups_case(lane_idx, turn, cars_extra=(), groups=True, params=None):
+    """3x3 grid of 300 m three-lane roads with turn groups; car 0 on lane
+    `lane_idx` of an approach of the centre junction, 40 m from its start,
+    routed to make `turn` (0 straight, 1 left, 2 right) there.  cars_extra:
+    (lane index on the same road, s, v) cars going straight on.  Returns
+    (scenario, state, approach lanes, out-road of car 0)."""
+    net = sc.grid_network(3, 300.0, 3, 13.89, lane_groups=groups)
+    ref = sc.grid_network(3, 300.0, 3, 13.89, lane_groups=True)  # turns are read from the grouped network
+    lr = net.lane_road()
+    nrl = net.n_road_lanes
+    r_in = [r for r in range(net.n_roads) if net.road_to[r] == 4][0]
+    lanes = list(range(int(net.road_lane_off[r_in]), int(net.road_lane_off[r_in + 1])))
+    # the out-road reached by `turn` (its junction lane leaves lane 0 for a left turn, the last lane for a right)
+    def out_road(tn):
+        src = lanes[0] if tn != 2 else lanes[-1]
+        jls = range(int(ref.jl_off[src]), int(ref.jl_off[src + 1]))
+        return [int(lr[ref.jl_target[j - nrl]]) for j in jls if ref.jl_turn[j - nrl] == tn][0]
+    r_out, r_straight = out_road(turn), out_road(0)
+    cars = [(lanes[lane_idx], 40.0, 8.0)] + [(lanes[o], s_, v_) for o, s_, v_ in cars_extra]
+    n = len(cars)
+    veh = sc.Vehicles(n=n, route_off=np.arange(0, 2 * n + 1, 2, dtype=np.int32),
+                      routes=np.array([r_in, r_out] + [r_in, r_straight] * (n - 1), dtype=np.int32),
+                      start_lane=np.array([c[0] for c in cars], dtype=np.int32), dep=np.zeros(n, dtype=np.int32),
+                      v0f=np.ones(n, dtype=np.float32))
+    st = dict(status=np.ones(n, dtype=np.int32), lane=np.array([c[0] for c in cars], dtype=np.int32),
+              s=np.array([c[1] for c in cars]), v=np.array([c[2] for c in cars]), rc=np.zeros(n, dtype=np.int32))
+    scen = sc.Scenario(net, veh, params if params is not None else sc.Params(), "groups")
+    return scen, st, lanes, r_out
+
+
+def check_lane_group_mandatory(libpath=None):
+    """R27 worked by hand: a car in the right lane that must turn left changes
+    one lane to the left in each of the next two steps (free road: the
+    changes are safe, no random draw) and then drives on in the left lane; a
+    car alongside in the middle lane (gap <= 0) forbids the change, so the
+    car stays and stops at the end of its lane."""
+    scen, st, lanes, r_out = _groups_case(2, 1)
+    o = _oracle(scen, st, libpath)
+    o.set_signal(list(range(scen.net.n_junctions)), oracle.POLICY_NONE)
+    o.step(1)
+    assert o.state()["lane"][0] == lanes[1]
+    o.step(1)
+    assert o.state()["lane"][0] == lanes[0]
+    for _ in range(60):
+        o.step(1)
+    lr = scen.net.lane_road()
+    stt = o.state()
+    assert stt["status"][0] == 2 or lr[stt["lane"][0]] == r_out or stt["lane"][0] >= scen.net.n_road_lanes
+    # blocked: the middle lane holds a standing queue over its whole length
+    # (5.5 m apart: no 5 m car fits) held by a red phase of the approach; the
+    # car stays in its lane and stops at its end
+    queue = [(1, 295.0 - 5.5 * k, 0.0) for k in range(54)]
+    scen, st, lanes, _ = _groups_case(2, 1, cars_extra=queue)
+    st["v"][0] = 0.0
+    net = scen.net
+    nrl = net.n_road_lanes
+    masks = [int(net.jl_mask[j - nrl]) for l in lanes for j in range(net.jl_off[l], net.jl_off[l + 1])]
+    red = [p for p in range(4) if all(((m >> p) & 1) == 0 for m in masks)][0]
+    o = _oracle(scen, st, libpath)
+    o.set_signal(list(range(net.n_junctions)), oracle.POLICY_MANUAL, [red] * net.n_junctions)
+    # the queue cannot spread out: the outer lanes are not entered (R25)
+    o.set_lane_restriction([lanes[0], lanes[2]], [1, 1])
+    L = float(scen.net.lane_length[lanes[2]])
+    for _ in range(120):
+        o.step(1)
+        stt = o.state()
+        assert stt["lane"][0] == lanes[2] and stt["s"][0] <= L + 1e-12
+    assert stt["v"][0] < 1e-6 and L - stt["s"][0] < 2.0 + 1e-6  # at the end of its lane
+
+
+def check_lane_group_keeps_inside(libpath=None):
+    """R27: a car in the left lane that turns left is in its group; behind a
+    stopped car, MOBIL wants the middle lane (it does change there without
+    lane groups) but the change would leave the group, so it never does."""
+    p = _mobil_params()
+    for groups, expect_change in ((True, False), (False, True)):
+        scen, st, lanes, _ = _groups_case(0, 1, cars_extra=[(0, 60.0, 0.0)], groups=groups, params=p)
+        o = _oracle(scen, st, libpath)
+        o.set_signal(list(range(scen.net.n_junctions)), oracle.POLICY_NONE)
+        changed = False
+        for _ in range(15):
+            o.step(1)
+            changed |= o.state()["lane"][0] == lanes[1]
+        assert changed == expect_change, groups
+
+
 ALL_CHECKS = [
     check_idm_free_road, check_idm_equilibrium, check_p_lc, check_mobil_case_A,
     check_mobil_case_B, check_mobil_case_C, check_mobil_case_D, check_mobil_mirror, check_neighbours_bruteforce,
     check_free_road_vs_rk4, check_platoon_equilibrium, check_red_light, check_signal_program,
     check_arrival_and_travel_time, check_insertion, check_conflict, check_max_pressure_argmax,
     check_max_pressure_timing, check_lane_queue_and_road_speed, check_lane_max_speed,
-    check_lane_restriction, check_reroute,
+    check_lane_restriction, check_reroute, check_lane_group_mandatory, check_lane_group_keeps_inside,
 ]

@@ -39,12 +39,17 @@ MUTATIONS = [
     ("maxp_min_green_off_by_one", "} else if (e >= O->phase_green[p0 + p]) {", "} else if (e > O->phase_green[p0 + p]) {"),
     ("queue_window_100m", "if (O->v[i] < 0.1 && O->L[l] - O->s[i] <= 50.0) out[l]++;",
      "if (O->v[i] < 0.1 && O->L[l] - O->s[i] <= 100.0) out[l]++;"),
-    ("restriction_no_stop", "(nl1 >= 0 && O->restricted[nl1])) {", "(0)) {"),
+    ("restriction_no_stop", "(nl1 >= 0 && O->restricted[nl1]) ||", "(0) ||"),
     ("restriction_ignored_by_mobil", "if (tl < lo || tl >= hi || O->restricted[tl]) continue;",
      "if (tl < lo || tl >= hi) continue;"),
     ("max_speed_setter_ignored", "for (int k = 0; k < n; ++k) O->vmax[lanes[k]] = vmax[k];", "(void)vmax;"),
     ("reroute_drops_road_just_left", "    if (prev >= 0) O->routes[beg + len++] = prev;\n", "\n"),
     ("reroute_start_unchecked", "        if (roads[0] != O->lane_road[O->lane[vid]]) return -1;\n", "\n"),
+    ("groups_mobil_may_leave", "        if (next_road >= 0 && !has_access(O, tl, next_road)) continue;  /* leaves the group (R27) */\n",
+     "\n"),
+    ("groups_no_access_no_stop", " || (lane < O->n_road_lanes && nl1 == -2)) {", ") {"),
+    ("groups_mandatory_wrong_way", "int dir = best < lane ? -1 : +1, tl = lane + dir;",
+     "int dir = best < lane ? +1 : -1, tl = lane + dir;\n        if (tl < lo || tl >= hi) return D;"),
     ("maxp_ties_to_smallest", "if (pk > pb || (pk == pb && best != p && k < best)) best = k;",
      "if (pk > pb || (pk == pb && k < best)) best = k;"),
 ]
