@@ -138,7 +138,7 @@ class Clocks:
 
 def city(args):
     from paper_2406_10661_gb300 import scenario as sc
-    return sc.city_scenario(seed=args.seed)
+    return sc.city_scenario(seed=args.seed, lane_groups=args.lane_groups)
 
 
 def cpu_oracle_rate(scen, state, budget_s=15.0, max_road=4000, steps_cap=60, max_pressure=False):
@@ -343,7 +343,8 @@ def run_ours(args):
                    "start": f"the simulation's own state at step {T_WARM} (set-up, untimed)",
                    "active_per_step": upd / args.steps,
                    "l2": "flushed between timed steps by a 256 MiB write (outside the events)",
-                   "signal_policy": args.policy, "parallelism": f"replicas x{world}"},
+                   "signal_policy": args.policy, "lane_groups": bool(args.lane_groups),
+                   "parallelism": f"replicas x{world}"},
         "step_hz": 1e3 / ms_per_step,
         "nominal_vehicle_steps_per_s": n_total * 1e3 / ms_per_step,
         "paper_context": {"step_hz": 84.09, "vehicles": 2464950, "hardware": "RTX 4090 + Xeon 8462Y",
@@ -498,6 +499,8 @@ def main():
     ap.add_argument("--workload", default="city", choices=["city", "batched", "serving"])
     ap.add_argument("--policy", default="fixed", choices=["fixed", "max_pressure"],
                     help="signal policy of every junction on the city workload")
+    ap.add_argument("--lane-groups", action="store_true",
+                    help="city lanes serve turn groups (left+straight / straight / right+straight)")
     ap.add_argument("--scenarios", type=int, default=64)
     ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--slots", type=int, default=64)

@@ -113,7 +113,9 @@ typedef struct MossNetwork {
 /*
  * Travel demand (§3.1 "Simulator Inputs"): vehicle i (id = i) drives the
  * road sequence routes[route_off[i] .. route_off[i+1]), consecutive roads
- * connected through a junction lane from every lane; it departs no earlier
+ * connected through a junction lane from at least one lane (a vehicle on a
+ * lane without access to its next road stops at the lane end and changes
+ * towards the lanes that have it: App. B.3 lane groups); it departs no earlier
  * than step dep[i] on lane start_lane[i] (a lane of its first road) and has
  * desired-speed factor v0f[i] (desired speed = v0f * lane speed limit).
  */
@@ -212,7 +214,7 @@ int moss_set_lane_restriction(moss_t h, int n, const int32_t* lane_ids, const in
  * gets the route roads[route_off[k] .. route_off[k+1]) (host arrays; road
  * ids).  The new route starts with the road the vehicle is on (a waiting
  * vehicle: the road of its start lane; a vehicle on a junction lane: the
- * road it is entering), every turn of it must be available from every lane,
+ * road it is entering), every turn of it must be available from some lane,
  * and the vehicle arrives at the end of its last road as every trip does
  * (no destination inside a road).  All requests are checked before any is
  * applied: MOSS_EINVAL (arrived vehicle, route not starting with the

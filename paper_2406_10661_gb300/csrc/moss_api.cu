@@ -199,7 +199,8 @@ int validate(MossHandle* h, const MossNetwork* net, const MossVehicles* veh, con
         if (net->jl_junction[k] < 0 || net->jl_junction[k] >= J) return fail(h, MOSS_EINVAL, "jl_junction range");
         if (net->jl_mask[k] < 0 || net->jl_mask[k] > 255) return fail(h, MOSS_EINVAL, "jl_mask must fit 8 bits");
     }
-    // out-roads reachable from every lane of each road
+    // out-roads reachable from some lane of each road (a vehicle on a lane
+    // without access changes lanes towards the group that has it, R27)
     road_out->assign(R, {});
     for (int r = 0; r < R; ++r) {
         std::vector<int32_t> common;
@@ -210,13 +211,9 @@ int validate(MossHandle* h, const MossNetwork* net, const MossVehicles* veh, con
             std::sort(outs.begin(), outs.end());
             if (std::adjacent_find(outs.begin(), outs.end()) != outs.end())
                 return fail(h, MOSS_EINVAL, "a lane has two junction lanes to the same road");
-            if (l == net->road_lane_off[r]) common = outs;
-            else {
-                std::vector<int32_t> x;
-                std::set_intersection(common.begin(), common.end(), outs.begin(), outs.end(),
-                                      std::back_inserter(x));
-                common.swap(x);
-            }
+            std::vector<int32_t> x;
+            std::set_union(common.begin(), common.end(), outs.begin(), outs.end(), std::back_inserter(x));
+            common.swap(x);
         }
         (*road_out)[r] = common;
     }
@@ -234,7 +231,7 @@ int validate(MossHandle* h, const MossNetwork* net, const MossVehicles* veh, con
             const auto& o = (*road_out)[veh->routes[k]];
             if (!std::binary_search(o.begin(), o.end(), veh->routes[k + 1]))
                 return fail(h, MOSS_EINVAL, "route of vehicle " + std::to_string(i) +
-                                                " uses a turn not available from every lane");
+                                                " uses a turn no lane of the road has");
         }
         const int sl = veh->start_lane[i];
         if (sl < 0 || sl >= NRL || road_of[sl] != veh->routes[a])
@@ -791,15 +788,13 @@ int set_lane(MossHandle* h, int n, const int32_t* lane_ids, const int32_t* vals,
     return MOSS_OK;
 }
 
-// road b is reachable from every lane of road a (the rule routes obey)
-bool turn_from_every_lane(const MossHandle* h, int a, int b) {
+// road b is reachable from some lane of road a (the rule routes obey)
+bool turn_from_some_lane(const MossHandle* h, int a, int b) {
     const int2 sp = h->road_span[a];
-    for (int l = sp.x; l < sp.y; ++l) {
-        bool ok = false;
-        for (int j = h->lanes[l].jb; j < h->lanes[l].je && !ok; ++j) ok = h->lanes[j].road == b;
-        if (!ok) return false;
-    }
-    return true;
+    for (int l = sp.x; l < sp.y; ++l)
+        for (int j = h->lanes[l].jb; j < h->lanes[l].je; ++j)
+            if (h->lanes[j].road == b) return true;
+    return false;
 }
 
 template <typename Real>
@@ -848,7 +843,7 @@ int reroute_impl(MossHandle* h, int n, const int32_t* vids, const int32_t* route
         }
         if (roads[a] != first) { why = "the route must start with the vehicle's road"; break; }
         for (int q = a; q + 1 < b; ++q)
-            if (!turn_from_every_lane(h, roads[q], roads[q + 1])) { why = "roads not joined"; break; }
+            if (!turn_from_some_lane(h, roads[q], roads[q + 1])) { why = "roads not joined"; break; }
     }
     if (!why.empty()) {
         k_mark_vehicles<<<nb, 256, 0, h->stream>>>(h->d_req, n, d_v, 0);

@@ -465,6 +465,14 @@ __device__ __forceinline__ LaneAcc<Real> accel_on_lane(const Ctx<Real>& c, const
             r.stop = 1; r.stop_gap = gs;
         }
     }
+    // no junction lane from this road lane to the next road of the route
+    // (lane groups, R27): stop at the lane end as before a red light
+    if (nl < 0 && li.lo >= 0 && rptr < rlast) {
+        const Real gs = Real(li.L) - s;
+        const Real as = idm(c, v, v0, gs, v);
+        if (as < a) a = as;
+        r.stop = 1; r.stop_gap = gs;
+    }
     r.a = a;
     return r;
 }
@@ -498,6 +506,7 @@ struct OwnPart {
     LaneAcc<Real> own;
     float u_lc, u_dir;  // the draws for p_LC and the direction (exact in FP32)
     int att;            // the attempt draw passed: MOBIL is evaluated
+    int mand;           // outside the lane group of the next road: mandatory change (R27)
 };
 
 template <typename Real>
@@ -505,10 +514,12 @@ __device__ __forceinline__ OwnPart<Real> decide_own(const Ctx<Real>& c, int i, c
                                                     const RecB& EB, const LaneInfo& li, int b, long long t,
                                                     uint32_t k0, uint32_t k1, int vbase) {
     OwnPart<Real> P;
-    P.att = 0; P.u_lc = 0.0f; P.u_dir = 0.0f;
+    P.att = 0; P.mand = 0; P.u_lc = 0.0f; P.u_dir = 0.0f;
     const int OL = (i > b) ? i - 1 : -1;
     P.own = accel_on_lane(c, li, E.s, E.v, Real(EB.v0f) * Real(li.vmax), OL, EB.nl, EB.rptr, EB.rlast);
     if (li.lo < 0 || li.hi - li.lo < 2) return P;  // junction lane or single-lane road
+    // no access to the next road from this lane: a mandatory change, no draw (R27)
+    if (EB.nl < 0 && EB.rptr < EB.rlast) { P.mand = 1; return P; }
     uint32_t w[4];
     philox4x32_10(k0, k1, uint32_t(E.id - vbase), uint32_t(t), 0u, 0u, w);
     const Real u_att = unit24<Real>(w[0]);
@@ -564,6 +575,10 @@ __device__ __forceinline__ Decision<Real> decide_mobil(const Ctx<Real>& c, int i
         const int side = (k == 0 && has_l) ? 0 : 1;
         const int tl = side == 0 ? lane - 1 : lane + 1;
         const LaneInfo ti = c.lane[tl];
+        // next lane from the target lane; a lane without access to the next
+        // road is outside the vehicle's group: not a side (R27)
+        const int nlt = (next_road >= 0) ? jl_toward(c, ti, next_road, EB.nl - li.jb) : -1;
+        if (next_road >= 0 && nlt < 0) continue;
         const int tb = c.cur.off[tl], te = c.cur.off[tl + 1];
         const int p = partition_point(c, tb, te, E.s, E.id);
         const int TL = (p > tb) ? p - 1 : -1, TF = (p < te) ? p : -1;
@@ -582,7 +597,6 @@ __device__ __forceinline__ Decision<Real> decide_mobil(const Ctx<Real>& c, int i
             if (!(g > Real(0))) ok = 0;
             if (rabs(g) < c.band * pos_scale) D.flag = 1;
         }
-        const int nlt = (next_road >= 0) ? jl_toward(c, ti, next_road, EB.nl - li.jb) : -1;
         const Real at_ego = accel_on_lane(c, ti, E.s, E.v, v0f * Real(ti.vmax), TL, nlt, EB.rptr, EB.rlast).a;
         Real a_new = Real(0), at_new = Real(0);
         if (TF >= 0) {
@@ -630,6 +644,61 @@ __device__ __forceinline__ Decision<Real> decide_mobil(const Ctx<Real>& c, int i
     D.tl = side == 0 ? lane - 1 : lane + 1;
     D.TL = TLs[side]; D.TF = TFs[side]; D.nlt = NLs[side];
     D.u = u[side];
+    return D;
+}
+
+// Mandatory change (R27) of a vehicle outside the lane group of its next
+// road: one lane towards the nearest lane of the group (ties: left) when the
+// safety part of R2 holds (gaps > 0, ã_new >= -b_safe); no random draw; in
+// the conflict rule R9 its utility is MAND_U, above any discretionary one.
+constexpr double MAND_U = 1e30;
+
+template <typename Real>
+__device__ __forceinline__ Decision<Real> decide_mandatory(const Ctx<Real>& c, int i, const RecA<Real>& E,
+                                                           const RecB& EB, const LaneInfo& li,
+                                                           const LaneAcc<Real>& own) {
+    Decision<Real> D;
+    D.cand = 0; D.dir = 0; D.tl = -1; D.TL = -1; D.TF = -1; D.flag = 0; D.nlt = -1; D.att = 0;
+    D.u = Real(0); D.scale = Real(1);
+    D.own = own;
+    const int lane = E.lane;
+    const int next_road = c.routes[EB.rptr + 1];
+    int best = -1;
+    for (int k = li.lo; k < li.hi; ++k) {
+        if (jl_toward(c, c.lane[k], next_road) < 0) continue;
+        const int dk = k > lane ? k - lane : lane - k, db = best > lane ? best - lane : lane - best;
+        if (best < 0 || dk < db) best = k;
+    }
+    if (best < 0) return D;
+    const int dir = best < lane ? -1 : 1, tl = lane + dir;
+    const LaneInfo ti = c.lane[tl];
+    if (ti.flags & LF_RESTRICTED) return D;
+    const int tb = c.cur.off[tl], te = c.cur.off[tl + 1];
+    const int p = partition_point(c, tb, te, E.s, E.id);
+    const int TL = (p > tb) ? p - 1 : -1, TF = (p < te) ? p : -1;
+    const Real pos_scale = E.s > Real(1) ? E.s : Real(1);
+    int ok = 1;
+    if (TL >= 0) {
+        const RecA<Real> T = c.cur.a[TL];
+        const Real g = T.s - c.len - E.s;
+        if (!(g > Real(0))) ok = 0;
+        if (rabs(g) < c.band * pos_scale) D.flag = 1;
+    }
+    if (TF >= 0) {
+        const RecA<Real> F = c.cur.a[TF];
+        const Real g = E.s - c.len - F.s;
+        if (!(g > Real(0))) ok = 0;
+        if (rabs(g) < c.band * pos_scale) D.flag = 1;
+        const Real at_new = acc_pair(c, F, c.cur.b[TF].v0f, ti.vmax, true, E.s, E.v);
+        if (!(at_new >= -c.b_safe)) ok = 0;
+        const Real sc = rabs(at_new) > Real(1) ? rabs(at_new) : Real(1);
+        if (rabs(at_new + c.b_safe) < c.band * sc) D.flag = 1;
+    }
+    if (!ok) return D;
+    D.cand = 1; D.dir = dir; D.tl = tl; D.TL = TL; D.TF = TF;
+    D.nlt = jl_toward(c, ti, next_road);
+    D.u = Real(MAND_U);
+    D.scale = Real(1);
     return D;
 }
 

@@ -45,10 +45,7 @@ __device__ void insert_departure(const Ctx<Real>& c, int l, int tag) {
     const int2 rs = c.route_span[vid];
     const int r0 = rs.x, r1 = rs.y - 1;
     int nl = -1;
-    if (r0 < r1) {
-        nl = jl_toward(c, c.lane[l], c.routes[r0 + 1]);
-        if (nl < 0) atomicOr(c.err, ERR_ROUTE);
-    }
+    if (r0 < r1) nl = jl_toward(c, c.lane[l], c.routes[r0 + 1]);  // -1: no access from this lane (R27)
     RecA<Real> A;
     A.s = Real(0); A.v = Real(0); A.id = vid; A.lane = l;
     RecB B;
@@ -116,8 +113,8 @@ __device__ __forceinline__ int integrate_emit(const Ctx<Real>& c, MetricAcc& acc
                 nl = ni.hi;  // entered a junction lane: next is its target road lane
             } else {
                 rptr += 1;  // entered the next road
+                // -1 on the last road, or without access from this lane (R27)
                 nl = (rptr < rlast) ? jl_toward(c, ni, c.routes[rptr + 1]) : -1;
-                if (rptr < rlast && nl < 0) atomicOr(c.err, ERR_ROUTE);
             }
             ex = sn - Real(ni.L);
         }
@@ -244,6 +241,13 @@ __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Rea
                     acc.mob += 1;
                     const Decision<Real> D = decide_mobil(c, i, E, EB, li, b, c.cur.off[lane + 1], P.own, P.u_lc,
                                                           P.u_dir);
+                    if (D.cand) {
+                        list_candidate(c, i, E, EB, sc, D, tag);
+                        cand = true;
+                    }
+                    fl = D.flag ? F_FLAGGED : 0;
+                } else if (P.mand) {
+                    const Decision<Real> D = decide_mandatory(c, i, E, EB, li, P.own);
                     if (D.cand) {
                         list_candidate(c, i, E, EB, sc, D, tag);
                         cand = true;

@@ -344,7 +344,7 @@ def perturbed_grid_network(G: int = 100, seed: int = 0, median_len: float = 250.
                            sigma_ln: float = 0.4, len_clip=(50.0, 1500.0),
                            lane_probs=(0.2, 0.4, 0.3, 0.1),
                            vmax_choices=(11.1, 13.89, 16.67), green: int = 30,
-                           amber: int = 3) -> Network:
+                           amber: int = 3, lane_groups: bool = False) -> Network:
     """City-scale synthetic network: grid topology, log-normal link lengths
     (median 250 m, sigma_ln 0.4, clipped to [50, 1500] m), 1-4 lanes per link
     with the given probabilities, speed limits from the given set, random
@@ -357,7 +357,7 @@ def perturbed_grid_network(G: int = 100, seed: int = 0, median_len: float = 250.
     lanes = st.choice(lane_probs, E) + 1
     lv = np.asarray(vmax_choices, dtype=np.float64)[st.integers(0, len(vmax_choices), E)]
     off = st.integers(0, 4 * (green + amber), G * G)
-    return build_network(jxy, links, lengths, lanes, lv, off, green, amber)
+    return build_network(jxy, links, lengths, lanes, lv, off, green, amber, lane_groups=lane_groups)
 
 
 # ----------------------------------------------------------------------------
@@ -560,14 +560,15 @@ def medium_scenario(seed: int = 0, n: int = 100_000) -> Scenario:
 
 
 def city_scenario(seed: int = 0, n: int = 2_464_950, G: int = 100,
-                  dest_pool: Optional[int] = 1024, dep_horizon: int = 3600) -> Scenario:
+                  dest_pool: Optional[int] = 1024, dep_horizon: int = 3600,
+                  lane_groups: bool = False) -> Scenario:
     """Perturbed 100x100 grid (39,600 roads, 1-4 lanes, log-normal lengths) with
     2,464,950 trips departing uniformly over 3,600 s; origins uniform over all
     roads, destinations uniform over a pool of 1,024 roads (trip attractors;
     it also bounds the shortest-path work to 1,024 Dijkstra runs)."""
-    net = perturbed_grid_network(G, seed=seed)
+    net = perturbed_grid_network(G, seed=seed, lane_groups=lane_groups)
     veh = random_demand(net, n, dep_horizon, seed=seed, dest_pool=dest_pool)
-    return Scenario(net, veh, Params(seed=seed), f"city{G}x{G}_{n}")
+    return Scenario(net, veh, Params(seed=seed), f"city{G}x{G}_{n}" + ("_groups" if lane_groups else ""))
 
 
 def batched_scenarios(k: int = 64, seed: int = 0, n_lo: int = 2000, n_hi: int = 300_000,

@@ -239,3 +239,62 @@ def test_city_one_step_parity_fp32():
     sim.step(1); ora.step(1)
     n, excused = compare_one_step(sim.state(), ora.state())
     assert n > 1_000_000 and excused <= n // 1000
+
+
+def test_ragged_batch_with_empty_member():
+    """A batch of uneven members, one with no vehicles and no junctions, one
+    with a single vehicle: every member equals its own run alone."""
+    empty_net = sc.corridor_network(2, (500.0,))
+    empty_veh = sc.Vehicles(n=0, route_off=np.zeros(1, np.int32), routes=np.zeros(0, np.int32),
+                            start_lane=np.zeros(0, np.int32), dep=np.zeros(0, np.int32),
+                            v0f=np.zeros(0, np.float32))
+    empty = sc.Scenario(empty_net, empty_veh, sc.Params(), "empty")
+    single = corridor((300.0, 300.0), [(1, 3)], n_lanes=2)
+    scens = [sc.small_scenario(seed=4), empty, single, sc.small_scenario(seed=5)]
+    for i, s in enumerate(scens):
+        s.params.scenario = i
+    batch = binding.Batch(scens, precision=32)
+    batch.step(250)
+    for i, s in enumerate(scens):
+        alone = _sim(s, 32)
+        alone.step(250)
+        a, b = alone.state(), batch.state(i)
+        for k in ("status", "lane", "rc", "flags", "s", "v"):
+            assert np.array_equal(a[k], b[k]), (i, k)
+        assert alone.metrics() == batch.metrics(i), i
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_long_queue_lane_spans_many_tiles(precision):
+    """One 8 km two-lane road holding a 1,500-car queue (the lane's segment
+    spans several 256-slot tiles; adjacent-lane searches over long segments;
+    entrants placed into long lanes) and exact position ties (order by id):
+    50 steps against the oracle."""
+    rng = np.random.default_rng(9)
+    cars = []
+    for k in range(1500):  # lane 0: a dense queue near the end, slowly moving
+        cars.append((0, 7900.0 - 5.2 * k, float(rng.uniform(0.0, 2.0))))  # last one at 105 m
+    for k in range(300):   # lane 1: sparser and faster, some cars side by side
+        cars.append((1, 7950.0 - 24.0 * k, float(rng.uniform(5.0, 12.0))))
+    for k in range(5):     # exact ties on lane 1 (ordered by id)
+        cars.append((1, 3000.0 + 0.0 * k, 3.0))
+    scen, st = one_road(2, 8000.0, cars, params=sc.Params(p_attempt=1.0))
+    sim, ora = _sim(scen, precision), _ora(scen)
+    _set_both(sim, ora, st if precision == 64 else _f32_state(st), 0)
+    for _ in range(5):
+        sim.step(10); ora.step(10)
+        g, r = sim.state(), ora.state()
+        if precision == 64:
+            assert np.array_equal(g["status"], r["status"])
+            act = r["status"] == 1
+            assert np.array_equal(g["lane"][act], r["lane"][act])
+            assert np.abs(g["s"][act] - r["s"][act]).max(initial=0) < 1e-6
+            assert np.abs(g["v"][act] - r["v"][act]).max(initial=0) < 1e-6
+            assert np.array_equal(g["flags"], r["flags"])
+    gm, rm = sim.metrics(), ora.metrics()
+    assert gm["errors"] == 0
+    if precision == 64:
+        for k in ("lane_changes", "flagged", "overlaps", "n_arrived", "mobil_evals"):
+            assert gm[k] == rm[k], (k, gm[k], rm[k])
+    else:
+        assert abs(gm["speed_sum"] - rm["speed_sum"]) <= 0.005 * rm["speed_sum"]
