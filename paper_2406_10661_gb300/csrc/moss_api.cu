@@ -64,6 +64,7 @@ struct MossHandle {
     int4* d_mp = nullptr;  // max-pressure state per junction
     int32_t *d_jj_off = nullptr, *d_jj_lane = nullptr, *d_jj_from = nullptr, *d_mp_press = nullptr;
     int n_jj = 0;
+    bool lane_groups = false;         // some road has a turn that not all of its lanes serve (R27)
     int2* d_road_span = nullptr;      // (first, end) road lanes per road
     std::vector<int2> road_span;
     std::vector<int> scen_road_off;   // [n_scen+1]
@@ -315,7 +316,8 @@ void enqueue_step(MossHandle* h, int cur, bool timed) {
     const Grids g = grids(h);
     cudaStream_t s = h->stream;
     if (timed) cudaEventRecord(h->ev[0], s);
-    k_decide<Real><<<g.decide_work + g.decide_ins, TILE, 0, s>>>(c, g.decide_work);
+    if (h->lane_groups) k_decide<Real, true><<<g.decide_work + g.decide_ins, TILE, 0, s>>>(c, g.decide_work);
+    else k_decide<Real, false><<<g.decide_work + g.decide_ins, TILE, 0, s>>>(c, g.decide_work);
     if (timed) cudaEventRecord(h->ev[1], s);
     k_resolve<Real><<<g.resolve, TILE, 0, s>>>(c);
     if (timed) cudaEventRecord(h->ev[2], s);
@@ -506,6 +508,19 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
     h->start_lanes.clear();
     for (int l = 0; l < NL; ++l)
         if (h->q_off[l + 1] > h->q_off[l]) h->start_lanes.push_back(l);
+
+    // lane groups: a road with a turn not served by all of its lanes
+    for (size_t r = 0; r < h->road_span.size() && !h->lane_groups; ++r) {
+        const int2 sp = h->road_span[r];
+        std::vector<int> all, first;
+        for (int l = sp.x; l < sp.y; ++l) {
+            std::vector<int> outs;
+            for (int j = h->lanes[l].jb; j < h->lanes[l].je; ++j) outs.push_back(h->lanes[j].road);
+            std::sort(outs.begin(), outs.end());
+            if (l == sp.x) first = outs;
+            else if (outs != first) h->lane_groups = true;
+        }
+    }
 
     // ---- device
     if (stream) {

@@ -414,7 +414,7 @@ struct LaneAcc {
 // Ego acceleration on a lane (record li) at (s, v): min over the leader (slot
 // ld in this lane, else lookahead over at most two lanes, R11) and the stop
 // line (R12).  nl: next lane from this lane on the ego's route (-1 none).
-template <typename Real>
+template <typename Real, bool Groups = true>
 __device__ __forceinline__ LaneAcc<Real> accel_on_lane(const Ctx<Real>& c, const LaneInfo& li, Real s,
                                                        Real v, Real v0, int ld, int nl, int rptr,
                                                        int rlast) {
@@ -467,7 +467,7 @@ __device__ __forceinline__ LaneAcc<Real> accel_on_lane(const Ctx<Real>& c, const
     }
     // no junction lane from this road lane to the next road of the route
     // (lane groups, R27): stop at the lane end as before a red light
-    if (nl < 0 && li.lo >= 0 && rptr < rlast) {
+    if (Groups && nl < 0 && li.lo >= 0 && rptr < rlast) {
         const Real gs = Real(li.L) - s;
         const Real as = idm(c, v, v0, gs, v);
         if (as < a) a = as;
@@ -509,17 +509,18 @@ struct OwnPart {
     int mand;           // outside the lane group of the next road: mandatory change (R27)
 };
 
-template <typename Real>
+template <typename Real, bool Groups = true>
 __device__ __forceinline__ OwnPart<Real> decide_own(const Ctx<Real>& c, int i, const RecA<Real>& E,
                                                     const RecB& EB, const LaneInfo& li, int b, long long t,
                                                     uint32_t k0, uint32_t k1, int vbase) {
     OwnPart<Real> P;
     P.att = 0; P.mand = 0; P.u_lc = 0.0f; P.u_dir = 0.0f;
     const int OL = (i > b) ? i - 1 : -1;
-    P.own = accel_on_lane(c, li, E.s, E.v, Real(EB.v0f) * Real(li.vmax), OL, EB.nl, EB.rptr, EB.rlast);
+    P.own = accel_on_lane<Real, Groups>(c, li, E.s, E.v, Real(EB.v0f) * Real(li.vmax), OL, EB.nl, EB.rptr,
+                                        EB.rlast);
     if (li.lo < 0 || li.hi - li.lo < 2) return P;  // junction lane or single-lane road
     // no access to the next road from this lane: a mandatory change, no draw (R27)
-    if (EB.nl < 0 && EB.rptr < EB.rlast) { P.mand = 1; return P; }
+    if (Groups && EB.nl < 0 && EB.rptr < EB.rlast) { P.mand = 1; return P; }
     uint32_t w[4];
     philox4x32_10(k0, k1, uint32_t(E.id - vbase), uint32_t(t), 0u, 0u, w);
     const Real u_att = unit24<Real>(w[0]);
@@ -530,7 +531,7 @@ __device__ __forceinline__ OwnPart<Real> decide_own(const Ctx<Real>& c, int i, c
     return P;
 }
 
-template <typename Real>
+template <typename Real, bool Groups = true>
 __device__ __forceinline__ Decision<Real> decide_mobil(const Ctx<Real>& c, int i, const RecA<Real>& E,
                                                        const RecB& EB, const LaneInfo& li, int b, int e,
                                                        const LaneAcc<Real>& own, float f_lc, float f_dir) {
@@ -578,7 +579,7 @@ __device__ __forceinline__ Decision<Real> decide_mobil(const Ctx<Real>& c, int i
         // next lane from the target lane; a lane without access to the next
         // road is outside the vehicle's group: not a side (R27)
         const int nlt = (next_road >= 0) ? jl_toward(c, ti, next_road, EB.nl - li.jb) : -1;
-        if (next_road >= 0 && nlt < 0) continue;
+        if (Groups && next_road >= 0 && nlt < 0) continue;
         const int tb = c.cur.off[tl], te = c.cur.off[tl + 1];
         const int p = partition_point(c, tb, te, E.s, E.id);
         const int TL = (p > tb) ? p - 1 : -1, TF = (p < te) ? p : -1;
@@ -597,7 +598,8 @@ __device__ __forceinline__ Decision<Real> decide_mobil(const Ctx<Real>& c, int i
             if (!(g > Real(0))) ok = 0;
             if (rabs(g) < c.band * pos_scale) D.flag = 1;
         }
-        const Real at_ego = accel_on_lane(c, ti, E.s, E.v, v0f * Real(ti.vmax), TL, nlt, EB.rptr, EB.rlast).a;
+        const Real at_ego =
+            accel_on_lane<Real, Groups>(c, ti, E.s, E.v, v0f * Real(ti.vmax), TL, nlt, EB.rptr, EB.rlast).a;
         Real a_new = Real(0), at_new = Real(0);
         if (TF >= 0) {
             const float fv0f = c.cur.b[TF].v0f;

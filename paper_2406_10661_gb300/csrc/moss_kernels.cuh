@@ -194,11 +194,14 @@ __device__ __forceinline__ void list_candidate(const Ctx<Real>& c, int i, const 
 // Per vehicle: the own-lane acceleration and the attempt draw, MOBIL if the
 // draw passed, then the update; lane-change candidates are finished by
 // k_resolve.
+// Groups: the network has lane groups (some road has a turn that not all of
+// its lanes serve), so the mandatory changes of R27 can occur; without them
+// that path is not compiled in.
 // MOSS_DECIDE_MIN_BLOCKS: resident blocks per SM the register budget targets.
 #ifndef MOSS_DECIDE_MIN_BLOCKS
 #define MOSS_DECIDE_MIN_BLOCKS 4
 #endif
-template <typename Real>
+template <typename Real, bool Groups>
 __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Real> c, int n_work) {
     if (*c.err & ERR_POISON) return;
     const int tag = c.cnt->tag;
@@ -234,19 +237,20 @@ __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Rea
                 }
                 const long long t = c.scen_step[sc];
                 const int b = c.cur.off[lane];
-                const OwnPart<Real> P = decide_own(c, i, E, EB, li, b, t, c.key0[sc], c.key1[sc], c.veh_base[sc]);
+                const OwnPart<Real> P =
+                    decide_own<Real, Groups>(c, i, E, EB, li, b, t, c.key0[sc], c.key1[sc], c.veh_base[sc]);
                 int fl = 0;
                 bool cand = false;
                 if (P.att) {
                     acc.mob += 1;
-                    const Decision<Real> D = decide_mobil(c, i, E, EB, li, b, c.cur.off[lane + 1], P.own, P.u_lc,
+                    const Decision<Real> D = decide_mobil<Real, Groups>(c, i, E, EB, li, b, c.cur.off[lane + 1], P.own, P.u_lc,
                                                           P.u_dir);
                     if (D.cand) {
                         list_candidate(c, i, E, EB, sc, D, tag);
                         cand = true;
                     }
                     fl = D.flag ? F_FLAGGED : 0;
-                } else if (P.mand) {
+                } else if (Groups && P.mand) {
                     const Decision<Real> D = decide_mandatory(c, i, E, EB, li, P.own);
                     if (D.cand) {
                         list_candidate(c, i, E, EB, sc, D, tag);
