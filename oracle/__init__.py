@@ -78,6 +78,8 @@ def _setup(lib):
     lib.mo_set_lane_restriction.argtypes = [vp, ctypes.c_int, vp, vp]
     lib.mo_lane_queue.argtypes = [vp, vp]
     lib.mo_set_vehicle_route.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
+    lib.mo_set_lane_plans.argtypes = [vp, vp]
+    lib.mo_set_road_plan.argtypes = [vp, ctypes.c_int, vp, vp]
     lib.mo_set_vehicle_route.restype = ctypes.c_int
     lib.mo_road_speed.argtypes = [vp, vp]
     lib.mo_idm.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
@@ -136,6 +138,10 @@ class Oracle:
             ctypes.c_uint(int(params.scenario) & 0xFFFFFFFF))
         if not self.h:
             raise MemoryError("oracle creation failed")
+        plans = getattr(net, "jl_plans", None)
+        if plans is not None:
+            pl = np.ascontiguousarray(plans, dtype=np.int32)
+            self._lib.mo_set_lane_plans(self.h, _p(pl))
 
     def __del__(self):
         h = getattr(self, "h", None)
@@ -189,6 +195,11 @@ class Oracle:
         l = np.ascontiguousarray(lanes, dtype=np.int32)
         f = np.ascontiguousarray(flags, dtype=np.int32)
         self._lib.mo_set_lane_restriction(self.h, len(l), _p(l), _p(f))
+
+    def set_road_plan(self, roads, plans) -> None:
+        r = np.ascontiguousarray(roads, dtype=np.int32)
+        p = np.ascontiguousarray(plans, dtype=np.int32)
+        self._lib.mo_set_road_plan(self.h, len(r), _p(r), _p(p))
 
     def set_vehicle_route(self, vid: int, roads) -> bool:
         """Replace the route of vehicle vid (reading R26); False if refused."""

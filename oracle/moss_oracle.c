@@ -107,6 +107,12 @@
  *       -b_safe) — a mandatory change, without random draws, entered in the
  *       conflict rule R9 with utility U_MAND (larger than any discretionary
  *       utility).  On the last road of the route there is no group.
+ *   R28 lane plans (§3.2 "Road", set_road_lane_plan): every junction lane
+ *       belongs to a set of plans (bit p of its plan mask); a road uses one
+ *       plan at a time (plan 0 at the start).  A junction lane outside the
+ *       current plan of its road is not used: no lane has access through it
+ *       (R27), nobody enters it, and it adds no pressure (R23).  Vehicles
+ *       already on it drive on.  A plan change applies from the next step.
  */
 #define U_MAND 1e30
 #include <math.h>
@@ -158,6 +164,7 @@ typedef struct {
     int *jl_from;                      /* road lane a junction lane leaves (absolute ids) */
     int *mp_phase, *mp_elapsed, *mp_pending; /* max-pressure state per junction (R23) */
     int *restricted;                   /* per lane: restricted from passing (R25) */
+    int *jl_plans, *road_plan;         /* R28: plan mask per lane (junction lanes), plan per road */
     /* vehicles */
     int n_veh;
     int *route_beg, *route_len, *routes, *start_lane, *dep;  /* route of vid: routes[beg .. beg+len) */
@@ -190,6 +197,12 @@ typedef struct {
 } Snap;
 
 static void* xcalloc(size_t n, size_t sz) { return calloc(n ? n : 1, sz); }
+
+/* junction lane j is part of the current plan of the road it leaves (R28) */
+static int jl_available(const Oracle* O, int j) {
+    return (O->jl_plans[j] >> O->road_plan[O->lane_road[O->jl_from[j]]]) & 1;
+}
+
 
 /* ------------------------------------------------------------------------ */
 /* Creation                                                                   */
@@ -247,6 +260,9 @@ void* mo_create(int n_roads, const int* road_lane_off, int n_lanes, int n_road_l
     O->mp_elapsed = (int*)xcalloc(n_junctions, sizeof(int));
     O->mp_pending = (int*)xcalloc(n_junctions, sizeof(int));
     O->restricted = (int*)xcalloc(n_lanes, sizeof(int));
+    O->jl_plans = (int*)xcalloc(n_lanes, sizeof(int));
+    for (int l = 0; l < n_lanes; ++l) O->jl_plans[l] = 0xff;
+    O->road_plan = (int*)xcalloc(n_roads, sizeof(int));
 
     O->route_beg = (int*)xcalloc(n_veh, sizeof(int));
     O->route_len = (int*)xcalloc(n_veh, sizeof(int));
@@ -309,7 +325,7 @@ void mo_destroy(void* h) {
     void* ptrs[] = {O->road_lane_off, O->lane_road, O->L, O->vmax, O->jl_off, O->jl_target,
                     O->jl_junction, O->jl_mask, O->junc_offset, O->junc_phase_off,
                     O->phase_green, O->phase_amber, O->junc_policy, O->junc_manual,
-                    O->jl_from, O->mp_phase, O->mp_elapsed, O->mp_pending, O->restricted, O->route_beg, O->route_len, O->routes, O->start_lane, O->dep, O->v0f, O->status,
+                    O->jl_from, O->mp_phase, O->mp_elapsed, O->mp_pending, O->restricted, O->jl_plans, O->road_plan, O->route_beg, O->route_len, O->routes, O->start_lane, O->dep, O->v0f, O->status,
                     O->lane, O->rc, O->flags, O->s, O->v, O->q_off, O->q_ids, O->q_head};
     for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); ++i) free(ptrs[i]);
     free(O);
@@ -443,6 +459,18 @@ int mo_set_vehicle_route(void* h, int vid, int n, const int* roads) {
     return 0;
 }
 
+/* R28: plan masks of the junction lanes (jl_plans[k] for junction lane
+ * n_road_lanes + k) and the plans of n roads */
+void mo_set_lane_plans(void* h, const int* jl_plans) {
+    Oracle* O = (Oracle*)h;
+    for (int l = O->n_road_lanes; l < O->n_lanes; ++l) O->jl_plans[l] = jl_plans[l - O->n_road_lanes];
+}
+
+void mo_set_road_plan(void* h, int n, const int* roads, const int* plans) {
+    Oracle* O = (Oracle*)h;
+    for (int k = 0; k < n; ++k) O->road_plan[roads[k]] = plans[k];
+}
+
 /* R24 metrics of the current state: queue length per lane (out[n_lanes]) and
  * average vehicle speed per road (out[n_roads]) */
 void mo_lane_queue(void* h, int* out) {
@@ -493,7 +521,7 @@ static void maxp_advance(Oracle* O, const int* lane_cnt) {
     long* press = (long*)xcalloc((size_t)O->n_junctions * 8, sizeof(long));
     for (int jl = O->n_road_lanes; jl < O->n_lanes; ++jl) {
         int j = O->jl_junction[jl];
-        if (O->junc_policy[j] != POLICY_MAXP) continue;
+        if (O->junc_policy[j] != POLICY_MAXP || !jl_available(O, jl)) continue;
         long d = (long)lane_cnt[O->jl_from[jl]] - (long)lane_cnt[O->jl_target[jl]];
         for (int p = 0; p < 8; ++p)
             if ((O->jl_mask[jl] >> p) & 1) press[(size_t)j * 8 + p] += d;
@@ -602,7 +630,7 @@ static int next_lane(const Oracle* O, int vid, int lane, int rc, int* rc_next) {
         if (rc >= last) return -1;
         int out_road = O->routes[r0 + rc + 1];
         for (int j = O->jl_off[lane]; j < O->jl_off[lane + 1]; ++j)
-            if (O->lane_road[O->jl_target[j]] == out_road) { *rc_next = rc; return j; }
+            if (O->lane_road[O->jl_target[j]] == out_road && jl_available(O, j)) { *rc_next = rc; return j; }
         return -2; /* route not drivable from this lane */
     }
     *rc_next = rc + 1;
@@ -690,7 +718,7 @@ typedef struct {
 /* road lane l has a junction lane to road r (R27) */
 static int has_access(const Oracle* O, int l, int r) {
     for (int j = O->jl_off[l]; j < O->jl_off[l + 1]; ++j)
-        if (O->lane_road[O->jl_target[j]] == r) return 1;
+        if (O->lane_road[O->jl_target[j]] == r && jl_available(O, j)) return 1;
     return 0;
 }
 

@@ -163,6 +163,8 @@ class Network:
     road_to: Optional[np.ndarray] = None
     road_reverse: Optional[np.ndarray] = None
     jl_turn: Optional[np.ndarray] = None   # 0 straight, 1 left, 2 right
+    # lane function plans: bit p of jl_plans[k] = junction lane k exists in plan p (None: all plans)
+    jl_plans: Optional[np.ndarray] = None
 
     @property
     def n_junction_lanes(self) -> int:
@@ -220,7 +222,8 @@ def _f32(a) -> np.ndarray:
 def build_network(jxy: np.ndarray, links: np.ndarray, link_len: np.ndarray,
                   link_lanes: np.ndarray, link_vmax: np.ndarray,
                   junc_offset: np.ndarray, green: int = 30, amber: int = 3,
-                  lane_width: float = 3.5, lane_groups: bool = False) -> Network:
+                  lane_width: float = 3.5, lane_groups: bool = False,
+                  lane_plans: bool = False) -> Network:
     """Build a network from junction grid coordinates and undirected links.
 
     jxy: int [J,2] grid coordinates (headings are taken from them, so a
@@ -230,7 +233,9 @@ def build_network(jxy: np.ndarray, links: np.ndarray, link_len: np.ndarray,
     junction except the U-turn; in-lane i feeds out-lane min(i, n_out-1).
     With ``lane_groups`` the lanes of a road with two or more lanes serve
     turn groups instead: the leftmost lane left and straight, the rightmost
-    lane right and straight, the lanes between straight only.
+    lane right and straight, the lanes between straight only.  With
+    ``lane_plans`` every lane keeps every turn but the junction lanes carry
+    two lane plans: plan 0 all turns from every lane, plan 1 the turn groups.
     Junction lane lengths: box side W = 2 * lane_width * (max lanes of the
     junction's roads); straight W, right turn pi*W/8, left turn 3*pi*W/8.
     Signals: 4 phases (NS through+right, NS left, EW through+right, EW left),
@@ -259,7 +264,7 @@ def build_network(jxy: np.ndarray, links: np.ndarray, link_len: np.ndarray,
     np.maximum.at(max_lanes_j, road_from, road_lanes)
     np.maximum.at(max_lanes_j, road_to, road_lanes)
 
-    jl_src, jl_tgt, jl_len, jl_vmax, jl_j, jl_mask, jl_turn = [], [], [], [], [], [], []
+    jl_src, jl_tgt, jl_len, jl_vmax, jl_j, jl_mask, jl_turn, jl_plan = [], [], [], [], [], [], [], []
     jl_count = np.zeros(n_road_lanes, dtype=np.int64)
     for r in range(R):
         j = road_to[r]
@@ -279,16 +284,16 @@ def build_network(jxy: np.ndarray, links: np.ndarray, link_len: np.ndarray,
                     turn, length = 2, math.pi * W / 8.0
                 else:
                     turn, length = 0, W
-                if lane_groups and road_lanes[r] > 1:
-                    n_in = road_lanes[r]
-                    allowed = {0} | ({1} if i == 0 else set()) | ({2} if i == n_in - 1 else set())
-                    if turn not in allowed:
-                        continue
+                n_in = road_lanes[r]
+                in_group = n_in == 1 or turn == 0 or (turn == 1 and i == 0) or (turn == 2 and i == n_in - 1)
+                if lane_groups and not in_group:
+                    continue
                 phase = (0 if ns else 2) + (1 if turn == 1 else 0)
                 tgt = road_lane_off[r2] + min(i, road_lanes[r2] - 1)
                 jl_src.append(src); jl_tgt.append(tgt); jl_len.append(length)
                 jl_vmax.append(min(road_vmax[r], road_vmax[r2])); jl_j.append(j)
                 jl_mask.append(1 << phase); jl_turn.append(turn)
+                jl_plan.append(1 | (2 if in_group else 0))
                 jl_count[src] += 1
     # junction lanes are already grouped by source lane (loop order)
     jl_off = np.zeros(n_road_lanes + 1, dtype=np.int64)
@@ -304,7 +309,8 @@ def build_network(jxy: np.ndarray, links: np.ndarray, link_len: np.ndarray,
         jl_junction=_i32(jl_j), jl_mask=_i32(jl_mask), junc_offset=_i32(junc_offset),
         junc_phase_off=_i32(junc_phase_off), phase_green=_i32(np.full(4 * J, green)),
         phase_amber=_i32(np.full(4 * J, amber)), road_from=_i32(road_from),
-        road_to=_i32(road_to), road_reverse=_i32(road_rev), jl_turn=_i32(jl_turn))
+        road_to=_i32(road_to), road_reverse=_i32(road_rev), jl_turn=_i32(jl_turn),
+        jl_plans=_i32(jl_plan) if lane_plans else None)
     net.validate()
     return net
 
@@ -325,7 +331,8 @@ def _grid_links(G: int) -> Tuple[np.ndarray, np.ndarray]:
 
 def grid_network(G: int, length: float = 200.0, lanes: int = 2, vmax: float = 13.89,
                  vmax_choices=None, offsets: bool = False, seed: int = 0,
-                 green: int = 30, amber: int = 3, lane_groups: bool = False) -> Network:
+                 green: int = 30, amber: int = 3, lane_groups: bool = False,
+                 lane_plans: bool = False) -> Network:
     """Manhattan grid of G x G signalised junctions (configs "small"/"medium")."""
     jxy, links = _grid_links(G)
     E = len(links)
@@ -337,7 +344,7 @@ def grid_network(G: int, length: float = 200.0, lanes: int = 2, vmax: float = 13
     cycle = 4 * (green + amber)
     off = st.integers(0, cycle, G * G) if offsets else np.zeros(G * G, dtype=np.int64)
     return build_network(jxy, links, np.full(E, length), np.full(E, lanes), lv, off,
-                         green, amber, lane_groups=lane_groups)
+                         green, amber, lane_groups=lane_groups, lane_plans=lane_plans)
 
 
 def perturbed_grid_network(G: int = 100, seed: int = 0, median_len: float = 250.0,

@@ -711,6 +711,39 @@ def check_lane_group_keeps_inside(libpath=None):
         assert changed == expect_change, groups
 
 
+def check_lane_plan_switch(libpath=None):
+    """R28 worked by hand: a 3x3 grid of 300 m two-lane roads with two lane
+    plans (plan 0: every lane every turn; plan 1: turn groups).  A car in
+    the right lane that turns left keeps its lane under plan 0; once its
+    road switches to plan 1 it is outside its group and changes to the left
+    lane in the next step (free road); under plan 0 again nobody has to."""
+    net = sc.grid_network(3, 300.0, 2, 13.89, lane_plans=True)
+    lr = net.lane_road()
+    nrl = net.n_road_lanes
+    r_in = [r for r in range(net.n_roads) if net.road_to[r] == 4][0]
+    lanes = list(range(int(net.road_lane_off[r_in]), int(net.road_lane_off[r_in + 1])))
+    jls = range(int(net.jl_off[lanes[0]]), int(net.jl_off[lanes[0] + 1]))
+    r_left = [int(lr[net.jl_target[j - nrl]]) for j in jls if net.jl_turn[j - nrl] == 1][0]
+    veh = sc.Vehicles(n=1, route_off=np.array([0, 2], dtype=np.int32), routes=np.array([r_in, r_left], dtype=np.int32),
+                      start_lane=np.array([lanes[1]], dtype=np.int32), dep=np.zeros(1, dtype=np.int32),
+                      v0f=np.ones(1, dtype=np.float32))
+    st = dict(status=np.ones(1, dtype=np.int32), lane=np.array([lanes[1]], dtype=np.int32), s=np.array([40.0]),
+              v=np.array([8.0]), rc=np.zeros(1, dtype=np.int32))
+    scen = sc.Scenario(net, veh, sc.Params(p_attempt=0.0), "plans")
+    o = _oracle(scen, st, libpath)
+    o.set_signal(list(range(net.n_junctions)), oracle.POLICY_NONE)
+    for _ in range(3):
+        o.step(1)
+        assert o.state()["lane"][0] == lanes[1]
+    o.set_road_plan([r_in], [1])
+    o.step(1)
+    assert o.state()["lane"][0] == lanes[0]
+    # back in plan 0 the left lane still has access: no change either way
+    o.set_road_plan([r_in], [0])
+    o.step(3)
+    assert o.state()["lane"][0] == lanes[0]
+
+
 ALL_CHECKS = [
     check_idm_free_road, check_idm_equilibrium, check_p_lc, check_mobil_case_A,
     check_mobil_case_B, check_mobil_case_C, check_mobil_case_D, check_mobil_mirror, check_neighbours_bruteforce,
@@ -718,4 +751,5 @@ ALL_CHECKS = [
     check_arrival_and_travel_time, check_insertion, check_conflict, check_max_pressure_argmax,
     check_max_pressure_timing, check_lane_queue_and_road_speed, check_lane_max_speed,
     check_lane_restriction, check_reroute, check_lane_group_mandatory, check_lane_group_keeps_inside,
+    check_lane_plan_switch,
 ]

@@ -50,6 +50,7 @@ MUTATIONS = [
     ("groups_no_access_no_stop", " || (lane < O->n_road_lanes && nl1 == -2)) {", ") {"),
     ("groups_mandatory_wrong_way", "int dir = best < lane ? -1 : +1, tl = lane + dir;",
      "int dir = best < lane ? +1 : -1, tl = lane + dir;\n        if (tl < lo || tl >= hi) return D;"),
+    ("plans_ignored", "return (O->jl_plans[j] >> O->road_plan[O->lane_road[O->jl_from[j]]]) & 1;", "return 1;"),
     ("maxp_ties_to_smallest", "if (pk > pb || (pk == pb && best != p && k < best)) best = k;",
      "if (pk > pb || (pk == pb && k < best)) best = k;"),
 ]
