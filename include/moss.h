@@ -108,6 +108,12 @@ typedef struct MossNetwork {
     const int32_t* junc_phase_off; /* [n_junctions+1] */
     const int32_t* phase_green;    /* [junc_phase_off[n_junctions]] steps */
     const int32_t* phase_amber;    /* [junc_phase_off[n_junctions]] steps */
+    /* lane function plans (§3.2 "Road"; optional, NULL = one plan): bit p of
+     * jl_plans[j - n_road_lanes] = junction lane j exists in plan p (p < 8).
+     * Every road starts in plan 0; moss_set_road_lane_plan switches it.  A
+     * junction lane outside the current plan of its road gives no access to
+     * its out-road (the lane-group rules apply) and carries no pressure. */
+    const int32_t* jl_plans;       /* [n_lanes-n_road_lanes] or NULL */
 } MossNetwork;
 
 /*
@@ -223,6 +229,17 @@ int moss_set_lane_restriction(moss_t h, int n, const int32_t* lane_ids, const in
  */
 int moss_set_vehicle_route(moss_t h, int n, const int32_t* vehicle_ids, const int32_t* route_off,
                            const int32_t* roads);
+
+/*
+ * Lane function plans (§3.2 "Road", set_road_lane_plan) of n roads of a
+ * single-scenario handle (scenario 0 of a batch): road road_ids[k] uses plan
+ * plan_idx[k] (0..7) from the next step.  The vehicles on those roads get
+ * their next lane again (a lane that loses access to a vehicle's next road
+ * puts it outside its lane group); vehicles on junction lanes drive on.
+ * Host arrays; MOSS_EINVAL for ids out of range (nothing changed).  Waits
+ * for the handle's stream.
+ */
+int moss_set_road_lane_plan(moss_t h, int n, const int32_t* road_ids, const int32_t* plan_idx);
 
 /*
  * Lane and road metrics of the current state (§3.3 "Lane Queue Length",

@@ -33,7 +33,7 @@ class MossNetwork(ctypes.Structure):
                 ("road_lane_off", _c_i32p), ("lane_length", _c_f32p), ("lane_vmax", _c_f32p),
                 ("jl_off", _c_i32p), ("jl_target", _c_i32p), ("jl_junction", _c_i32p),
                 ("jl_mask", _c_i32p), ("junc_offset", _c_i32p), ("junc_phase_off", _c_i32p),
-                ("phase_green", _c_i32p), ("phase_amber", _c_i32p)]
+                ("phase_green", _c_i32p), ("phase_amber", _c_i32p), ("jl_plans", _c_i32p)]
 
 
 class MossVehicles(ctypes.Structure):
@@ -76,6 +76,7 @@ SIGNATURES = {
     "moss_set_signal_policy": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p, ctypes.c_int32]),
     "moss_get_signal_state": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p, _c_i32p, _c_i32p, _c_i32p]),
     "moss_set_vehicle_route": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p, _c_i32p, _c_i32p]),
+    "moss_set_road_lane_plan": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p, _c_i32p]),
     "moss_set_lane_max_speed": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p, ctypes.POINTER(ctypes.c_float)]),
     "moss_set_lane_restriction": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p, _c_i32p]),
     "moss_get_lane_queue": (ctypes.c_int, [_vp, _c_i32p]),
@@ -170,7 +171,8 @@ def _net_struct(net, keep: list) -> MossNetwork:
                        i32(net.road_lane_off), f32(net.lane_length), f32(net.lane_vmax),
                        i32(net.jl_off), i32(net.jl_target), i32(net.jl_junction), i32(net.jl_mask),
                        i32(net.junc_offset), i32(net.junc_phase_off), i32(net.phase_green),
-                       i32(net.phase_amber))
+                       i32(net.phase_amber),
+                       i32(net.jl_plans) if getattr(net, "jl_plans", None) is not None else None)
 
 
 def _veh_struct(veh, keep: list) -> MossVehicles:
@@ -289,6 +291,12 @@ class Simulation(_Handle):
         j = np.ascontiguousarray(junctions, dtype=np.int32)
         _check(self.lib.moss_set_signal_policy(self.h, len(j), _ptr(j, ctypes.c_int32),
                                                int(policy)), self.h)
+
+    def set_road_lane_plan(self, roads: Sequence[int], plans) -> None:
+        r = np.ascontiguousarray(roads, dtype=np.int32)
+        p = np.ascontiguousarray(plans, dtype=np.int32)
+        _check(self.lib.moss_set_road_lane_plan(self.h, len(r), _ptr(r, ctypes.c_int32), _ptr(p, ctypes.c_int32)),
+               self.h)
 
     def set_vehicle_route(self, vehicles: Sequence[int], routes) -> None:
         """New routes (lists of road ids) for the given vehicles (all or nothing)."""

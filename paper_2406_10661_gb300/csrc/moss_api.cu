@@ -65,6 +65,9 @@ struct MossHandle {
     int32_t *d_jj_off = nullptr, *d_jj_lane = nullptr, *d_jj_from = nullptr, *d_mp_press = nullptr;
     int n_jj = 0;
     bool lane_groups = false;         // some road has a turn that not all of its lanes serve (R27)
+    std::vector<int32_t> jl_plans;    // plan mask per lane (junction lanes; 0xff = every plan), R28
+    int32_t* d_jl_plans = nullptr;
+    int8_t* d_road_mark = nullptr;    // roads whose plan a setter changes
     int2* d_road_span = nullptr;      // (first, end) road lanes per road
     std::vector<int2> road_span;
     std::vector<int> scen_road_off;   // [n_scen+1]
@@ -199,6 +202,8 @@ int validate(MossHandle* h, const MossNetwork* net, const MossVehicles* veh, con
         if (net->jl_target[k] < 0 || net->jl_target[k] >= NRL) return fail(h, MOSS_EINVAL, "jl_target range");
         if (net->jl_junction[k] < 0 || net->jl_junction[k] >= J) return fail(h, MOSS_EINVAL, "jl_junction range");
         if (net->jl_mask[k] < 0 || net->jl_mask[k] > 255) return fail(h, MOSS_EINVAL, "jl_mask must fit 8 bits");
+        if (net->jl_plans && (net->jl_plans[k] < 0 || net->jl_plans[k] > 255))
+            return fail(h, MOSS_EINVAL, "jl_plans must fit 8 bits");
     }
     // out-roads reachable from some lane of each road (a vehicle on a lane
     // without access changes lanes towards the group that has it, R27)
@@ -430,6 +435,7 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
     h->start_lane.resize(NV); h->v0f.resize(NV); h->veh_scen.resize(NV);
     h->scen_veh_off.assign(n + 1, 0); h->scen_lane_off.assign(n + 1, 0); h->scen_junc_off.assign(n + 1, 0);
     h->scen_road_off.assign(n + 1, 0);
+    h->jl_plans.assign(tot_lanes, 0xff);
     h->road_span.assign(tot_roads, make_int2(0, 0));
     h->key0.resize(n); h->key1.resize(n);
     int LO = 0, JO = 0, VO = 0, RO = 0, PO = 0, ROFF = 0;
@@ -465,6 +471,13 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
             for (int j = nt.jl_off[l]; j < nt.jl_off[l + 1]; ++j) h->lane_src_road[LO + j] = RO + road_of[l];
         for (int r = 0; r < nt.n_roads; ++r)
             h->road_span[RO + r] = make_int2(LO + nt.road_lane_off[r], LO + nt.road_lane_off[r + 1]);
+        if (nt.jl_plans) {
+            h->lane_groups = true;  // a plan can take a turn away from some lanes
+            for (int q = 0; q < nt.n_lanes - NRL; ++q) {
+                h->jl_plans[LO + NRL + q] = nt.jl_plans[q];
+                if (!(nt.jl_plans[q] & 1)) h->lanes[LO + NRL + q].flags |= LF_OFF;  // roads start in plan 0
+            }
+        }
         for (int j = 0; j < nt.n_junctions; ++j) {
             h->junc_scen[JO + j] = k;
             junc_offset[JO + j] = nt.junc_offset[j];
@@ -572,6 +585,8 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
         if (span.empty()) span.push_back(make_int2(0, 0));
         TRY(upload(h, &h->d_road_span, span));
         TRY(dalloc(h, &h->d_lstage, 2 * (size_t)std::max(NL, 1)));
+        TRY(upload(h, &h->d_jl_plans, h->jl_plans.empty() ? std::vector<int32_t>(1, 0xff) : h->jl_plans));
+        TRY(upload(h, &h->d_road_mark, std::vector<int8_t>(std::max<long long>(tot_roads, 1), 0)));
         TRY(dalloc(h, (char**)&h->d_mbuf, sizeof(double) * (size_t)std::max(std::max(NL, (int)tot_roads), 1)));
         h->n_jj = jj_off[NJ];
     }
@@ -737,7 +752,7 @@ int scen_state(MossHandle* h, int s, MossState* out) {
 
 int jl_toward_host(const MossHandle* h, int l, int out_road) {
     for (int j = h->lanes[l].jb; j < h->lanes[l].je; ++j)
-        if (h->lanes[j].road == out_road) return j;
+        if (h->lanes[j].road == out_road && !(h->lanes[j].flags & LF_OFF)) return j;
     return -1;
 }
 
@@ -1072,6 +1087,50 @@ int moss_set_signal_policy(moss_t h, int n, const int32_t* junction_ids, int32_t
     else enqueue_set_signal<float>(h, n, policy);
     CK(cudaGetLastError());
     return MOSS_OK;
+}
+
+int moss_set_road_lane_plan(moss_t h, int n, const int32_t* road_ids, const int32_t* plan_idx) {
+    if (!h) return MOSS_EINVAL;
+    const int nr0 = h->scen_road_off[1];
+    if (n < 0 || (n > 0 && (!road_ids || !plan_idx))) return fail(h, MOSS_EINVAL, "bad arrays");
+    for (int k = 0; k < n; ++k) {
+        if (road_ids[k] < 0 || road_ids[k] >= nr0) return fail(h, MOSS_EINVAL, "road id out of range");
+        if (plan_idx[k] < 0 || plan_idx[k] > 7) return fail(h, MOSS_EINVAL, "plan index must be 0..7");
+    }
+    if (n == 0) return MOSS_OK;
+    CK(cudaStreamSynchronize(h->stream));
+    int32_t* d = nullptr;
+    if (cudaMalloc(&d, 2 * (size_t)n * 4) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, MOSS_ENOMEM, "plan setter scratch");
+    }
+    cudaError_t e = cudaMemcpy(d, road_ids, n * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d + n, plan_idx, n * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        const int nb = (n + 255) / 256, grid = std::max(1, h->sm_count * 4);
+        if (h->precision == 64) {
+            Ctx<double> c = make_ctx<double>(h, h->parity);
+            k_set_plan<double><<<nb, 256, 0, h->stream>>>(c, n, d, d + n, h->d_jl_plans, h->d_road_mark);
+            k_plan_next_lanes<double><<<grid, 256, 0, h->stream>>>(c, h->d_road_mark);
+        } else {
+            Ctx<float> c = make_ctx<float>(h, h->parity);
+            k_set_plan<float><<<nb, 256, 0, h->stream>>>(c, n, d, d + n, h->d_jl_plans, h->d_road_mark);
+            k_plan_next_lanes<float><<<grid, 256, 0, h->stream>>>(c, h->d_road_mark);
+        }
+        k_unmark_roads<<<nb, 256, 0, h->stream>>>(n, d, h->d_road_mark);
+        e = cudaStreamSynchronize(h->stream);
+    }
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(h, MOSS_ECUDA, cudaGetErrorString(e));
+    for (int k = 0; k < n; ++k) {  // the host copy of the lane table
+        const int2 sp = h->road_span[road_ids[k]];
+        for (int l = sp.x; l < sp.y; ++l)
+            for (int j = h->lanes[l].jb; j < h->lanes[l].je; ++j) {
+                const bool on = (h->jl_plans[j] >> plan_idx[k]) & 1;
+                h->lanes[j].flags = on ? (h->lanes[j].flags & ~LF_OFF) : (h->lanes[j].flags | LF_OFF);
+            }
+    }
+    return check_device(h);
 }
 
 int moss_set_vehicle_route(moss_t h, int n, const int32_t* vehicle_ids, const int32_t* route_off,

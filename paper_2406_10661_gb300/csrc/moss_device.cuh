@@ -119,7 +119,10 @@ struct alignas(32) LaneInfo {
     int lo, hi, jb, je, road;
     unsigned short scen, flags;
 };
-enum : int { LF_RESTRICTED = 1 };  // restricted from passing: not entered (R25)
+enum : int {
+    LF_RESTRICTED = 1,  // restricted from passing: not entered (R25)
+    LF_OFF = 2          // junction lane outside the current lane plan of its road (R28)
+};
 
 // One 16-byte record per junction (signal program; policy and manual phase
 // are mutable and kept apart)
@@ -308,7 +311,7 @@ template <typename Real>
 __device__ __forceinline__ void mp_accumulate(const Ctx<Real>& c, int k) {
     const int jl = c.jj_lane[k];
     const LaneInfo ji = c.lane[jl];
-    if (c.junc_policy[ji.jb] != POL_MAXP) return;
+    if (c.junc_policy[ji.jb] != POL_MAXP || (ji.flags & LF_OFF)) return;
     const int from = c.jj_from[k], to = ji.hi;
     const int d = (c.cur.off[from + 1] - c.cur.off[from]) - (c.cur.off[to + 1] - c.cur.off[to]);
     if (d == 0) return;
@@ -378,11 +381,17 @@ __device__ __forceinline__ int light_of(const Ctx<Real>& c, const LaneInfo& ji) 
 // junction lane leaving road lane (record li) towards road out_road (-1 if
 // none); `hint` is tried first (the position of the matching junction lane of
 // a neighbouring lane of the same road, usually the same)
+// (junction lanes outside the road's current lane plan do not count, R28)
 template <typename Real>
 __device__ __forceinline__ int jl_toward(const Ctx<Real>& c, const LaneInfo& li, int out_road, int hint = -1) {
-    if (hint >= 0 && li.jb + hint < li.je && c.lane[li.jb + hint].road == out_road) return li.jb + hint;
-    for (int j = li.jb; j < li.je; ++j)
-        if (c.lane[j].road == out_road) return j;
+    if (hint >= 0 && li.jb + hint < li.je) {
+        const LaneInfo x = c.lane[li.jb + hint];
+        if (x.road == out_road && !(x.flags & LF_OFF)) return li.jb + hint;
+    }
+    for (int j = li.jb; j < li.je; ++j) {
+        const LaneInfo x = c.lane[j];
+        if (x.road == out_road && !(x.flags & LF_OFF)) return j;
+    }
     return -1;
 }
 

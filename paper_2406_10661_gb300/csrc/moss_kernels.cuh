@@ -790,6 +790,43 @@ __global__ void k_apply_routes(Ctx<Real> c, const int32_t* req, int nv, const in
     }
 }
 
+// Lane plans (R28): road roads[k] switches to plan plans[k] (junction lanes
+// outside it get LF_OFF) and is marked; then the vehicles on the marked
+// roads' lanes get their next lane again; then the marks are cleared.
+template <typename Real>
+__global__ void k_set_plan(Ctx<Real> c, int n, const int32_t* roads, const int32_t* plans, const int32_t* jl_plans,
+                           int8_t* road_mark) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int r = roads[k], p = plans[k];
+    const int2 sp = c.road_span[r];
+    LaneInfo* lanes = const_cast<LaneInfo*>(c.lane);
+    for (int l = sp.x; l < sp.y; ++l)
+        for (int j = lanes[l].jb; j < lanes[l].je; ++j) {
+            const bool on = (jl_plans[j] >> p) & 1;
+            lanes[j].flags = on ? (lanes[j].flags & ~LF_OFF) : (lanes[j].flags | LF_OFF);
+        }
+    road_mark[r] = 1;
+}
+
+template <typename Real>
+__global__ void k_plan_next_lanes(Ctx<Real> c, const int8_t* road_mark) {
+    const int n = c.cnt->n_cur;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const RecA<Real> a = c.cur.a[i];
+        const LaneInfo li = c.lane[a.lane];
+        if (li.lo < 0 || !road_mark[li.road]) continue;
+        RecB b = c.cur.b[i];
+        b.nl = b.rptr < b.rlast ? jl_toward(c, li, c.routes[b.rptr + 1]) : -1;
+        c.cur.b[i] = b;
+    }
+}
+
+__global__ void k_unmark_roads(int n, const int32_t* roads, int8_t* road_mark) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) road_mark[roads[k]] = 0;
+}
+
 // Failure-detection self-test: the look-back of tile 1 waits on tile word 0,
 // which nothing publishes, so the bounded wait must give up and report.
 __global__ void k_selftest_wait(unsigned long long* words, int* err) {

@@ -59,3 +59,31 @@ def test_fp32_one_step_parity_lane_groups():
     for k in ("s", "v"):
         err = np.abs(g[k][ok] - r[k][ok]) / np.maximum(np.abs(r[k][ok]), 1.0)
         assert (err <= 1e-5).all(), (k, float(err.max()))
+
+
+def test_fp64_rollout_lane_plan_switches():
+    """Reading R28: roads switch between their two lane plans (all turns from
+    every lane / turn groups) during the rollout; identical to the oracle."""
+    net = sc.grid_network(4, 200.0, 3, 13.89, lane_plans=True)
+    veh = sc.random_demand(net, 1500, 300, seed=3)
+    scen = sc.Scenario(net, veh, sc.Params(seed=3), "plans")
+    sim = binding.Simulation(net, veh, scen.params, precision=64)
+    ora = oracle.Oracle(net, veh, scen.params)
+    rng = np.random.default_rng(8)
+    for chunk in range(8):
+        roads = rng.choice(net.n_roads, net.n_roads // 2, replace=False)
+        plans = rng.integers(0, 2, len(roads))
+        sim.set_road_lane_plan(roads, plans)
+        ora.set_road_plan(roads, plans)
+        sim.step(60); ora.step(60)
+        g, r = sim.state(), ora.state()
+        assert np.array_equal(g["status"], r["status"]), chunk
+        act = r["status"] == 1
+        assert np.array_equal(g["lane"][act], r["lane"][act]), chunk
+        assert np.abs(g["s"][act] - r["s"][act]).max(initial=0) < 1e-6
+        assert np.abs(g["v"][act] - r["v"][act]).max(initial=0) < 1e-6
+        assert np.array_equal(g["flags"], r["flags"])
+    gm, rm = sim.metrics(), ora.metrics()
+    for k in ("n_arrived", "vehicle_updates", "lane_changes", "flagged", "inserted", "errors"):
+        assert gm[k] == rm[k], (k, gm[k], rm[k])
+    assert gm["errors"] == 0
