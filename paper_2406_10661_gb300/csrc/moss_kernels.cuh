@@ -189,11 +189,54 @@ __device__ __forceinline__ void list_candidate(const Ctx<Real>& c, int i, const 
 }
 
 // ---------------------------------------------------------------------------
+// The vehicles whose attempt draw passed are queued in shared memory, one
+// queue of 64 entries per warp, and MOBIL runs over a warp's queue 32 at a
+// time: a warp otherwise carries the whole MOBIL evaluation of any one of
+// its lanes while the others idle.
+template <typename Real>
+struct MobilQueue {
+    Real a[2 * TILE], gap[2 * TILE], sgap[2 * TILE];  // own-lane kinematics (LaneAcc)
+    int i[2 * TILE], lane[2 * TILE], bits[2 * TILE], nl[2 * TILE];
+    float u_lc[2 * TILE], u_dir[2 * TILE];
+    int n[TILE / 32];
+};
+
+// MOBIL and the update of queued vehicle k (the snapshot and lane records
+// are read again; the own-lane part comes from the queue)
+template <typename Real, bool Groups>
+__device__ __forceinline__ void mobil_finish(const Ctx<Real>& c, const MobilQueue<Real>& q, int k, MetricAcc& acc,
+                                             int tag) {
+    const int i = q.i[k], lane = q.lane[k];
+    const RecA<Real> E = c.cur.a[i];
+    const RecB EB = c.cur.b[i];
+    const LaneInfo li = c.lane[lane];
+    const int b = c.cur.off[lane], e = c.cur.off[lane + 1];
+    LaneAcc<Real> own;
+    own.a = q.a[k]; own.gap = q.gap[k]; own.stop_gap = q.sgap[k];
+    const int bits = q.bits[k];
+    own.has_leader = bits & 1; own.stop = (bits >> 1) & 1; own.overlap = (bits >> 2) & 1;
+    own.nl = q.nl[k];
+    const int sc = li.scen;
+    if (sc != acc.scen) {
+        macc_flush_thread(acc, c.metrics);
+        macc_reset(acc, sc);
+    }
+    const Decision<Real> D = decide_mobil<Real, Groups>(c, i, E, EB, li, b, e, own, q.u_lc[k], q.u_dir[k]);
+    if (D.cand) {
+        list_candidate(c, i, E, EB, sc, D, tag);
+        return;
+    }
+    const long long t = c.scen_step[sc];
+    if (integrate_emit(c, acc, i, E, EB, own, lane, D.flag ? F_FLAGGED : 0, own.overlap != 0, t, sc, tag))
+        atomicAdd(&c.tile_leave[i / TILE], 1);
+}
+
+// ---------------------------------------------------------------------------
 // k_decide: blocks [0, n_work) take 256-slot tiles of the current snapshot
 // (one vehicle per thread); blocks [n_work, gridDim) run the insertion.
 // Per vehicle: the own-lane acceleration and the attempt draw, MOBIL if the
-// draw passed, then the update; lane-change candidates are finished by
-// k_resolve.
+// draw passed (from the warp's queue, above), then the update; lane-change
+// candidates are finished by k_resolve.
 // Groups: the network has lane groups (some road has a turn that not all of
 // its lanes serve), so the mandatory changes of R27 can occur; without them
 // that path is not compiled in.
@@ -219,10 +262,15 @@ __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Rea
     const int t_beg = blockIdx.x * per, t_end = min(n_tiles, t_beg + per);
     MetricAcc acc;
     macc_reset(acc, -1);
-    for (int tile = t_beg; tile < t_end; ++tile) {
+    __shared__ MobilQueue<Real> q;
+    const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31, qb = warp * 64;
+    if (wl == 0) q.n[warp] = 0;
+    __syncwarp();
+    for (int tile = t_beg;; ++tile) {
+        const bool last = tile >= t_end;
         const int i = tile * TILE + threadIdx.x;
         int leaver = 0;
-        if (i < n) {
+        if (!last && i < n) {
             const RecA<Real> E = c.cur.a[i];
             const RecB EB = c.cur.b[i];
             const int lane = E.lane;
@@ -243,13 +291,13 @@ __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Rea
                 bool cand = false;
                 if (P.att) {
                     acc.mob += 1;
-                    const Decision<Real> D = decide_mobil<Real, Groups>(c, i, E, EB, li, b, c.cur.off[lane + 1], P.own, P.u_lc,
-                                                          P.u_dir);
-                    if (D.cand) {
-                        list_candidate(c, i, E, EB, sc, D, tag);
-                        cand = true;
-                    }
-                    fl = D.flag ? F_FLAGGED : 0;
+                    const int k = qb + warp_claim(&q.n[warp]);
+                    q.i[k] = i; q.lane[k] = lane;
+                    q.a[k] = P.own.a; q.gap[k] = P.own.gap; q.sgap[k] = P.own.stop_gap;
+                    q.bits[k] = (P.own.has_leader ? 1 : 0) | (P.own.stop ? 2 : 0) | (P.own.overlap ? 4 : 0);
+                    q.nl[k] = P.own.nl;
+                    q.u_lc[k] = P.u_lc; q.u_dir[k] = P.u_dir;
+                    cand = true;  // finished from the queue
                 } else if (Groups && P.mand) {
                     const Decision<Real> D = decide_mandatory(c, i, E, EB, li, P.own);
                     if (D.cand) {
@@ -264,6 +312,18 @@ __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Rea
         // leavers of this tile (k_lanescan zeroes the counters after reading them)
         const unsigned lb = __ballot_sync(0xffffffffu, leaver);
         if ((threadIdx.x & 31) == 0 && lb) atomicAdd(&c.tile_leave[tile], __popc(lb));
+        // MOBIL over the last 32 entries of the warp's queue once it holds
+        // 32, and over what is left after the last tile
+        __syncwarp();
+        const int nq = q.n[warp];
+        const int take = last ? nq : (nq >= 32 ? 32 : 0);
+        if (take > 0) {
+            if (wl < take) mobil_finish<Real, Groups>(c, q, qb + nq - take + wl, acc, tag);
+            __syncwarp();
+            if (wl == 0) q.n[warp] = nq - take;
+            __syncwarp();
+        }
+        if (last) break;
     }
     macc_flush_block<TILE>(acc, c.metrics);
 }
