@@ -327,7 +327,7 @@ int moss_kernel_times(moss_t h, double* ms4, int64_t* steps);
  * Autotuner of the launch schedule: times the next steps of the simulation
  * (9 x trial_steps of them; they are simulated normally, and the results do
  * not depend on the schedule) under candidate block counts per SM of the
- * step kernels, keeps the fastest (coordinate search: decide in {2,3,4},
+ * step kernels, keeps the fastest (coordinate search: decide in {3,4,5},
  * lanescan in {1,2,4}, place in {4,8,16}) and re-captures the step graphs.
  * chosen3 (may be NULL) receives the chosen decide/lanescan/place values.
  */

@@ -1359,7 +1359,7 @@ int moss_autotune(moss_t h, int trial_steps, int* chosen3) {
     CK(cudaStreamSynchronize(h->stream));
     // coordinate search over blocks per SM of each kernel; results do not
     // depend on the launch configuration, only the time does
-    static const int cand_decide[] = {2, 3, 4};
+    static const int cand_decide[] = {3, 4, 5};
     static const int cand_lanescan[] = {1, 2, 4};
     static const int cand_place[] = {4, 8, 16};
     const int* cands[3] = {cand_decide, cand_lanescan, cand_place};

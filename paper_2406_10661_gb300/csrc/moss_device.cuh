@@ -77,6 +77,12 @@ struct Counters {
 template <typename Real> struct RecA;
 template <> struct alignas(16) RecA<float> { float s, v; int id, lane; };
 template <> struct alignas(16) RecA<double> { double s, v; int id, lane; };
+// a record that belongs to no lane (neighbour slot outside the snapshot)
+template <typename Real> __host__ __device__ __forceinline__ RecA<Real> no_rec() {
+    RecA<Real> r;
+    r.s = Real(0); r.v = Real(0); r.id = -1; r.lane = -1;
+    return r;
+}
 struct alignas(16) RecB {
     float v0f;
     int rptr;   // index in routes[] of the current road (junction lane: the road just left)
@@ -420,25 +426,25 @@ struct LaneAcc {
     int has_leader, stop, overlap, nl;  // nl: the next lane from this lane on the route
 };
 
-// Ego acceleration on a lane (record li) at (s, v): min over the leader (slot
-// ld in this lane, else lookahead over at most two lanes, R11) and the stop
-// line (R12).  nl: next lane from this lane on the ego's route (-1 none).
+// Ego acceleration on a lane (record li) at (s, v): min over the leader (the
+// vehicle at (ld_s, ld_v) in this lane if has_ld, else lookahead over at
+// most two lanes, R11) and the stop line (R12).  nl: next lane from this
+// lane on the ego's route (-1 none).
 template <typename Real, bool Groups = true>
 __device__ __forceinline__ LaneAcc<Real> accel_on_lane(const Ctx<Real>& c, const LaneInfo& li, Real s,
-                                                       Real v, Real v0, int ld, int nl, int rptr,
-                                                       int rlast) {
+                                                       Real v, Real v0, bool has_ld, Real ld_s, Real ld_v,
+                                                       int nl, int rptr, int rlast) {
     LaneAcc<Real> r;
     r.has_leader = 0; r.stop = 0; r.overlap = 0; r.gap = Real(0); r.stop_gap = Real(0); r.nl = nl;
     Real a = idm_free(c, v, v0);
-    if (ld >= 0) {
-        const RecA<Real> L = c.cur.a[ld];
-        const Real gap = L.s - c.len - s;
-        a = idm(c, v, v0, gap, v - L.v);
+    if (has_ld) {
+        const Real gap = ld_s - c.len - s;
+        a = idm(c, v, v0, gap, v - ld_v);
         r.has_leader = 1; r.gap = gap; r.overlap = gap < Real(0);
     }
     if (nl >= 0) {
         const LaneInfo ni = c.lane[nl];
-        if (ld < 0) {
+        if (!has_ld) {
             Real base = Real(li.L) - s;
             int x = nl;
             LaneInfo xi = ni;
@@ -518,15 +524,17 @@ struct OwnPart {
     int mand;           // outside the lane group of the next road: mandatory change (R27)
 };
 
+// The neighbours in the own lane are the records of slots i - 1 and i + 1
+// when their lane is the ego's (read with the ego's record, not after its
+// lane's bounds).
 template <typename Real, bool Groups = true>
-__device__ __forceinline__ OwnPart<Real> decide_own(const Ctx<Real>& c, int i, const RecA<Real>& E,
-                                                    const RecB& EB, const LaneInfo& li, int b, long long t,
+__device__ __forceinline__ OwnPart<Real> decide_own(const Ctx<Real>& c, const RecA<Real>& E, const RecB& EB,
+                                                    const LaneInfo& li, const RecA<Real>& OLr, long long t,
                                                     uint32_t k0, uint32_t k1, int vbase) {
     OwnPart<Real> P;
     P.att = 0; P.mand = 0; P.u_lc = 0.0f; P.u_dir = 0.0f;
-    const int OL = (i > b) ? i - 1 : -1;
-    P.own = accel_on_lane<Real, Groups>(c, li, E.s, E.v, Real(EB.v0f) * Real(li.vmax), OL, EB.nl, EB.rptr,
-                                        EB.rlast);
+    P.own = accel_on_lane<Real, Groups>(c, li, E.s, E.v, Real(EB.v0f) * Real(li.vmax), OLr.lane == E.lane, OLr.s,
+                                        OLr.v, EB.nl, EB.rptr, EB.rlast);
     if (li.lo < 0 || li.hi - li.lo < 2) return P;  // junction lane or single-lane road
     // no access to the next road from this lane: a mandatory change, no draw (R27)
     if (Groups && EB.nl < 0 && EB.rptr < EB.rlast) { P.mand = 1; return P; }
@@ -541,29 +549,25 @@ __device__ __forceinline__ OwnPart<Real> decide_own(const Ctx<Real>& c, int i, c
 }
 
 template <typename Real, bool Groups = true>
-__device__ __forceinline__ Decision<Real> decide_mobil(const Ctx<Real>& c, int i, const RecA<Real>& E,
-                                                       const RecB& EB, const LaneInfo& li, int b, int e,
+__device__ __forceinline__ Decision<Real> decide_mobil(const Ctx<Real>& c, const RecA<Real>& E, const RecB& EB,
+                                                       const LaneInfo& li, const RecA<Real>& OLr,
+                                                       const RecA<Real>& OFr, float of_v0f,
                                                        const LaneAcc<Real>& own, float f_lc, float f_dir) {
     Decision<Real> D;
     D.cand = 0; D.dir = 0; D.tl = -1; D.TL = -1; D.TF = -1; D.flag = 0; D.nlt = -1; D.att = 1;
     D.u = Real(0); D.scale = Real(1);
     D.own = own;
     const int lane = E.lane;
-    const int OL = (i > b) ? i - 1 : -1;
     const Real v0f = Real(EB.v0f);
     const Real u_lc = Real(f_lc), u_dir = Real(f_dir);
 
-    const int OF = (i + 1 < e) ? i + 1 : -1;
     Real a_old = Real(0), at_old = Real(0);
-    if (OF >= 0) {
-        const RecA<Real> F = c.cur.a[OF];
-        const float fv0f = c.cur.b[OF].v0f;
-        a_old = acc_pair(c, F, fv0f, li.vmax, true, E.s, E.v);
-        if (OL >= 0) {
-            const RecA<Real> L = c.cur.a[OL];
-            at_old = acc_pair(c, F, fv0f, li.vmax, true, L.s, L.v);
+    if (OFr.lane == lane) {
+        a_old = acc_pair(c, OFr, of_v0f, li.vmax, true, E.s, E.v);
+        if (OLr.lane == lane) {
+            at_old = acc_pair(c, OFr, of_v0f, li.vmax, true, OLr.s, OLr.v);
         } else {
-            at_old = acc_pair(c, F, fv0f, li.vmax, false, Real(0), Real(0));
+            at_old = acc_pair(c, OFr, of_v0f, li.vmax, false, Real(0), Real(0));
         }
     }
     // next road of the route (for the target lane's junction lane)
@@ -608,7 +612,8 @@ __device__ __forceinline__ Decision<Real> decide_mobil(const Ctx<Real>& c, int i
             if (rabs(g) < c.band * pos_scale) D.flag = 1;
         }
         const Real at_ego =
-            accel_on_lane<Real, Groups>(c, ti, E.s, E.v, v0f * Real(ti.vmax), TL, nlt, EB.rptr, EB.rlast).a;
+            accel_on_lane<Real, Groups>(c, ti, E.s, E.v, v0f * Real(ti.vmax), TL >= 0, TLr.s, TLr.v, nlt, EB.rptr,
+                                        EB.rlast).a;
         Real a_new = Real(0), at_new = Real(0);
         if (TF >= 0) {
             const float fv0f = c.cur.b[TF].v0f;

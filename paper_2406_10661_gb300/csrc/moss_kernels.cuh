@@ -169,8 +169,11 @@ __device__ __forceinline__ void list_candidate(const Ctx<Real>& c, int i, const 
     else if (D.TL >= 0) gp = D.TL + 1;
     else gp = c.cur.off[D.tl];
     const LaneInfo ti = c.lane[D.tl];
-    const LaneAcc<Real> T =
-        accel_on_lane(c, ti, E.s, E.v, Real(EB.v0f) * Real(ti.vmax), D.TL, D.nlt, EB.rptr, EB.rlast);
+    RecA<Real> TLr;
+    TLr.s = Real(0); TLr.v = Real(0);
+    if (D.TL >= 0) TLr = c.cur.a[D.TL];
+    const LaneAcc<Real> T = accel_on_lane(c, ti, E.s, E.v, Real(EB.v0f) * Real(ti.vmax), D.TL >= 0, TLr.s, TLr.v,
+                                          D.nlt, EB.rptr, EB.rlast);
     Cand<Real> C;
     C.E = E; C.EB = EB;
     C.slot = i; C.gap = gp + D.tl;
@@ -204,13 +207,19 @@ struct MobilQueue {
 // MOBIL and the update of queued vehicle k (the snapshot and lane records
 // are read again; the own-lane part comes from the queue)
 template <typename Real, bool Groups>
-__device__ __forceinline__ void mobil_finish(const Ctx<Real>& c, const MobilQueue<Real>& q, int k, MetricAcc& acc,
-                                             int tag) {
+__device__ __forceinline__ void mobil_finish(const Ctx<Real>& c, const MobilQueue<Real>& q, int k, int n,
+                                             MetricAcc& acc, int tag) {
     const int i = q.i[k], lane = q.lane[k];
     const RecA<Real> E = c.cur.a[i];
     const RecB EB = c.cur.b[i];
     const LaneInfo li = c.lane[lane];
-    const int b = c.cur.off[lane], e = c.cur.off[lane + 1];
+    RecA<Real> OLr = no_rec<Real>(), OFr = no_rec<Real>();
+    float of_v0f = 0.0f;
+    if (i > 0) OLr = c.cur.a[i - 1];
+    if (i + 1 < n) {
+        OFr = c.cur.a[i + 1];
+        of_v0f = c.cur.b[i + 1].v0f;
+    }
     LaneAcc<Real> own;
     own.a = q.a[k]; own.gap = q.gap[k]; own.stop_gap = q.sgap[k];
     const int bits = q.bits[k];
@@ -221,7 +230,7 @@ __device__ __forceinline__ void mobil_finish(const Ctx<Real>& c, const MobilQueu
         macc_flush_thread(acc, c.metrics);
         macc_reset(acc, sc);
     }
-    const Decision<Real> D = decide_mobil<Real, Groups>(c, i, E, EB, li, b, e, own, q.u_lc[k], q.u_dir[k]);
+    const Decision<Real> D = decide_mobil<Real, Groups>(c, E, EB, li, OLr, OFr, of_v0f, own, q.u_lc[k], q.u_dir[k]);
     if (D.cand) {
         list_candidate(c, i, E, EB, sc, D, tag);
         return;
@@ -242,7 +251,7 @@ __device__ __forceinline__ void mobil_finish(const Ctx<Real>& c, const MobilQueu
 // that path is not compiled in.
 // MOSS_DECIDE_MIN_BLOCKS: resident blocks per SM the register budget targets.
 #ifndef MOSS_DECIDE_MIN_BLOCKS
-#define MOSS_DECIDE_MIN_BLOCKS 4
+#define MOSS_DECIDE_MIN_BLOCKS 5
 #endif
 template <typename Real, bool Groups>
 __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Real> c, int n_work) {
@@ -273,6 +282,7 @@ __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Rea
         if (!last && i < n) {
             const RecA<Real> E = c.cur.a[i];
             const RecB EB = c.cur.b[i];
+            const RecA<Real> OLr = i > 0 ? c.cur.a[i - 1] : no_rec<Real>();
             const int lane = E.lane;
             if ((unsigned)lane >= (unsigned)c.n_lanes) {
                 atomicOr(c.err, ERR_RANGE);
@@ -284,9 +294,8 @@ __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Rea
                     macc_reset(acc, sc);
                 }
                 const long long t = c.scen_step[sc];
-                const int b = c.cur.off[lane];
                 const OwnPart<Real> P =
-                    decide_own<Real, Groups>(c, i, E, EB, li, b, t, c.key0[sc], c.key1[sc], c.veh_base[sc]);
+                    decide_own<Real, Groups>(c, E, EB, li, OLr, t, c.key0[sc], c.key1[sc], c.veh_base[sc]);
                 int fl = 0;
                 bool cand = false;
                 if (P.att) {
@@ -318,7 +327,7 @@ __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Rea
         const int nq = q.n[warp];
         const int take = last ? nq : (nq >= 32 ? 32 : 0);
         if (take > 0) {
-            if (wl < take) mobil_finish<Real, Groups>(c, q, qb + nq - take + wl, acc, tag);
+            if (wl < take) mobil_finish<Real, Groups>(c, q, qb + nq - take + wl, n, acc, tag);
             __syncwarp();
             if (wl == 0) q.n[warp] = nq - take;
             __syncwarp();
