@@ -95,6 +95,7 @@ struct MossHandle {
     int32_t* d_stage = nullptr;          // setter staging (2 * n_junctions)
     int32_t* h_stage = nullptr;          // pinned host staging of setter arguments (2 * n_junctions)
     cudaEvent_t stage_free = nullptr;    // recorded after the last copy out of h_stage
+    long long* h_rb = nullptr;           // pinned readback: a metric record, its step, the error word
 
     // launch configuration (blocks per SM) of the step kernels; moss_autotune picks them
     int cfg_decide = MOSS_DECIDE_MIN_BLOCKS, cfg_lanescan = 4, cfg_place = 8;
@@ -385,9 +386,9 @@ int build_graphs(MossHandle* h) {
 
 // read back the device error word; recoverable reports are cleared once read,
 // a poisoning error stays (every later step of the handle is skipped)
-int check_device(MossHandle* h) {
-    int err = 0;
-    CK(cudaMemcpy(&err, &h->d_cnt->err, sizeof(int), cudaMemcpyDeviceToHost));
+// the device error word, already read back: a status (a recoverable error is
+// cleared on the device; the poison bit stays)
+int device_status(MossHandle* h, int err) {
     if (err == 0) return MOSS_OK;
     if (!(err & ERR_POISON)) {
         const int zero = 0;
@@ -399,6 +400,12 @@ int check_device(MossHandle* h) {
     if (err & ERR_TRANSFER) m += " transfer overflow;";
     if (err & ERR_RANGE) m += " index out of range;";
     return fail(h, MOSS_EDEVICE, m);
+}
+
+int check_device(MossHandle* h) {
+    int err = 0;
+    CK(cudaMemcpy(&err, &h->d_cnt->err, sizeof(int), cudaMemcpyDeviceToHost));
+    return device_status(h, err);
 }
 
 // ---- create (n scenarios as one union network) ------------------------------
@@ -648,6 +655,7 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
     TRY(upload(h, &h->d_cnt, c0));
     TRY(dalloc(h, &h->d_stage, 2 * std::max(NJ, 1)));
     CK(cudaHostAlloc((void**)&h->h_stage, sizeof(int32_t) * 2 * std::max(NJ, 1), cudaHostAllocDefault));
+    CK(cudaHostAlloc((void**)&h->h_rb, sizeof(long long) * (M_NFIELDS + 2), cudaHostAllocDefault));
     CK(cudaEventCreateWithFlags(&h->stage_free, cudaEventDisableTiming));
     CK(cudaEventRecord(h->stage_free, h->stream));
     for (int k = 0; k <= N_STEP_KERNELS; ++k) CK(cudaEventCreate(&h->ev[k]));
@@ -667,6 +675,8 @@ void free_all(MossHandle* h) {
     if (h->stage_free) cudaEventDestroy(h->stage_free);
     if (h->h_stage) cudaFreeHost(h->h_stage);
     h->h_stage = nullptr;
+    if (h->h_rb) cudaFreeHost(h->h_rb);
+    h->h_rb = nullptr;
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     h->stream = nullptr;
 }
@@ -674,11 +684,17 @@ void free_all(MossHandle* h) {
 int scen_metrics(MossHandle* h, int s, MossMetrics* out) {
     if (!out) return fail(h, MOSS_EINVAL, "null output");
     if (s < 0 || s >= h->n_scen) return fail(h, MOSS_EINVAL, "scenario index out of range");
+    // one stream round trip: the record, the step and the error word are
+    // copied behind the queued work into pinned memory, then one wait
+    long long* M = h->h_rb;
+    CK(cudaMemcpyAsync(M, h->d_metrics + (size_t)s * M_NFIELDS, M_NFIELDS * sizeof(long long),
+                       cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(M + M_NFIELDS, h->d_step + s, sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(M + M_NFIELDS + 1, &h->d_cnt->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    long long M[M_NFIELDS];
-    long long step = 0;
-    CK(cudaMemcpy(M, h->d_metrics + (size_t)s * M_NFIELDS, sizeof(M), cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(&step, h->d_step + s, sizeof(long long), cudaMemcpyDeviceToHost));
+    const long long step = M[M_NFIELDS];
+    int err = 0;
+    std::memcpy(&err, M + M_NFIELDS + 1, sizeof(int));
     const int nv = h->scen_veh_off[s + 1] - h->scen_veh_off[s];
     out->step = step;
     out->n_active = M[M_CUR_ACTIVE];
@@ -693,7 +709,7 @@ int scen_metrics(MossHandle* h, int s, MossMetrics* out) {
     out->inserted = M[M_INSERTED];
     out->errors = M[M_ERRORS];
     out->mobil_evals = M[M_MOBIL];
-    return check_device(h);
+    return device_status(h, err);
 }
 
 template <typename Real>
