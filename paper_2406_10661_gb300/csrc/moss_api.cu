@@ -1063,18 +1063,19 @@ int moss_batch_set_signal_phase(moss_t h, int scenario, int n, const int32_t* ju
     const int j0 = h->scen_junc_off[scenario], nj = h->scen_junc_off[scenario + 1] - j0;
     if (n > nj) return fail(h, MOSS_EINVAL, "more junctions than the scenario has");
     if (n == 0) return MOSS_OK;
-    for (int k = 0; k < n; ++k) {
-        const int j = junction_ids[k];
-        if (j < 0 || j >= nj) return fail(h, MOSS_EINVAL, "junction id out of range");
-        const int np = h->junc_phase_off[j0 + j + 1] - h->junc_phase_off[j0 + j];
-        if (phase_idx[k] < 0 || phase_idx[k] >= std::max(np, 1))
-            return fail(h, MOSS_EINVAL, "phase index out of range");
-    }
-    // the pinned staging area is reused: wait until the previous copy out of it ran
+    // the pinned staging area is reused: wait until the previous copy out of
+    // it ran; then one pass checks and stages (nothing is enqueued on failure)
     CK(cudaEventSynchronize(h->stage_free));
+    const int32_t* po = h->junc_phase_off.data() + j0;
+    int32_t* sj = h->h_stage;
+    int32_t* sp = h->h_stage + n;
     for (int k = 0; k < n; ++k) {
-        h->h_stage[k] = j0 + junction_ids[k];
-        h->h_stage[n + k] = phase_idx[k];
+        const int j = junction_ids[k], p = phase_idx[k];
+        if (j < 0 || j >= nj) return fail(h, MOSS_EINVAL, "junction id out of range");
+        const int np = po[j + 1] - po[j];
+        if (p < 0 || p >= std::max(np, 1)) return fail(h, MOSS_EINVAL, "phase index out of range");
+        sj[k] = j0 + j;
+        sp[k] = p;
     }
     CK(cudaMemcpyAsync(h->d_stage, h->h_stage, 2 * n * 4, cudaMemcpyHostToDevice, h->stream));
     CK(cudaEventRecord(h->stage_free, h->stream));
