@@ -10,6 +10,8 @@ Levels (tolerances from the method's specification):
   * FP32 rollouts: network speed and trip completions within 0.5%;
   * a batch equals its scenarios run alone.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -86,6 +88,53 @@ def test_fp64_rollout_matches_oracle_small():
         assert gm[k] == rm[k], (k, gm[k], rm[k])
     assert abs(gm["tt_sum"] - rm["tt_sum"]) < 1e-9
     assert abs(gm["speed_sum"] - rm["speed_sum"]) <= 1e-6 * rm["speed_sum"]
+
+
+def _with_attempt(scen, p_att):
+    return dataclasses.replace(scen, params=dataclasses.replace(scen.params, p_attempt=p_att))
+
+
+@pytest.mark.parametrize("p_att", [0.0, 1.0])
+def test_fp64_rollout_attempt_extremes(p_att):
+    """Attempt probability 0 (no vehicle evaluates MOBIL, the MOBIL queues stay
+    empty) and 1 (every vehicle on a multi-lane road evaluates it, so the
+    queues fill and drain in full rounds of 32): FP64 rollout identical to
+    the oracle's."""
+    scen = _with_attempt(sc.small_scenario(), p_att)
+    sim, ora = _sim(scen, 64), _ora(scen)
+    for chunk in range(3):
+        sim.step(100); ora.step(100)
+        g, r = sim.state(), ora.state()
+        assert np.array_equal(g["status"], r["status"])
+        act = r["status"] == 1
+        assert np.array_equal(g["lane"][act], r["lane"][act])
+        assert np.array_equal(g["rc"][act], r["rc"][act])
+        assert np.abs(g["s"][act] - r["s"][act]).max(initial=0) < 1e-6
+        assert np.abs(g["v"][act] - r["v"][act]).max(initial=0) < 1e-6
+        assert np.array_equal(g["flags"], r["flags"])
+    gm, rm = sim.metrics(), ora.metrics()
+    for k in ("n_active", "n_arrived", "vehicle_updates", "lane_changes", "flagged", "mobil_evals"):
+        assert gm[k] == rm[k], (k, gm[k], rm[k])
+    if p_att == 0.0:
+        assert gm["mobil_evals"] == 0 and gm["lane_changes"] == 0
+    else:
+        assert gm["mobil_evals"] > 0.5 * gm["vehicle_updates"] and gm["lane_changes"] > 0
+
+
+def test_medium_one_step_parity_every_vehicle_attempts_fp32():
+    """30x30 grid of three-lane roads with attempt probability 1: one FP32 step
+    from a step-600 state, every vehicle compared (MOBIL from full queues on
+    tens of thousands of vehicles)."""
+    scen = _with_attempt(sc.medium_scenario(), 1.0)
+    sim = _sim(scen, 32)
+    sim.step(600)
+    st = sim.state()
+    ora = _ora(scen)
+    ora.set_state(st["status"], st["lane"], st["s"], st["v"], st["rc"], 600)
+    sim.step(1); ora.step(1)
+    n, excused = compare_one_step(sim.state(), ora.state())
+    assert n > 10_000 and excused <= n // 1000
+    assert sim.metrics()["mobil_evals"] > 0
 
 
 @pytest.mark.parametrize("t0", [60, 150, 300, 450, 599])
