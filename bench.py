@@ -43,7 +43,7 @@ SPEC_BYTES = {  # algorithmic bytes per unit, FP32 state
 STEP_BYTES = 64.0      # whole step: read and write one 8x4 B state record per vehicle update
 
 
-PROFILE = os.path.join(ROOT, "profiles", "step_kernels_city100x100_2464950.md")
+PROFILES = os.path.join(ROOT, "profiles")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2406_10661_gb300", "csrc", f)
                   for f in ("moss_device.cuh", "moss_kernels.cuh")]
 
@@ -57,12 +57,12 @@ def kernel_source_hash() -> str:
     return h.hexdigest()
 
 
-def captured_traffic(kernel: str):
-    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu
-    summary, if that capture was taken from the current kernel sources (the
-    summary records their SHA-256); else None."""
+def captured_traffic(kernel: str, workload: str = "city100x100_2464950"):
+    """DRAM bytes (read + write) per launch of `kernel` on `workload` from the
+    committed ncu summary of that workload, if the capture was taken from the
+    current kernel sources (the summary records their SHA-256); else None."""
     try:
-        with open(PROFILE) as f:
+        with open(os.path.join(PROFILES, f"step_kernels_{workload}.md")) as f:
             for line in f:
                 parts = line.split()
                 if len(parts) == 4 and parts[0] == "traffic:" and parts[1] == kernel:
@@ -141,14 +141,16 @@ def city(args):
     return sc.city_scenario(seed=args.seed, lane_groups=args.lane_groups)
 
 
-def cpu_oracle_rate(scen, state, budget_s=15.0, max_road=4000, steps_cap=60, max_pressure=False):
+def cpu_oracle_rate(scen, state, budget_s=15.0, max_road=4000, steps_cap=60, max_pressure=False,
+                    t_state=T_WARM):
     """The FP64 oracle, as it stands, on the roads with id < max_road of the
-    given state (a contiguous band of the grid at the same density)."""
+    given state (a contiguous band of the grid at the same density) at step
+    t_state."""
     import oracle
     from paper_2406_10661_gb300 import scenario as sc
     sample = sc.region_sample(state, scen.net, max_road)
     o = oracle.Oracle(scen.net, scen.veh, scen.params)
-    o.set_state(sample["status"], sample["lane"], sample["s"], sample["v"], sample["rc"], T_WARM)
+    o.set_state(sample["status"], sample["lane"], sample["s"], sample["v"], sample["rc"], t_state)
     if max_pressure:
         o.set_signal(list(range(scen.net.n_junctions)), oracle.POLICY_MAX_PRESSURE)
     o.step(1)  # untimed warm-up
@@ -162,7 +164,7 @@ def cpu_oracle_rate(scen, state, budget_s=15.0, max_road=4000, steps_cap=60, max
     m1 = o.metrics()
     upd = m1["vehicle_updates"] - m0["vehicle_updates"]
     return {"value": upd / dt, "unit": "vehicle-updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 oracle, {n} steps from the GPU's step-{T_WARM} state restricted to roads "
+            "sample": f"FP64 oracle, {n} steps from the GPU's step-{t_state} state restricted to roads "
                       f"0..{max_road - 1} ({int((sample['status'] == 1).sum())} active vehicles), "
                       f"single thread, {dt:.1f} s"}
 
@@ -228,7 +230,18 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     binding.load()
-    scen = city(args)
+    saturated = None
+    if args.workload == "saturated":
+        # every trip on the road at once (the kernels at full occupancy)
+        from paper_2406_10661_gb300 import scenario as sc
+        scen, saturated = sc.saturated_city(seed=args.seed)
+        t_start = 0
+        start_desc = ("all trips on the road at step 0, evenly spaced in proportion to lane length "
+                      "(set_state; set-up, untimed)")
+    else:
+        scen = city(args)
+        t_start = T_WARM
+        start_desc = f"the simulation's own state at step {T_WARM} (set-up, untimed)"
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     with torch.cuda.stream(stream):
@@ -236,7 +249,10 @@ def run_ours(args):
         mp = args.policy == "max_pressure"
         if mp:  # every junction under the adaptive max-pressure policy from step 0
             sim.set_signal_policy(np.arange(scen.net.n_junctions, dtype=np.int32), binding.POLICY_MAX_PRESSURE)
-        sim.step(T_WARM)  # set-up: the simulation reaches its own step-3600 state
+        if saturated is not None:
+            sim.set_state(*saturated, 0)
+        else:
+            sim.step(T_WARM)  # set-up: the simulation reaches its own step-3600 state
         state0 = sim.state() if world == 1 else None
         for _ in range(args.warmup):
             sim.step(1)
@@ -301,7 +317,7 @@ def run_ours(args):
         jids = torch.arange(J, dtype=torch.int32).pin_memory().numpy()
         offs = scen.net.junc_offset.astype(np.int64)
         e2e_steps = args.steps
-        t_first = T_WARM + args.warmup + args.steps + ksteps
+        t_first = t_start + args.warmup + args.steps + ksteps
         phases = torch.empty((e2e_steps, J), dtype=torch.int32).pin_memory().numpy()
         phases[:] = ((t_first + np.arange(e2e_steps)[:, None] + offs[None, :]) % 132) // 33
         me0 = sim.metrics()
@@ -333,7 +349,8 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     cpu = None if world > 1 else cpu_oracle_rate(scen, state0, budget_s=args.cpu_budget,
-                                                 max_pressure=args.policy == "max_pressure")
+                                                 max_pressure=args.policy == "max_pressure",
+                                                 t_state=t_start)
     n_total = int(scen.veh.n)
     line = {
         "metric": "vehicle-updates/s", "value": value, "unit": "vehicle-updates/s", "n_gpus": world,
@@ -342,7 +359,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": scen.name, "roads": int(scen.net.n_roads), "lanes": n_lanes,
                    "vehicles": n_total, "dt_s": 1.0,
-                   "start": f"the simulation's own state at step {T_WARM} (set-up, untimed)",
+                   "start": start_desc,
                    "active_per_step": upd / args.steps,
                    "l2": "flushed between timed steps by a 256 MiB write (outside the events)",
                    "signal_policy": args.policy, "lane_groups": bool(args.lane_groups),
@@ -352,7 +369,7 @@ def run_ours(args):
         "paper_context": {"step_hz": 84.09, "vehicles": 2464950, "hardware": "RTX 4090 + Xeon 8462Y",
                           "note": "different network (CBLab Roadnet-L); context only"},
         "roofline": {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": captured_traffic(f"k_{dom}"),
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": captured_traffic(f"k_{dom}", scen.name),
                      "peak_source": peak_kind,
                      "bytes_per_unit": SPEC_BYTES[dom], "units_per_launch": units[dom],
                      "avg_launch_ms": avg_ms[dom]},
@@ -498,7 +515,9 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-roads", type=int, default=1000)
-    ap.add_argument("--workload", default="city", choices=["city", "batched", "serving"])
+    ap.add_argument("--workload", default="city", choices=["city", "saturated", "batched", "serving"],
+                    help="city: the city from its own step-3600 state; saturated: the city network "
+                         "with all 2,464,950 trips on the road at once")
     ap.add_argument("--policy", default="fixed", choices=["fixed", "max_pressure"],
                     help="signal policy of every junction on the city workload")
     ap.add_argument("--lane-groups", action="store_true",

@@ -578,6 +578,63 @@ def city_scenario(seed: int = 0, n: int = 2_464_950, G: int = 100,
     return Scenario(net, veh, Params(seed=seed), f"city{G}x{G}_{n}" + ("_groups" if lane_groups else ""))
 
 
+def saturated_city(seed: int = 0, n: int = 2_464_950, G: int = 100, hops: int = 24,
+                   v0_sigma: float = 0.1, v0_clip=(0.7, 1.3)):
+    """The city network with all n trips on the road at once (a measurement
+    state, not a rollout): every road lane holds a share of the n vehicles in
+    proportion to its length (largest remainders), evenly spaced; that is
+    about 10 m per vehicle, the spacing at which n vehicles fit on the
+    network.  Each vehicle drives at the speed whose IDM safe distance
+    s0 + v T equals its gap (capped by its desired speed).  A trip's route
+    starts on the road it stands on and continues for `hops` roads by a
+    seeded random walk over the turns its junction lanes offer (ending early
+    at a road without one).  Returns (scenario, state) where state is
+    (status, lane, s, v, rc) for ``set_state`` at step 0."""
+    net = perturbed_grid_network(G, seed=seed)
+    prm = Params(seed=seed)
+    st = Stream(seed, 606)
+    NRL = net.n_road_lanes
+    L = net.lane_length[:NRL].astype(np.float64)
+    q = L / L.sum() * n
+    cnt = np.floor(q).astype(np.int64)
+    rest = n - int(cnt.sum())
+    cnt[np.argsort(-(q - cnt), kind="stable")[:rest]] += 1
+    lane = np.repeat(np.arange(NRL, dtype=np.int64), cnt)
+    rank = np.arange(n) - np.repeat(np.cumsum(cnt) - cnt, cnt)  # 0 = front of the lane
+    spacing = np.repeat(L / np.maximum(cnt, 1), cnt)
+    s = np.repeat(L, cnt) - (rank + 0.5) * spacing
+    v0f = np.clip(1.0 + v0_sigma * st.normal(n), v0_clip[0], v0_clip[1])
+    vmax = net.lane_vmax[:NRL].astype(np.float64)[lane]
+    v = np.clip((spacing - prm.veh_len - prm.s0) / prm.T, 0.0, v0f * vmax)
+    # turns per road: the roads that the junction lanes of its lanes feed
+    rl = net.lane_road()
+    src = np.repeat(rl[:NRL], np.diff(net.jl_off))
+    dst = rl[net.jl_target]
+    pairs = np.unique(np.stack([src, dst], axis=1), axis=0)
+    out_off = np.zeros(net.n_roads + 1, dtype=np.int64)
+    np.add.at(out_off, pairs[:, 0] + 1, 1)
+    out_off = np.cumsum(out_off)
+    out_road = pairs[:, 1]
+    road = rl[lane].astype(np.int64)
+    routes = np.full((n, hops + 1), -1, dtype=np.int64)
+    routes[:, 0] = road
+    alive = np.ones(n, dtype=bool)
+    cur = road.copy()
+    for h in range(1, hops + 1):
+        deg = out_off[cur + 1] - out_off[cur]
+        alive &= deg > 0
+        pick = (st.uniform(n) * np.maximum(deg, 1)).astype(np.int64)
+        nxt = out_road[np.minimum(out_off[cur] + pick, len(out_road) - 1)]
+        cur = np.where(alive, nxt, cur)
+        routes[:, h] = np.where(alive, cur, -1)
+    rlen = (routes >= 0).sum(axis=1)
+    route_off = np.concatenate([[0], np.cumsum(rlen)])
+    veh = Vehicles(n=n, route_off=_i32(route_off), routes=_i32(routes[routes >= 0]),
+                   start_lane=_i32(lane), dep=_i32(np.zeros(n)), v0f=_f32(v0f))
+    state = (np.ones(n, dtype=np.int32), _i32(lane), s, v, np.zeros(n, dtype=np.int32))
+    return Scenario(net, veh, prm, f"city{G}x{G}_saturated_{n}"), state
+
+
 def batched_scenarios(k: int = 64, seed: int = 0, n_lo: int = 2000, n_hi: int = 300_000,
                       dep_horizon: int = 1800, only=None) -> List[Scenario]:
     """k independent grid scenarios of uneven size: vehicles log-uniform in

@@ -290,6 +290,19 @@ def test_city_one_step_parity_fp32():
     assert n > 1_000_000 and excused <= n // 1000
 
 
+def test_saturated_city_one_step_parity_fp32():
+    """The state of the saturated measurement: all 2,464,950 trips of the
+    city on the road at once, evenly spaced.  One FP32 step on both sides
+    from the same (FP32-rounded) state, every vehicle compared."""
+    scen, (status, lane, s, v, rc) = sc.saturated_city()
+    st = _f32_state({"status": status, "lane": lane, "s": s, "v": v, "rc": rc})
+    sim, ora = _sim(scen, 32), _ora(scen)
+    _set_both(sim, ora, st, 0)
+    sim.step(1); ora.step(1)
+    n, excused = compare_one_step(sim.state(), ora.state())
+    assert n > 2_000_000 and excused <= n // 1000
+
+
 def test_ragged_batch_with_empty_member():
     """A batch of uneven members, one with no vehicles and no junctions, one
     with a single vehicle: every member equals its own run alone."""
