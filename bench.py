@@ -148,8 +148,8 @@ def cpu_oracle_rate(scen, state, budget_s=15.0, max_road=4000, steps_cap=60, max
     t_state."""
     import oracle
     from paper_2406_10661_gb300 import scenario as sc
-    sample = sc.region_sample(state, scen.net, max_road)
-    o = oracle.Oracle(scen.net, scen.veh, scen.params)
+    veh, sample = sc.region_band(state, scen.net, scen.veh, 0, max_road)
+    o = oracle.Oracle(scen.net, veh, scen.params)
     o.set_state(sample["status"], sample["lane"], sample["s"], sample["v"], sample["rc"], t_state)
     if max_pressure:
         o.set_signal(list(range(scen.net.n_junctions)), oracle.POLICY_MAX_PRESSURE)
@@ -169,6 +169,89 @@ def cpu_oracle_rate(scen, state, budget_s=15.0, max_road=4000, steps_cap=60, max
                       f"single thread, {dt:.1f} s"}
 
 
+class OracleBands:
+    """The FP64 oracle, as it stands, on n host cores at once: road ids
+    [0, road_hi) are cut into n contiguous bands, each band's vehicles of the
+    given state are stepped by their own oracle instance in their own thread
+    (the oracle is C behind ctypes, which releases the GIL during a step),
+    and the threads step in lockstep: one step() advances every band by one
+    step and returns its wall time (the slowest band's)."""
+
+    def __init__(self, scen, state, t_state, n=None, road_hi=None, max_pressure=False):
+        import threading
+        import oracle
+        from paper_2406_10661_gb300 import scenario as sc
+        self.n = n or os.cpu_count() or 1
+        hi = scen.net.n_roads if road_hi is None else min(road_hi, scen.net.n_roads)
+        bounds = np.linspace(0, hi, self.n + 1).astype(np.int64)
+        self.orcs = []
+        for k in range(self.n):
+            veh, smp = sc.region_band(state, scen.net, scen.veh, int(bounds[k]), int(bounds[k + 1]))
+            o = oracle.Oracle(scen.net, veh, scen.params)
+            o.set_state(smp["status"], smp["lane"], smp["s"], smp["v"], smp["rc"], t_state)
+            if max_pressure:
+                o.set_signal(list(range(scen.net.n_junctions)), oracle.POLICY_MAX_PRESSURE)
+            self.orcs.append(o)
+        self._go = threading.Barrier(self.n + 1)
+        self._done = threading.Barrier(self.n + 1)
+        self._stop = False
+        self._threads = [threading.Thread(target=self._work, args=(k,), daemon=True) for k in range(self.n)]
+        for t in self._threads:
+            t.start()
+
+    def _work(self, k):
+        while True:
+            self._go.wait()
+            if self._stop:
+                return
+            self.orcs[k].step(1)
+            self._done.wait()
+
+    def step(self) -> float:
+        t0 = time.perf_counter()
+        self._go.wait()
+        self._done.wait()
+        return time.perf_counter() - t0
+
+    def updates(self) -> float:
+        return sum(o.metrics()["vehicle_updates"] for o in self.orcs)
+
+    def active(self) -> int:
+        return int(sum(o.metrics()["n_active"] for o in self.orcs))
+
+    def close(self):
+        self._stop = True
+        self._go.wait()
+        for t in self._threads:
+            t.join()
+
+
+def cpu_oracle_all_cores(scen, state, budget_s=15.0, t_state=T_WARM, max_pressure=False, threads=None,
+                         steps_cap=200):
+    """The oracle on every host core (OracleBands over the whole state),
+    stepped for max(2 s, budget_s / cores) of wall time: about budget_s of
+    CPU work in all.  value = all updates / wall time."""
+    pool = OracleBands(scen, state, t_state, n=threads, max_pressure=max_pressure)
+    try:
+        pool.step()  # untimed warm-up
+        per_s = max(2.0, budget_s / pool.n)
+        u0 = pool.updates()
+        wall, steps = 0.0, 0
+        while steps < steps_cap and wall < per_s:
+            wall += pool.step()
+            steps += 1
+        upd = pool.updates() - u0
+    finally:
+        pool.close()
+    n = pool.n
+    return {"value": upd / wall, "unit": "vehicle-updates/s", "cores": n, "kind": "oracle",
+            "sample": f"FP64 oracle on all {n} host cores: the GPU's step-{t_state} state cut into {n} "
+                      f"bands of road ids, one oracle instance and thread per band, stepped together; "
+                      f"{steps} steps of the whole network ({upd / max(steps, 1):.0f} vehicles per step) "
+                      f"in {wall:.1f} s",
+            "per_core": upd / wall / n}
+
+
 def reduce_ranks(dist, dev_s: float, updates: float, device=None):
     """Replicas: the job's time is the slowest rank's, its work the sum of all
     ranks' vehicle updates.  Returns (max seconds, summed updates)."""
@@ -185,33 +268,34 @@ def run_reference(args):
     if rank != 0:
         return
     scen = city(args)
-    import oracle
     from paper_2406_10661_gb300 import scenario as sc
     # a synthetic state of the same workload at the same step (built from the
-    # inputs only; the reference arm runs none of the CUDA path)
+    # inputs only; the reference arm runs none of the CUDA path), stepped by
+    # the oracle on every host core (one band of road ids per core)
     warm = sc.warm_state(scen.net, scen.veh, T_WARM, spacing=9.0, seed=args.seed)
-    sample = sc.region_sample(warm, scen.net, args.ref_roads)
-    o = oracle.Oracle(scen.net, scen.veh, scen.params)
-    o.set_state(sample["status"], sample["lane"], sample["s"], sample["v"], sample["rc"], T_WARM)
-    o.step(args.warmup)
-    m0 = o.metrics()
-    t0 = time.perf_counter()
-    o.step(args.steps)
-    dt = time.perf_counter() - t0
-    m1 = o.metrics()
-    upd = m1["vehicle_updates"] - m0["vehicle_updates"]
+    pool = OracleBands(scen, warm, T_WARM, road_hi=args.ref_roads)
+    try:
+        for _ in range(args.warmup):
+            pool.step()
+        u0 = pool.updates()
+        dt = sum(pool.step() for _ in range(args.steps))
+        upd = pool.updates() - u0
+        act = pool.active()
+    finally:
+        pool.close()
     value = upd / dt
+    roads = scen.net.n_roads if args.ref_roads is None else min(args.ref_roads, scen.net.n_roads)
     line = {
         "impl": "reference", "metric": "vehicle-updates/s", "value": value, "unit": "vehicle-updates/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": scen.name, "roads": int(scen.net.n_roads), "vehicles": int(scen.veh.n),
-                   "start": f"synthetic state at step {T_WARM} (9 m spacing)", "sample_roads": args.ref_roads},
-        "cpu_baseline": {"value": value, "unit": "vehicle-updates/s", "cores": 1, "kind": "oracle",
-                         "sample": f"each step: the FP64 oracle over roads 0..{args.ref_roads - 1} of a "
-                                   f"synthetic step-{T_WARM} state ({int((sample['status'] == 1).sum())} "
-                                   f"active vehicles)"},
+                   "start": f"synthetic state at step {T_WARM} (9 m spacing)", "sample_roads": roads},
+        "cpu_baseline": {"value": value, "unit": "vehicle-updates/s", "cores": pool.n, "kind": "oracle",
+                         "sample": f"each step: the FP64 oracle over roads 0..{roads - 1} of a synthetic "
+                                   f"step-{T_WARM} state on {pool.n} host cores (one band of road ids and "
+                                   f"one oracle instance per core; {act} active vehicles after the run)"},
         "e2e": {"value": value, "unit": "vehicle-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -348,9 +432,14 @@ def run_ours(args):
         if dist:
             dist.destroy_process_group()
         return
-    cpu = None if world > 1 else cpu_oracle_rate(scen, state0, budget_s=args.cpu_budget,
-                                                 max_pressure=args.policy == "max_pressure",
-                                                 t_state=t_start)
+    cpu = None
+    if world == 1:
+        # the oracle on all host cores (bands of the same state), and on one
+        cpu = cpu_oracle_all_cores(scen, state0, budget_s=args.cpu_budget, t_state=t_start,
+                                   max_pressure=args.policy == "max_pressure")
+        cpu["single_thread"] = cpu_oracle_rate(scen, state0, budget_s=args.cpu_budget,
+                                               max_pressure=args.policy == "max_pressure",
+                                               t_state=t_start)
     n_total = int(scen.veh.n)
     line = {
         "metric": "vehicle-updates/s", "value": value, "unit": "vehicle-updates/s", "n_gpus": world,
@@ -514,7 +603,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--ref-roads", type=int, default=1000)
+    ap.add_argument("--ref-roads", type=int, default=None,
+                    help="reference arm: step only roads [0, REF_ROADS) (default: the whole network)")
     ap.add_argument("--workload", default="city", choices=["city", "saturated", "batched", "serving"],
                     help="city: the city from its own step-3600 state; saturated: the city network "
                          "with all 2,464,950 trips on the road at once")

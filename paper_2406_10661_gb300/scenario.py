@@ -768,16 +768,33 @@ def warm_state(net: Network, veh: Vehicles, t_warm: int, spacing: float = 20.0,
     return dict(status=status, lane=lane, s=s, v=v, rc=rc)
 
 
-def region_sample(state: dict, net: Network, max_road: int) -> dict:
-    """The vehicles of ``state`` on roads with id < max_road (a contiguous band
-    of the grid); every other non-waiting vehicle is marked finished.  Used to
-    time the slow CPU oracle on a bounded slice of a city-scale state with
-    the same density."""
-    out = {k: np.array(x, copy=True) for k, x in state.items()}
+def vehicle_subset(veh: Vehicles, idx: np.ndarray) -> Vehicles:
+    """The trips idx (sorted) of ``veh`` as a trip set of their own (new ids
+    0..len(idx)-1 in the same order)."""
+    idx = np.asarray(idx, dtype=np.int64)
+    lens = np.diff(veh.route_off).astype(np.int64)[idx]
+    off = np.concatenate([[0], np.cumsum(lens)])
+    pos = np.repeat(veh.route_off[idx].astype(np.int64) - off[:-1], lens) + np.arange(off[-1])
+    return Vehicles(n=len(idx), route_off=_i32(off), routes=_i32(veh.routes[pos]),
+                    start_lane=_i32(veh.start_lane[idx]), dep=_i32(veh.dep[idx]), v0f=_f32(veh.v0f[idx]))
+
+
+def region_band(state: dict, net: Network, veh: Vehicles, lo: int, hi: int):
+    """The part of ``state`` that belongs to roads [lo, hi): the vehicles
+    active on a lane of such a road (on a junction lane: of the road it
+    leads to) and the waiting ones whose start lane is on one, as a trip set
+    of their own with its state (so that a simulator holding only this band
+    does work in proportion to it).  Bands that partition the road ids
+    partition the active and waiting vehicles.  Returns (vehicles, state)."""
     lr = net.lane_road()
-    act = out["status"] == 1
-    keep = act & (lr[np.maximum(out["lane"], 0)] < max_road) & (out["lane"] < net.n_road_lanes)
-    drop = act & ~keep
-    out["status"][drop] = 2
-    out["lane"][drop] = -1
-    return out
+    lr[net.n_road_lanes:] = lr[net.jl_target]
+    st, ln = state["status"], state["lane"]
+    road = lr[np.maximum(ln, 0)]
+    keep_a = (st == 1) & (road >= lo) & (road < hi)
+    sroad = lr[veh.start_lane]
+    keep_w = (st == 0) & (sroad >= lo) & (sroad < hi)
+    idx = np.nonzero(keep_a | keep_w)[0]
+    sub = {k: np.array(x)[idx].copy() for k, x in state.items()}
+    return vehicle_subset(veh, idx), sub
+
+

@@ -62,3 +62,47 @@ def test_oracle_steps_from_saturated_state():
     # (vehicles that reach the same road lane from two junction lanes in one
     # step may overlap: the model has no merge rule, the overlap metric counts
     # them, so no gap bound is asserted here)
+
+
+def test_region_bands_partition_the_state():
+    """Bands of road ids partition the active and waiting vehicles; each band
+    is a trip set of its own with the same routes, start lanes and state."""
+    scen = sc.small_scenario()
+    o = oracle.Oracle(scen.net, scen.veh, scen.params)
+    o.step(150)
+    st = o.state()
+    st = {k: st[k] for k in ("status", "lane", "s", "v", "rc")}
+    net, veh = scen.net, scen.veh
+    bounds = [0, 10, 25, 48]
+    seen = []
+    for lo, hi in zip(bounds[:-1], bounds[1:]):
+        sub_veh, sub = sc.region_band(st, net, veh, lo, hi)
+        sub_veh.validate(net)
+        assert sub_veh.n == len(sub["status"])
+        assert set(np.unique(sub["status"]).tolist()) <= {0, 1}
+        # the band's trips, in id order, with their own routes
+        keep = []
+        lane_road = net.lane_road()
+        for i in range(veh.n):
+            ln = st["lane"][i]
+            if st["status"][i] == 1 and ln < net.n_road_lanes:
+                road = lane_road[ln]
+            elif st["status"][i] == 1:  # junction lane: the road it leads to
+                road = lane_road[net.jl_target[ln - net.n_road_lanes]]
+            elif st["status"][i] == 0:
+                road = net.lane_road()[veh.start_lane[i]]
+            else:
+                continue
+            if lo <= road < hi:
+                keep.append(i)
+        assert len(keep) == sub_veh.n
+        for j, i in enumerate(keep):
+            assert np.array_equal(sub_veh.routes[sub_veh.route_off[j]:sub_veh.route_off[j + 1]],
+                                  veh.routes[veh.route_off[i]:veh.route_off[i + 1]])
+            assert sub_veh.start_lane[j] == veh.start_lane[i] and sub_veh.dep[j] == veh.dep[i]
+            for k in st:
+                assert sub[k][j] == st[k][i]
+        seen += keep
+    live = np.nonzero(st["status"] <= 1)[0]
+    assert sorted(seen) == live.tolist()
+    assert ((st["status"] == 1) & (st["lane"] >= net.n_road_lanes)).any()  # junction lanes covered
