@@ -432,6 +432,7 @@ def run_ours(args):
         if dist:
             dist.destroy_process_group()
         return
+    wname = scen.name + ("_maxpressure" if args.policy == "max_pressure" else "")
     cpu = None
     if world == 1:
         # the oracle on all host cores (bands of the same state), and on one
@@ -446,7 +447,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": scen.name, "roads": int(scen.net.n_roads), "lanes": n_lanes,
+        "config": {"workload": wname, "roads": int(scen.net.n_roads), "lanes": n_lanes,
                    "vehicles": n_total, "dt_s": 1.0,
                    "start": start_desc,
                    "active_per_step": upd / args.steps,
@@ -458,7 +459,7 @@ def run_ours(args):
         "paper_context": {"step_hz": 84.09, "vehicles": 2464950, "hardware": "RTX 4090 + Xeon 8462Y",
                           "note": "different network (CBLab Roadnet-L); context only"},
         "roofline": {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": captured_traffic(f"k_{dom}", scen.name),
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": captured_traffic(f"k_{dom}", wname),
                      "peak_source": peak_kind,
                      "bytes_per_unit": SPEC_BYTES[dom], "units_per_launch": units[dom],
                      "avg_launch_ms": avg_ms[dom]},
