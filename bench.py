@@ -195,22 +195,35 @@ class OracleBands:
         self._go = threading.Barrier(self.n + 1)
         self._done = threading.Barrier(self.n + 1)
         self._stop = False
+        self._error = None
         self._threads = [threading.Thread(target=self._work, args=(k,), daemon=True) for k in range(self.n)]
         for t in self._threads:
             t.start()
 
     def _work(self, k):
-        while True:
-            self._go.wait()
-            if self._stop:
-                return
-            self.orcs[k].step(1)
-            self._done.wait()
+        import threading
+        try:
+            while True:
+                self._go.wait()
+                if self._stop:
+                    return
+                self.orcs[k].step(1)
+                self._done.wait()
+        except threading.BrokenBarrierError:
+            return
+        except Exception as e:  # an oracle error ends the run instead of stalling it
+            self._error = e
+            self._go.abort()
+            self._done.abort()
 
     def step(self) -> float:
+        import threading
         t0 = time.perf_counter()
-        self._go.wait()
-        self._done.wait()
+        try:
+            self._go.wait()
+            self._done.wait()
+        except threading.BrokenBarrierError:
+            raise RuntimeError(f"oracle band failed: {self._error!r}")
         return time.perf_counter() - t0
 
     def updates(self) -> float:
@@ -220,8 +233,12 @@ class OracleBands:
         return int(sum(o.metrics()["n_active"] for o in self.orcs))
 
     def close(self):
+        import threading
         self._stop = True
-        self._go.wait()
+        try:
+            self._go.wait()
+        except threading.BrokenBarrierError:
+            pass
         for t in self._threads:
             t.join()
 

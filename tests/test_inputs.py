@@ -106,3 +106,39 @@ def test_region_bands_partition_the_state():
     live = np.nonzero(st["status"] <= 1)[0]
     assert sorted(seen) == live.tolist()
     assert ((st["status"] == 1) & (st["lane"] >= net.n_road_lanes)).any()  # junction lanes covered
+
+
+def test_oracle_bands_lockstep_equals_serial():
+    """The all-cores CPU baseline: bands stepped together in threads give the
+    same vehicle updates as the same band oracles stepped one after another;
+    a band that fails ends the run with an error instead of stalling it."""
+    import pytest
+    bench = pytest.importorskip("bench")
+    scen, (status, lane, s, v, rc) = _small()
+    state = {"status": status, "lane": lane, "s": s, "v": v, "rc": rc}
+    pool = bench.OracleBands(scen, state, 0, n=3)
+    try:
+        for _ in range(4):
+            pool.step()
+        par = [o.metrics() for o in pool.orcs]
+    finally:
+        pool.close()
+    bounds = np.linspace(0, scen.net.n_roads, 4).astype(np.int64)
+    for k in range(3):
+        veh, smp = sc.region_band(state, scen.net, scen.veh, int(bounds[k]), int(bounds[k + 1]))
+        o = oracle.Oracle(scen.net, veh, scen.params)
+        o.set_state(smp["status"], smp["lane"], smp["s"], smp["v"], smp["rc"], 0)
+        o.step(4)
+        m = o.metrics()
+        assert m["vehicle_updates"] == par[k]["vehicle_updates"] and m["n_active"] == par[k]["n_active"]
+    assert sum(m["vehicle_updates"] for m in par) == 4 * scen.veh.n
+
+    pool = bench.OracleBands(scen, state, 0, n=2)
+
+    def planted(n):
+        raise ValueError("planted")
+
+    pool.orcs[1].step = planted
+    with pytest.raises(RuntimeError, match="planted"):
+        pool.step()
+    pool.close()
