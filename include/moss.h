@@ -12,10 +12,14 @@
  *   - IDM car following (App. B.3, equations (1)-(2), delta = 4), randomized
  *     MOBIL lane changing (App. B.3) with deterministic conflict resolution;
  *   - red/amber stop before the next lane's signal (App. B.3), fixed-time,
- *     manual and no-signal policies (§3.2, "Traffic Signal");
+ *     manual, no-signal and max-pressure policies (§3.2, "Traffic Signal");
+ *   - lane groups with mandatory lane changes and road lane plans (App. B.3;
+ *     §3.2, "Road"), lane speed limits and restrictions (§3.2, "Lane"),
+ *     vehicle re-routing (§3.2, "Vehicle");
  *   - transfer across junctions, departure insertion and arrival handling
  *     (App. B.2, prepare/update streams);
- *   - throughput, average travelling time and network speed (§3.3).
+ *   - throughput, average travelling time, network speed, lane queue length
+ *     and road speed (§3.3).
  *
  * Units: metres, seconds, m/s.  One step advances dt seconds.  Vehicle state
  * is kept in FP32 (precision 32) or FP64 (precision 64, used to compare
