@@ -419,8 +419,12 @@ def run_ours(args):
         offs = scen.net.junc_offset.astype(np.int64)
         e2e_steps = args.steps
         t_first = t_start + args.warmup + args.steps + ksteps
-        phases = torch.empty((e2e_steps, J), dtype=torch.int32).pin_memory().numpy()
-        phases[:] = ((t_first + np.arange(e2e_steps)[:, None] + offs[None, :]) % 132) // 33
+        phases = torch.empty((2 * e2e_steps, J), dtype=torch.int32).pin_memory().numpy()
+        phases[:] = ((t_first + np.arange(2 * e2e_steps)[:, None] + offs[None, :]) % 132) // 33
+        # pipelined loop (the headline): step k+1's actions and launch are
+        # enqueued before step k's metrics are read (moss_metrics_enqueue /
+        # moss_metrics_read), so the host work of a step overlaps the previous
+        # step on the GPU; every step's actions go in and its metrics come out
         me0 = sim.metrics()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -428,9 +432,21 @@ def run_ours(args):
             if not mp:
                 sim.set_signal_phase(jids, phases[k])
             sim.step(1)
-            mk = sim.metrics()
+            sim.metrics_enqueue(k % 2)
+            if k > 0:
+                mk = sim.metrics_read((k - 1) % 2)
+        mk = sim.metrics_read((e2e_steps - 1) % 2)
         e2e_s = time.perf_counter() - t0
         e2e_upd = mk["vehicle_updates"] - me0["vehicle_updates"]
+        # the same loop with a synchronous read after every step
+        ms0 = sim.metrics()
+        t0 = time.perf_counter()
+        for k in range(e2e_steps):
+            if not mp:
+                sim.set_signal_phase(jids, phases[e2e_steps + k])
+            sim.step(1)
+            msk = sim.metrics()
+        e2e_sync = (msk["vehicle_updates"] - ms0["vehicle_updates"]) / (time.perf_counter() - t0)
         # the lane / road metric calls of the public API on the same state
         # (kernel + device-to-host copy of the per-lane / per-road arrays)
         metric_ms = {}
@@ -486,8 +502,11 @@ def run_ours(args):
         "e2e": {"value": e2e_val, "unit": "vehicle-updates/s", "h2d_bytes_per_step": 0 if mp else 8 * J,
                 "d2h_bytes_per_step": 12 * 8 + 8 + 4,  # metric fields, step counter, error word
                 "steps": e2e_steps,
-                "api": ("moss_step(1) + moss_get_metrics per step" if mp else
-                        "moss_set_signal_phase + moss_step(1) + moss_get_metrics per step")},
+                "api": ("" if mp else "moss_set_signal_phase + ") + "moss_step(1) + moss_metrics_enqueue per "
+                       "step, step k's metrics read (moss_metrics_read) after step k+1 is enqueued",
+                "sync_value": e2e_sync,
+                "sync_api": ("" if mp else "moss_set_signal_phase + ") + "moss_step(1) + moss_get_metrics "
+                            "(waits for the step) per step"},
         "gpu_launches": 4 * args.steps,
         "metric_calls_ms": metric_ms,
         "wall_s_timed_region": wall,

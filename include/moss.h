@@ -276,6 +276,22 @@ int moss_get_signal_state(moss_t h, int n, const int32_t* junction_ids, int32_t*
 /* Wait for the handle's stream and copy the cumulative metrics. */
 int moss_get_metrics(moss_t h, MossMetrics* out);
 
+/*
+ * Metrics without waiting for the stream (§3.3 metrics, read while the next
+ * steps run): moss_metrics_enqueue copies the cumulative metrics of
+ * `scenario` (0 for a single-scenario handle) as they are after all work
+ * enqueued so far into readback slot `slot` (0 <= slot < MOSS_METRIC_SLOTS,
+ * pinned host memory owned by the handle) and returns at once;
+ * moss_metrics_read waits for that copy only and converts it, so a caller
+ * can enqueue step k + 1 before reading step k.  Enqueuing into a slot whose
+ * copy was not read yet first waits for that copy.  MOSS_EINVAL for a slot
+ * out of range or read without an enqueue; device errors raised by the work
+ * before the copy are reported by the read.
+ */
+#define MOSS_METRIC_SLOTS 4
+int moss_metrics_enqueue(moss_t h, int scenario, int slot);
+int moss_metrics_read(moss_t h, int slot, MossMetrics* out);
+
 /* Wait for the handle's stream and copy the per-vehicle state (by id). */
 int moss_get_state(moss_t h, MossState* out);
 

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libmoss.so")
 
 MOSS_OK, MOSS_EINVAL, MOSS_ENOMEM, MOSS_ECUDA, MOSS_ETIMEOUT, MOSS_EBUDGET, MOSS_EDEVICE = range(7)
 POLICY_FIXED_TIME, POLICY_MANUAL, POLICY_NONE, POLICY_MAX_PRESSURE = 0, 1, 2, 3
+METRIC_SLOTS = 4  # readback slots of metrics_enqueue / metrics_read
 F_FLAGGED, F_CHANGED, F_CANDIDATE, F_TRANSFER, F_ARRIVED, F_INSERTED, F_CONFLICT_LOST = (
     1, 2, 4, 8, 16, 32, 64)
 
@@ -95,6 +96,8 @@ SIGNATURES = {
                                          _vp, ctypes.POINTER(_vp)]),
     "moss_batch_size": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "moss_batch_get_metrics": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(MossMetrics)]),
+    "moss_metrics_enqueue": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "moss_metrics_read": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(MossMetrics)]),
     "moss_batch_get_state": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(MossState)]),
     "moss_batch_set_signal_phase": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _c_i32p,
                                                    _c_i32p]),
@@ -226,6 +229,17 @@ class _Handle:
         out = np.zeros(3, dtype=np.int32)
         _check(self.lib.moss_autotune(self.h, int(trial_steps), _ptr(out, ctypes.c_int32)), self.h)
         return dict(zip(("decide", "lanescan", "place"), out.tolist()))
+
+    def metrics_enqueue(self, slot: int, scenario: int = 0) -> None:
+        """Queue a copy of the metrics (as after the work enqueued so far) into
+        a readback slot without waiting."""
+        _check(self.lib.moss_metrics_enqueue(self.h, int(scenario), int(slot)), self.h)
+
+    def metrics_read(self, slot: int) -> Dict[str, float]:
+        """Wait for the copy in a readback slot and return those metrics."""
+        m = MossMetrics()
+        _check(self.lib.moss_metrics_read(self.h, int(slot), ctypes.byref(m)), self.h)
+        return m.as_dict()
 
     def kernel_times(self):
         ms = np.zeros(4, dtype=np.float64)

@@ -17,6 +17,8 @@
 
 using namespace moss;
 
+constexpr int RB_WORDS = M_NFIELDS + 2;  // readback slot: metric record, step, error word
+
 namespace {
 
 struct SnapBufs {
@@ -95,7 +97,13 @@ struct MossHandle {
     int32_t* d_stage = nullptr;          // setter staging (2 * n_junctions)
     int32_t* h_stage = nullptr;          // pinned host staging of setter arguments (2 * n_junctions)
     cudaEvent_t stage_free = nullptr;    // recorded after the last copy out of h_stage
-    long long* h_rb = nullptr;           // pinned readback: a metric record, its step, the error word
+    // pinned readback: per slot a metric record, its step and the error word;
+    // slots [0, MOSS_METRIC_SLOTS) serve moss_metrics_enqueue/read, the last
+    // one moss_get_metrics
+    long long* h_rb = nullptr;
+    cudaEvent_t rb_ev[MOSS_METRIC_SLOTS] = {};
+    int rb_scen[MOSS_METRIC_SLOTS] = {};
+    bool rb_pending[MOSS_METRIC_SLOTS] = {};
 
     // launch configuration (blocks per SM) of the step kernels; moss_autotune picks them
     int cfg_decide = MOSS_DECIDE_MIN_BLOCKS, cfg_lanescan = 4, cfg_place = 8;
@@ -655,7 +663,10 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
     TRY(upload(h, &h->d_cnt, c0));
     TRY(dalloc(h, &h->d_stage, 2 * std::max(NJ, 1)));
     CK(cudaHostAlloc((void**)&h->h_stage, sizeof(int32_t) * 2 * std::max(NJ, 1), cudaHostAllocDefault));
-    CK(cudaHostAlloc((void**)&h->h_rb, sizeof(long long) * (M_NFIELDS + 2), cudaHostAllocDefault));
+    CK(cudaHostAlloc((void**)&h->h_rb, sizeof(long long) * RB_WORDS * (MOSS_METRIC_SLOTS + 1),
+                     cudaHostAllocDefault));
+    for (int k = 0; k < MOSS_METRIC_SLOTS; ++k)
+        CK(cudaEventCreateWithFlags(&h->rb_ev[k], cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&h->stage_free, cudaEventDisableTiming));
     CK(cudaEventRecord(h->stage_free, h->stream));
     for (int k = 0; k <= N_STEP_KERNELS; ++k) CK(cudaEventCreate(&h->ev[k]));
@@ -677,21 +688,26 @@ void free_all(MossHandle* h) {
     h->h_stage = nullptr;
     if (h->h_rb) cudaFreeHost(h->h_rb);
     h->h_rb = nullptr;
+    for (int k = 0; k < MOSS_METRIC_SLOTS; ++k)
+        if (h->rb_ev[k]) cudaEventDestroy(h->rb_ev[k]);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     h->stream = nullptr;
 }
 
-int scen_metrics(MossHandle* h, int s, MossMetrics* out) {
-    if (!out) return fail(h, MOSS_EINVAL, "null output");
-    if (s < 0 || s >= h->n_scen) return fail(h, MOSS_EINVAL, "scenario index out of range");
-    // one stream round trip: the record, the step and the error word are
-    // copied behind the queued work into pinned memory, then one wait
-    long long* M = h->h_rb;
+// copies of scenario s's metric record, its step and the device error word,
+// behind the work queued so far, into readback slot `slot`
+int enqueue_readback(MossHandle* h, int s, int slot) {
+    long long* M = h->h_rb + (size_t)slot * RB_WORDS;
     CK(cudaMemcpyAsync(M, h->d_metrics + (size_t)s * M_NFIELDS, M_NFIELDS * sizeof(long long),
                        cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(M + M_NFIELDS, h->d_step + s, sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(M + M_NFIELDS + 1, &h->d_cnt->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
+    return MOSS_OK;
+}
+
+// the metrics of scenario s from a completed readback slot
+int readback_metrics(MossHandle* h, int s, int slot, MossMetrics* out) {
+    const long long* M = h->h_rb + (size_t)slot * RB_WORDS;
     const long long step = M[M_NFIELDS];
     int err = 0;
     std::memcpy(&err, M + M_NFIELDS + 1, sizeof(int));
@@ -710,6 +726,15 @@ int scen_metrics(MossHandle* h, int s, MossMetrics* out) {
     out->errors = M[M_ERRORS];
     out->mobil_evals = M[M_MOBIL];
     return device_status(h, err);
+}
+
+int scen_metrics(MossHandle* h, int s, MossMetrics* out) {
+    if (!out) return fail(h, MOSS_EINVAL, "null output");
+    if (s < 0 || s >= h->n_scen) return fail(h, MOSS_EINVAL, "scenario index out of range");
+    // one stream round trip: the copies go behind the queued work, one wait
+    TRY(enqueue_readback(h, s, MOSS_METRIC_SLOTS));
+    CK(cudaStreamSynchronize(h->stream));
+    return readback_metrics(h, s, MOSS_METRIC_SLOTS, out);
 }
 
 template <typename Real>
@@ -1229,6 +1254,29 @@ int moss_get_metrics(moss_t h, MossMetrics* out) {
 int moss_batch_get_metrics(moss_t h, int scenario, MossMetrics* out) {
     if (!h) return MOSS_EINVAL;
     return scen_metrics(h, scenario, out);
+}
+
+int moss_metrics_enqueue(moss_t h, int scenario, int slot) {
+    if (!h) return MOSS_EINVAL;
+    if (scenario < 0 || scenario >= h->n_scen) return fail(h, MOSS_EINVAL, "scenario index out of range");
+    if (slot < 0 || slot >= MOSS_METRIC_SLOTS) return fail(h, MOSS_EINVAL, "metric slot out of range");
+    // a slot still in flight is waited for before its memory is reused
+    if (h->rb_pending[slot]) CK(cudaEventSynchronize(h->rb_ev[slot]));
+    TRY(enqueue_readback(h, scenario, slot));
+    CK(cudaEventRecord(h->rb_ev[slot], h->stream));
+    h->rb_pending[slot] = true;
+    h->rb_scen[slot] = scenario;
+    return MOSS_OK;
+}
+
+int moss_metrics_read(moss_t h, int slot, MossMetrics* out) {
+    if (!h) return MOSS_EINVAL;
+    if (!out) return fail(h, MOSS_EINVAL, "null output");
+    if (slot < 0 || slot >= MOSS_METRIC_SLOTS) return fail(h, MOSS_EINVAL, "metric slot out of range");
+    if (!h->rb_pending[slot]) return fail(h, MOSS_EINVAL, "nothing enqueued in this metric slot");
+    CK(cudaEventSynchronize(h->rb_ev[slot]));
+    h->rb_pending[slot] = false;
+    return readback_metrics(h, h->rb_scen[slot], slot, out);
 }
 
 int moss_get_state(moss_t h, MossState* out) {
