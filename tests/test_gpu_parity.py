@@ -162,6 +162,23 @@ def test_fp32_rollout_aggregates_small():
     assert gm["errors"] == 0
 
 
+@pytest.mark.slow
+def test_fp32_rollout_aggregates_medium():
+    """30x30 grid of three-lane roads, 100,000 trips: the full FP32 rollout of
+    3,600 steps against the FP64 oracle's (about two minutes of oracle time);
+    network speed and completions within 0.5%."""
+    scen = sc.medium_scenario()
+    sim, ora = _sim(scen, 32), _ora(scen)
+    sim.step(3600); ora.step(3600)
+    gm, rm = sim.metrics(), ora.metrics()
+    gs = gm["speed_sum"] / gm["vehicle_updates"]
+    rs = rm["speed_sum"] / rm["vehicle_updates"]
+    assert abs(gs - rs) <= 0.005 * rs, (gs, rs)
+    assert rm["n_arrived"] > 1000
+    assert abs(gm["n_arrived"] - rm["n_arrived"]) <= 0.005 * rm["n_arrived"], (gm, rm)
+    assert gm["errors"] == 0
+
+
 # ---------------------------------------------------------------------------
 # hand-built states
 def _one_step_hand(scen, st, step, precision):
