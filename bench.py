@@ -552,12 +552,22 @@ def run_batched(args):
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        e0.record(stream)
-        batch.step(args.steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
+        with Clocks(local) as clk:
+            e0.record(stream)
+            batch.step(args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
         b_ms = e0.elapsed_time(e1)
         u1 = sum(batch.metrics(i)["vehicle_updates"] for i in range(len(scens)))
+        # per-step latency of the batch: K further steps, events around each
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for a, b in evs:
+            a.record(stream)
+            batch.step(1)
+            b.record(stream)
+        torch.cuda.synchronize()
+        lat = np.array([a.elapsed_time(b) for a, b in evs])
         batch.close()
         b_s, b_upd = b_ms / 1e3, float(u1 - u0)
         if dist:
@@ -585,6 +595,10 @@ def run_batched(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * b_s / args.steps,
             "higher_is_better": True, "scaling": "strong", "dtype": "f32",
             "data": "synthetic",
+            "step_hz": args.steps / b_s,
+            "p50_step_ms": float(np.percentile(lat, 50)), "p99_step_ms": float(np.percentile(lat, 99)),
+            "latency_how": f"{args.steps} further steps of the whole batch, CUDA events around each",
+            "clocks": clk.summary(),
             "config": {"workload": f"batched{args.scenarios}", "scenarios": args.scenarios,
                        "scenarios_rank0": len(scens),
                        "vehicles_rank0": int(sum(x.veh.n for x in scens)),
