@@ -35,7 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 T_WARM = 3600   # the timed steps start at this step
-SPEC_BYTES = {  # algorithmic bytes per unit, FP32 state
+SPEC_BYTES = {  # algorithmic bytes per unit with FP32 state (32 B snapshot record per vehicle)
     "decide": 41.0,    # per active vehicle: read its 32 B record, write code + s' + v' (9 B)
     "lanescan": 20.0,  # per lane: read 2 offsets + leave + enter, write offset + leavers-before
     "place": 73.0,     # per active vehicle: read code, s', v' and the 32 B record, write 32 B
