@@ -76,7 +76,7 @@ class _Active:
         self.bytes = bytes_      # admission accounting (the estimate, or more if larger)
         self.actual = actual     # bytes the handle holds
         self.step = 0
-        self.pending: List = []  # (start event, end event)
+        self.pending: List = []  # (start event, end event, steps in between)
 
 
 class Server:
@@ -116,28 +116,33 @@ class Server:
         self.peak_bytes = max(self.peak_bytes, self.actual_in_use)
 
     def _launch_step(self, a: _Active) -> None:
+        """The request's actions (at an action step) and then its steps up to
+        the next action step or its horizon, as one launch on its stream."""
         import torch
         req = a.req
         if a.step % self.action_every == 0:
             nj = int(req.scenario.net.n_junctions)
             if nj:
                 a.sim.set_signal_phase(np.arange(nj, dtype=np.int32), actions_for(req, a.step, nj))
+        k = min(self.action_every - a.step % self.action_every, req.horizon - a.step)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(a.stream)
-        a.sim.step(1)
+        a.sim.step(k)
         e1.record(a.stream)
-        a.pending.append((e0, e1))
-        a.step += 1
+        a.pending.append((e0, e1, k))
+        a.step += k
 
     def _collect(self, a: _Active, block: bool) -> None:
+        """Per-step latency of finished launches: the launch's GPU time over
+        its steps (one entry per step)."""
         keep = []
-        for e0, e1 in a.pending:
+        for e0, e1, k in a.pending:
             if block or e1.query():
                 e1.synchronize()
-                a.req.step_ms.append(e0.elapsed_time(e1))
+                a.req.step_ms.extend([e0.elapsed_time(e1) / k] * k)
             else:
-                keep.append((e0, e1))
+                keep.append((e0, e1, k))
         a.pending = keep
 
     def _retire(self, a: _Active, now: float) -> None:
