@@ -137,6 +137,29 @@ def test_medium_one_step_parity_every_vehicle_attempts_fp32():
     assert sim.metrics()["mobil_evals"] > 0
 
 
+def test_fp64_rollout_matches_oracle_medium():
+    """30x30 grid of three-lane roads, 100,000 trips: 600 FP64 steps on both
+    sides (up to tens of thousands of vehicles, a third of them evaluating
+    MOBIL each step); identical discrete state and flags every 100 steps,
+    positions and speeds within 1e-6."""
+    scen = sc.medium_scenario()
+    sim, ora = _sim(scen, 64), _ora(scen)
+    for chunk in range(6):
+        sim.step(100); ora.step(100)
+        g, r = sim.state(), ora.state()
+        assert np.array_equal(g["status"], r["status"])
+        act = r["status"] == 1
+        assert np.array_equal(g["lane"][act], r["lane"][act])
+        assert np.array_equal(g["rc"][act], r["rc"][act])
+        assert np.abs(g["s"][act] - r["s"][act]).max(initial=0) < 1e-6
+        assert np.abs(g["v"][act] - r["v"][act]).max(initial=0) < 1e-6
+        assert np.array_equal(g["flags"], r["flags"])
+    assert act.sum() > 20_000
+    gm, rm = sim.metrics(), ora.metrics()
+    for k in ("n_active", "n_arrived", "vehicle_updates", "lane_changes", "flagged", "mobil_evals"):
+        assert gm[k] == rm[k], (k, gm[k], rm[k])
+
+
 @pytest.mark.parametrize("t0", [60, 150, 300, 450, 599])
 def test_fp32_one_step_parity_small(t0):
     scen = sc.small_scenario()
