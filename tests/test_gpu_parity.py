@@ -330,6 +330,29 @@ def test_city_one_step_parity_fp32():
     assert n > 1_000_000 and excused <= n // 1000
 
 
+def test_city_fp64_steps_identical_to_oracle():
+    """Full size in FP64: the city simulated on the GPU to step 3600 (about two
+    million vehicles), then three steps on both sides from that state; every
+    vehicle's discrete state and flags identical, positions and speeds within
+    1e-6."""
+    scen = sc.city_scenario()
+    sim = _sim(scen, 64)
+    sim.step(3600)
+    st = sim.state()
+    assert (st["status"] == 1).sum() > 1_000_000
+    ora = _ora(scen)
+    ora.set_state(st["status"], st["lane"], st["s"], st["v"], st["rc"], 3600)
+    sim.step(3); ora.step(3)
+    g, r = sim.state(), ora.state()
+    assert np.array_equal(g["status"], r["status"])
+    act = r["status"] == 1
+    assert np.array_equal(g["lane"][act], r["lane"][act])
+    assert np.array_equal(g["rc"][act], r["rc"][act])
+    assert np.abs(g["s"][act] - r["s"][act]).max(initial=0) < 1e-6
+    assert np.abs(g["v"][act] - r["v"][act]).max(initial=0) < 1e-6
+    assert np.array_equal(g["flags"], r["flags"])
+
+
 def test_saturated_city_one_step_parity_fp32():
     """The state of the saturated measurement: all 2,464,950 trips of the
     city on the road at once, evenly spaced.  One FP32 step on both sides
