@@ -49,11 +49,17 @@ KERNEL_SOURCES = [os.path.join(ROOT, "paper_2406_10661_gb300", "csrc", f)
 
 
 def kernel_source_hash() -> str:
+    """SHA-256 of the kernel sources without their comments and blank space
+    (an edit of a comment does not invalidate a capture; any code change does)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()
 
 

@@ -12,12 +12,17 @@
 // search in the adjacent lane's segment (adjacent lanes of a road are
 // adjacent in memory).
 //
-// One step = three kernels:
-//   k_decide    per vehicle: sensing, IDM (App. B.3 eqs. (1)-(2)), randomized
-//               MOBIL (App. B.3) with deterministic conflict resolution,
-//               ballistic integration with clamps, transfer at lane ends and
-//               arrival (App. B.2 update stream 1); extra blocks run the
+// One step = four kernels:
+//   k_decide    per vehicle: sensing, IDM (App. B.3 eqs. (1)-(2)), the
+//               randomized MOBIL decision (App. B.3; run from a per-warp
+//               shared-memory queue of the vehicles whose attempt draw
+//               passed), ballistic integration with clamps, transfer at lane
+//               ends and arrival (App. B.2 update stream 1); lane-change
+//               candidates are listed for k_resolve; extra blocks run the
 //               departure insertion (App. B.2 update stream 3);
+//   k_resolve   deterministic conflict resolution between candidates entering
+//               the same gap from both sides, and their update; max-pressure
+//               phase sums (§3.2);
 //   k_lanescan  per-lane sizes of the next snapshot -> offsets (single-pass
 //               decoupled look-back scan), prefix of leavers per slot tile,
 //               signal states of the next step (§3.2 policies);
