@@ -202,6 +202,39 @@ def test_fp32_rollout_aggregates_medium():
     assert gm["errors"] == 0
 
 
+def test_fp32_rollout_invariants_medium():
+    """Invariants of the GPU state itself along an FP32 rollout of the 30x30
+    grid (checked every 100 steps): conservation of trips, 0 <= s <= L and
+    v >= 0 for active vehicles, a vehicle on a road lane sits on the road its
+    route cursor names (on a junction lane: the junction lane leads to the
+    next road of the route), no device error."""
+    scen = sc.medium_scenario()
+    net, veh = scen.net, scen.veh
+    sim = _sim(scen, 32)
+    L = net.lane_length.astype(np.float64)
+    lane_road = net.lane_road()
+    target_road = lane_road[net.jl_target]
+    n_active_seen = 0
+    for _ in range(9):
+        sim.step(100)
+        st, m = sim.state(), sim.metrics()
+        assert m["errors"] == 0
+        assert m["n_active"] + m["n_waiting"] + m["n_arrived"] == veh.n
+        act = st["status"] == 1
+        assert int(act.sum()) == m["n_active"] and int((st["status"] == 2).sum()) == m["n_arrived"]
+        n_active_seen = max(n_active_seen, int(act.sum()))
+        ln, s_, v_, rc = st["lane"][act], st["s"][act], st["v"][act], st["rc"][act]
+        assert (s_ >= 0).all() and (s_ <= L[ln] + 1e-3).all() and (v_ >= 0).all()
+        ids = np.nonzero(act)[0]
+        cur_road = veh.routes[veh.route_off[ids] + rc]
+        on_road = ln < net.n_road_lanes
+        assert (lane_road[ln[on_road]] == cur_road[on_road]).all()
+        jl = ~on_road
+        nxt = veh.routes[np.minimum(veh.route_off[ids[jl]] + rc[jl] + 1, veh.route_off[ids[jl] + 1] - 1)]
+        assert (target_road[ln[jl] - net.n_road_lanes] == nxt).all()
+    assert n_active_seen > 20_000
+
+
 # ---------------------------------------------------------------------------
 # hand-built states
 def _one_step_hand(scen, st, step, precision):
