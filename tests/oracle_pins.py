@@ -744,6 +744,186 @@ def check_lane_plan_switch(libpath=None):
     assert o.state()["lane"][0] == lanes[0]
 
 
+# --------------------------------------------------------------------------
+# Lookahead (§3.1 sensing: the first vehicle of the next lane when the own
+# lane has no leader; App. B.3; reading R11).  Hand-worked on a one-lane
+# corridor of three 300 m roads joined by 10 m junction lanes, all signals
+# off (no stop line).  Lane ids: road lanes 0, 1, 2; junction lane 3 joins
+# road 0 to road 1, junction lane 4 road 1 to road 2.  Every gap below is
+# worked from the geometry: (L_lane - s_ego) + (lengths of the empty lanes
+# passed) + s_rear - length, with the REARMOST vehicle of the lane seen.
+# --------------------------------------------------------------------------
+def _lookahead_case(cars, libpath):
+    """cars: list of (lane, s, v); car 0 is the ego.  Route cursor from the
+    lane: road lane r -> r, junction lane 3 / 4 -> 0 / 1 (the road just left)."""
+    scen = corridor((300.0, 300.0, 300.0), [(0, 0)] * len(cars), turn_len=10.0)
+    rc_of = {0: 0, 1: 1, 2: 2, 3: 0, 4: 1}
+    st = dict(status=np.ones(len(cars), dtype=np.int32),
+              lane=np.array([c[0] for c in cars], dtype=np.int32),
+              s=np.array([c[1] for c in cars], dtype=np.float64),
+              v=np.array([c[2] for c in cars], dtype=np.float64),
+              rc=np.array([rc_of[c[0]] for c in cars], dtype=np.int32))
+    o = _oracle(scen, st, libpath)
+    o.set_signal([0, 1], oracle.POLICY_NONE)
+    return o, o.decision(0)
+
+
+def _assert_lookahead(o, d, leader, gap, v_ego, v_leader):
+    v0 = float(np.float32(13.89))
+    assert d["own_stop"] == 0
+    assert d["own_has_leader"] == 1 and d["own_leader"] == leader, (d["own_leader"], leader)
+    assert d["own_gap"] == gap, (d["own_gap"], gap)
+    assert d["a_own"] == o.idm(v_ego, v0, gap, v_ego - v_leader)
+
+
+def check_lookahead_next_lane(libpath=None):
+    """Ego at the front of road 0; the junction lane holds cars at s = 8 and
+    s = 1.5: the rearmost (s = 1.5) is the leader, gap (300 - 250) + 1.5 - 5."""
+    o, d = _lookahead_case([(0, 250.0, 10.0), (3, 8.0, 6.0), (3, 1.5, 4.0)], libpath)
+    _assert_lookahead(o, d, 2, 46.5, 10.0, 4.0)
+
+
+def check_lookahead_second_lane(libpath=None):
+    """Empty junction lane: the rearmost car of road 1 (s = 20 among s = 20,
+    60) leads; the gap adds the 10 m junction lane: 50 + 10 + 20 - 5."""
+    o, d = _lookahead_case([(0, 250.0, 10.0), (1, 60.0, 9.0), (1, 20.0, 3.0)], libpath)
+    _assert_lookahead(o, d, 2, 75.0, 10.0, 3.0)
+
+
+def check_lookahead_from_junction_lane(libpath=None):
+    """Ego on junction lane 3 at s = 4 with road 1 empty: the lane after road
+    1 on the route (junction lane 4) is searched: (10 - 4) + 300 + 3 - 5."""
+    o, d = _lookahead_case([(3, 4.0, 8.0), (4, 3.0, 2.0)], libpath)
+    _assert_lookahead(o, d, 1, 304.0, 8.0, 2.0)
+
+
+def check_lookahead_bounded(libpath=None):
+    """At most two lanes are searched: with the junction lane and road 1 empty,
+    a car on junction lane 4 is not seen (free road), nor is anything when
+    both next lanes are empty; an own-lane leader is used before any car
+    ahead on the next lanes."""
+    v0 = float(np.float32(13.89))
+    for cars in ([(0, 250.0, 10.0), (4, 5.0, 0.0)], [(0, 250.0, 10.0)]):
+        o, d = _lookahead_case(cars, libpath)
+        assert d["own_has_leader"] == 0 and d["own_leader"] == -1, d
+        assert d["a_own"] == o.idm_free(10.0, v0)
+    o, d = _lookahead_case([(0, 250.0, 10.0), (0, 290.0, 7.0), (3, 2.0, 0.0)], libpath)
+    _assert_lookahead(o, d, 1, 35.0, 10.0, 7.0)
+
+
+# --------------------------------------------------------------------------
+# Randomized MOBIL draws and direction (App. B.3; readings R3-R6): the
+# attempt gate u_att < p_attempt, the change gate u_lc < p_LC(u_T), and the
+# side (u_T > 0: left iff u_dir u_T < max(0, u_L); u_T = 0: uniform over the
+# feasible sides).  The uniforms are checked against the Philox4x32-10 words
+# of counter (vehicle id, step, 0, 0) (the generator is pinned by its known
+# answer); u_L, u_R come from states whose utilities the hand cases pin.
+# --------------------------------------------------------------------------
+def _draws(k0, k1, vid, t):
+    w = oracle.philox4x32_10(k0, k1, [vid, t, 0, 0])
+    return [float(int(x) >> 8) * 2.0 ** -24 for x in w[:3]]
+
+
+def _p_lc_reading(p, uT):
+    if uT >= 1.0:
+        return p.p_hi
+    if uT > 0.0:
+        return p.p_lo + (p.p_hi - p.p_lo) * uT
+    return p.p_lo
+
+
+def _gate_and_side(d, p):
+    """(attempted, candidate, direction) the readings give for decision d."""
+    att = d["u_att"] < p.p_attempt
+    uLp = d["uL"] if (d["feasL"] and d["uL"] > 0) else 0.0
+    uRp = d["uR"] if (d["feasR"] and d["uR"] > 0) else 0.0
+    uT = uLp + uRp
+    if not att or not d["u_lc"] < _p_lc_reading(p, uT):
+        return att, False, 0
+    if uT > 0:
+        return att, True, -1 if d["u_dir"] * uT < uLp else 1
+    sides = [s for s, f in ((-1, d["feasL"]), (1, d["feasR"])) if f]
+    if not sides:
+        return att, False, 0
+    if len(sides) == 2:
+        return att, True, -1 if d["u_dir"] < 0.5 else 1
+    return att, True, sides[0]
+
+
+def _scan_gates(cars, p, libpath, steps=300, n_lanes=3):
+    scen, st = one_road(n_lanes, 1000.0, cars, params=p)
+    o = _oracle(scen, st, libpath)
+    k0, k1 = p.seed & 0xFFFFFFFF, (p.seed >> 32) ^ p.scenario
+    seen = {"att": 0, "cand": 0, "left": 0, "right": 0}
+    last = None
+    for t in range(steps):
+        o.set_state(st["status"], st["lane"], st["s"], st["v"], st["rc"], t)
+        d = o.decision(0)
+        assert [d["u_att"], d["u_lc"], d["u_dir"]] == _draws(k0, k1, 0, t), t
+        att, cand, dr = _gate_and_side(d, p)
+        assert d["attempted"] == att and d["cand"] == cand, (t, d)
+        if cand:
+            assert d["dir"] == dr, (t, d)
+            seen["left" if dr < 0 else "right"] += 1
+        seen["att"] += att
+        seen["cand"] += cand
+        if att:
+            last = d
+    return seen, last
+
+
+def check_mobil_draw_gates(libpath=None):
+    """Ego in the middle of three lanes behind a slow leader (case A's own
+    lane), both adjacent lanes empty: u_L = u_R > 0 (the mirror pin), u_T >=
+    1, p_LC = p_hi; over 300 steps of draws every attempt / change / side
+    decision is the one the gates give, and both sides occur."""
+    p = sc.Params(seed=7)
+    seen, d = _scan_gates([(1, 100.0, 10.0), (1, 120.0, 5.0)], p, libpath)
+    assert d["uL"] == d["uR"] > 0 and d["feasL"] == d["feasR"] == 1 and d["pLC"] == p.p_hi
+    assert seen["left"] > 10 and seen["right"] > 10, seen
+    # unequal utilities on both sides (a car 50 m ahead in the right lane
+    # lowers u_R, a larger threshold lowers both): 0 < u_R < u_L, u_T in
+    # (0, 1), p_LC on its linear branch; left is taken about u_L / u_T of
+    # the time, right otherwise
+    p2 = sc.Params(seed=11, a_th=1.5)
+    seen2, d2 = _scan_gates([(1, 100.0, 10.0), (1, 125.0, 8.0), (2, 150.0, 8.0)], p2, libpath)
+    assert d2["feasL"] == d2["feasR"] == 1 and 0.0 < d2["uR"] < d2["uL"] and 0.0 < d2["uT"] < 1.0, d2
+    assert p2.p_lo < d2["pLC"] < p2.p_hi
+    assert seen2["left"] > seen2["right"] > 3 and seen2["att"] > seen2["cand"], seen2
+
+
+def check_mobil_uniform_side(libpath=None):
+    """u_T = 0 (a lone car on free road: u = -a_th on every side) with p_lo
+    raised to 0.3 so that changes occur: a change iff u_lc < 0.3, left iff
+    u_dir < 0.5 when both sides are feasible, the only feasible side
+    otherwise (ego on the leftmost lane: always right)."""
+    p = sc.Params(seed=3, p_lo=0.3, p_attempt=1.0)
+    seen, d = _scan_gates([(1, 100.0, 10.0)], p, libpath)
+    assert d["uT"] == 0.0 and d["pLC"] == 0.3
+    assert seen["left"] > 10 and seen["right"] > 10, seen
+    seen2, _ = _scan_gates([(0, 100.0, 10.0)], p, libpath)
+    assert seen2["cand"] > 10 and seen2["left"] == 0, seen2
+
+
+def check_mobil_gate_boundaries(libpath=None):
+    """The gates are strict: with p_attempt set to the step's own u_att no
+    attempt is made, with p_hi (u_T >= 1) set to the step's own u_lc no change
+    is made, and one unit of 2^-24 above each, they pass."""
+    cars = [(1, 100.0, 10.0), (1, 120.0, 5.0)]
+    base = sc.Params(seed=7, p_attempt=1.0)
+    scen, st = one_road(3, 1000.0, cars, params=base)
+    d0 = _oracle(scen, st, libpath, step=17).decision(0)
+    ua, ul = d0["u_att"], d0["u_lc"]
+    assert 0.0 < ua < 1.0 and 0.0 < ul < 0.9
+    for p_att, want in ((ua, 0), (ua + 2.0 ** -24, 1)):
+        s2, st2 = one_road(3, 1000.0, cars, params=sc.Params(seed=7, p_attempt=p_att))
+        assert _oracle(s2, st2, libpath, step=17).decision(0)["attempted"] == want, (p_att, want)
+    for p_hi, want in ((ul, 0), (ul + 2.0 ** -24, 1)):
+        s2, st2 = one_road(3, 1000.0, cars, params=sc.Params(seed=7, p_attempt=1.0, p_hi=p_hi))
+        d = _oracle(s2, st2, libpath, step=17).decision(0)
+        assert d["pLC"] == p_hi and d["cand"] == want, (p_hi, want, d)
+
+
 ALL_CHECKS = [
     check_idm_free_road, check_idm_equilibrium, check_p_lc, check_mobil_case_A,
     check_mobil_case_B, check_mobil_case_C, check_mobil_case_D, check_mobil_mirror, check_neighbours_bruteforce,
@@ -751,5 +931,7 @@ ALL_CHECKS = [
     check_arrival_and_travel_time, check_insertion, check_conflict, check_max_pressure_argmax,
     check_max_pressure_timing, check_lane_queue_and_road_speed, check_lane_max_speed,
     check_lane_restriction, check_reroute, check_lane_group_mandatory, check_lane_group_keeps_inside,
-    check_lane_plan_switch,
+    check_lane_plan_switch, check_lookahead_next_lane, check_lookahead_second_lane,
+    check_lookahead_from_junction_lane, check_lookahead_bounded, check_mobil_draw_gates,
+    check_mobil_uniform_side, check_mobil_gate_boundaries,
 ]

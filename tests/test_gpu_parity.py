@@ -259,6 +259,61 @@ def test_conflict_hand_case(precision):
     compare_one_step(g, r, 1e-5 if precision == 32 else 1e-12)
 
 
+# the hand-worked lookahead states of the oracle pins (R11): the rearmost car
+# of the next lane, of the lane after an empty junction lane, from a
+# junction lane, and the two-lane bound
+LOOKAHEAD_CASES = [
+    [(0, 250.0, 10.0), (3, 8.0, 6.0), (3, 1.5, 4.0)],
+    [(0, 250.0, 10.0), (1, 60.0, 9.0), (1, 20.0, 3.0)],
+    [(3, 4.0, 8.0), (4, 3.0, 2.0)],
+    [(0, 250.0, 10.0), (4, 5.0, 0.0)],
+    [(0, 250.0, 10.0), (0, 290.0, 7.0), (3, 2.0, 0.0)],
+]
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+@pytest.mark.parametrize("case", range(len(LOOKAHEAD_CASES)))
+def test_lookahead_hand_cases(case, precision):
+    cars = LOOKAHEAD_CASES[case]
+    scen = corridor((300.0, 300.0, 300.0), [(0, 0)] * len(cars), turn_len=10.0)
+    rc_of = {0: 0, 1: 1, 2: 2, 3: 0, 4: 1}
+    st = dict(status=np.ones(len(cars), dtype=np.int32), lane=np.array([c[0] for c in cars], dtype=np.int32),
+              s=np.array([c[1] for c in cars]), v=np.array([c[2] for c in cars]),
+              rc=np.array([rc_of[c[0]] for c in cars], dtype=np.int32))
+    sim, ora = _sim(scen, precision), _ora(scen)
+    _set_both(sim, ora, st, 0)
+    sim.set_signal_policy([0, 1], binding.POLICY_NONE)
+    ora.set_signal([0, 1], oracle.POLICY_NONE)
+    for _ in range(3):
+        sim.step(1); ora.step(1)
+        g, r = sim.state(), ora.state()
+        assert g["lane"].tolist() == r["lane"].tolist() and g["status"].tolist() == r["status"].tolist()
+        tol = 1e-5 if precision == 32 else 1e-12
+        assert np.all(np.abs(g["s"] - r["s"]) <= tol * np.maximum(np.abs(r["s"]), 1.0))
+        assert np.all(np.abs(g["v"] - r["v"]) <= tol * np.maximum(np.abs(r["v"]), 1.0))
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_mobil_draw_gates_hand_states(precision):
+    """The draw-gate pin states (R3-R6): both sides positive and equal (p_LC =
+    p_hi), unequal with u_T in (0, 1), and u_T = 0 with p_lo raised: one step
+    from each of 40 steps of draws; lane (change and side) and kinematics as
+    the oracle's."""
+    states = [([(1, 100.0, 10.0), (1, 120.0, 5.0)], sc.Params(seed=7)),
+              ([(1, 100.0, 10.0), (1, 125.0, 8.0), (2, 150.0, 8.0)], sc.Params(seed=11, a_th=1.5)),
+              ([(1, 100.0, 10.0)], sc.Params(seed=3, p_lo=0.3, p_attempt=1.0))]
+    changed = 0
+    for cars, prm in states:
+        scen, st = one_road(3, 1000.0, cars, params=prm)
+        for t in range(0, 40):
+            g, r = _one_step_hand(scen, st, t, precision)
+            assert g["lane"].tolist() == r["lane"].tolist(), (cars, t)
+            assert (g["flags"] & ~binding.F_FLAGGED).tolist() == (r["flags"] & ~binding.F_FLAGGED).tolist()
+            compare_one_step(g, r, 1e-5 if precision == 32 else 1e-12)
+            changed += int(r["lane"][0] != st["lane"][0])
+    assert changed > 20
+
+
 @pytest.mark.parametrize("precision", [32, 64])
 def test_red_light_and_transfer(precision):
     scen = corridor((300.0, 300.0), [(0, 0), (0, 3)])

@@ -3,7 +3,6 @@ that the pin battery catches every one of them."""
 import os
 import subprocess
 import sys
-import tempfile
 
 import pytest
 
@@ -53,16 +52,45 @@ MUTATIONS = [
     ("plans_ignored", "return (O->jl_plans[j] >> O->road_plan[O->lane_road[O->jl_from[j]]]) & 1;", "return 1;"),
     ("maxp_ties_to_smallest", "if (pk > pb || (pk == pb && best != p && k < best)) best = k;",
      "if (pk > pb || (pk == pb && k < best)) best = k;"),
+    ("lookahead_frontmost",
+     "if (best < 0 || ahead_of(S, best, S->s[m], m)) best = m;\n    }\n    return best;\n}\n\n/* next lane on",
+     "if (best < 0 || ahead_of(S, m, S->s[best], best)) best = m;\n    }\n    return best;\n}\n\n/* next lane on"),
+    ("lookahead_second_lane_length_dropped", "base += O->L[nl];", ";"),
+    ("lookahead_gap_without_length", "double gap = base + S->s[rr] - O->len;", "double gap = base + S->s[rr];"),
+    ("lookahead_one_lane", "for (int k = 0; k < 2 && nl >= 0; ++k) {", "for (int k = 0; k < 1 && nl >= 0; ++k) {"),
+    ("lookahead_third_lane", "nl = (k == 0) ? next_lane(O, vid, nl, rcn, &rcm) : -1;",
+     "nl = next_lane(O, vid, nl, rcn, &rcm);\n            if (k == 1 && nl >= 0) { int rr2 = rearmost_on(S, nl); if (rr2 >= 0) "
+     "{ a = idm(O, v, v0, base + O->L[nl] + S->s[rr2] - O->len, v - S->v[rr2]); r.has_leader = 1; r.leader = rr2; } }"),
+    ("mobil_side_swapped", "side = q > 0.0 ? 0 : 1;", "side = q > 0.0 ? 1 : 0;"),
+    ("mobil_uniform_side_flipped", "if (feas[0] && feas[1]) side = D.u_dir < 0.5 ? 0 : 1;",
+     "if (feas[0] && feas[1]) side = D.u_dir < 0.5 ? 1 : 0;"),
+    ("mobil_uniform_side_ignores_feasibility", "if (feas[0] && feas[1]) side = D.u_dir < 0.5 ? 0 : 1;",
+     "if (1) side = D.u_dir < 0.5 ? 0 : 1;"),
+    ("mobil_attempt_gate_not_strict", "if (!(D.u_att < O->p_att)) return D;", "if (!(D.u_att <= O->p_att)) return D;"),
+    ("mobil_change_gate_not_strict", "if (!(D.u_lc < D.pLC)) return D;", "if (!(D.u_lc <= D.pLC)) return D;"),
+    ("mobil_draw_words_swapped", "D.u_att = unit24(w[0]); D.u_lc = unit24(w[1]);",
+     "D.u_att = unit24(w[1]); D.u_lc = unit24(w[0]);"),
+    ("philox_counter_order_swapped", "uint32_t ctr[4] = {(uint32_t)vid, (uint32_t)t, 0u, 0u}",
+     "uint32_t ctr[4] = {(uint32_t)t, (uint32_t)vid, 0u, 0u}"),
 ]
 
+# Every check runs; each failed assertion is reported at once (a planted
+# mistake may also corrupt the oracle's memory later in the battery, so a
+# crash alone does not count as caught).
 BATTERY = r"""
 import sys
 sys.path.insert(0, {tests!r}); sys.path.insert(0, {root!r})
 import oracle_pins as P
 lib = sys.argv[1]
+failed = 0
 for c in P.ALL_CHECKS + [P.check_permutation_invariance]:
-    c(libpath=lib)
-print("ALL PINS PASSED")
+    try:
+        c(libpath=lib)
+    except AssertionError:
+        failed += 1
+        print("FAIL", c.__name__, flush=True)
+if not failed:
+    print("ALL PINS PASSED")
 """
 
 
@@ -79,3 +107,4 @@ def test_planted_mistake_is_caught(name, orig, planted, tmp_path):
     r = subprocess.run([sys.executable, "-c", code, str(so)], capture_output=True, text=True,
                        timeout=600)
     assert "ALL PINS PASSED" not in r.stdout, f"planted mistake {name} was not caught"
+    assert "FAIL " in r.stdout, f"planted mistake {name} failed no pin (stderr: {r.stderr[-300:]})"
