@@ -182,14 +182,21 @@ typedef struct MossState {
 
 typedef struct MossHandle* moss_t;
 
-/* Build a simulation of one scenario at step 0 with every vehicle waiting.
- * cuda_stream: a cudaStream_t to run on, or NULL for a handle-owned stream.
- * Errors: MOSS_EINVAL (inconsistent arrays, delta != 4, precision not 32/64),
- * MOSS_ENOMEM, MOSS_ECUDA.  On error *out is NULL. */
+/* Build a simulation of one scenario at step 0 with every vehicle waiting
+ * (§3.1 "Python API": the initialization functions; §3.1 "Simulator Inputs":
+ * a road network and a travel demand).  cuda_stream: a cudaStream_t to run
+ * on, or NULL for a handle-owned stream.  The handle's device memory comes
+ * from cudaMalloc (see moss_batch_create_with_allocator for a caller's
+ * allocator).  Errors: MOSS_EINVAL (inconsistent arrays, delta != 4,
+ * precision not 32/64), MOSS_ENOMEM, MOSS_ECUDA.  On error *out is NULL. */
 int moss_create(const MossNetwork* net, const MossVehicles* veh, const MossParams* prm,
                 void* cuda_stream, moss_t* out);
 
-/* Enqueue n >= 0 steps (asynchronous; replays a captured CUDA graph). */
+/* Enqueue n >= 0 steps of dt seconds (§3.1 "Python API": next_step, the call
+ * that advances the simulation; App. B.2: one step is the prepare and update
+ * phases over every vehicle).  Asynchronous on the handle's stream; replays
+ * a captured CUDA graph.  MOSS_EINVAL for n < 0; device errors are reported
+ * by the next waiting call. */
 int moss_step(moss_t h, int n);
 
 /* Set the phase of n junctions (batch setter, §3.1 "_batch" API, §3.2
@@ -273,7 +280,9 @@ int moss_batch_get_road_speed(moss_t h, int scenario, double* speed);
 int moss_get_signal_state(moss_t h, int n, const int32_t* junction_ids, int32_t* phase, int32_t* elapsed,
                           int32_t* next_phase);
 
-/* Wait for the handle's stream and copy the cumulative metrics. */
+/* Wait for the handle's stream and copy the cumulative metrics into the
+ * caller's struct (§3.3: throughput, average travelling time, network
+ * speed).  Returns a pending device error (MOSS_ETIMEOUT, MOSS_EDEVICE). */
 int moss_get_metrics(moss_t h, MossMetrics* out);
 
 /*
@@ -292,31 +301,43 @@ int moss_get_metrics(moss_t h, MossMetrics* out);
 int moss_metrics_enqueue(moss_t h, int scenario, int slot);
 int moss_metrics_read(moss_t h, int slot, MossMetrics* out);
 
-/* Wait for the handle's stream and copy the per-vehicle state (by id). */
+/* Wait for the handle's stream and copy the per-vehicle state (by id) into
+ * the caller's arrays (§3.1 "Python API": the getter functions, such as the
+ * vehicles' speeds and positions).  Returns a pending device error. */
 int moss_get_state(moss_t h, MossState* out);
 
-/* Replace the per-vehicle state and set the step counter; s and v are
- * rounded to the handle's precision.  Waiting vehicles must form the tail of
- * each start lane's departure queue ordered by (dep, id); active vehicles
- * must sit on a lane of their route's road rc with 0 <= s <= length.
- * Metrics are kept.  MOSS_EINVAL if the state is inconsistent. */
+/* Replace the per-vehicle state and set the step counter (no counterpart in
+ * the paper: checkpoint/resume, used to start from a given state in tests,
+ * measurement and serving); s and v are rounded to the handle's precision.
+ * Waiting vehicles must form the tail of each start lane's departure queue
+ * ordered by (dep, id); active vehicles must sit on a lane of their route's
+ * road rc with 0 <= s <= length.  Metrics are kept.  MOSS_EINVAL if the
+ * state is inconsistent (nothing is changed). */
 int moss_set_state(moss_t h, const MossState* in, int64_t step);
 
-/* Wait for all work enqueued on the handle. */
+/* Wait for all work enqueued on the handle and report a pending device error
+ * (no counterpart in the paper: the CUDA stream of the C ABI). */
 int moss_synchronize(moss_t h);
 
-/* Device bytes held by the handle. */
+/* Device bytes held by the handle (no counterpart in the paper; used for
+ * admission by memory budget when serving). */
 int moss_device_bytes(moss_t h, size_t* out);
 
-/* Release the handle and its device memory (NULL is ignored). */
+/* Release the handle and its device memory (NULL is ignored); waits for the
+ * handle's stream first.  No counterpart in the paper (resource management
+ * of the C ABI). */
 void moss_destroy(moss_t h);
 
-/* Text of the handle's last error ("" if none); valid until the next call. */
+/* Text of the handle's last error ("" if none); valid until the next call.
+ * No counterpart in the paper (error reporting of the C ABI). */
 const char* moss_last_error(moss_t h);
 
 /*
- * Batching: n independent scenarios advanced together, one launch per step
- * kernel for all of them (scenarios of uneven size share every launch).
+ * Batching (no counterpart in the paper, whose "_batch" setters of §3.1
+ * batch the calls of one simulation; this runs the many rollouts that the
+ * optimisation loops of §4 need): n independent scenarios advanced
+ * together, one launch per step kernel for all of them (scenarios of uneven
+ * size share every launch).
  * Each scenario keeps its own vehicle ids, random streams (seed, scenario)
  * and step counter, so its trajectory is the same alone and in the batch.
  * Model parameters other than seed/scenario must be equal across scenarios
@@ -326,6 +347,29 @@ const char* moss_last_error(moss_t h);
  */
 int moss_batch_create(int n, const MossNetwork* nets, const MossVehicles* vehs,
                       const MossParams* prms, void* cuda_stream, moss_t* out);
+
+/*
+ * Device allocator of a handle (no counterpart in the paper): lets a caller
+ * whose framework owns the device memory — PyTorch's caching allocator, for
+ * one — back every device buffer of a handle.  alloc returns device memory of
+ * at least `bytes` bytes, aligned to 256 bytes, usable on cuda_stream (the
+ * handle's stream), or NULL on failure (the call then returns MOSS_ENOMEM);
+ * release gets back each pointer with its size and the same stream, after
+ * the stream has finished with it.  ctx is passed through.  Both must be set.
+ */
+typedef struct MossAllocator {
+    void* (*alloc)(size_t bytes, void* cuda_stream, void* ctx);
+    void (*release)(void* ptr, size_t bytes, void* cuda_stream, void* ctx);
+    void* ctx;
+} MossAllocator;
+
+/* moss_batch_create whose device buffers come from `allocator` (NULL: the
+ * same as moss_batch_create).  The allocator must outlive the handle; setter
+ * scratch and a growing route buffer are taken from it too.  MOSS_EINVAL if
+ * only one of its functions is set. */
+int moss_batch_create_with_allocator(int n, const MossNetwork* nets, const MossVehicles* vehs,
+                                     const MossParams* prms, void* cuda_stream, const MossAllocator* allocator,
+                                     moss_t* out);
 int moss_batch_size(moss_t h, int* out);
 int moss_batch_get_metrics(moss_t h, int scenario, MossMetrics* out);
 int moss_batch_get_state(moss_t h, int scenario, MossState* out);
@@ -376,7 +420,11 @@ int moss_selftest_bounded_wait(void* cuda_stream);
  * the current ones: newsize(l) = d_off_cur[l+1] - d_off_cur[l] - d_leave[l] +
  * d_enter[l]; d_off_next[0..n_lanes] = exclusive prefix sums of newsize (the
  * last entry is the total); d_lbefore[0..n_lanes-1] = exclusive prefix sums
- * of d_leave.  All five arrays are DEVICE int32 arrays owned by the caller
+ * of d_leave.  Preconditions: every newsize(l) >= 0 (a lane cannot lose more
+ * vehicles than it holds plus those entering), and the sums of newsize and of
+ * d_leave over all lanes are below 2^31.  A negative newsize is reported
+ * (d_off_next[n_lanes] = -1, the other entries are then meaningless); totals
+ * of 2^31 or more are not detected.  All five arrays are DEVICE int32 arrays owned by the caller
  * (d_off_cur and d_off_next have n_lanes+1 entries).  The work is enqueued
  * on cuda_stream (NULL = the legacy default stream) and the call returns
  * without waiting.
@@ -386,11 +434,14 @@ int moss_selftest_bounded_wait(void* cuda_stream);
  * loads the library until the process exits.  Limit: n_lanes <=
  * MOSS_NOALLOC_MAX_LANES; larger sizes return MOSS_EINVAL.  The first call on
  * a device looks up that array's device address (and the SM count) with the
- * device current; make that first call before any stream capture.  Every
+ * device current and keeps it for the life of the process; make that first
+ * call before any stream capture, and do not use the call across a
+ * cudaDeviceReset (or a release of the device's primary context), after
+ * which the kept address may no longer be the array's.  Every
  * call reuses the same array (each call clears it first), so calls that can
  * overlap on the GPU — on different streams, or from different threads —
  * race and must be serialised by the caller.  If a bounded device-side wait
- * gives up, d_off_next[n_lanes] is set to -1.  Returns MOSS_OK, MOSS_EINVAL
+ * gives up, d_off_next[n_lanes] is set to -1 as well.  Returns MOSS_OK, MOSS_EINVAL
  * (bad size or null array) or MOSS_ECUDA (a CUDA call failed).
  */
 #define MOSS_NOALLOC_MAX_LANES (1 << 22)

@@ -67,6 +67,32 @@ class MossState(ctypes.Structure):
                 ("rc", _c_i32p), ("flags", _c_i32p)]
 
 
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class MossAllocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("release", RELEASE_FN), ("ctx", ctypes.c_void_p)]
+
+
+def torch_allocator():
+    """A MossAllocator backed by PyTorch's caching allocator (device memory
+    of a handle comes from torch's pool, on the handle's stream).  Keep the
+    returned object alive as long as the handle."""
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:
+            return None
+
+    def _release(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return MossAllocator(ALLOC_FN(_alloc), RELEASE_FN(_release), None)
+
+
 # every symbol include/moss.h declares, with its signature
 _vp = ctypes.c_void_p
 SIGNATURES = {
@@ -95,6 +121,9 @@ SIGNATURES = {
                                          ctypes.POINTER(MossVehicles), ctypes.POINTER(MossParams),
                                          _vp, ctypes.POINTER(_vp)]),
     "moss_batch_size": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "moss_batch_create_with_allocator": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(MossNetwork),
+                                                        ctypes.POINTER(MossVehicles), ctypes.POINTER(MossParams),
+                                                        _vp, ctypes.POINTER(MossAllocator), ctypes.POINTER(_vp)]),
     "moss_batch_get_metrics": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(MossMetrics)]),
     "moss_metrics_enqueue": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "moss_metrics_read": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(MossMetrics)]),
@@ -261,15 +290,22 @@ def _state_arrays(n: int):
 class Simulation(_Handle):
     """One scenario on the GPU (``moss_create``)."""
 
-    def __init__(self, net, veh, params, precision: int = 32, stream: Optional[int] = None):
+    def __init__(self, net, veh, params, precision: int = 32, stream: Optional[int] = None,
+                 allocator: Optional[MossAllocator] = None):
         super().__init__()
         keep: list = []
         n = _net_struct(net, keep)
         v = _veh_struct(veh, keep)
         p = _prm_struct(params, precision)
         h = _vp()
-        rc = self.lib.moss_create(ctypes.byref(n), ctypes.byref(v), ctypes.byref(p),
-                                  _vp(stream) if stream else None, ctypes.byref(h))
+        if allocator is None:
+            rc = self.lib.moss_create(ctypes.byref(n), ctypes.byref(v), ctypes.byref(p),
+                                      _vp(stream) if stream else None, ctypes.byref(h))
+        else:
+            self._allocator = allocator  # the callbacks must outlive the handle
+            rc = self.lib.moss_batch_create_with_allocator(1, ctypes.byref(n), ctypes.byref(v), ctypes.byref(p),
+                                                           _vp(stream) if stream else None,
+                                                           ctypes.byref(allocator), ctypes.byref(h))
         _check(rc)
         self.h = h
         self.n = int(veh.n)

@@ -56,7 +56,8 @@ struct MossHandle {
     std::vector<uint32_t> key0, key1;
 
     // ---- device
-    std::vector<void*> allocs;
+    std::vector<std::pair<void*, size_t>> allocs;  // device buffers and their sizes
+    MossAllocator allocator{};                       // caller's device allocator (alloc == NULL: cudaMalloc)
     size_t bytes = 0;
     LaneInfo* d_lane = nullptr;
     float* d_v0f = nullptr;
@@ -133,16 +134,30 @@ int cuda_fail(MossHandle* h, cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);        \
     } while (0)
 
+// device memory of the handle: the caller's allocator when one was given
+// (on the handle's stream), else cudaMalloc; nullptr on failure
+void* raw_alloc(MossHandle* h, size_t nb) {
+    if (h->allocator.alloc) return h->allocator.alloc(nb, (void*)h->stream, h->allocator.ctx);
+    void* q = nullptr;
+    if (cudaMalloc(&q, nb) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return q;
+}
+
+void raw_free(MossHandle* h, void* p, size_t nb) {
+    if (!p) return;
+    if (h->allocator.alloc) h->allocator.release(p, nb, (void*)h->stream, h->allocator.ctx);
+    else cudaFree(p);
+}
+
 template <typename T>
 int dalloc(MossHandle* h, T** p, size_t count) {
-    void* q = nullptr;
     const size_t nb = std::max<size_t>(count, 1) * sizeof(T);
-    cudaError_t e = cudaMalloc(&q, nb);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(h, MOSS_ENOMEM, "cudaMalloc of " + std::to_string(nb) + " bytes failed");
-    }
-    h->allocs.push_back(q);
+    void* q = raw_alloc(h, nb);
+    if (!q) return fail(h, MOSS_ENOMEM, "device allocation of " + std::to_string(nb) + " bytes failed");
+    h->allocs.emplace_back(q, nb);
     h->bytes += nb;
     *p = (T*)q;
     return MOSS_OK;
@@ -333,7 +348,9 @@ void enqueue_step(MossHandle* h, int cur, bool timed) {
     if (h->lane_groups) k_decide<Real, true><<<g.decide_work + g.decide_ins, TILE, 0, s>>>(c, g.decide_work);
     else k_decide<Real, false><<<g.decide_work + g.decide_ins, TILE, 0, s>>>(c, g.decide_work);
     if (timed) cudaEventRecord(h->ev[1], s);
+#if !MOSS_FOLD_RESOLVE
     k_resolve<Real><<<g.resolve, TILE, 0, s>>>(c);
+#endif
     if (timed) cudaEventRecord(h->ev[2], s);
     k_lanescan<Real><<<g.lanescan, LANESCAN_THREADS, 0, s>>>(c);
     if (timed) cudaEventRecord(h->ev[3], s);
@@ -679,7 +696,7 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
 void free_all(MossHandle* h) {
     destroy_graphs(h);
     if (h->stream) cudaStreamSynchronize(h->stream);
-    for (void* p : h->allocs) cudaFree(p);
+    for (auto& a : h->allocs) raw_free(h, a.first, a.second);
     h->allocs.clear();
     for (int k = 0; k <= N_STEP_KERNELS; ++k)
         if (h->ev[k]) cudaEventDestroy(h->ev[k]);
@@ -874,10 +891,13 @@ int reroute_impl(MossHandle* h, int n, const int32_t* vids, const int32_t* route
     // device scratch for this call
     int32_t *d_v = nullptr, *d_lane = nullptr;
     int2* d_sp = nullptr;
-    auto cleanup = [&]() { cudaFree(d_v); cudaFree(d_lane); cudaFree(d_sp); };
-    if (cudaMalloc(&d_v, n * 4) != cudaSuccess || cudaMalloc(&d_lane, n * 4) != cudaSuccess ||
-        cudaMalloc(&d_sp, n * sizeof(int2)) != cudaSuccess) {
-        cudaGetLastError();
+    auto cleanup = [&]() {
+        raw_free(h, d_v, n * 4); raw_free(h, d_lane, n * 4); raw_free(h, d_sp, n * sizeof(int2));
+    };
+    d_v = (int32_t*)raw_alloc(h, n * 4);
+    d_lane = (int32_t*)raw_alloc(h, n * 4);
+    d_sp = (int2*)raw_alloc(h, n * sizeof(int2));
+    if (!d_v || !d_lane || !d_sp) {
         cleanup();
         return fail(h, MOSS_ENOMEM, "re-routing scratch");
     }
@@ -934,9 +954,8 @@ int reroute_impl(MossHandle* h, int n, const int32_t* vids, const int32_t* route
     }
     if (h->routes.size() > h->routes_cap) {  // grow the device route buffer
         const size_t cap = std::max(h->routes.size(), 2 * h->routes_cap);
-        int32_t* nr = nullptr;
-        if (cudaMalloc(&nr, cap * 4) != cudaSuccess) {
-            cudaGetLastError();
+        int32_t* nr = (int32_t*)raw_alloc(h, cap * 4);
+        if (!nr) {
             h->routes.resize(old);
             k_mark_vehicles<<<nb, 256, 0, h->stream>>>(h->d_req, n, d_v, 0);
             cudaStreamSynchronize(h->stream);
@@ -944,9 +963,12 @@ int reroute_impl(MossHandle* h, int n, const int32_t* vids, const int32_t* route
             return fail(h, MOSS_ENOMEM, "route buffer");
         }
         cudaMemcpy(nr, h->d_routes, old * 4, cudaMemcpyDeviceToDevice);
-        for (auto& p : h->allocs)
-            if (p == (void*)h->d_routes) p = (void*)nr;
-        cudaFree(h->d_routes);
+        for (auto& a : h->allocs)
+            if (a.first == (void*)h->d_routes) {
+                raw_free(h, a.first, a.second);
+                h->bytes += cap * 4 - a.second;
+                a = std::make_pair((void*)nr, cap * 4);
+            }
         h->d_routes = nr;
         h->routes_cap = cap;
         destroy_graphs(h);
@@ -1026,11 +1048,19 @@ int moss_create(const MossNetwork* net, const MossVehicles* veh, const MossParam
 
 int moss_batch_create(int n, const MossNetwork* nets, const MossVehicles* vehs,
                       const MossParams* prms, void* cuda_stream, moss_t* out) {
+    return moss_batch_create_with_allocator(n, nets, vehs, prms, cuda_stream, nullptr, out);
+}
+
+int moss_batch_create_with_allocator(int n, const MossNetwork* nets, const MossVehicles* vehs,
+                                     const MossParams* prms, void* cuda_stream, const MossAllocator* allocator,
+                                     moss_t* out) {
     if (!out) return MOSS_EINVAL;
     *out = nullptr;
     if (!nets || !vehs || !prms) return MOSS_EINVAL;
+    if (allocator && (!allocator->alloc || !allocator->release)) return MOSS_EINVAL;
     MossHandle* h = new (std::nothrow) MossHandle();
     if (!h) return MOSS_ENOMEM;
+    if (allocator) h->allocator = *allocator;
     int rc;
     try {
         rc = create_impl(n, nets, vehs, prms, cuda_stream, h);
@@ -1141,11 +1171,8 @@ int moss_set_road_lane_plan(moss_t h, int n, const int32_t* road_ids, const int3
     }
     if (n == 0) return MOSS_OK;
     CK(cudaStreamSynchronize(h->stream));
-    int32_t* d = nullptr;
-    if (cudaMalloc(&d, 2 * (size_t)n * 4) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(h, MOSS_ENOMEM, "plan setter scratch");
-    }
+    int32_t* d = (int32_t*)raw_alloc(h, 2 * (size_t)n * 4);
+    if (!d) return fail(h, MOSS_ENOMEM, "plan setter scratch");
     cudaError_t e = cudaMemcpy(d, road_ids, n * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d + n, plan_idx, n * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
@@ -1162,7 +1189,7 @@ int moss_set_road_lane_plan(moss_t h, int n, const int32_t* road_ids, const int3
         k_unmark_roads<<<nb, 256, 0, h->stream>>>(n, d, h->d_road_mark);
         e = cudaStreamSynchronize(h->stream);
     }
-    cudaFree(d);
+    raw_free(h, d, 2 * (size_t)n * 4);
     if (e != cudaSuccess) return fail(h, MOSS_ECUDA, cudaGetErrorString(e));
     for (int k = 0; k < n; ++k) {  // the host copy of the lane table
         const int2 sp = h->road_span[road_ids[k]];
@@ -1356,7 +1383,7 @@ int moss_set_state(moss_t h, const MossState* in, int64_t step) {
     CK(cudaMemcpy(h->d_metrics + M_CUR_ACTIVE, cur, sizeof(cur), cudaMemcpyHostToDevice));
     Counters c{};
     CK(cudaMemcpy(&c, h->d_cnt + h->parity, sizeof(c), cudaMemcpyDeviceToHost));
-    c.n_cur = (int)n_act; c.n_ent = 0; c.n_cand = 0; c.ticket_lane = 0;
+    c.n_cur = (int)n_act; c.n_ent = 0; c.n_cand = 0; c.ticket_lane = 0; c.res_done = 0;
     CK(cudaMemcpy(h->d_cnt + h->parity, &c, sizeof(c), cudaMemcpyHostToDevice));
     TRY(junction_init(h));
     CK(cudaStreamSynchronize(h->stream));

@@ -75,8 +75,14 @@ struct Counters {
     int tag;         // step tag of the per-lane lists (never 0)
     int err;         // device error bits (set 0 only)
     int n_mp;        // junctions under max pressure (set 0 only)
-    int pad;
+    int res_done;    // k_lanescan tickets of candidate / pressure work finished
 };
+
+// the candidates are resolved in the first tickets of k_lanescan instead of a
+// kernel of their own
+#ifndef MOSS_FOLD_RESOLVE
+#define MOSS_FOLD_RESOLVE 1
+#endif
 
 // snapshot records
 template <typename Real> struct RecA;
@@ -222,11 +228,12 @@ __device__ __forceinline__ void philox4x32_10(uint32_t k0, uint32_t k1, uint32_t
                                               uint32_t c2, uint32_t c3, uint32_t out[4]) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
-        const uint32_t n0 = hi1 ^ c1 ^ k0;
-        const uint32_t n2 = hi0 ^ c3 ^ k1;
-        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        // one widening multiply per product (high and low words together)
+        const unsigned long long p0 = (unsigned long long)c0 * 0xD2511F53u;
+        const unsigned long long p1 = (unsigned long long)c2 * 0xCD9E8D57u;
+        const uint32_t n0 = uint32_t(p1 >> 32) ^ c1 ^ k0;
+        const uint32_t n2 = uint32_t(p0 >> 32) ^ c3 ^ k1;
+        c0 = n0; c1 = uint32_t(p1); c2 = n2; c3 = uint32_t(p0);
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
@@ -378,15 +385,18 @@ __device__ __forceinline__ int mp_advance(const Ctx<Real>& c, int j) {
 }
 
 // light of a junction lane (its lane record ji) for this step
-template <typename Real>
-__device__ __forceinline__ int light_of(const Ctx<Real>& c, const LaneInfo& ji) {
-    const int st = c.junc_state[ji.jb];
+__device__ __forceinline__ int light_from(int st, const LaneInfo& ji) {
     if (st & 512) return LIGHT_GREEN;
     const int p = st & 15, mask = ji.je;
     if (!((mask >> p) & 1)) return LIGHT_RED;
     if (!(st & 256)) return LIGHT_GREEN;
     const int nx = (st >> 10) & 15;  // the phase after the amber
     return ((mask >> nx) & 1) ? LIGHT_GREEN : LIGHT_AMBER;
+}
+
+template <typename Real>
+__device__ __forceinline__ int light_of(const Ctx<Real>& c, const LaneInfo& ji) {
+    return light_from(c.junc_state[ji.jb], ji);
 }
 
 // junction lane leaving road lane (record li) towards road out_road (-1 if

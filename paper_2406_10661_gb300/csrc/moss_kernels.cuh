@@ -346,13 +346,8 @@ __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Rea
 // stored utilities, so the outcome is consistent.  Then the update on the
 // target lane (granted) or with the stored own-lane kinematics (lost).
 template <typename Real>
-__global__ void __launch_bounds__(TILE) k_resolve(Ctx<Real> c) {
-    if (*c.err & ERR_POISON) return;
-    const int nc = c.cnt->n_cand;
-    const int tag = c.cnt->tag;
-    MetricAcc acc;
-    macc_reset(acc, -1);
-    for (int k = blockIdx.x * TILE + threadIdx.x; k < nc; k += gridDim.x * TILE) {
+__device__ __forceinline__ void resolve_one(const Ctx<Real>& c, MetricAcc& acc, int k, int nc, int tag) {
+    {
         const Cand<Real> C = c.cands[k];
         const int i = C.slot;
         const RecA<Real> E = C.E;
@@ -398,6 +393,16 @@ __global__ void __launch_bounds__(TILE) k_resolve(Ctx<Real> c) {
         if (integrate_emit(c, acc, i, E, EB, la, nlane, fl, (C.bits & CB_OVERLAP) != 0, t, sc, tag))
             atomicAdd(&c.tile_leave[i / TILE], 1);
     }
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(TILE) k_resolve(Ctx<Real> c) {
+    if (*c.err & ERR_POISON) return;
+    const int nc = c.cnt->n_cand;
+    const int tag = c.cnt->tag;
+    MetricAcc acc;
+    macc_reset(acc, -1);
+    for (int k = blockIdx.x * TILE + threadIdx.x; k < nc; k += gridDim.x * TILE) resolve_one(c, acc, k, nc, tag);
     // the phase pressures of the max-pressure junctions (read by k_lanescan)
     if (*c.n_mp > 0)
         for (int k = blockIdx.x * TILE + threadIdx.x; k < c.n_jj; k += gridDim.x * TILE) mp_accumulate(c, k);
@@ -627,13 +632,60 @@ template <typename Real>
 __global__ void __launch_bounds__(LANESCAN_THREADS) k_lanescan(Ctx<Real> c) {
     if (*c.err & ERR_POISON) return;
     __shared__ int s_tile;
-    const int n_tickets = c.n_lane_tiles + 1 + c.n_junc_chunks;
+#if MOSS_FOLD_RESOLVE
+    // first tickets: the lane-change candidates (k_resolve's work) and the
+    // max-pressure sums, in chunks of TILE; the later tickets wait until all
+    // of those are done (their blocks hold earlier tickets, so they are
+    // running: the wait is bounded)
+    __shared__ int s_ready;
+    const int nc = c.cnt->n_cand;
+    const int tag = c.cnt->tag;
+    const int r_cand = (nc + TILE - 1) / TILE;
+    const int n_res = r_cand + (*c.n_mp > 0 ? (c.n_jj + TILE - 1) / TILE : 0);
+    if (threadIdx.x == 0) s_ready = n_res == 0;
+#else
+    const int n_res = 0;
+#endif
+    const int n_tickets = n_res + c.n_lane_tiles + 1 + c.n_junc_chunks;
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(&c.cnt->ticket_lane, 1);
         __syncthreads();
-        const int tile = s_tile;
+        int tile = s_tile;
         __syncthreads();
         if (tile >= n_tickets) return;
+#if MOSS_FOLD_RESOLVE
+        if (tile < n_res) {
+            if (tile < r_cand) {
+                MetricAcc acc;
+                macc_reset(acc, -1);
+                const int k = tile * TILE + threadIdx.x;
+                if (k < nc) resolve_one(c, acc, k, nc, tag);
+                macc_flush_block<TILE>(acc, c.metrics);
+            } else {
+                const int k = (tile - r_cand) * TILE + threadIdx.x;
+                if (k < c.n_jj) mp_accumulate(c, k);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(&c.cnt->res_done, 1);
+            }
+            continue;
+        }
+        if (!s_ready) {
+            if (threadIdx.x == 0) {
+                cuda::atomic_ref<int, cuda::thread_scope_device> done(c.cnt->res_done);
+                long long spins = 0;
+                while (done.load(cuda::memory_order_acquire) < n_res) {
+                    if (++spins > SPIN_LIMIT) { atomicOr(c.err, ERR_TIMEOUT); break; }
+                    if (spins > 16) __nanosleep(64);
+                }
+                s_ready = 1;
+            }
+            __syncthreads();
+        }
+        tile -= n_res;
+#endif
         if (tile < c.n_lane_tiles) {
             lanescan_tile(c, tile);
         } else if (tile == c.n_lane_tiles) {
@@ -682,6 +734,7 @@ __global__ void __launch_bounds__(TILE) k_place(Ctx<Real> c) {
         if (threadIdx.x == 0) {
             c.cnt_next->n_ent = 0;
             c.cnt_next->n_cand = 0;
+            c.cnt_next->res_done = 0;
             c.cnt_next->ticket_lane = 0;
             c.cnt_next->tag = tag >= 0x3fffffff ? 1 : tag + 1;
         }

@@ -26,7 +26,7 @@ constexpr int NA_MAX_DEVICES = 64;
 struct NoallocScratch {
     unsigned long long tile[NA_MAX_TILES];  // look-back words: flag:2 | leavers:31 | sizes:31
     int ticket;                             // dynamic tile counter
-    int err;                                // a bounded wait gave up
+    int err;                                // a bounded wait gave up, or a lane's new size was negative
     int pad[62];
 };
 
@@ -75,6 +75,10 @@ __global__ void __launch_bounds__(NA_THREADS) k_noalloc_lanescan(NoallocScratch*
             if (l < n) {
                 lv[k] = leave[l];
                 ns[k] = off_cur[l + 1] - off_cur[l] - lv[k] + enter[l];
+                if (ns[k] < 0) {  // violated precondition: reported, and kept out of the packed sums
+                    atomicOr(&sc->err, 2);
+                    ns[k] = 0;
+                }
             } else {
                 ns[k] = 0; lv[k] = 0;
             }

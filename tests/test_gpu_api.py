@@ -73,3 +73,44 @@ def test_metric_slot_misuse_refused():
     sim.metrics_read(1)
     with pytest.raises(binding.MossError):
         sim.metrics_read(1)          # already read
+
+
+def test_torch_allocator_backs_the_handle():
+    """A handle whose device buffers come from PyTorch's caching allocator
+    (moss_batch_create_with_allocator): the bytes torch reports allocated grow
+    by at least the handle's size, the rollout equals one on cudaMalloc'd
+    buffers (including a re-route, whose device scratch comes from the
+    allocator too), and destroying the handle gives the memory back to
+    torch's pool."""
+    import torch
+    scen = sc.small_scenario()
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    alloc = binding.torch_allocator()
+    sim = binding.Simulation(scen.net, scen.veh, scen.params, allocator=alloc)
+    ref = binding.Simulation(scen.net, scen.veh, scen.params)
+    assert torch.cuda.memory_allocated() - before >= sim.device_bytes() > 0
+    sim.step(150); ref.step(150)
+    # a re-route of a waiting vehicle (setter scratch from the allocator)
+    st = ref.state()
+    waiting = np.nonzero(st["status"] == 0)[0]
+    if len(waiting):
+        vid = int(waiting[-1])
+        r0 = int(scen.veh.routes[scen.veh.route_off[vid]])
+        for s_ in (sim, ref):
+            s_.set_vehicle_route([vid], [[r0]])
+    sim.step(150); ref.step(150)
+    a, b = sim.state(), ref.state()
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    assert sim.metrics() == ref.metrics()
+    sim.close()
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() <= before + 4096
+
+
+def test_allocator_with_one_function_is_refused():
+    scen = sc.small_scenario()
+    bad = binding.MossAllocator(binding.torch_allocator().alloc, binding.RELEASE_FN(), None)
+    with pytest.raises(binding.MossError):
+        binding.Simulation(scen.net, scen.veh, scen.params, allocator=bad)

@@ -477,6 +477,51 @@ def test_ragged_batch_with_empty_member():
         assert alone.metrics() == batch.metrics(i), i
 
 
+def test_fp64_ragged_batch_matches_oracle_per_member():
+    """A ragged FP64 batch against one oracle instance per member (not only
+    against its members run alone): an empty member, a single-road member,
+    grids of 3x3 to 8x8 with up to 6,000 trips, their own seeds and scenario
+    ids (so their random streams differ), scenario-major lanes and vehicles
+    at the batch boundaries.  After 300 steps every member's discrete state
+    and flags equal its oracle's, positions and speeds within 1e-6, and its
+    metrics match."""
+    empty_net = sc.corridor_network(2, (500.0,))
+    empty_veh = sc.Vehicles(n=0, route_off=np.zeros(1, np.int32), routes=np.zeros(0, np.int32),
+                            start_lane=np.zeros(0, np.int32), dep=np.zeros(0, np.int32),
+                            v0f=np.zeros(0, np.float32))
+    empty = sc.Scenario(empty_net, empty_veh, sc.Params(), "empty")
+    one_road_scen, _ = one_road(3, 800.0, [(0, 10.0, 5.0)])
+    one_road_scen.veh.dep[:] = 0
+    grids = []
+    for k, (G, n, L) in enumerate([(3, 400, 150.0), (5, 2500, 200.0), (8, 6000, 250.0), (4, 1200, 300.0)]):
+        net = sc.grid_network(G, L, 2 + (k % 2), 13.89, offsets=True, seed=10 + k)
+        veh = sc.random_demand(net, n, 200, seed=10 + k)
+        grids.append(sc.Scenario(net, veh, sc.Params(seed=100 + k), f"grid{G}"))
+    scens = [grids[0], empty, grids[1], one_road_scen, grids[2], grids[3]]
+    for i, s_ in enumerate(scens):
+        s_.params.scenario = i
+    batch = binding.Batch(scens, precision=64)
+    batch.step(300)
+    for i, s_ in enumerate(scens):
+        ora = _ora(s_)
+        ora.step(300)
+        g, r = batch.state(i), ora.state()
+        assert np.array_equal(g["status"], r["status"]), i
+        act = r["status"] == 1
+        for k in ("lane", "rc"):
+            assert np.array_equal(g[k][act], r[k][act]), (i, k)
+        assert np.array_equal(g["flags"], r["flags"]), i
+        if act.any():
+            assert np.abs(g["s"][act] - r["s"][act]).max() < 1e-6, i
+            assert np.abs(g["v"][act] - r["v"][act]).max() < 1e-6, i
+        gm, rm = batch.metrics(i), ora.metrics()
+        for k in ("step", "n_active", "n_waiting", "n_arrived", "vehicle_updates", "lane_changes", "flagged",
+                  "overlaps", "inserted", "mobil_evals"):
+            assert gm[k] == rm[k], (i, k, gm[k], rm[k])
+        assert abs(gm["tt_sum"] - rm["tt_sum"]) < 1e-9
+        assert abs(gm["speed_sum"] - rm["speed_sum"]) <= 1e-6 * max(rm["speed_sum"], 1.0)
+
+
 @pytest.mark.parametrize("precision", [32, 64])
 def test_long_queue_lane_spans_many_tiles(precision):
     """One 8 km two-lane road holding a 1,500-car queue (the lane's segment
