@@ -518,18 +518,30 @@ def run_ours(args):
         "wall_s_timed_region": wall,
         "cpu_baseline": cpu,
     }
+    if world == 1 and args.workload == "city" and not args.city_only:
+        # the batched (64 uneven scenarios) and served (Poisson rollout
+        # requests) parts of the metric, each with its own clock record
+        b = run_batched(args, emit=False)
+        line["batched"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "step_hz", "p50_step_ms",
+                                              "p99_step_ms", "batched_over_sequential", "clocks", "config",
+                                              "sequential", "latency_how") if k in b}
+        sv = run_serving(args, emit=False)
+        line["served"] = {k: sv[k] for k in ("value", "unit", "p50_step_ms", "p99_step_ms", "wall_s", "config",
+                                             "clocks", "all_at_once", "sequential", "all_at_once_over_sequential",
+                                             "results_equal_alone_and_mixed", "peak_slots", "how")}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
 
-def run_batched(args):
+def run_batched(args, emit=True):
     """64 uneven scenarios advanced together (one set of launches per step,
     replayed from a CUDA graph, autotuned schedule) against stepping the same
     scenarios one at a time; both from the step-900 state the simulation
     reaches, K timed steps each.  Under torchrun every rank takes every
     world-th scenario (no exchange between ranks); the job's rate is the
-    summed updates over the slowest rank's time."""
+    summed updates over the slowest rank's time.  Returns the line (printed
+    when emit)."""
     import torch
     from paper_2406_10661_gb300 import binding, scenario as sc, serving
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -538,7 +550,8 @@ def run_batched(args):
     dist = None
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        if emit:
+            dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     binding.load()
     t0 = time.perf_counter()
@@ -592,10 +605,10 @@ def run_batched(args):
                 seq_ms += e0.elapsed_time(e1)
                 seq_upd += sim.metrics()["vehicle_updates"] - m0
                 sim.close()
-    if dist:
+    if dist and emit:
         dist.destroy_process_group()
     if rank != 0:
-        return
+        return None
     b_val = b_upd / b_s
     line = {"metric": "vehicle-updates/s (batched)", "value": b_val, "unit": "vehicle-updates/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * b_s / args.steps,
@@ -617,46 +630,67 @@ def run_batched(args):
                               "how": "the same scenarios, one handle each, stepped one scenario at a time"}
         line["batched_over_sequential"] = b_val / s_val
         line["same_updates"] = int(b_upd) == int(seq_upd)
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
-def run_serving(args):
-    """Poisson stream of rollout requests served with continuous admission by
-    device-memory budget; p50/p99 step latency and aggregate vehicle-updates/s,
-    against serving the same requests one at a time."""
+def _fresh(reqs):
+    """the same requests with their results cleared (scenarios shared)"""
+    from paper_2406_10661_gb300 import serving
+    return [serving.Request(rid=r.rid, scenario=r.scenario, horizon=r.horizon, arrival=r.arrival,
+                            action_seed=r.action_seed) for r in reqs]
+
+
+def run_serving(args, emit=True):
+    """A Poisson stream of rollout requests served by continuous batching: the
+    requests share one resident slot batch (one set of launches per step for
+    all in flight), admitted into free slots as they arrive; p50/p99 step
+    latency and aggregate vehicle-updates/s, against serving the same
+    requests one at a time, and with every request available at once (the
+    capacity).  Returns the line (printed when emit)."""
     import torch
     from paper_2406_10661_gb300 import binding, serving
     binding.load()
     t0 = time.perf_counter()
-    reqs = serving.poisson_requests(args.requests, rate_hz=20.0, seed=args.seed)
+    base = serving.poisson_requests(args.requests, rate_hz=20.0, seed=args.seed)
     gen_s = time.perf_counter() - t0
     free, total = torch.cuda.mem_get_info()
     budget = int(min(args.budget_gb * 2 ** 30, 0.8 * free))
-    stats = serving.Server(budget, max_slots=args.slots).run(reqs, realtime=True)
-    seq_reqs = serving.poisson_requests(args.requests, rate_hz=20.0, seed=args.seed)
-    seq = serving.Server(budget, max_slots=1).run(seq_reqs, realtime=False)
-    # capacity: the same requests all available at once (as for the one-at-a-time run)
-    sat_reqs = serving.poisson_requests(args.requests, rate_hz=20.0, seed=args.seed)
+    reqs = _fresh(base)
+    with Clocks(torch.cuda.current_device()) as clk:
+        stats = serving.Server(budget, max_slots=args.slots).run(reqs, realtime=True)
+    sat_reqs = _fresh(base)
     sat = serving.Server(budget, max_slots=args.slots).run(sat_reqs, realtime=False)
-    same = all(a.metrics == b.metrics == c.metrics for a, b, c in zip(reqs, seq_reqs, sat_reqs))
+    seq_reqs = _fresh(base[: args.seq_requests])
+    seq = serving.Server(budget, max_slots=1).run(seq_reqs, realtime=False)
+    same = all(a.metrics == b.metrics for a, b in zip(reqs, sat_reqs)) and \
+        all(a.metrics == b.metrics for a, b in zip(reqs, seq_reqs))
+    sat_head = sum(r.metrics["vehicle_updates"] for r in sat_reqs[: args.seq_requests])
     line = {"metric": "vehicle-updates/s (served)", "value": stats["vehicle_updates_per_s"],
             "unit": "vehicle-updates/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"serving{args.requests}", "arrivals": "Poisson 20/s",
                        "vehicles": "log-uniform 5k-500k", "horizon": "uniform 300-3600 steps",
                        "actions": "signal phases of every junction every 10 steps",
-                       "budget_bytes": budget, "max_slots": args.slots, "generation_s": gen_s},
+                       "budget_bytes": budget, "slots": stats["slots"], "generation_s": gen_s},
             "p50_step_ms": stats["p50_step_ms"], "p99_step_ms": stats["p99_step_ms"],
-            "wall_s": stats["wall_s"], "peak_slots": stats["peak_slots"], "peak_bytes": stats["peak_bytes"],
-            "sequential": {"value": seq["vehicle_updates_per_s"], "p50_step_ms": seq["p50_step_ms"],
-                           "p99_step_ms": seq["p99_step_ms"], "wall_s": seq["wall_s"]},
-            "served_over_sequential": stats["vehicle_updates_per_s"] / max(seq["vehicle_updates_per_s"], 1e-9),
+            "wall_s": stats["wall_s"], "peak_slots": stats["peak_slots"], "device_bytes": stats["peak_bytes"],
+            "batch_steps": stats["slot_steps"], "request_steps": stats["steps"],
+            "how": "one slot batch (moss_slots_create); requests loaded into free slots as they arrive, one "
+                   "set of launches per step for all of them; latency = chunk time / steps",
+            "clocks": clk.summary(),
             "all_at_once": {"value": sat["vehicle_updates_per_s"], "p50_step_ms": sat["p50_step_ms"],
                             "p99_step_ms": sat["p99_step_ms"], "wall_s": sat["wall_s"],
-                            "how": "the same requests all available at once, up to max_slots on the GPU",
-                            "over_sequential": sat["vehicle_updates_per_s"] / max(seq["vehicle_updates_per_s"], 1e-9)},
-            "results_equal_alone_and_mixed": same}
-    print(json.dumps(line), flush=True)
+                            "how": "the same requests all available at once (capacity)"},
+            "sequential": {"value": seq["vehicle_updates_per_s"], "requests": len(seq_reqs),
+                           "p50_step_ms": seq["p50_step_ms"], "wall_s": seq["wall_s"],
+                           "how": f"the first {len(seq_reqs)} requests one at a time (one slot)"},
+            "all_at_once_over_sequential": sat["vehicle_updates_per_s"] / max(seq["vehicle_updates_per_s"], 1e-9),
+            "results_equal_alone_and_mixed": same, "head_updates_all_at_once": sat_head}
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def main():
@@ -677,8 +711,12 @@ def main():
     ap.add_argument("--lane-groups", action="store_true",
                     help="city lanes serve turn groups (left+straight / straight / right+straight)")
     ap.add_argument("--scenarios", type=int, default=64)
-    ap.add_argument("--requests", type=int, default=100)
-    ap.add_argument("--slots", type=int, default=64)
+    ap.add_argument("--requests", type=int, default=300)
+    ap.add_argument("--seq-requests", type=int, default=40,
+                    help="serving: requests served one at a time for the sequential comparison")
+    ap.add_argument("--slots", type=int, default=32)
+    ap.add_argument("--city-only", action="store_true",
+                    help="city workload: leave out the batched and served sub-results")
     ap.add_argument("--budget-gb", type=float, default=64.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

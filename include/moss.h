@@ -297,7 +297,7 @@ int moss_get_metrics(moss_t h, MossMetrics* out);
  * out of range or read without an enqueue; device errors raised by the work
  * before the copy are reported by the read.
  */
-#define MOSS_METRIC_SLOTS 4
+#define MOSS_METRIC_SLOTS 64
 int moss_metrics_enqueue(moss_t h, int scenario, int slot);
 int moss_metrics_read(moss_t h, int slot, MossMetrics* out);
 
@@ -375,6 +375,67 @@ int moss_batch_get_metrics(moss_t h, int scenario, MossMetrics* out);
 int moss_batch_get_state(moss_t h, int scenario, MossState* out);
 int moss_batch_set_signal_phase(moss_t h, int scenario, int n, const int32_t* junction_ids,
                                 const int32_t* phase_idx);
+/* The same for junctions of several scenarios in one call (§3.1 "_batch"
+ * setters: one transfer for many calls): entry k sets junction
+ * junction_ids[k] of scenario scenarios[k] (its own ids) to phase
+ * phase_idx[k].  MOSS_EINVAL if any entry is out of range (nothing is
+ * changed). */
+int moss_batch_set_signal_phases(moss_t h, int n, const int32_t* scenarios, const int32_t* junction_ids,
+                                 const int32_t* phase_idx);
+
+/*
+ * Slot batches: continuous batching for serving rollouts (no counterpart in
+ * the paper; it serves the many concurrent rollouts of the optimisation
+ * loops of §4).  A slot batch is one resident batch of n slots, each with a
+ * fixed capacity; scenarios are loaded into free slots while the others
+ * run, so one set of launches per step (moss_step) advances every scenario
+ * in flight.  An empty, retired or frozen slot does not advance.
+ *
+ * Capacities: a slot takes any scenario with at most n_lanes lanes (road
+ * and junction lanes), n_roads roads, n_junctions junctions, n_phases signal
+ * phases in all, n_vehicles vehicles and n_route_entries route entries, and
+ * without lane groups or lane plans.  The slot also holds one padding lane,
+ * road and junction (isolated, empty) of its own.
+ *
+ * Per-slot calls take the slot index as the scenario index of the batch
+ * calls (moss_batch_get_metrics, moss_batch_get_state,
+ * moss_batch_set_signal_phase, moss_batch_get_lane_queue,
+ * moss_batch_get_road_speed: with the loaded scenario's own ids and sizes).
+ * Lane setters, re-routing, lane plans, signal policies and moss_set_state
+ * are not available on slot batches (MOSS_EINVAL).
+ */
+typedef struct MossSlotCaps {
+    int32_t n_lanes, n_roads, n_junctions, n_phases, n_vehicles, n_route_entries;
+} MossSlotCaps;
+
+/* Create a slot batch of n empty slots with the given capacities; prm gives
+ * the model parameters every loaded scenario must share (seed and scenario
+ * id may differ).  allocator: as for moss_batch_create_with_allocator (NULL:
+ * cudaMalloc).  Errors: MOSS_EINVAL, MOSS_ENOMEM, MOSS_ECUDA. */
+int moss_slots_create(int n, const MossSlotCaps* caps, const MossParams* prm, void* cuda_stream,
+                      const MossAllocator* allocator, moss_t* out);
+
+/* Load a scenario into slot `slot` at its step 0 (every vehicle waiting,
+ * fixed-time signals, metrics zero, random streams from its own seed and
+ * scenario id), to run from the next step.  The slot must be empty, or
+ * retired with at least one moss_step enqueued since (that step removes its
+ * vehicles).  The tables are copied in stream order behind the work already
+ * enqueued, without waiting for it (the host arrays may be freed on return).
+ * MOSS_EINVAL if the scenario is inconsistent, larger than the slot, has
+ * lane groups or plans, or differs in model parameters; the slot is then
+ * left empty. */
+int moss_slot_load(moss_t h, int slot, const MossNetwork* net, const MossVehicles* veh, const MossParams* prm);
+
+/* Retire slot `slot`: the next step removes its vehicles and the slot stops
+ * advancing; enqueue or read its metrics first.  A slot that is empty or
+ * retired already is left as it is.  Asynchronous (stream order). */
+int moss_slot_retire(moss_t h, int slot);
+
+/* Freeze slot `slot` once its own step counter reaches stop_at (its
+ * vehicles, clock, signals and metrics stand still from then on; -1: never),
+ * so that its results at that step can be read while other slots run on.
+ * Asynchronous (stream order).  MOSS_EINVAL for a slot not loaded. */
+int moss_slot_set_horizon(moss_t h, int slot, int64_t stop_at);
 
 /*
  * Kernel timing for measurement: when enabled, every step records CUDA

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libmoss.so")
 
 MOSS_OK, MOSS_EINVAL, MOSS_ENOMEM, MOSS_ECUDA, MOSS_ETIMEOUT, MOSS_EBUDGET, MOSS_EDEVICE = range(7)
 POLICY_FIXED_TIME, POLICY_MANUAL, POLICY_NONE, POLICY_MAX_PRESSURE = 0, 1, 2, 3
-METRIC_SLOTS = 4  # readback slots of metrics_enqueue / metrics_read
+METRIC_SLOTS = 64  # readback slots of metrics_enqueue / metrics_read
 F_FLAGGED, F_CHANGED, F_CANDIDATE, F_TRANSFER, F_ARRIVED, F_INSERTED, F_CONFLICT_LOST = (
     1, 2, 4, 8, 16, 32, 64)
 
@@ -65,6 +65,11 @@ class MossMetrics(ctypes.Structure):
 class MossState(ctypes.Structure):
     _fields_ = [("status", _c_i32p), ("lane", _c_i32p), ("s", _c_f64p), ("v", _c_f64p),
                 ("rc", _c_i32p), ("flags", _c_i32p)]
+
+
+class MossSlotCaps(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in ("n_lanes", "n_roads", "n_junctions", "n_phases", "n_vehicles",
+                                              "n_route_entries")]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -121,6 +126,12 @@ SIGNATURES = {
                                          ctypes.POINTER(MossVehicles), ctypes.POINTER(MossParams),
                                          _vp, ctypes.POINTER(_vp)]),
     "moss_batch_size": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "moss_slots_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(MossSlotCaps), ctypes.POINTER(MossParams),
+                                         _vp, ctypes.POINTER(MossAllocator), ctypes.POINTER(_vp)]),
+    "moss_slot_load": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(MossNetwork), ctypes.POINTER(MossVehicles),
+                                      ctypes.POINTER(MossParams)]),
+    "moss_slot_retire": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "moss_slot_set_horizon": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int64]),
     "moss_batch_create_with_allocator": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(MossNetwork),
                                                         ctypes.POINTER(MossVehicles), ctypes.POINTER(MossParams),
                                                         _vp, ctypes.POINTER(MossAllocator), ctypes.POINTER(_vp)]),
@@ -130,6 +141,7 @@ SIGNATURES = {
     "moss_batch_get_state": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(MossState)]),
     "moss_batch_set_signal_phase": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _c_i32p,
                                                    _c_i32p]),
+    "moss_batch_set_signal_phases": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p, _c_i32p, _c_i32p]),
     "moss_set_kernel_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "moss_kernel_times": (ctypes.c_int, [_vp, _c_f64p, ctypes.POINTER(ctypes.c_int64)]),
     "moss_lane_offsets_noalloc": (ctypes.c_int, [ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -435,3 +447,67 @@ class Batch(_Handle):
         p = np.ascontiguousarray(phases, dtype=np.int32)
         _check(self.lib.moss_batch_set_signal_phase(self.h, int(i), len(j), _ptr(j, ctypes.c_int32),
                                                     _ptr(p, ctypes.c_int32)), self.h)
+
+    def set_signal_phases(self, scenarios, junctions, phases) -> None:
+        """Phases of junctions of several scenarios in one call."""
+        s = np.ascontiguousarray(scenarios, dtype=np.int32)
+        j = np.ascontiguousarray(junctions, dtype=np.int32)
+        p = np.ascontiguousarray(phases, dtype=np.int32)
+        _check(self.lib.moss_batch_set_signal_phases(self.h, len(j), _ptr(s, ctypes.c_int32),
+                                                     _ptr(j, ctypes.c_int32), _ptr(p, ctypes.c_int32)), self.h)
+
+
+def slot_caps(scen) -> Dict[str, int]:
+    """The capacities a slot needs to take scenario `scen` (moss_slot_load)."""
+    net, veh = scen.net, scen.veh
+    nph = int(net.junc_phase_off[net.n_junctions]) if net.n_junctions else 0
+    return {"n_lanes": int(net.n_lanes), "n_roads": int(net.n_roads), "n_junctions": int(net.n_junctions),
+            "n_phases": nph, "n_vehicles": int(veh.n),
+            "n_route_entries": int(veh.route_off[veh.n]) if veh.n else 0}
+
+
+def fits(caps: Dict[str, int], need: Dict[str, int]) -> bool:
+    return all(need[k] <= caps[k] for k in need)
+
+
+class Slots(Batch):
+    """A slot batch (``moss_slots_create``): fixed-capacity slots into which
+    scenarios are loaded while the others run; every ``step`` advances all
+    loaded slots with one set of launches.  The per-slot getters and setters
+    are those of ``Batch`` with the slot index."""
+
+    def __init__(self, caps: List[Dict[str, int]], params, precision: int = 32, stream: Optional[int] = None,
+                 allocator: Optional[MossAllocator] = None):
+        _Handle.__init__(self)
+        k = len(caps)
+        arr = (MossSlotCaps * k)(*[MossSlotCaps(*[int(c[f]) for f, _ in MossSlotCaps._fields_]) for c in caps])
+        p = _prm_struct(params, precision)
+        h = _vp()
+        if allocator is not None:
+            self._allocator = allocator
+        _check(self.lib.moss_slots_create(k, arr, ctypes.byref(p), _vp(stream) if stream else None,
+                                          ctypes.byref(allocator) if allocator is not None else None,
+                                          ctypes.byref(h)))
+        self.h = h
+        self.k = k
+        self.precision = precision
+        self.caps = [dict(c) for c in caps]
+        self.sizes = [0] * k
+        self.nets = [None] * k
+
+    def load(self, slot: int, scen) -> None:
+        keep: list = []
+        n = _net_struct(scen.net, keep)
+        v = _veh_struct(scen.veh, keep)
+        p = _prm_struct(scen.params, self.precision)
+        _check(self.lib.moss_slot_load(self.h, int(slot), ctypes.byref(n), ctypes.byref(v), ctypes.byref(p)), self.h)
+        self.sizes[slot] = int(scen.veh.n)
+        self.nets[slot] = scen.net
+
+    def retire(self, slot: int) -> None:
+        _check(self.lib.moss_slot_retire(self.h, int(slot)), self.h)
+        self.sizes[slot] = 0
+        self.nets[slot] = None
+
+    def set_horizon(self, slot: int, stop_at: int) -> None:
+        _check(self.lib.moss_slot_set_horizon(self.h, int(slot), int(stop_at)), self.h)

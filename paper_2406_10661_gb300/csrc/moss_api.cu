@@ -4,12 +4,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "moss.h"
@@ -30,6 +32,16 @@ struct SnapBufs {
 constexpr int N_STEP_KERNELS = 4;  // decide, resolve, lanescan, place (launch order)
 
 }  // namespace
+
+// a slot of a slot batch: first index and capacity of its lanes, roads,
+// junctions, phases, junction-lane entries (jj), vehicles, route entries and
+// start-lane entries (SO, one per lane)
+struct SlotInfo {
+    int LO = 0, nl_cap = 0, RO = 0, nr_cap = 0, JO = 0, nj_cap = 0, PO = 0, np_cap = 0;
+    int JJ = 0, njj_cap = 0, VO = 0, nv_cap = 0, QO = 0, nq_cap = 0, SO = 0;
+    bool loaded = false, retired = false;
+    long long retire_step = 0;  // steps enqueued when it was retired
+};
 
 struct MossHandle {
     int precision = 32;
@@ -53,6 +65,16 @@ struct MossHandle {
     std::vector<float> v0f;
     std::vector<int32_t> q_off, q_ids, start_lanes;
     std::vector<int32_t> scen_veh_off, scen_lane_off, scen_junc_off;
+    std::vector<int> scen_nv, scen_nl, scen_nj, scen_nr;  // vehicles, lanes, junctions, roads in use per scenario
+    std::vector<int32_t> junc_offset, phase_green, phase_amber;
+    std::vector<int32_t> jj_off, jj_lane, jj_from;  // junction lanes grouped by junction (CSR)
+    std::vector<int32_t> q_head;                     // initial departure-queue heads
+    bool slots = false;                              // a slot batch (moss_slots_create)
+    char* h_load = nullptr;                          // pinned staging of slot loads
+    size_t load_cap = 0;
+    cudaEvent_t load_free = nullptr;                 // recorded after the last copy out of h_load
+    std::vector<SlotInfo> slot;
+    long long steps_enqueued = 0;
     std::vector<uint32_t> key0, key1;
 
     // ---- device
@@ -83,6 +105,8 @@ struct MossHandle {
     uint32_t *d_key0 = nullptr, *d_key1 = nullptr;
     int32_t* d_veh_base = nullptr;
     long long *d_step = nullptr, *d_metrics = nullptr;
+    int32_t* d_scen_ctl = nullptr;    // per scenario: SC_FROZEN / SC_RETIRE
+    long long* d_stop_at = nullptr;   // per scenario: step at which it freezes (-1: never)
     SnapBufs snap[2]{};
     int8_t* d_code = nullptr;
     void* d_stay = nullptr;  // SV<Real>[cap]
@@ -171,6 +195,21 @@ int upload(MossHandle* h, T** p, const std::vector<T>& v) {
     return MOSS_OK;
 }
 
+// fn(i0, i1) over [0, n) in contiguous chunks on the host's threads (large n)
+template <typename F>
+void parallel_for(long long n, F fn) {
+    const int hw = (int)std::thread::hardware_concurrency();
+    const int T = n < (1 << 16) ? 1 : std::max(1, std::min(hw, 32));
+    if (T == 1) { fn(0ll, n); return; }
+    std::vector<std::thread> th;
+    const long long per = (n + T - 1) / T;
+    for (int t = 0; t < T; ++t) {
+        const long long a = t * per, b = std::min(n, a + per);
+        if (a < b) th.emplace_back([=] { fn(a, b); });
+    }
+    for (auto& x : th) x.join();
+}
+
 #define TRY(call)              \
     do {                       \
         int r_ = (call);       \
@@ -231,7 +270,8 @@ int validate(MossHandle* h, const MossNetwork* net, const MossVehicles* veh, con
     }
     // out-roads reachable from some lane of each road (a vehicle on a lane
     // without access changes lanes towards the group that has it, R27)
-    road_out->assign(R, {});
+    // (a flat CSR: the route check below is the hot loop of validation)
+    std::vector<int32_t> ro_off(R + 1, 0), ro;
     for (int r = 0; r < R; ++r) {
         std::vector<int32_t> common;
         for (int l = net->road_lane_off[r]; l < net->road_lane_off[r + 1]; ++l) {
@@ -245,29 +285,53 @@ int validate(MossHandle* h, const MossNetwork* net, const MossVehicles* veh, con
             std::set_union(common.begin(), common.end(), outs.begin(), outs.end(), std::back_inserter(x));
             common.swap(x);
         }
-        (*road_out)[r] = common;
+        ro.insert(ro.end(), common.begin(), common.end());
+        ro_off[r + 1] = (int32_t)ro.size();
     }
+    (void)road_out;
     const int N = veh->n;
     if (N < 0 || N >= (1 << 30)) return fail(h, MOSS_EINVAL, "vehicle count out of range");
     if (N > 0 && (!veh->route_off || !veh->routes || !veh->start_lane || !veh->dep || !veh->v0f))
         return fail(h, MOSS_EINVAL, "missing vehicle array");
     if (N > 0 && veh->route_off[0] != 0) return fail(h, MOSS_EINVAL, "route_off[0] != 0");
-    for (int i = 0; i < N; ++i) {
+    // the vehicles in parallel chunks; the first failing vehicle is reported
+    // (code 1..6 of the checks below)
+    auto check = [&](int i) -> int {
         const int a = veh->route_off[i], b = veh->route_off[i + 1];
-        if (b <= a) return fail(h, MOSS_EINVAL, "every route needs at least one road");
+        if (b <= a) return 1;
         for (int k = a; k < b; ++k)
-            if (veh->routes[k] < 0 || veh->routes[k] >= R) return fail(h, MOSS_EINVAL, "route road out of range");
+            if (veh->routes[k] < 0 || veh->routes[k] >= R) return 2;
         for (int k = a; k + 1 < b; ++k) {
-            const auto& o = (*road_out)[veh->routes[k]];
-            if (!std::binary_search(o.begin(), o.end(), veh->routes[k + 1]))
-                return fail(h, MOSS_EINVAL, "route of vehicle " + std::to_string(i) +
-                                                " uses a turn no lane of the road has");
+            const int32_t* ob = ro.data() + ro_off[veh->routes[k]];
+            const int32_t* oe = ro.data() + ro_off[veh->routes[k] + 1];
+            if (!std::binary_search(ob, oe, veh->routes[k + 1])) return 3;
         }
         const int sl = veh->start_lane[i];
-        if (sl < 0 || sl >= NRL || road_of[sl] != veh->routes[a])
-            return fail(h, MOSS_EINVAL, "start lane must be a lane of the first road");
-        if (veh->dep[i] < 0) return fail(h, MOSS_EINVAL, "negative departure step");
-        if (!(veh->v0f[i] > 0.f) || !std::isfinite(veh->v0f[i])) return fail(h, MOSS_EINVAL, "v0f must be > 0");
+        if (sl < 0 || sl >= NRL || road_of[sl] != veh->routes[a]) return 4;
+        if (veh->dep[i] < 0) return 5;
+        if (!(veh->v0f[i] > 0.f) || !std::isfinite(veh->v0f[i])) return 6;
+        return 0;
+    };
+    std::atomic<long long> bad{(long long)N};
+    parallel_for(N, [&](long long i0, long long i1) {
+        for (long long i = i0; i < i1 && i < bad.load(std::memory_order_relaxed); ++i)
+            if (check((int)i)) {
+                long long cur = bad.load();
+                while (i < cur && !bad.compare_exchange_weak(cur, i)) {}
+                return;
+            }
+    });
+    if (bad.load() < N) {
+        const int i = (int)bad.load();
+        switch (check(i)) {
+            case 1: return fail(h, MOSS_EINVAL, "every route needs at least one road");
+            case 2: return fail(h, MOSS_EINVAL, "route road out of range");
+            case 3: return fail(h, MOSS_EINVAL, "route of vehicle " + std::to_string(i) +
+                                                    " uses a turn no lane of the road has");
+            case 4: return fail(h, MOSS_EINVAL, "start lane must be a lane of the first road");
+            case 5: return fail(h, MOSS_EINVAL, "negative departure step");
+            default: return fail(h, MOSS_EINVAL, "v0f must be > 0");
+        }
     }
     return MOSS_OK;
 }
@@ -299,6 +363,7 @@ Ctx<Real> make_ctx(MossHandle* h, int cur) {
     c.q_off = h->d_q_off; c.q_ids = h->d_q_ids; c.q_head = h->d_q_head;
     c.start_lanes = h->d_start_lanes; c.n_start = (int)h->start_lanes.size();
     c.key0 = h->d_key0; c.key1 = h->d_key1; c.veh_base = h->d_veh_base; c.scen_step = h->d_step;
+    c.scen_ctl = h->d_scen_ctl; c.stop_at = h->d_stop_at;
     c.metrics = h->d_metrics;
     for (int k = 0; k < 2; ++k) {
         const SnapBufs& b = h->snap[k == 0 ? cur : 1 - cur];
@@ -364,16 +429,17 @@ void enqueue(MossHandle* h, int cur, bool timed) {
 }
 
 template <typename Real>
-void enqueue_junction_init(MossHandle* h) {
+void enqueue_junction_init(MossHandle* h, int j0, int j1) {
     Ctx<Real> c = make_ctx<Real>(h, h->parity);
-    const int nb = std::max(1, std::min((h->n_junctions + 255) / 256, h->sm_count * 4));
-    k_junction_init<Real><<<nb, 256, 0, h->stream>>>(c);
+    const int nb = std::max(1, std::min((j1 - j0 + 255) / 256, h->sm_count * 4));
+    k_junction_init<Real><<<nb, 256, 0, h->stream>>>(c, j0, j1);
 }
 
-int junction_init(MossHandle* h) {
-    if (h->n_junctions == 0) return MOSS_OK;
-    if (h->precision == 64) enqueue_junction_init<double>(h);
-    else enqueue_junction_init<float>(h);
+// signal states of the current step of junctions [j0, j1)
+int junction_init(MossHandle* h, int j0, int j1) {
+    if (j1 <= j0) return MOSS_OK;
+    if (h->precision == 64) enqueue_junction_init<double>(h, j0, j1);
+    else enqueue_junction_init<float>(h, j0, j1);
     CK(cudaGetLastError());
     return MOSS_OK;
 }
@@ -434,94 +500,63 @@ int check_device(MossHandle* h) {
 }
 
 // ---- create (n scenarios as one union network) ------------------------------
-int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const MossParams* prms,
-                void* stream, MossHandle* h) {
-    if (n < 1) return fail(h, MOSS_EINVAL, "need at least one scenario");
-    if (n > 65535) return fail(h, MOSS_EINVAL, "at most 65535 scenarios in a batch");
-    h->prm = prms[0];
-    h->precision = prms[0].precision;
-    h->n_scen = n;
-    for (int k = 1; k < n; ++k)
-        if (!same_model(prms[0], prms[k]))
-            return fail(h, MOSS_EINVAL, "batched scenarios must share the model parameters");
-    long long tot_lanes = 0, tot_j = 0, tot_v = 0, tot_routes = 0, tot_ph = 0, tot_roads = 0;
-    std::vector<std::vector<std::vector<int32_t>>> outs(n);
-    for (int k = 0; k < n; ++k) {
-        TRY(validate(h, &nets[k], &vehs[k], &prms[k], &outs[k]));
-        tot_lanes += nets[k].n_lanes; tot_j += nets[k].n_junctions; tot_v += vehs[k].n;
-        tot_routes += vehs[k].n ? vehs[k].route_off[vehs[k].n] : 0;
-        tot_ph += nets[k].n_junctions ? nets[k].junc_phase_off[nets[k].n_junctions] : 0;
-        tot_roads += nets[k].n_roads;
+
+// the host tables of scenario k written at the given bases (first lane,
+// junction, vehicle, road, phase and route entry of the scenario)
+void fill_scenario(MossHandle* h, int k, const MossNetwork& nt, const MossVehicles& vh, const MossParams& pr,
+                   int LO, int JO, int VO, int RO, int PO, int ROFF) {
+    const int NRL = nt.n_road_lanes;
+    std::vector<int32_t> road_of(NRL);
+    for (int r = 0; r < nt.n_roads; ++r)
+        for (int l = nt.road_lane_off[r]; l < nt.road_lane_off[r + 1]; ++l) road_of[l] = r;
+    for (int l = 0; l < nt.n_lanes; ++l) {
+        LaneInfo& li = h->lanes[LO + l];
+        li.scen = k;
+        li.flags = 0;
+        li.L = nt.lane_length[l];
+        li.vmax = nt.lane_vmax[l];
+        if (l < NRL) {
+            const int r = road_of[l];
+            li.lo = LO + nt.road_lane_off[r];
+            li.hi = LO + nt.road_lane_off[r + 1];
+            li.jb = LO + nt.jl_off[l];
+            li.je = LO + nt.jl_off[l + 1];
+            li.road = RO + r;
+        } else {
+            const int q = l - NRL;
+            li.lo = -1;
+            li.hi = LO + nt.jl_target[q];
+            li.jb = JO + nt.jl_junction[q];
+            li.je = nt.jl_mask[q];
+            li.road = RO + road_of[nt.jl_target[q]];
+        }
+        h->lane_src_road[LO + l] = -1;
+        h->jl_plans[LO + l] = 0xff;
     }
-    if (tot_lanes >= (1ll << 30) || tot_v >= (1ll << 30) || tot_routes >= (1ll << 31) - 1 ||
-        tot_roads >= (1ll << 30))
-        return fail(h, MOSS_EINVAL, "batch too large for 32-bit indices");
-    h->n_lanes = (int)tot_lanes; h->n_junctions = (int)tot_j; h->n_veh = (int)tot_v;
-    h->n_phases = (int)tot_ph;
-    const int NL = h->n_lanes, NJ = h->n_junctions, NV = h->n_veh;
-    h->lanes.resize(NL);
-    h->lane_src_road.assign(NL, -1);
-    h->junc_scen.resize(NJ); h->junc_phase_off.resize(NJ + 1);
-    std::vector<int32_t> junc_offset(NJ), phase_green(tot_ph), phase_amber(tot_ph);
-    h->route_span.resize(NV); h->routes.resize(tot_routes); h->dep.resize(NV);
-    h->start_lane.resize(NV); h->v0f.resize(NV); h->veh_scen.resize(NV);
-    h->scen_veh_off.assign(n + 1, 0); h->scen_lane_off.assign(n + 1, 0); h->scen_junc_off.assign(n + 1, 0);
-    h->scen_road_off.assign(n + 1, 0);
-    h->jl_plans.assign(tot_lanes, 0xff);
-    h->road_span.assign(tot_roads, make_int2(0, 0));
-    h->key0.resize(n); h->key1.resize(n);
-    int LO = 0, JO = 0, VO = 0, RO = 0, PO = 0, ROFF = 0;
-    for (int k = 0; k < n; ++k) {
-        const MossNetwork& nt = nets[k];
-        const MossVehicles& vh = vehs[k];
-        const int NRL = nt.n_road_lanes;
-        std::vector<int32_t> road_of(NRL);
-        for (int r = 0; r < nt.n_roads; ++r)
-            for (int l = nt.road_lane_off[r]; l < nt.road_lane_off[r + 1]; ++l) road_of[l] = r;
-        for (int l = 0; l < nt.n_lanes; ++l) {
-            LaneInfo& li = h->lanes[LO + l];
-            li.scen = k;
-            li.L = nt.lane_length[l];
-            li.vmax = nt.lane_vmax[l];
-            if (l < NRL) {
-                const int r = road_of[l];
-                li.lo = LO + nt.road_lane_off[r];
-                li.hi = LO + nt.road_lane_off[r + 1];
-                li.jb = LO + nt.jl_off[l];
-                li.je = LO + nt.jl_off[l + 1];
-                li.road = RO + r;
-            } else {
-                const int q = l - NRL;
-                li.lo = -1;
-                li.hi = LO + nt.jl_target[q];
-                li.jb = JO + nt.jl_junction[q];
-                li.je = nt.jl_mask[q];
-                li.road = RO + road_of[nt.jl_target[q]];
-            }
+    for (int l = 0; l < NRL; ++l)
+        for (int j = nt.jl_off[l]; j < nt.jl_off[l + 1]; ++j) h->lane_src_road[LO + j] = RO + road_of[l];
+    for (int r = 0; r < nt.n_roads; ++r)
+        h->road_span[RO + r] = make_int2(LO + nt.road_lane_off[r], LO + nt.road_lane_off[r + 1]);
+    if (nt.jl_plans) {
+        h->lane_groups = true;  // a plan can take a turn away from some lanes
+        for (int q = 0; q < nt.n_lanes - NRL; ++q) {
+            h->jl_plans[LO + NRL + q] = nt.jl_plans[q];
+            if (!(nt.jl_plans[q] & 1)) h->lanes[LO + NRL + q].flags |= LF_OFF;  // roads start in plan 0
         }
-        for (int l = 0; l < NRL; ++l)
-            for (int j = nt.jl_off[l]; j < nt.jl_off[l + 1]; ++j) h->lane_src_road[LO + j] = RO + road_of[l];
-        for (int r = 0; r < nt.n_roads; ++r)
-            h->road_span[RO + r] = make_int2(LO + nt.road_lane_off[r], LO + nt.road_lane_off[r + 1]);
-        if (nt.jl_plans) {
-            h->lane_groups = true;  // a plan can take a turn away from some lanes
-            for (int q = 0; q < nt.n_lanes - NRL; ++q) {
-                h->jl_plans[LO + NRL + q] = nt.jl_plans[q];
-                if (!(nt.jl_plans[q] & 1)) h->lanes[LO + NRL + q].flags |= LF_OFF;  // roads start in plan 0
-            }
-        }
-        for (int j = 0; j < nt.n_junctions; ++j) {
-            h->junc_scen[JO + j] = k;
-            junc_offset[JO + j] = nt.junc_offset[j];
-            h->junc_phase_off[JO + j] = PO + nt.junc_phase_off[j];
-        }
-        const int nph = nt.n_junctions ? nt.junc_phase_off[nt.n_junctions] : 0;
-        for (int q = 0; q < nph; ++q) {
-            phase_green[PO + q] = nt.phase_green[q];
-            phase_amber[PO + q] = nt.phase_amber[q];
-        }
-        for (int i = 0; i < vh.n; ++i) {
-            const int g = VO + i;
+    }
+    for (int j = 0; j < nt.n_junctions; ++j) {
+        h->junc_scen[JO + j] = k;
+        h->junc_offset[JO + j] = nt.junc_offset[j];
+        h->junc_phase_off[JO + j] = PO + nt.junc_phase_off[j];
+    }
+    const int nph = nt.n_junctions ? nt.junc_phase_off[nt.n_junctions] : 0;
+    for (int q = 0; q < nph; ++q) {
+        h->phase_green[PO + q] = nt.phase_green[q];
+        h->phase_amber[PO + q] = nt.phase_amber[q];
+    }
+    parallel_for(vh.n, [&](long long i0, long long i1) {
+        for (long long i = i0; i < i1; ++i) {
+            const int g = VO + (int)i;
             const int a = vh.route_off[i], b = vh.route_off[i + 1];
             for (int q = a; q < b; ++q) h->routes[ROFF + q] = RO + vh.routes[q];
             h->route_span[g] = make_int2(ROFF + a, ROFF + b);
@@ -530,44 +565,83 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
             h->v0f[g] = vh.v0f[i];
             h->veh_scen[g] = k;
         }
-        h->key0[k] = (uint32_t)(prms[k].seed & 0xffffffffull);
-        h->key1[k] = (uint32_t)(prms[k].seed >> 32) ^ prms[k].scenario;
-        ROFF += vh.n ? vh.route_off[vh.n] : 0;
-        LO += nt.n_lanes; JO += nt.n_junctions; VO += vh.n; RO += nt.n_roads; PO += nph;
-        h->scen_veh_off[k + 1] = VO; h->scen_lane_off[k + 1] = LO; h->scen_junc_off[k + 1] = JO;
-        h->scen_road_off[k + 1] = RO;
-    }
-    h->junc_phase_off[NJ] = PO;
-    // departure queues per start lane ordered by (dep, id) (R18)
-    h->q_off.assign(NL + 1, 0);
-    for (int i = 0; i < NV; ++i) h->q_off[h->start_lane[i] + 1]++;
-    for (int l = 0; l < NL; ++l) h->q_off[l + 1] += h->q_off[l];
-    h->q_ids.resize(NV);
-    {
-        std::vector<int32_t> fill(h->q_off.begin(), h->q_off.end() - 1);
-        for (int i = 0; i < NV; ++i) h->q_ids[fill[h->start_lane[i]]++] = i;
-        for (int l = 0; l < NL; ++l)
-            std::stable_sort(h->q_ids.begin() + h->q_off[l], h->q_ids.begin() + h->q_off[l + 1],
-                             [&](int a, int b) { return h->dep[a] < h->dep[b]; });
-    }
-    h->start_lanes.clear();
-    for (int l = 0; l < NL; ++l)
-        if (h->q_off[l + 1] > h->q_off[l]) h->start_lanes.push_back(l);
+    });
+    h->key0[k] = (uint32_t)(pr.seed & 0xffffffffull);
+    h->key1[k] = (uint32_t)(pr.seed >> 32) ^ pr.scenario;
+}
 
-    // lane groups: a road with a turn not served by all of its lanes
-    for (size_t r = 0; r < h->road_span.size() && !h->lane_groups; ++r) {
+// network of a road with a turn that not all of its lanes serve (R27)
+bool has_lane_groups(const MossHandle* h, int r0, int r1) {
+    for (int r = r0; r < r1; ++r) {
         const int2 sp = h->road_span[r];
-        std::vector<int> all, first;
+        std::vector<int> first;
         for (int l = sp.x; l < sp.y; ++l) {
             std::vector<int> outs;
             for (int j = h->lanes[l].jb; j < h->lanes[l].je; ++j) outs.push_back(h->lanes[j].road);
             std::sort(outs.begin(), outs.end());
             if (l == sp.x) first = outs;
-            else if (outs != first) h->lane_groups = true;
+            else if (outs != first) return true;
         }
     }
+    return false;
+}
 
-    // ---- device
+// departure queues of the vehicles [v0, v1) on the lanes [l0, l1): the CSR
+// q_off[l0 .. l1] from q_base on, ordered by (dep, id) (R18); every lane
+// after the last one with vehicles is empty, the last lane's range ends at
+// q_end (entries past the vehicles are never reached: q_head starts there)
+void build_queues(MossHandle* h, int l0, int l1, int v0, int v1, int q_base, int q_end) {
+    for (int l = l0; l <= l1; ++l) h->q_off[l] = 0;
+    for (int i = v0; i < v1; ++i) h->q_off[h->start_lane[i] + 1]++;
+    h->q_off[l0] = q_base;
+    for (int l = l0; l < l1; ++l) h->q_off[l + 1] += h->q_off[l];
+    std::vector<int32_t> fill(h->q_off.begin() + l0, h->q_off.begin() + l1);
+    for (int i = v0; i < v1; ++i) h->q_ids[fill[h->start_lane[i] - l0]++] = i;
+    for (int l = l0; l < l1; ++l) {
+        std::stable_sort(h->q_ids.begin() + h->q_off[l], h->q_ids.begin() + h->q_off[l + 1],
+                         [&](int a, int b) { return h->dep[a] < h->dep[b]; });
+        h->q_head[l] = h->q_off[l];
+    }
+    // entries past the vehicles belong to the last lane (a padding lane of a
+    // slot, with no vehicles of its own) and are never reached: its queue
+    // head starts at their end
+    if (q_end > h->q_off[l1]) {
+        for (int q = h->q_off[l1]; q < q_end; ++q) h->q_ids[q] = q_base;
+        h->q_head[l1 - 1] = q_end;
+    }
+    h->q_off[l1] = q_end;
+}
+
+// junction lanes of the junctions [j0, j1) (lanes [l0, l1)) grouped by
+// junction from jj_base on, with the road lane each one leaves (the
+// pressures of the max-pressure policy); the last junction's range ends at
+// jj_end (padding entries name lane pad, a road lane, which adds nothing)
+void build_jj(MossHandle* h, int j0, int j1, int l0, int l1, int jj_base, int jj_end, int pad) {
+    for (int j = j0; j <= j1; ++j) h->jj_off[j] = 0;
+    std::vector<int32_t> from(l1 - l0, -1);
+    for (int l = l0; l < l1; ++l)
+        if (h->lanes[l].lo >= 0)
+            for (int q = h->lanes[l].jb; q < h->lanes[l].je; ++q) from[q - l0] = l;
+    for (int l = l0; l < l1; ++l)
+        if (h->lanes[l].lo < 0) h->jj_off[h->lanes[l].jb + 1]++;
+    h->jj_off[j0] = jj_base;
+    for (int j = j0; j < j1; ++j) h->jj_off[j + 1] += h->jj_off[j];
+    std::vector<int32_t> fill(h->jj_off.begin() + j0, h->jj_off.begin() + j1);
+    for (int l = l0; l < l1; ++l)
+        if (h->lanes[l].lo < 0) {
+            const int q = fill[h->lanes[l].jb - j0]++;
+            h->jj_lane[q] = l;
+            h->jj_from[q] = from[l - l0];
+        }
+    for (int q = h->jj_off[j1]; q < jj_end; ++q) { h->jj_lane[q] = pad; h->jj_from[q] = pad; }
+    h->jj_off[j1] = jj_end;
+}
+
+// device buffers and graphs for the host tables of h (shared by batches and
+// slot batches)
+int device_setup(MossHandle* h, void* stream) {
+    const int NL = h->n_lanes, NJ = h->n_junctions, NV = h->n_veh, n = h->n_scen;
+    const long long tot_roads = (long long)h->road_span.size();
     if (stream) {
         h->stream = (cudaStream_t)stream;
     } else {
@@ -579,55 +653,45 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
     TRY(upload(h, &h->d_lane, h->lanes));
     std::vector<JuncInfo> junc(NJ);
     for (int j = 0; j < NJ; ++j) {
-        junc[j].offset = junc_offset[j];
+        junc[j].offset = h->junc_offset[j];
         junc[j].phase_off = h->junc_phase_off[j];
         junc[j].np = h->junc_phase_off[j + 1] - h->junc_phase_off[j];
         junc[j].scen = h->junc_scen[j];
     }
+    // a slot's padding junction holds its spare phases but has no signal
+    for (const SlotInfo& si : h->slot) junc[si.JO + si.nj_cap - 1].np = 0;
     TRY(upload(h, &h->d_junc, junc));
-    TRY(upload(h, &h->d_phase_green, phase_green));
-    TRY(upload(h, &h->d_phase_amber, phase_amber));
+    TRY(upload(h, &h->d_phase_green, h->phase_green));
+    TRY(upload(h, &h->d_phase_amber, h->phase_amber));
     TRY(upload(h, &h->d_junc_policy, std::vector<int32_t>(NJ, POL_FIXED)));
     TRY(upload(h, &h->d_junc_manual, std::vector<int32_t>(NJ, 0)));
     TRY(dalloc(h, &h->d_junc_state, NJ));
+    TRY(upload(h, &h->d_jj_off, h->jj_off));
     {
-        // junction lanes of every junction with the road lane each one leaves
-        // (the pressures of the max-pressure policy)
-        std::vector<int32_t> from(NL, -1), jj_off(NJ + 1, 0);
-        for (int l = 0; l < NL; ++l)
-            if (h->lanes[l].lo >= 0)
-                for (int q = h->lanes[l].jb; q < h->lanes[l].je; ++q) from[q] = l;
-        for (int l = 0; l < NL; ++l)
-            if (h->lanes[l].lo < 0) jj_off[h->lanes[l].jb + 1]++;
-        for (int j = 0; j < NJ; ++j) jj_off[j + 1] += jj_off[j];
-        std::vector<int32_t> jj_lane(std::max(jj_off[NJ], 1)), jj_from(std::max(jj_off[NJ], 1));
-        std::vector<int32_t> fill(jj_off.begin(), jj_off.end() - 1);
-        for (int l = 0; l < NL; ++l)
-            if (h->lanes[l].lo < 0) {
-                const int q = fill[h->lanes[l].jb]++;
-                jj_lane[q] = l;
-                jj_from[q] = from[l];
-            }
-        TRY(upload(h, &h->d_jj_off, jj_off));
-        TRY(upload(h, &h->d_jj_lane, jj_lane));
-        TRY(upload(h, &h->d_jj_from, jj_from));
-        TRY(upload(h, &h->d_mp, std::vector<int4>(std::max(NJ, 1), make_int4(0, 1, -1, 0))));
-        TRY(upload(h, &h->d_mp_press, std::vector<int32_t>((size_t)std::max(NJ, 1) * 8, 0)));
+        std::vector<int32_t> a(h->jj_lane), b(h->jj_from);
+        if (a.empty()) { a.push_back(0); b.push_back(0); }
+        TRY(upload(h, &h->d_jj_lane, a));
+        TRY(upload(h, &h->d_jj_from, b));
+    }
+    h->n_jj = h->jj_off[NJ];
+    TRY(upload(h, &h->d_mp, std::vector<int4>(std::max(NJ, 1), make_int4(0, 1, -1, 0))));
+    TRY(upload(h, &h->d_mp_press, std::vector<int32_t>((size_t)std::max(NJ, 1) * 8, 0)));
+    {
         std::vector<int2> span(h->road_span);
         if (span.empty()) span.push_back(make_int2(0, 0));
         TRY(upload(h, &h->d_road_span, span));
-        TRY(dalloc(h, &h->d_lstage, 2 * (size_t)std::max(NL, 1)));
-        TRY(upload(h, &h->d_jl_plans, h->jl_plans.empty() ? std::vector<int32_t>(1, 0xff) : h->jl_plans));
-        TRY(upload(h, &h->d_road_mark, std::vector<int8_t>(std::max<long long>(tot_roads, 1), 0)));
-        TRY(dalloc(h, (char**)&h->d_mbuf, sizeof(double) * (size_t)std::max(std::max(NL, (int)tot_roads), 1)));
-        h->n_jj = jj_off[NJ];
     }
+    TRY(dalloc(h, &h->d_lstage, 2 * (size_t)std::max(NL, 1)));
+    TRY(upload(h, &h->d_jl_plans, h->jl_plans.empty() ? std::vector<int32_t>(1, 0xff) : h->jl_plans));
+    TRY(upload(h, &h->d_road_mark, std::vector<int8_t>(std::max<long long>(tot_roads, 1), 0)));
+    TRY(dalloc(h, (char**)&h->d_mbuf, sizeof(double) * (size_t)std::max(std::max(NL, (int)tot_roads), 1)));
     {
         std::vector<int2> span(h->route_span);
         if (span.empty()) span.push_back(make_int2(0, 0));
         TRY(upload(h, &h->d_route_span, span));
         // room for re-routed vehicles' routes (grown on demand)
-        h->routes_cap = h->routes.size() + std::max<size_t>(h->routes.size() / 4, 1 << 16);
+        if (!h->slots) h->routes_cap = h->routes.size() + std::max<size_t>(h->routes.size() / 4, 1 << 16);
+        else h->routes_cap = std::max<size_t>(h->routes.size(), 1);
         TRY(dalloc(h, &h->d_routes, h->routes_cap));
         if (!h->routes.empty())
             CK(cudaMemcpy(h->d_routes, h->routes.data(), h->routes.size() * 4, cudaMemcpyHostToDevice));
@@ -639,13 +703,15 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
     TRY(upload(h, &h->d_vflags, std::vector<int32_t>(NV, 0)));
     TRY(upload(h, &h->d_q_off, h->q_off));
     TRY(upload(h, &h->d_q_ids, h->q_ids));
-    TRY(upload(h, &h->d_q_head, std::vector<int32_t>(h->q_off.begin(), h->q_off.end() - 1)));
+    TRY(upload(h, &h->d_q_head, h->q_head));
     TRY(upload(h, &h->d_start_lanes, h->start_lanes));
     TRY(upload(h, &h->d_key0, h->key0));
     TRY(upload(h, &h->d_key1, h->key1));
     TRY(upload(h, &h->d_veh_base, std::vector<int32_t>(h->scen_veh_off.begin(), h->scen_veh_off.end() - 1)));
     TRY(upload(h, &h->d_step, std::vector<long long>(n, 0)));
     TRY(upload(h, &h->d_metrics, std::vector<long long>((size_t)n * M_NFIELDS, 0)));
+    TRY(upload(h, &h->d_scen_ctl, std::vector<int32_t>(n, h->slots ? SC_FROZEN : 0)));
+    TRY(upload(h, &h->d_stop_at, std::vector<long long>(n, -1)));
     const size_t cap = std::max(NV, 1);
     const size_t ra = reca_size(h->precision);
     for (int k = 0; k < 2; ++k) {
@@ -686,10 +752,312 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
         CK(cudaEventCreateWithFlags(&h->rb_ev[k], cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&h->stage_free, cudaEventDisableTiming));
     CK(cudaEventRecord(h->stage_free, h->stream));
+    CK(cudaEventCreateWithFlags(&h->load_free, cudaEventDisableTiming));
+    CK(cudaEventRecord(h->load_free, h->stream));
     for (int k = 0; k <= N_STEP_KERNELS; ++k) CK(cudaEventCreate(&h->ev[k]));
-    TRY(junction_init(h));
+    TRY(junction_init(h, 0, NJ));
     CK(cudaStreamSynchronize(h->stream));
     TRY(build_graphs(h));
+    return MOSS_OK;
+}
+
+int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const MossParams* prms,
+                void* stream, MossHandle* h) {
+    if (n < 1) return fail(h, MOSS_EINVAL, "need at least one scenario");
+    if (n > 65535) return fail(h, MOSS_EINVAL, "at most 65535 scenarios in a batch");
+    h->prm = prms[0];
+    h->precision = prms[0].precision;
+    h->n_scen = n;
+    for (int k = 1; k < n; ++k)
+        if (!same_model(prms[0], prms[k]))
+            return fail(h, MOSS_EINVAL, "batched scenarios must share the model parameters");
+    long long tot_lanes = 0, tot_j = 0, tot_v = 0, tot_routes = 0, tot_ph = 0, tot_roads = 0;
+    std::vector<std::vector<std::vector<int32_t>>> outs(n);
+    for (int k = 0; k < n; ++k) {
+        TRY(validate(h, &nets[k], &vehs[k], &prms[k], &outs[k]));
+        tot_lanes += nets[k].n_lanes; tot_j += nets[k].n_junctions; tot_v += vehs[k].n;
+        tot_routes += vehs[k].n ? vehs[k].route_off[vehs[k].n] : 0;
+        tot_ph += nets[k].n_junctions ? nets[k].junc_phase_off[nets[k].n_junctions] : 0;
+        tot_roads += nets[k].n_roads;
+    }
+    if (tot_lanes >= (1ll << 30) || tot_v >= (1ll << 30) || tot_routes >= (1ll << 31) - 1 ||
+        tot_roads >= (1ll << 30))
+        return fail(h, MOSS_EINVAL, "batch too large for 32-bit indices");
+    h->n_lanes = (int)tot_lanes; h->n_junctions = (int)tot_j; h->n_veh = (int)tot_v;
+    h->n_phases = (int)tot_ph;
+    const int NL = h->n_lanes, NJ = h->n_junctions, NV = h->n_veh;
+    h->lanes.resize(NL);
+    h->lane_src_road.assign(NL, -1);
+    h->junc_scen.resize(NJ); h->junc_phase_off.resize(NJ + 1);
+    h->junc_offset.assign(NJ, 0); h->phase_green.assign(tot_ph, 0); h->phase_amber.assign(tot_ph, 0);
+    h->route_span.resize(NV); h->routes.resize(tot_routes); h->dep.resize(NV);
+    h->start_lane.resize(NV); h->v0f.resize(NV); h->veh_scen.resize(NV);
+    h->scen_veh_off.assign(n + 1, 0); h->scen_lane_off.assign(n + 1, 0); h->scen_junc_off.assign(n + 1, 0);
+    h->scen_road_off.assign(n + 1, 0);
+    h->scen_nv.assign(n, 0); h->scen_nl.assign(n, 0); h->scen_nj.assign(n, 0); h->scen_nr.assign(n, 0);
+    h->jl_plans.assign(tot_lanes, 0xff);
+    h->road_span.assign(tot_roads, make_int2(0, 0));
+    h->key0.resize(n); h->key1.resize(n);
+    int LO = 0, JO = 0, VO = 0, RO = 0, PO = 0, ROFF = 0;
+    for (int k = 0; k < n; ++k) {
+        const MossNetwork& nt = nets[k];
+        const MossVehicles& vh = vehs[k];
+        fill_scenario(h, k, nt, vh, prms[k], LO, JO, VO, RO, PO, ROFF);
+        const int nph = nt.n_junctions ? nt.junc_phase_off[nt.n_junctions] : 0;
+        ROFF += vh.n ? vh.route_off[vh.n] : 0;
+        h->scen_nv[k] = vh.n; h->scen_nl[k] = nt.n_lanes; h->scen_nj[k] = nt.n_junctions; h->scen_nr[k] = nt.n_roads;
+        LO += nt.n_lanes; JO += nt.n_junctions; VO += vh.n; RO += nt.n_roads; PO += nph;
+        h->scen_veh_off[k + 1] = VO; h->scen_lane_off[k + 1] = LO; h->scen_junc_off[k + 1] = JO;
+        h->scen_road_off[k + 1] = RO;
+    }
+    h->junc_phase_off[NJ] = PO;
+    // departure queues per start lane ordered by (dep, id) (R18)
+    h->q_off.assign(NL + 1, 0);
+    h->q_head.assign(std::max(NL, 1), 0);
+    h->q_ids.resize(NV);
+    build_queues(h, 0, NL, 0, NV, 0, NV);
+    h->q_head.resize(NL);
+    h->start_lanes.clear();
+    for (int l = 0; l < NL; ++l)
+        if (h->q_off[l + 1] > h->q_off[l]) h->start_lanes.push_back(l);
+    if (!h->lane_groups) h->lane_groups = has_lane_groups(h, 0, (int)tot_roads);
+    // junction lanes grouped by junction
+    int n_jl = 0;
+    for (int l = 0; l < NL; ++l) n_jl += h->lanes[l].lo < 0;
+    h->jj_off.assign(NJ + 1, 0);
+    h->jj_lane.assign(n_jl, 0); h->jj_from.assign(n_jl, 0);
+    build_jj(h, 0, NJ, 0, NL, 0, n_jl, 0);
+    return device_setup(h, stream);
+}
+
+// ---- slot batches (serving): scenarios loaded into fixed-capacity slots ----
+
+// lanes [l0, l1) of slot k as padding: isolated one-lane roads of 1 m (road
+// rpad) with no junction lanes and no vehicles
+void fill_padding(MossHandle* h, int k, int l0, int l1, int rpad) {
+    for (int l = l0; l < l1; ++l) {
+        LaneInfo& li = h->lanes[l];
+        li.L = 1.0f; li.vmax = 1.0f;
+        li.lo = l; li.hi = l + 1; li.jb = l0; li.je = l0;
+        li.road = rpad; li.scen = (unsigned short)k; li.flags = 0;
+        h->lane_src_road[l] = -1;
+        h->jl_plans[l] = 0xff;
+    }
+}
+
+// slot k empty: every lane, road and junction padding, no vehicles (with
+// vehicles: also every vehicle and route entry of its capacity, else only the
+// ones the slot's last scenario used)
+void clear_slot(MossHandle* h, int k, bool vehicles) {
+    const SlotInfo& S = h->slot[k];
+    const int lpad = S.LO + S.nl_cap - 1, rpad = S.RO + S.nr_cap - 1;
+    fill_padding(h, k, S.LO, S.LO + S.nl_cap, rpad);
+    for (int r = S.RO; r < S.RO + S.nr_cap; ++r) h->road_span[r] = make_int2(lpad, lpad + 1);
+    for (int j = S.JO; j < S.JO + S.nj_cap; ++j) {
+        h->junc_scen[j] = k; h->junc_offset[j] = 0; h->junc_phase_off[j] = S.PO;
+    }
+    h->junc_phase_off[S.JO + S.nj_cap] = S.PO + S.np_cap;  // the padding junction owns the spare phases
+    for (int q = S.PO; q < S.PO + S.np_cap; ++q) { h->phase_green[q] = 1; h->phase_amber[q] = 0; }
+    const int nv = vehicles ? S.nv_cap : h->scen_nv[k];
+    for (int g = S.VO; g < S.VO + nv; ++g) {
+        h->route_span[g] = make_int2(S.QO, S.QO);
+        h->dep[g] = 0; h->start_lane[g] = lpad; h->v0f[g] = 1.0f; h->veh_scen[g] = k;
+    }
+    if (vehicles)
+        for (int q = S.QO; q < S.QO + S.nq_cap; ++q) h->routes[q] = rpad;
+    build_queues(h, S.LO, S.LO + S.nl_cap, S.VO, S.VO, S.VO, S.VO + S.nv_cap);
+    for (int q = 0; q < S.nl_cap; ++q) h->start_lanes[S.SO + q] = lpad;
+    build_jj(h, S.JO, S.JO + S.nj_cap, S.LO, S.LO + S.nl_cap, S.JJ, S.JJ + S.njj_cap, lpad);
+    h->scen_nv[k] = 0; h->scen_nl[k] = 0; h->scen_nj[k] = 0; h->scen_nr[k] = 0;
+}
+
+int create_slots_impl(int n, const MossSlotCaps* caps, const MossParams* prm, void* stream, MossHandle* h) {
+    if (n < 1 || n > 65535) return fail(h, MOSS_EINVAL, "1 to 65535 slots");
+    if (!caps || !prm) return fail(h, MOSS_EINVAL, "null argument");
+    if (prm->delta != 4.0) return fail(h, MOSS_EINVAL, "only delta = 4 is supported");
+    if (prm->precision != 32 && prm->precision != 64) return fail(h, MOSS_EINVAL, "precision must be 32 or 64");
+    h->prm = *prm;
+    h->precision = prm->precision;
+    h->n_scen = n;
+    h->slots = true;
+    h->slot.resize(n);
+    long long L = 0, R = 0, J = 0, P = 0, JJ = 0, V = 0, Q = 0, S = 0;
+    for (int k = 0; k < n; ++k) {
+        const MossSlotCaps& c = caps[k];
+        if (c.n_lanes < 0 || c.n_roads < 0 || c.n_junctions < 0 || c.n_phases < 0 || c.n_vehicles < 0 ||
+            c.n_route_entries < 0)
+            return fail(h, MOSS_EINVAL, "negative slot capacity");
+        SlotInfo& si = h->slot[k];
+        // one padding lane, road and junction beyond the stated capacity
+        si.LO = (int)L; si.nl_cap = c.n_lanes + 1;
+        si.RO = (int)R; si.nr_cap = c.n_roads + 1;
+        si.JO = (int)J; si.nj_cap = c.n_junctions + 1;
+        si.PO = (int)P; si.np_cap = c.n_phases;
+        si.JJ = (int)JJ; si.njj_cap = c.n_lanes;
+        si.VO = (int)V; si.nv_cap = c.n_vehicles;
+        si.QO = (int)Q; si.nq_cap = c.n_route_entries;
+        si.SO = (int)S;
+        L += si.nl_cap; R += si.nr_cap; J += si.nj_cap; P += si.np_cap; JJ += si.njj_cap; V += si.nv_cap;
+        Q += si.nq_cap; S += si.nl_cap;
+    }
+    if (L >= (1ll << 30) || V >= (1ll << 30) || Q >= (1ll << 31) - 1 || R >= (1ll << 30) || JJ >= (1ll << 30))
+        return fail(h, MOSS_EINVAL, "slot capacities too large for 32-bit indices");
+    h->n_lanes = (int)L; h->n_junctions = (int)J; h->n_veh = (int)V; h->n_phases = (int)P;
+    h->lanes.assign(L, LaneInfo{});
+    h->lane_src_road.assign(L, -1);
+    h->junc_scen.assign(J, 0); h->junc_phase_off.assign(J + 1, 0);
+    h->junc_offset.assign(J, 0); h->phase_green.assign(P, 1); h->phase_amber.assign(P, 0);
+    h->route_span.assign(V, make_int2(0, 0)); h->routes.assign(Q, 0); h->dep.assign(V, 0);
+    h->start_lane.assign(V, 0); h->v0f.assign(V, 1.0f); h->veh_scen.assign(V, 0);
+    h->scen_veh_off.assign(n + 1, 0); h->scen_lane_off.assign(n + 1, 0); h->scen_junc_off.assign(n + 1, 0);
+    h->scen_road_off.assign(n + 1, 0);
+    h->scen_nv.assign(n, 0); h->scen_nl.assign(n, 0); h->scen_nj.assign(n, 0); h->scen_nr.assign(n, 0);
+    h->jl_plans.assign(L, 0xff);
+    h->road_span.assign(R, make_int2(0, 0));
+    h->key0.assign(n, 0); h->key1.assign(n, 0);
+    h->q_off.assign(L + 1, 0); h->q_head.assign(L, 0); h->q_ids.assign(std::max<long long>(V, 1), 0);
+    h->start_lanes.assign(S, 0);
+    h->jj_off.assign(J + 1, 0); h->jj_lane.assign(JJ, 0); h->jj_from.assign(JJ, 0);
+    for (int k = 0; k < n; ++k) {
+        const SlotInfo& si = h->slot[k];
+        h->scen_veh_off[k + 1] = si.VO + si.nv_cap; h->scen_lane_off[k + 1] = si.LO + si.nl_cap;
+        h->scen_junc_off[k + 1] = si.JO + si.nj_cap; h->scen_road_off[k + 1] = si.RO + si.nr_cap;
+        clear_slot(h, k, true);
+        h->key0[k] = (uint32_t)(prm->seed & 0xffffffffull);
+        h->key1[k] = (uint32_t)(prm->seed >> 32) ^ (prm->scenario + (uint32_t)k);
+    }
+    h->q_ids.resize(V);
+    h->lane_groups = false;
+    return device_setup(h, stream);
+}
+
+// Asynchronous upload of host ranges through the pinned load staging area:
+// the copies run in stream order behind the work already queued (so a slot's
+// tables are replaced only after the steps enqueued before the load), and the
+// host does not wait for them.
+struct Stager {
+    MossHandle* h;
+    size_t off = 0;
+    template <typename T>
+    int put(T* d, const std::vector<T>& v, long long b, long long cnt) {
+        return put_ptr(d + b, v.data() + b, cnt);
+    }
+    template <typename T>
+    int put_ptr(T* d, const T* src, long long cnt) {
+        if (cnt <= 0) return MOSS_OK;
+        const size_t nb = (size_t)cnt * sizeof(T);
+        std::memcpy(h->h_load + off, src, nb);
+        CK(cudaMemcpyAsync(d, h->h_load + off, nb, cudaMemcpyHostToDevice, h->stream));
+        off += (nb + 15) & ~size_t(15);
+        return MOSS_OK;
+    }
+};
+
+// room for `bytes` in the load staging area once the previous load's copies ran
+int stage_reserve(MossHandle* h, size_t bytes) {
+    CK(cudaEventSynchronize(h->load_free));
+    if (bytes > h->load_cap) {
+        if (h->h_load) cudaFreeHost(h->h_load);
+        h->h_load = nullptr;
+        h->load_cap = 0;
+        CK(cudaHostAlloc((void**)&h->h_load, bytes, cudaHostAllocDefault));
+        h->load_cap = bytes;
+    }
+    return MOSS_OK;
+}
+
+int load_slot_impl(MossHandle* h, int k, const MossNetwork* net, const MossVehicles* veh, const MossParams* prm) {
+    if (!h->slots) return fail(h, MOSS_EINVAL, "not a slot batch (moss_slots_create)");
+    if (k < 0 || k >= h->n_scen) return fail(h, MOSS_EINVAL, "slot index out of range");
+    std::vector<std::vector<int32_t>> outs;
+    TRY(validate(h, net, veh, prm, &outs));
+    if (!same_model(h->prm, *prm)) return fail(h, MOSS_EINVAL, "the slot batch's model parameters differ");
+    SlotInfo& S = h->slot[k];
+    if (S.loaded && !S.retired) return fail(h, MOSS_EINVAL, "slot in use: retire it first");
+    if (S.loaded && h->steps_enqueued <= S.retire_step)
+        return fail(h, MOSS_EINVAL, "retired slot still holds its vehicles: step once first");
+    const int nph = net->n_junctions ? net->junc_phase_off[net->n_junctions] : 0;
+    const int nq = veh->n ? veh->route_off[veh->n] : 0;
+    if (net->n_lanes > S.nl_cap - 1 || net->n_roads > S.nr_cap - 1 || net->n_junctions > S.nj_cap - 1 ||
+        nph > S.np_cap || net->n_lanes - net->n_road_lanes > S.njj_cap || veh->n > S.nv_cap || nq > S.nq_cap)
+        return fail(h, MOSS_EINVAL, "scenario larger than the slot's capacity");
+    clear_slot(h, k, false);
+    fill_scenario(h, k, *net, *veh, *prm, S.LO, S.JO, S.VO, S.RO, S.PO, S.QO);
+    if (has_lane_groups(h, S.RO, S.RO + net->n_roads) || net->jl_plans) {
+        h->lane_groups = false;
+        clear_slot(h, k, false);
+        return fail(h, MOSS_EINVAL, "slot batches take networks without lane groups or plans");
+    }
+    // padding junction after the scenario's junctions owns the spare phases
+    for (int j = S.JO + net->n_junctions; j <= S.JO + S.nj_cap; ++j) h->junc_phase_off[j] = S.PO + nph;
+    h->junc_phase_off[S.JO + S.nj_cap] = S.PO + S.np_cap;
+    build_queues(h, S.LO, S.LO + S.nl_cap, S.VO, S.VO + veh->n, S.VO, S.VO + S.nv_cap);
+    {
+        int q = S.SO;
+        for (int l = S.LO; l < S.LO + S.nl_cap; ++l)
+            if (h->q_off[l + 1] > h->q_off[l] && l < S.LO + net->n_lanes) h->start_lanes[q++] = l;
+        for (; q < S.SO + S.nl_cap; ++q) h->start_lanes[q] = S.LO + S.nl_cap - 1;
+    }
+    build_jj(h, S.JO, S.JO + S.nj_cap, S.LO, S.LO + S.nl_cap, S.JJ, S.JJ + S.njj_cap, S.LO + S.nl_cap - 1);
+    // device ranges of the slot (asynchronous, in stream order)
+    std::vector<JuncInfo> junc(S.nj_cap);
+    for (int q = 0; q < S.nj_cap; ++q) {
+        const int j = S.JO + q;
+        junc[q].offset = h->junc_offset[j];
+        junc[q].phase_off = h->junc_phase_off[j];
+        junc[q].np = q + 1 < S.nj_cap ? h->junc_phase_off[j + 1] - h->junc_phase_off[j] : 0;
+        junc[q].scen = k;
+    }
+    const std::vector<int4> mp0(S.nj_cap, make_int4(0, 1, -1, 0));
+    const size_t need = 16 * 24 + sizeof(LaneInfo) * S.nl_cap + sizeof(JuncInfo) * S.nj_cap + 8 * (size_t)S.np_cap +
+                        sizeof(int4) * S.nj_cap + 4 * (size_t)(S.nj_cap + 1) + 8 * (size_t)S.njj_cap +
+                        sizeof(int2) * S.nr_cap + 4 * (size_t)S.nl_cap + sizeof(int2) * (size_t)S.nv_cap +
+                        4 * (size_t)S.nq_cap + 12 * (size_t)S.nv_cap + 4 * (size_t)(S.nl_cap + 1) +
+                        8 * (size_t)S.nl_cap + 16;
+    TRY(stage_reserve(h, need));
+    Stager st{h};
+    TRY(st.put(h->d_lane, h->lanes, S.LO, S.nl_cap));
+    TRY(st.put_ptr(h->d_junc + S.JO, junc.data(), S.nj_cap));
+    TRY(st.put(h->d_phase_green, h->phase_green, S.PO, S.np_cap));
+    TRY(st.put(h->d_phase_amber, h->phase_amber, S.PO, S.np_cap));
+    TRY(st.put_ptr(h->d_mp + S.JO, mp0.data(), S.nj_cap));
+    TRY(st.put(h->d_jj_off, h->jj_off, S.JO, S.nj_cap + 1));
+    TRY(st.put(h->d_jj_lane, h->jj_lane, S.JJ, S.njj_cap));
+    TRY(st.put(h->d_jj_from, h->jj_from, S.JJ, S.njj_cap));
+    TRY(st.put(h->d_road_span, h->road_span, S.RO, S.nr_cap));
+    TRY(st.put(h->d_jl_plans, h->jl_plans, S.LO, S.nl_cap));
+    // vehicles and route entries past the scenario's are never read (they
+    // are in no queue): only the used parts go up
+    TRY(st.put(h->d_route_span, h->route_span, S.VO, veh->n));
+    TRY(st.put(h->d_routes, h->routes, S.QO, nq));
+    TRY(st.put(h->d_dep, h->dep, S.VO, veh->n));
+    TRY(st.put(h->d_v0f, h->v0f, S.VO, veh->n));
+    TRY(st.put(h->d_q_off, h->q_off, S.LO, S.nl_cap + 1));
+    TRY(st.put(h->d_q_ids, h->q_ids, S.VO, veh->n));
+    TRY(st.put(h->d_q_head, h->q_head, S.LO, S.nl_cap));
+    TRY(st.put(h->d_start_lanes, h->start_lanes, S.SO, S.nl_cap));
+    TRY(st.put(h->d_key0, h->key0, k, 1));
+    TRY(st.put(h->d_key1, h->key1, k, 1));
+    CK(cudaEventRecord(h->load_free, h->stream));
+    // fixed-time policy (0), no manual phase, no pressure, every vehicle
+    // waiting (0) without flags, clock and metrics at 0, running (control 0),
+    // no horizon (-1)
+    CK(cudaMemsetAsync(h->d_junc_policy + S.JO, 0, 4 * (size_t)S.nj_cap, h->stream));
+    CK(cudaMemsetAsync(h->d_junc_manual + S.JO, 0, 4 * (size_t)S.nj_cap, h->stream));
+    CK(cudaMemsetAsync(h->d_mp_press + (size_t)S.JO * 8, 0, 32 * (size_t)S.nj_cap, h->stream));
+    if (veh->n > 0) {
+        CK(cudaMemsetAsync(h->d_vstatus + S.VO, 0, 4 * (size_t)veh->n, h->stream));
+        CK(cudaMemsetAsync(h->d_vflags + S.VO, 0, 4 * (size_t)veh->n, h->stream));
+    }
+    CK(cudaMemsetAsync(h->d_step + k, 0, 8, h->stream));
+    CK(cudaMemsetAsync(h->d_metrics + (size_t)k * M_NFIELDS, 0, 8 * (size_t)M_NFIELDS, h->stream));
+    CK(cudaMemsetAsync(h->d_scen_ctl + k, 0, 4, h->stream));
+    CK(cudaMemsetAsync(h->d_stop_at + k, 0xff, 8, h->stream));
+    TRY(junction_init(h, S.JO, S.JO + S.nj_cap));
+    h->scen_nv[k] = veh->n; h->scen_nl[k] = net->n_lanes; h->scen_nj[k] = net->n_junctions;
+    h->scen_nr[k] = net->n_roads;
+    S.loaded = true;
+    S.retired = false;
     return MOSS_OK;
 }
 
@@ -701,6 +1069,9 @@ void free_all(MossHandle* h) {
     for (int k = 0; k <= N_STEP_KERNELS; ++k)
         if (h->ev[k]) cudaEventDestroy(h->ev[k]);
     if (h->stage_free) cudaEventDestroy(h->stage_free);
+    if (h->load_free) cudaEventDestroy(h->load_free);
+    if (h->h_load) cudaFreeHost(h->h_load);
+    h->h_load = nullptr;
     if (h->h_stage) cudaFreeHost(h->h_stage);
     h->h_stage = nullptr;
     if (h->h_rb) cudaFreeHost(h->h_rb);
@@ -728,7 +1099,7 @@ int readback_metrics(MossHandle* h, int s, int slot, MossMetrics* out) {
     const long long step = M[M_NFIELDS];
     int err = 0;
     std::memcpy(&err, M + M_NFIELDS + 1, sizeof(int));
-    const int nv = h->scen_veh_off[s + 1] - h->scen_veh_off[s];
+    const int nv = h->scen_nv[s];
     out->step = step;
     out->n_active = M[M_CUR_ACTIVE];
     out->n_waiting = nv - M[M_CUR_ACTIVE] - M[M_CUR_ARRIVED];
@@ -787,7 +1158,7 @@ int scen_state(MossHandle* h, int s, MossState* out) {
     }
     CK(cudaMemcpy(status.data(), h->d_vstatus, NV * 4, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(vflags.data(), h->d_vflags, NV * 4, cudaMemcpyDeviceToHost));
-    const int v0 = h->scen_veh_off[s], v1 = h->scen_veh_off[s + 1];
+    const int v0 = h->scen_veh_off[s], v1 = v0 + h->scen_nv[s];
     const int lo = h->scen_lane_off[s];
     const long long tag = (step - 1) & 0xFFFFFF;
     for (int g = v0; g < v1; ++g) {
@@ -856,6 +1227,7 @@ void enqueue_set_lane(MossHandle* h, int n, int mode) {
 }
 
 int set_lane(MossHandle* h, int n, const int32_t* lane_ids, const int32_t* vals, int mode) {
+    if (h->slots) return fail(h, MOSS_EINVAL, "lane setters are not available on slot batches");
     const int nl = h->scen_lane_off[1];
     if (n < 0 || (n > 0 && (!lane_ids || !vals)) || n > nl) return fail(h, MOSS_EINVAL, "bad arrays");
     for (int k = 0; k < n; ++k)
@@ -990,6 +1362,7 @@ int reroute_impl(MossHandle* h, int n, const int32_t* vids, const int32_t* route
 }
 
 int reroute(MossHandle* h, int n, const int32_t* vids, const int32_t* route_off, const int32_t* roads) {
+    if (h->slots) return fail(h, MOSS_EINVAL, "re-routing is not available on slot batches");
     const int nv0 = h->scen_veh_off[1], nr0 = h->scen_road_off[1];
     if (n < 0 || (n > 0 && (!vids || !route_off || !roads))) return fail(h, MOSS_EINVAL, "bad arrays");
     if (n == 0) return MOSS_OK;
@@ -1011,7 +1384,7 @@ template <typename Real>
 int scen_lane_metrics(MossHandle* h, int s, int32_t* queue, double* speed) {
     Ctx<Real> c = make_ctx<Real>(h, h->parity);
     if (queue) {
-        const int l0 = h->scen_lane_off[s], l1 = h->scen_lane_off[s + 1];
+        const int l0 = h->scen_lane_off[s], l1 = l0 + h->scen_nl[s];
         if (l1 > l0) {
             k_lane_queue<Real><<<(l1 - l0 + 255) / 256, 256, 0, h->stream>>>(c, l0, l1, (int32_t*)h->d_mbuf);
             CK(cudaGetLastError());
@@ -1020,7 +1393,7 @@ int scen_lane_metrics(MossHandle* h, int s, int32_t* queue, double* speed) {
         }
     }
     if (speed) {
-        const int r0 = h->scen_road_off[s], r1 = h->scen_road_off[s + 1];
+        const int r0 = h->scen_road_off[s], r1 = r0 + h->scen_nr[s];
         if (r1 > r0) {
             k_road_speed<Real><<<(r1 - r0 + 255) / 256, 256, 0, h->stream>>>(c, r0, r1, (double*)h->d_mbuf);
             CK(cudaGetLastError());
@@ -1080,6 +1453,7 @@ int moss_batch_create_with_allocator(int n, const MossNetwork* nets, const MossV
 int moss_step(moss_t h, int n) {
     if (!h) return MOSS_EINVAL;
     if (n < 0) return fail(h, MOSS_EINVAL, "negative step count");
+    h->steps_enqueued += n;
     if (h->timing) {
         for (int k = 0; k < n; ++k) {
             enqueue(h, h->parity, true);
@@ -1115,7 +1489,7 @@ int moss_batch_set_signal_phase(moss_t h, int scenario, int n, const int32_t* ju
     if (!h) return MOSS_EINVAL;
     if (scenario < 0 || scenario >= h->n_scen) return fail(h, MOSS_EINVAL, "scenario out of range");
     if (n < 0 || (n > 0 && (!junction_ids || !phase_idx))) return fail(h, MOSS_EINVAL, "bad arrays");
-    const int j0 = h->scen_junc_off[scenario], nj = h->scen_junc_off[scenario + 1] - j0;
+    const int j0 = h->scen_junc_off[scenario], nj = h->scen_nj[scenario];
     if (n > nj) return fail(h, MOSS_EINVAL, "more junctions than the scenario has");
     if (n == 0) return MOSS_OK;
     // the pinned staging area is reused: wait until the previous copy out of
@@ -1140,9 +1514,37 @@ int moss_batch_set_signal_phase(moss_t h, int scenario, int n, const int32_t* ju
     return MOSS_OK;
 }
 
+int moss_batch_set_signal_phases(moss_t h, int n, const int32_t* scenarios, const int32_t* junction_ids,
+                                 const int32_t* phase_idx) {
+    if (!h) return MOSS_EINVAL;
+    if (n < 0 || (n > 0 && (!scenarios || !junction_ids || !phase_idx))) return fail(h, MOSS_EINVAL, "bad arrays");
+    if (n > h->n_junctions) return fail(h, MOSS_EINVAL, "more entries than the batch has junctions");
+    if (n == 0) return MOSS_OK;
+    CK(cudaEventSynchronize(h->stage_free));
+    int32_t* sj = h->h_stage;
+    int32_t* sp = h->h_stage + n;
+    for (int k = 0; k < n; ++k) {
+        const int s = scenarios[k], j = junction_ids[k], p = phase_idx[k];
+        if (s < 0 || s >= h->n_scen) return fail(h, MOSS_EINVAL, "scenario out of range");
+        if (j < 0 || j >= h->scen_nj[s]) return fail(h, MOSS_EINVAL, "junction id out of range");
+        const int g = h->scen_junc_off[s] + j;
+        const int np = h->junc_phase_off[g + 1] - h->junc_phase_off[g];
+        if (p < 0 || p >= std::max(np, 1)) return fail(h, MOSS_EINVAL, "phase index out of range");
+        sj[k] = g;
+        sp[k] = p;
+    }
+    CK(cudaMemcpyAsync(h->d_stage, h->h_stage, 2 * n * 4, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaEventRecord(h->stage_free, h->stream));
+    if (h->precision == 64) enqueue_set_signal<double>(h, n, POL_MANUAL);
+    else enqueue_set_signal<float>(h, n, POL_MANUAL);
+    CK(cudaGetLastError());
+    return MOSS_OK;
+}
+
 int moss_set_signal_policy(moss_t h, int n, const int32_t* junction_ids, int32_t policy) {
     if (!h) return MOSS_EINVAL;
     if (policy < 0 || policy > 3) return fail(h, MOSS_EINVAL, "unknown policy");
+    if (h->slots) return fail(h, MOSS_EINVAL, "signal policies are not available on slot batches");
     const int nj = h->scen_junc_off[1];
     if (n < 0 || (n > 0 && !junction_ids) || n > nj) return fail(h, MOSS_EINVAL, "bad arrays");
     if (n == 0) return MOSS_OK;
@@ -1163,6 +1565,7 @@ int moss_set_signal_policy(moss_t h, int n, const int32_t* junction_ids, int32_t
 
 int moss_set_road_lane_plan(moss_t h, int n, const int32_t* road_ids, const int32_t* plan_idx) {
     if (!h) return MOSS_EINVAL;
+    if (h->slots) return fail(h, MOSS_EINVAL, "lane plans are not available on slot batches");
     const int nr0 = h->scen_road_off[1];
     if (n < 0 || (n > 0 && (!road_ids || !plan_idx))) return fail(h, MOSS_EINVAL, "bad arrays");
     for (int k = 0; k < n; ++k) {
@@ -1319,7 +1722,7 @@ int moss_batch_get_state(moss_t h, int scenario, MossState* out) {
 
 int moss_set_state(moss_t h, const MossState* in, int64_t step) {
     if (!h) return MOSS_EINVAL;
-    if (h->n_scen != 1) return fail(h, MOSS_EINVAL, "moss_set_state takes single-scenario handles");
+    if (h->n_scen != 1 || h->slots) return fail(h, MOSS_EINVAL, "moss_set_state takes single-scenario handles");
     if (!in || !in->status || !in->lane || !in->s || !in->v || !in->rc)
         return fail(h, MOSS_EINVAL, "null state array");
     if (step < 0) return fail(h, MOSS_EINVAL, "negative step");
@@ -1385,7 +1788,7 @@ int moss_set_state(moss_t h, const MossState* in, int64_t step) {
     CK(cudaMemcpy(&c, h->d_cnt + h->parity, sizeof(c), cudaMemcpyDeviceToHost));
     c.n_cur = (int)n_act; c.n_ent = 0; c.n_cand = 0; c.ticket_lane = 0; c.res_done = 0;
     CK(cudaMemcpy(h->d_cnt + h->parity, &c, sizeof(c), cudaMemcpyHostToDevice));
-    TRY(junction_init(h));
+    TRY(junction_init(h, 0, h->n_junctions));
     CK(cudaStreamSynchronize(h->stream));
     return MOSS_OK;
 }
@@ -1399,6 +1802,64 @@ int moss_synchronize(moss_t h) {
 int moss_device_bytes(moss_t h, size_t* out) {
     if (!h || !out) return MOSS_EINVAL;
     *out = h->bytes;
+    return MOSS_OK;
+}
+
+int moss_slots_create(int n, const MossSlotCaps* caps, const MossParams* prm, void* cuda_stream,
+                      const MossAllocator* allocator, moss_t* out) {
+    if (!out) return MOSS_EINVAL;
+    *out = nullptr;
+    if (allocator && (!allocator->alloc || !allocator->release)) return MOSS_EINVAL;
+    MossHandle* h = new (std::nothrow) MossHandle();
+    if (!h) return MOSS_ENOMEM;
+    if (allocator) h->allocator = *allocator;
+    int rc;
+    try {
+        rc = create_slots_impl(n, caps, prm, cuda_stream, h);
+    } catch (const std::bad_alloc&) {
+        rc = fail(h, MOSS_ENOMEM, "host allocation failed");
+    }
+    if (rc != MOSS_OK) {
+        fprintf(stderr, "moss_slots_create: %s\n", h->err.c_str());
+        free_all(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return MOSS_OK;
+}
+
+int moss_slot_load(moss_t h, int slot, const MossNetwork* net, const MossVehicles* veh, const MossParams* prm) {
+    if (!h) return MOSS_EINVAL;
+    if (!net || !veh || !prm) return fail(h, MOSS_EINVAL, "null argument");
+    try {
+        return load_slot_impl(h, slot, net, veh, prm);
+    } catch (const std::bad_alloc&) {
+        return fail(h, MOSS_ENOMEM, "host allocation failed");
+    }
+}
+
+int moss_slot_retire(moss_t h, int slot) {
+    if (!h) return MOSS_EINVAL;
+    if (!h->slots) return fail(h, MOSS_EINVAL, "not a slot batch");
+    if (slot < 0 || slot >= h->n_scen) return fail(h, MOSS_EINVAL, "slot index out of range");
+    SlotInfo& S = h->slot[slot];
+    if (!S.loaded || S.retired) return MOSS_OK;
+    k_put_i32<<<1, 1, 0, h->stream>>>(h->d_scen_ctl + slot, SC_RETIRE | SC_FROZEN);
+    CK(cudaGetLastError());
+    S.retired = true;
+    S.retire_step = h->steps_enqueued;
+    h->scen_nv[slot] = 0; h->scen_nl[slot] = 0; h->scen_nj[slot] = 0; h->scen_nr[slot] = 0;
+    return MOSS_OK;
+}
+
+int moss_slot_set_horizon(moss_t h, int slot, int64_t stop_at) {
+    if (!h) return MOSS_EINVAL;
+    if (!h->slots) return fail(h, MOSS_EINVAL, "not a slot batch");
+    if (slot < 0 || slot >= h->n_scen) return fail(h, MOSS_EINVAL, "slot index out of range");
+    if (!h->slot[slot].loaded || h->slot[slot].retired) return fail(h, MOSS_EINVAL, "slot not loaded");
+    k_put_i64<<<1, 1, 0, h->stream>>>(h->d_stop_at + slot, stop_at < 0 ? -1ll : (long long)stop_at);
+    CK(cudaGetLastError());
     return MOSS_OK;
 }
 

@@ -51,6 +51,11 @@ enum : int {
 };
 constexpr double SPEED_FX = 16777216.0;  // speed sums in units of 2^-24 m/s
 
+// per-scenario control (slot batches): a frozen scenario does not advance
+// (its vehicles keep their state, its clock and signals stand still); a
+// retiring one has its vehicles removed by the next step
+enum : int { SC_FROZEN = 1, SC_RETIRE = 2 };
+
 // device error bits (Counters::err)
 enum : int { ERR_TIMEOUT = 1, ERR_ROUTE = 2, ERR_TRANSFER = 4, ERR_RANGE = 8 };
 // errors after which the state can no longer be trusted: every later kernel
@@ -195,6 +200,8 @@ struct Ctx {
     const int32_t* veh_base;  // first global vehicle id of the scenario
     long long* scen_step;
     long long* metrics;  // [n_scen][M_NFIELDS]
+    int32_t* scen_ctl;   // [n_scen] SC_* bits (slot batches; 0 otherwise)
+    const long long* stop_at;  // [n_scen] step at which a scenario freezes (-1: never)
     // ---- snapshots (current -> next)
     Snap<Real> cur, nxt;
     // ---- per-step scratch
@@ -329,7 +336,8 @@ template <typename Real>
 __device__ __forceinline__ void mp_accumulate(const Ctx<Real>& c, int k) {
     const int jl = c.jj_lane[k];
     const LaneInfo ji = c.lane[jl];
-    if (c.junc_policy[ji.jb] != POL_MAXP || (ji.flags & LF_OFF)) return;
+    if (ji.lo >= 0) return;  // a padding entry of a slot batch (names a road lane)
+    if (c.junc_policy[ji.jb] != POL_MAXP || (ji.flags & LF_OFF) || c.scen_ctl[ji.scen]) return;
     const int from = c.jj_from[k], to = ji.hi;
     const int d = (c.cur.off[from + 1] - c.cur.off[from]) - (c.cur.off[to + 1] - c.cur.off[to]);
     if (d == 0) return;

@@ -30,6 +30,7 @@ __device__ void insert_departure(const Ctx<Real>& c, int l, int tag) {
     const LaneInfo ls = c.lane[l];
     if (ls.flags & LF_RESTRICTED) return;  // no departure onto a restricted lane (R25)
     const int sc = ls.scen;
+    if (c.scen_ctl[sc]) return;  // a frozen or retiring slot
     const long long t = c.scen_step[sc];
     if ((long long)c.dep[vid] > t) return;
     const int b = c.cur.off[l], e = c.cur.off[l + 1];
@@ -293,29 +294,46 @@ __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Rea
                     macc_flush_thread(acc, c.metrics);
                     macc_reset(acc, sc);
                 }
-                const long long t = c.scen_step[sc];
-                const OwnPart<Real> P =
-                    decide_own<Real, Groups>(c, E, EB, li, OLr, t, c.key0[sc], c.key1[sc], c.veh_base[sc]);
-                int fl = 0;
-                bool cand = false;
-                if (P.att) {
-                    acc.mob += 1;
-                    const int k = qb + warp_claim(&q.n[warp]);
-                    q.i[k] = i; q.lane[k] = lane;
-                    q.a[k] = P.own.a; q.gap[k] = P.own.gap; q.sgap[k] = P.own.stop_gap;
-                    q.bits[k] = (P.own.has_leader ? 1 : 0) | (P.own.stop ? 2 : 0) | (P.own.overlap ? 4 : 0);
-                    q.nl[k] = P.own.nl;
-                    q.u_lc[k] = P.u_lc; q.u_dir[k] = P.u_dir;
-                    cand = true;  // finished from the queue
-                } else if (Groups && P.mand) {
-                    const Decision<Real> D = decide_mandatory(c, i, E, EB, li, P.own);
-                    if (D.cand) {
-                        list_candidate(c, i, E, EB, sc, D, tag);
-                        cand = true;
+                const int ctl = c.scen_ctl[sc];
+                if (ctl) {
+                    // a slot that does not advance: a frozen one keeps its
+                    // vehicles as they are, a retiring one removes them
+                    if (ctl & SC_RETIRE) {
+                        c.code[i] = C_ARRIVE;
+                        c.vstatus[E.id] = 2;
+                        atomicAdd(&c.leave[lane], 1);
+                        leaver = 1;
+                    } else {
+                        c.code[i] = C_STAY;
+                        SV<Real> w;
+                        w.s = E.s; w.v = E.v;
+                        c.stay[i] = w;
                     }
-                    fl = D.flag ? F_FLAGGED : 0;
+                } else {
+                    const long long t = c.scen_step[sc];
+                    const OwnPart<Real> P =
+                        decide_own<Real, Groups>(c, E, EB, li, OLr, t, c.key0[sc], c.key1[sc], c.veh_base[sc]);
+                    int fl = 0;
+                    bool cand = false;
+                    if (P.att) {
+                        acc.mob += 1;
+                        const int k = qb + warp_claim(&q.n[warp]);
+                        q.i[k] = i; q.lane[k] = lane;
+                        q.a[k] = P.own.a; q.gap[k] = P.own.gap; q.sgap[k] = P.own.stop_gap;
+                        q.bits[k] = (P.own.has_leader ? 1 : 0) | (P.own.stop ? 2 : 0) | (P.own.overlap ? 4 : 0);
+                        q.nl[k] = P.own.nl;
+                        q.u_lc[k] = P.u_lc; q.u_dir[k] = P.u_dir;
+                        cand = true;  // finished from the queue
+                    } else if (Groups && P.mand) {
+                        const Decision<Real> D = decide_mandatory(c, i, E, EB, li, P.own);
+                        if (D.cand) {
+                            list_candidate(c, i, E, EB, sc, D, tag);
+                            cand = true;
+                        }
+                        fl = D.flag ? F_FLAGGED : 0;
+                    }
+                    if (!cand) leaver = integrate_emit(c, acc, i, E, EB, P.own, lane, fl, P.own.overlap != 0, t, sc, tag);
                 }
-                if (!cand) leaver = integrate_emit(c, acc, i, E, EB, P.own, lane, fl, P.own.overlap != 0, t, sc, tag);
             }
         }
         // leavers of this tile (k_lanescan zeroes the counters after reading them)
@@ -694,7 +712,7 @@ __global__ void __launch_bounds__(LANESCAN_THREADS) k_lanescan(Ctx<Real> c) {
             // signal states of the next step
             const int j0 = (tile - c.n_lane_tiles - 1) * JUNC_CHUNK;
             const int j = j0 + threadIdx.x;
-            if (j < c.n_junctions)
+            if (j < c.n_junctions && !c.scen_ctl[c.junc[j].scen])
                 c.junc_state[j] = c.junc_policy[j] == POL_MAXP ? mp_advance(c, j) : junction_state_at(c, j, 1);
         }
         __syncthreads();
@@ -738,7 +756,12 @@ __global__ void __launch_bounds__(TILE) k_place(Ctx<Real> c) {
             c.cnt_next->ticket_lane = 0;
             c.cnt_next->tag = tag >= 0x3fffffff ? 1 : tag + 1;
         }
-        for (int s = threadIdx.x; s < c.n_scen; s += TILE) c.scen_step[s] += 1;
+        for (int s = threadIdx.x; s < c.n_scen; s += TILE) {
+            if (c.scen_ctl[s]) continue;  // frozen or retiring: its clock stands still
+            const long long t = c.scen_step[s] + 1;
+            c.scen_step[s] = t;
+            if (t == c.stop_at[s]) c.scen_ctl[s] = SC_FROZEN;  // reached its horizon
+        }
     }
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int i = tile * TILE + threadIdx.x;
@@ -806,8 +829,8 @@ __global__ void __launch_bounds__(TILE) k_place(Ctx<Real> c) {
 // signal states for the current step of every junction (after creation or
 // a state reset)
 template <typename Real>
-__global__ void k_junction_init(Ctx<Real> c) {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < c.n_junctions; j += gridDim.x * blockDim.x)
+__global__ void k_junction_init(Ctx<Real> c, int j0, int j1) {
+    for (int j = j0 + blockIdx.x * blockDim.x + threadIdx.x; j < j1; j += gridDim.x * blockDim.x)
         c.junc_state[j] = junction_state_at(c, j, 0);
 }
 
@@ -948,6 +971,10 @@ __global__ void k_unmark_roads(int n, const int32_t* roads, int8_t* road_mark) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n) road_mark[roads[k]] = 0;
 }
+
+// single values written in stream order (slot control, horizons)
+__global__ void k_put_i32(int32_t* p, int32_t v) { *p = v; }
+__global__ void k_put_i64(long long* p, long long v) { *p = v; }
 
 // Failure-detection self-test: the look-back of tile 1 waits on tile word 0,
 // which nothing publishes, so the bounded wait must give up and report.

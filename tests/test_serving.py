@@ -37,21 +37,83 @@ def test_actions_reproducible():
     assert np.array_equal(a, serving.actions_for(r, 10, 16)) and a.min() >= 0 and a.max() < 4
 
 
+def _run_plain(req, every=10):
+    """The request on a handle of its own (moss_create), outside any server:
+    its actions every `every` steps, then its steps up to the next action."""
+    scen = req.scenario
+    sim = binding.Simulation(scen.net, scen.veh, scen.params)
+    nj = int(scen.net.n_junctions)
+    t = 0
+    while t < req.horizon:
+        sim.set_signal_phase(np.arange(nj, dtype=np.int32), serving.actions_for(req, t, nj))
+        k = min(every, req.horizon - t)
+        sim.step(k)
+        t += k
+    m, st = sim.metrics(), sim.state()
+    sim.close()
+    return m, st
+
+
 @pytest.mark.gpu
 def test_alone_equals_mixed():
+    """Requests of different sizes and horizons (not multiples of the action
+    interval) share the launches of one slot batch: each result equals the
+    request run alone in a one-slot server and on a handle of its own."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
-    mixed = _requests()
-    stats = serving.Server(1 << 34, max_slots=8, keep_state=True).run(mixed, realtime=False)
+    mixed = _requests(6, horizons=(150, 93, 200, 121, 67, 180))
+    mixed[4].scenario = sc.medium_scenario(n=20_000)
+    mixed[4].scenario.params.scenario = 4
+    stats = serving.Server(1 << 34, max_slots=3, keep_state=True).run(mixed, realtime=False)
     assert stats["peak_slots"] >= 2  # the rollouts overlapped
+    assert stats["slot_steps"] < sum(r.horizon for r in mixed)  # launches were shared
     for r in mixed:
-        alone = _requests()[r.rid]
+        alone = _requests(6, horizons=(150, 93, 200, 121, 67, 180))[r.rid]
+        if r.rid == 4:
+            alone.scenario = mixed[4].scenario
         serving.Server(1 << 34, max_slots=1, keep_state=True).run([alone], realtime=False)
         assert alone.metrics == r.metrics, r.rid
         for k in ("status", "lane", "rc", "s", "v", "flags"):
             assert np.array_equal(alone.state[k], r.state[k]), (r.rid, k)
         assert r.metrics["step"] == r.horizon and len(r.step_ms) == r.horizon
+        m, st = _run_plain(r)
+        assert m == r.metrics, r.rid
+        for k in ("status", "lane", "rc", "s", "v", "flags"):
+            assert np.array_equal(st[k], r.state[k]), (r.rid, k)
+
+
+@pytest.mark.gpu
+def test_slot_reuse_and_refusals():
+    """A slot is reused after a retire and a step; loading into a busy slot,
+    a retired slot before its vehicles left, or a scenario larger than the
+    slot is refused, and the slot stays usable."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    a, b = sc.small_scenario(seed=1), sc.small_scenario(seed=2)
+    big = sc.medium_scenario(n=20_000)
+    caps = binding.slot_caps(a)
+    slots = binding.Slots([caps], a.params)
+    slots.load(0, a)
+    with pytest.raises(binding.MossError):
+        slots.load(0, b)  # busy
+    slots.step(60)
+    m1 = slots.metrics(0)
+    slots.retire(0)
+    with pytest.raises(binding.MossError):
+        slots.load(0, b)  # its vehicles are still there
+    slots.step(1)
+    with pytest.raises(binding.MossError):
+        slots.load(0, big)  # too large
+    slots.load(0, b)
+    slots.step(60)
+    ref = binding.Simulation(b.net, b.veh, b.params)
+    ref.step(60)
+    assert slots.metrics(0) == ref.metrics() and m1["step"] == 60
+    st, rs = slots.state(0), ref.state()
+    for k in st:
+        assert np.array_equal(st[k], rs[k]), k
 
 
 @pytest.mark.gpu
@@ -60,7 +122,7 @@ def test_budget_admission():
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     reqs = _requests()
-    one = serving.estimate_device_bytes(reqs[0].scenario)
+    one = serving.estimate_slot_bytes(binding.slot_caps(reqs[0].scenario))
     srv = serving.Server(int(2.5 * one), max_slots=8)
     stats = srv.run(reqs, realtime=False)
     assert stats["peak_slots"] <= 2 and all(r.metrics is not None for r in reqs)
