@@ -345,6 +345,13 @@ def run_ours(args):
         t_start = 0
         start_desc = ("all trips on the road at step 0, evenly spaced in proportion to lane length "
                       "(set_state; set-up, untimed)")
+    elif args.workload == "medium":
+        # the 30x30 grid (100,000 trips) from its own step-1800 state: a small
+        # case of the same kernels (for detailed profiles)
+        from paper_2406_10661_gb300 import scenario as sc
+        scen = sc.medium_scenario(seed=args.seed)
+        t_start = 1800
+        start_desc = "the simulation's own state at step 1800 (set-up, untimed)"
     else:
         scen = city(args)
         t_start = T_WARM
@@ -359,7 +366,7 @@ def run_ours(args):
         if saturated is not None:
             sim.set_state(*saturated, 0)
         else:
-            sim.step(T_WARM)  # set-up: the simulation reaches its own step-3600 state
+            sim.step(t_start)  # set-up: the simulation reaches its own state at the start step
         state0 = sim.state() if world == 1 else None
         for _ in range(args.warmup):
             sim.step(1)
@@ -513,7 +520,7 @@ def run_ours(args):
                 "sync_value": e2e_sync,
                 "sync_api": ("" if mp else "moss_set_signal_phase + ") + "moss_step(1) + moss_get_metrics "
                             "(waits for the step) per step"},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": sim.step_launches() * args.steps,
         "metric_calls_ms": metric_ms,
         "wall_s_timed_region": wall,
         "cpu_baseline": cpu,
@@ -524,7 +531,7 @@ def run_ours(args):
         b = run_batched(args, emit=False)
         line["batched"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "step_hz", "p50_step_ms",
                                               "p99_step_ms", "batched_over_sequential", "clocks", "config",
-                                              "sequential", "latency_how") if k in b}
+                                              "sequential", "latency_how", "single_launch") if k in b}
         sv = run_serving(args, emit=False)
         line["served"] = {k: sv[k] for k in ("value", "unit", "p50_step_ms", "p99_step_ms", "wall_s", "config",
                                              "clocks", "all_at_once", "sequential", "all_at_once_over_sequential",
@@ -587,6 +594,17 @@ def run_batched(args, emit=True):
             b.record(stream)
         torch.cuda.synchronize()
         lat = np.array([a.elapsed_time(b) for a, b in evs])
+        # the same steps as one cooperative launch each (moss_set_step_mode 1)
+        batch.set_step_mode(1)
+        batch.step(args.warmup)
+        u2 = sum(batch.metrics(i)["vehicle_updates"] for i in range(len(scens)))
+        e0.record(stream)
+        batch.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        one_ms = e0.elapsed_time(e1)
+        one_upd = sum(batch.metrics(i)["vehicle_updates"] for i in range(len(scens))) - u2
+        batch.set_step_mode(0)
         batch.close()
         b_s, b_upd = b_ms / 1e3, float(u1 - u0)
         if dist:
@@ -617,6 +635,9 @@ def run_batched(args, emit=True):
             "step_hz": args.steps / b_s,
             "p50_step_ms": float(np.percentile(lat, 50)), "p99_step_ms": float(np.percentile(lat, 99)),
             "latency_how": f"{args.steps} further steps of the whole batch, CUDA events around each",
+            "single_launch": {"value": one_upd / (one_ms / 1e3), "ms_per_step": one_ms / args.steps,
+                              "how": "the same batch, each step one cooperative launch (grid-wide barriers "
+                                     "between the phases), graph-replayed; further steps"},
             "clocks": clk.summary(),
             "config": {"workload": f"batched{args.scenarios}", "scenarios": args.scenarios,
                        "scenarios_rank0": len(scens),
@@ -703,7 +724,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-roads", type=int, default=None,
                     help="reference arm: step only roads [0, REF_ROADS) (default: the whole network)")
-    ap.add_argument("--workload", default="city", choices=["city", "saturated", "batched", "serving"],
+    ap.add_argument("--workload", default="city", choices=["city", "saturated", "medium", "batched", "serving"],
                     help="city: the city from its own step-3600 state; saturated: the city network "
                          "with all 2,464,950 trips on the road at once")
     ap.add_argument("--policy", default="fixed", choices=["fixed", "max_pressure"],

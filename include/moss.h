@@ -449,6 +449,23 @@ int moss_set_kernel_timing(moss_t h, int enable);
 int moss_kernel_times(moss_t h, double* ms4, int64_t* steps);
 
 /*
+ * Launch form of a step (no counterpart in the paper, whose step is a
+ * sequence of kernels on several streams, App. B.2): mode 0 (the default)
+ * replays three kernels per step from a captured CUDA graph; mode 1 runs the
+ * whole step as one cooperative launch (every block resident at once, the
+ * kernels' work as phases separated by grid-wide barriers whose waits are
+ * bounded: MOSS_ETIMEOUT), also graph-replayed.  Results do not depend on
+ * the mode.  Waits for the handle's stream and re-captures the graphs.
+ * MOSS_EINVAL for another mode, or mode 1 on a device without cooperative
+ * launch.
+ */
+int moss_set_step_mode(moss_t h, int mode);
+
+/* Kernel launches of the library per step in the current mode (3 in mode 0:
+ * decide, lane scan with the conflict resolution, place; 1 in mode 1). */
+int moss_step_launches(moss_t h, int* out);
+
+/*
  * Autotuner of the launch schedule: times the next steps of the simulation
  * (9 x trial_steps of them; they are simulated normally, and the results do
  * not depend on the schedule) under candidate block counts per SM of the

@@ -146,6 +146,8 @@ SIGNATURES = {
     "moss_kernel_times": (ctypes.c_int, [_vp, _c_f64p, ctypes.POINTER(ctypes.c_int64)]),
     "moss_lane_offsets_noalloc": (ctypes.c_int, [ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "moss_autotune": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p]),
+    "moss_set_step_mode": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "moss_step_launches": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "moss_selftest_bounded_wait": (ctypes.c_int, [_vp]),
 }
 
@@ -261,6 +263,16 @@ class _Handle:
         out = ctypes.c_size_t(0)
         _check(self.lib.moss_device_bytes(self.h, ctypes.byref(out)), self.h)
         return int(out.value)
+
+    def step_launches(self) -> int:
+        """Kernel launches of the library per step in the current mode."""
+        out = ctypes.c_int(0)
+        _check(self.lib.moss_step_launches(self.h, ctypes.byref(out)), self.h)
+        return int(out.value)
+
+    def set_step_mode(self, mode: int) -> None:
+        """0: three kernels per step (graph); 1: one cooperative launch per step."""
+        _check(self.lib.moss_set_step_mode(self.h, int(mode)), self.h)
 
     def set_kernel_timing(self, on: bool) -> None:
         _check(self.lib.moss_set_kernel_timing(self.h, int(bool(on))), self.h)

@@ -134,6 +134,9 @@ struct MossHandle {
     int cfg_decide = MOSS_DECIDE_MIN_BLOCKS, cfg_lanescan = 4, cfg_place = 8;
 
     int parity = 0;  // snapshot buffer holding the current step
+    int step_mode = 0;               // 0: three kernels per step; 1: one cooperative launch
+    unsigned* d_bar = nullptr;       // grid barrier of the cooperative step (count, generation)
+    cudaError_t launch_err = cudaSuccess;
     cudaGraphExec_t g2[2] = {nullptr, nullptr}, g1[2] = {nullptr, nullptr};
     bool timing = false;
     cudaEvent_t ev[N_STEP_KERNELS + 1] = {};
@@ -398,10 +401,29 @@ Grids grids(const MossHandle* h) {
     g.decide_ins = ns > 0 ? (ns + TILE - 1) / TILE : 0;  // one start lane per thread
     // candidates are a few per cent of the vehicles; the kernel strides over them
     g.resolve = std::max(1, std::min(h->max_slot_tiles, h->sm_count * 2));
-    const int tickets = h->n_lane_tiles + 1 + h->n_junc_chunks;
+    // the lane scan's tickets, plus (MOSS_FOLD_RESOLVE) the candidate and
+    // max-pressure chunks in front of them: their number is known on the
+    // device only, so the grid takes every resident block it may need
+    const int tickets = h->n_lane_tiles + 1 + h->n_junc_chunks + (MOSS_FOLD_RESOLVE ? (h->n_jj + TILE - 1) / TILE + 8 : 0);
     g.lanescan = std::max(1, std::min(tickets, h->sm_count * h->cfg_lanescan));
     g.place = std::max(1, std::min(2 * h->max_slot_tiles, h->sm_count * h->cfg_place));
     return g;
+}
+
+// the step as one cooperative launch (moss_set_step_mode 1): every block of
+// the grid resident, one per SM slot the occupancy allows
+template <typename Real, bool Groups>
+cudaError_t launch_coop(MossHandle* h, Ctx<Real>& c) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_coop<Real, Groups>, TILE, 0);
+    if (e != cudaSuccess) return e;
+    int grid = std::max(1, per_sm) * h->sm_count;
+    int n_work = std::max(1, std::min(h->max_slot_tiles, grid));
+    const int ns = (int)h->start_lanes.size();
+    int n_ins = ns > 0 ? (ns + TILE - 1) / TILE : 0;
+    unsigned* bar = h->d_bar;
+    void* args[] = {(void*)&c, (void*)&n_work, (void*)&n_ins, (void*)&bar};
+    return cudaLaunchCooperativeKernel((const void*)k_step_coop<Real, Groups>, grid, TILE, args, 0, h->stream);
 }
 
 template <typename Real>
@@ -410,6 +432,13 @@ void enqueue_step(MossHandle* h, int cur, bool timed) {
     const Grids g = grids(h);
     cudaStream_t s = h->stream;
     if (timed) cudaEventRecord(h->ev[0], s);
+    if (h->step_mode == 1) {
+        const cudaError_t e = h->lane_groups ? launch_coop<Real, true>(h, c) : launch_coop<Real, false>(h, c);
+        if (e != cudaSuccess) h->launch_err = e;
+        if (timed)
+            for (int q = 1; q <= N_STEP_KERNELS; ++q) cudaEventRecord(h->ev[q], s);
+        return;
+    }
     if (h->lane_groups) k_decide<Real, true><<<g.decide_work + g.decide_ins, TILE, 0, s>>>(c, g.decide_work);
     else k_decide<Real, false><<<g.decide_work + g.decide_ins, TILE, 0, s>>>(c, g.decide_work);
     if (timed) cudaEventRecord(h->ev[1], s);
@@ -463,8 +492,13 @@ int build_graphs(MossHandle* h) {
         for (int nsteps = 1; nsteps <= 2; ++nsteps) {
             cudaGraph_t g = nullptr;
             CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+            h->launch_err = cudaSuccess;
             for (int k = 0; k < nsteps; ++k) enqueue(h, (p + k) & 1, false);
             CK(cudaStreamEndCapture(h->stream, &g));
+            if (h->launch_err != cudaSuccess) {
+                cudaGraphDestroy(g);
+                return cuda_fail(h, h->launch_err, "cooperative step launch");
+            }
             cudaGraphExec_t ex = nullptr;
             cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
             cudaGraphDestroy(g);
@@ -744,6 +778,7 @@ int device_setup(MossHandle* h, void* stream) {
     std::vector<Counters> c0(2, Counters{});
     c0[0].tag = 1;
     TRY(upload(h, &h->d_cnt, c0));
+    TRY(upload(h, &h->d_bar, std::vector<unsigned>(2, 0u)));
     TRY(dalloc(h, &h->d_stage, 2 * std::max(NJ, 1)));
     CK(cudaHostAlloc((void**)&h->h_stage, sizeof(int32_t) * 2 * std::max(NJ, 1), cudaHostAllocDefault));
     CK(cudaHostAlloc((void**)&h->h_rb, sizeof(long long) * RB_WORDS * (MOSS_METRIC_SLOTS + 1),
@@ -1860,6 +1895,34 @@ int moss_slot_set_horizon(moss_t h, int slot, int64_t stop_at) {
     if (!h->slot[slot].loaded || h->slot[slot].retired) return fail(h, MOSS_EINVAL, "slot not loaded");
     k_put_i64<<<1, 1, 0, h->stream>>>(h->d_stop_at + slot, stop_at < 0 ? -1ll : (long long)stop_at);
     CK(cudaGetLastError());
+    return MOSS_OK;
+}
+
+int moss_set_step_mode(moss_t h, int mode) {
+    if (!h) return MOSS_EINVAL;
+    if (mode != 0 && mode != 1) return fail(h, MOSS_EINVAL, "step mode must be 0 or 1");
+    if (mode == 1) {
+        int coop = 0;
+        CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device));
+        if (!coop) return fail(h, MOSS_EINVAL, "the device has no cooperative launch");
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    const int old = h->step_mode;
+    h->step_mode = mode;
+    destroy_graphs(h);
+    const int rc = build_graphs(h);
+    if (rc != MOSS_OK) {
+        h->step_mode = old;
+        destroy_graphs(h);
+        TRY(build_graphs(h));
+        return rc;
+    }
+    return MOSS_OK;
+}
+
+int moss_step_launches(moss_t h, int* out) {
+    if (!h || !out) return MOSS_EINVAL;
+    *out = h->step_mode == 1 ? 1 : (MOSS_FOLD_RESOLVE ? 3 : 4);
     return MOSS_OK;
 }
 

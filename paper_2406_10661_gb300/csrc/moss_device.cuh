@@ -12,23 +12,24 @@
 // search in the adjacent lane's segment (adjacent lanes of a road are
 // adjacent in memory).
 //
-// One step = four kernels:
+// One step = three kernels:
 //   k_decide    per vehicle: sensing, IDM (App. B.3 eqs. (1)-(2)), the
 //               randomized MOBIL decision (App. B.3; run from a per-warp
 //               shared-memory queue of the vehicles whose attempt draw
 //               passed), ballistic integration with clamps, transfer at lane
 //               ends and arrival (App. B.2 update stream 1); lane-change
-//               candidates are listed for k_resolve; extra blocks run the
-//               departure insertion (App. B.2 update stream 3);
-//   k_resolve   deterministic conflict resolution between candidates entering
-//               the same gap from both sides, and their update; max-pressure
-//               phase sums (§3.2);
-//   k_lanescan  per-lane sizes of the next snapshot -> offsets (single-pass
-//               decoupled look-back scan), prefix of leavers per slot tile,
-//               signal states of the next step (§3.2 policies);
+//               candidates are listed for the resolution; extra blocks run
+//               the departure insertion (App. B.2 update stream 3);
+//   k_lanescan  first tickets: deterministic conflict resolution between
+//               candidates entering the same gap from both sides, and their
+//               update; max-pressure phase sums (§3.2); then per-lane sizes of
+//               the next snapshot -> offsets (single-pass decoupled look-back
+//               scan), prefix of leavers per slot tile, signal states of the
+//               next step (§3.2 policies);
 //   k_place     writes the next snapshot: vehicles that kept their lane keep
 //               their relative order (no overtaking within a lane), vehicles
 //               that entered a lane are merged by (s, id).
+// (k_step_coop runs the same three as phases of one cooperative launch.)
 #pragma once
 
 #include <cuda/atomic>
@@ -267,7 +268,9 @@ __device__ __forceinline__ long long speed_fixed(double v) { return (long long)l
 // Denominators here are desired speeds and gaps >= 1e-3 m, far from the
 // range where the approximation degrades.
 template <typename Real> __device__ __forceinline__ Real qdiv(Real x, Real y) { return x / y; }
+#if !MOSS_IEEE_DIV
 template <> __device__ __forceinline__ float qdiv<float>(float x, float y) { return __fdividef(x, y); }
+#endif
 
 // ---------------------------------------------------------------------------
 // IDM, App. B.3 eqs. (1)-(2), delta = 4 as ((v/v0)^2)^2.

@@ -254,13 +254,15 @@ __device__ __forceinline__ void mobil_finish(const Ctx<Real>& c, const MobilQueu
 #ifndef MOSS_DECIDE_MIN_BLOCKS
 #define MOSS_DECIDE_MIN_BLOCKS 5
 #endif
+// The work of block vb of nvb (k_decide's grid, or a virtual block of the
+// single-launch step): vb < n_work takes a run of slot tiles, the others run
+// the insertion.
 template <typename Real, bool Groups>
-__global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Real> c, int n_work) {
-    if (*c.err & ERR_POISON) return;
+__device__ __forceinline__ void decide_block(const Ctx<Real>& c, int n_work, int vb, int nvb) {
     const int tag = c.cnt->tag;
-    if ((int)blockIdx.x >= n_work) {
-        const int stride = (gridDim.x - n_work) * TILE;
-        for (int k = (blockIdx.x - n_work) * TILE + threadIdx.x; k < c.n_start; k += stride)
+    if (vb >= n_work) {
+        const int stride = (nvb - n_work) * TILE;
+        for (int k = (vb - n_work) * TILE + threadIdx.x; k < c.n_start; k += stride)
             insert_departure(c, c.start_lanes[k], tag);
         return;
     }
@@ -269,7 +271,7 @@ __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Rea
     // each block takes a contiguous run of tiles: a thread's scenario (and so
     // its metric partials) changes rarely, and neighbouring lanes stay close
     const int per = (n_tiles + n_work - 1) / n_work;
-    const int t_beg = blockIdx.x * per, t_end = min(n_tiles, t_beg + per);
+    const int t_beg = vb * per, t_end = min(n_tiles, t_beg + per);
     MetricAcc acc;
     macc_reset(acc, -1);
     __shared__ MobilQueue<Real> q;
@@ -353,6 +355,12 @@ __global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Rea
         if (last) break;
     }
     macc_flush_block<TILE>(acc, c.metrics);
+}
+
+template <typename Real, bool Groups>
+__global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Real> c, int n_work) {
+    if (*c.err & ERR_POISON) return;
+    decide_block<Real, Groups>(c, n_work, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -595,7 +603,7 @@ __device__ __forceinline__ void lanescan_tile(const Ctx<Real>& c, int tile) {
 // free of bank conflicts), 16-byte coalesced stores out.  The counter arrays
 // are padded to a multiple of 1024 entries and hold zeros past the tiles in
 // use.
-constexpr int TP_CHUNK = 8192;
+constexpr int TP_CHUNK = 4096;
 __device__ __forceinline__ int tp_pad(int k) { return k + (k >> 5); }
 
 template <typename Real>
@@ -647,8 +655,7 @@ __device__ __forceinline__ void tile_prefix_scan(const Ctx<Real>& c) {
 // tiles, above).  Ticket n_lane_tiles: the leaver prefix per slot tile.
 // Remaining tickets: signal states of the next step for chunks of junctions.
 template <typename Real>
-__global__ void __launch_bounds__(LANESCAN_THREADS) k_lanescan(Ctx<Real> c) {
-    if (*c.err & ERR_POISON) return;
+__device__ __forceinline__ void lanescan_blocks(const Ctx<Real>& c) {
     __shared__ int s_tile;
 #if MOSS_FOLD_RESOLVE
     // first tickets: the lane-change candidates (k_resolve's work) and the
@@ -719,6 +726,12 @@ __global__ void __launch_bounds__(LANESCAN_THREADS) k_lanescan(Ctx<Real> c) {
     }
 }
 
+template <typename Real>
+__global__ void __launch_bounds__(LANESCAN_THREADS) k_lanescan(Ctx<Real> c) {
+    if (*c.err & ERR_POISON) return;
+    lanescan_blocks(c);
+}
+
 // ---------------------------------------------------------------------------
 // k_place: writes the next snapshot.  Stayer tiles (one per block iteration):
 // a vehicle that kept its lane goes to off'[lane] + (stayers ahead of it in
@@ -737,8 +750,7 @@ __device__ __forceinline__ int entrants_ahead(const Ctx<Real>& c, int lane, Real
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(TILE) k_place(Ctx<Real> c) {
-    if (*c.err & ERR_POISON) return;
+__device__ __forceinline__ void place_blocks(const Ctx<Real>& c, int vb, int nvb) {
     __shared__ int s_warp[TILE / 32];
     const int n = c.cnt->n_cur;
     const int n_ent = c.cnt->n_ent;
@@ -748,7 +760,7 @@ __global__ void __launch_bounds__(TILE) k_place(Ctx<Real> c) {
     // closing the step: the next step's counters (k_lanescan already wrote
     // its vehicle count) and every scenario's clock; no kernel of this step
     // reads them after this point
-    if (blockIdx.x == 0) {
+    if (vb == 0) {
         if (threadIdx.x == 0) {
             c.cnt_next->n_ent = 0;
             c.cnt_next->n_cand = 0;
@@ -763,7 +775,7 @@ __global__ void __launch_bounds__(TILE) k_place(Ctx<Real> c) {
             if (t == c.stop_at[s]) c.scen_ctl[s] = SC_FROZEN;  // reached its horizon
         }
     }
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    for (int tile = vb; tile < n_tiles; tile += nvb) {
         const int i = tile * TILE + threadIdx.x;
         const bool valid = i < n;
         const int8_t code = valid ? c.code[i] : C_STAY;
@@ -800,7 +812,7 @@ __global__ void __launch_bounds__(TILE) k_place(Ctx<Real> c) {
     }
     // entrants: one warp per entrant; the warp counts the stayers of the
     // lane's old segment that are ahead of it, 32 slots per round
-    const int gwarp = blockIdx.x * (TILE / 32) + warp, nwarps = gridDim.x * (TILE / 32);
+    const int gwarp = vb * (TILE / 32) + warp, nwarps = nvb * (TILE / 32);
     for (int q = gwarp; q < n_ent; q += nwarps) {
         const RecA<Real> Q = c.ea[q];
         const int lane = Q.lane;
@@ -822,8 +834,60 @@ __global__ void __launch_bounds__(TILE) k_place(Ctx<Real> c) {
         }
     }
     // clear the lane look-back words for the next step (k_lanescan is done)
-    for (int k = blockIdx.x * TILE + threadIdx.x; k < c.n_lane_tiles; k += gridDim.x * TILE)
+    for (int k = vb * TILE + threadIdx.x; k < c.n_lane_tiles; k += nvb * TILE)
         c.lane_tiles[k] = 0ull;
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(TILE) k_place(Ctx<Real> c) {
+    if (*c.err & ERR_POISON) return;
+    place_blocks(c, blockIdx.x, gridDim.x);
+}
+
+// ---------------------------------------------------------------------------
+// The whole step as one cooperative launch (every block resident at once):
+// the work of k_decide, k_lanescan and k_place as three phases separated by
+// grid-wide barriers.  A barrier is a count of arrived blocks and a
+// generation word; a wait that exceeds SPIN_LIMIT sets ERR_TIMEOUT and every
+// block leaves the step.
+__device__ __forceinline__ bool grid_sync(unsigned* bar, int* err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> gen(bar[1]);
+        const unsigned g = gen.load(cuda::memory_order_relaxed);
+        __threadfence();
+        if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
+            bar[0] = 0u;
+            gen.store(g + 1u, cuda::memory_order_release);
+        } else {
+            long long spins = 0;
+            while (gen.load(cuda::memory_order_acquire) == g) {
+                if (++spins > SPIN_LIMIT) { atomicOr(err, ERR_TIMEOUT); break; }
+                if (spins > 16) __nanosleep(32);
+            }
+        }
+        __threadfence();
+        s_ok = !(*((volatile int*)err) & ERR_POISON);
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+#ifndef MOSS_COOP_MIN_BLOCKS
+#define MOSS_COOP_MIN_BLOCKS 4
+#endif
+template <typename Real, bool Groups>
+__global__ void __launch_bounds__(TILE, MOSS_COOP_MIN_BLOCKS) k_step_coop(Ctx<Real> c, int n_work, int n_ins,
+                                                                          unsigned* bar) {
+    if (*c.err & ERR_POISON) return;
+    // decide: n_work tile runs, then n_ins insertion blocks, as virtual blocks
+    for (int vb = blockIdx.x; vb < n_work + n_ins; vb += gridDim.x)
+        decide_block<Real, Groups>(c, n_work, vb, n_work + n_ins);
+    if (!grid_sync(bar, c.err)) return;
+    lanescan_blocks(c);
+    if (!grid_sync(bar, c.err)) return;
+    place_blocks(c, blockIdx.x, gridDim.x);
 }
 
 // signal states for the current step of every junction (after creation or

@@ -42,13 +42,13 @@ def test_traffic_only_for_matching_workload_and_code(tmp_path, monkeypatch):
 def test_committed_profiles_have_traffic_lines():
     """Every committed launch-list summary carries one well-formed traffic line
     (bytes per launch and the SHA-256 of the code it was captured from) for
-    each of the four step kernels."""
+    each of the three step kernels."""
     import re
     prof = os.path.join(bench.ROOT, "profiles")
     names = [f for f in os.listdir(prof) if f.startswith("step_kernels_")]
     assert "step_kernels_city100x100_2464950.md" in names
-    pat = re.compile(r"^traffic: (k_decide|k_resolve|k_lanescan|k_place) [0-9]+ sha256:[0-9a-f]{64}$")
+    pat = re.compile(r"^traffic: (k_decide|k_lanescan|k_place) [0-9]+ sha256:[0-9a-f]{64}$")
     for f in names:
         with open(os.path.join(prof, f)) as fh:
             kernels = [m.group(1) for m in (pat.match(line.strip()) for line in fh) if m]
-        assert sorted(kernels) == ["k_decide", "k_lanescan", "k_place", "k_resolve"], f
+        assert sorted(kernels) == ["k_decide", "k_lanescan", "k_place"], f

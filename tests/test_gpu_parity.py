@@ -556,3 +556,34 @@ def test_long_queue_lane_spans_many_tiles(precision):
             assert gm[k] == rm[k], (k, gm[k], rm[k])
     else:
         assert abs(gm["speed_sum"] - rm["speed_sum"]) <= 0.005 * rm["speed_sum"]
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_single_launch_step_equals_kernel_sequence(precision):
+    """The step as one cooperative launch (moss_set_step_mode 1) gives the
+    same state and metrics as the sequence of kernels, on a ragged batch;
+    in FP64 both equal the oracle run per member."""
+    scens = [sc.small_scenario(seed=4), sc.medium_scenario(n=15_000), sc.small_scenario(seed=5)]
+    for i, s_ in enumerate(scens):
+        s_.params.scenario = i
+    a = binding.Batch(scens, precision=precision)
+    b = binding.Batch(scens, precision=precision)
+    b.set_step_mode(1)
+    a.step(160); b.step(160)
+    b.set_step_mode(0)
+    a.step(7); b.step(7)
+    b.set_step_mode(1)
+    a.step(33); b.step(33)
+    for i, s_ in enumerate(scens):
+        x, y = a.state(i), b.state(i)
+        for k in x:
+            assert np.array_equal(x[k], y[k]), (i, k)
+        assert a.metrics(i) == b.metrics(i), i
+        if precision == 64:
+            ora = _ora(s_)
+            ora.step(200)
+            r = ora.state()
+            assert np.array_equal(y["status"], r["status"]), i
+            act = r["status"] == 1
+            assert np.array_equal(y["lane"][act], r["lane"][act]), i
+            assert np.abs(y["s"][act] - r["s"][act]).max(initial=0) < 1e-6, i
