@@ -96,6 +96,7 @@ struct MossHandle {
     int2* d_road_span = nullptr;      // (first, end) road lanes per road
     std::vector<int2> road_span;
     std::vector<int> scen_road_off;   // [n_scen+1]
+    std::vector<int4> scen_lanes;     // [n_scen] first lane, first junction lane, end of the lanes in use
     int32_t* d_lstage = nullptr;      // setter arguments for lanes (2 * n_lanes)
     void* d_mbuf = nullptr;           // metric output (max(n_lanes, n_roads) doubles)
     int2* d_route_span = nullptr;
@@ -103,6 +104,7 @@ struct MossHandle {
             *d_vflags = nullptr;
     int32_t *d_q_off = nullptr, *d_q_ids = nullptr, *d_q_head = nullptr, *d_start_lanes = nullptr;
     uint32_t *d_key0 = nullptr, *d_key1 = nullptr;
+    int4* d_scen_lanes = nullptr;
     int32_t* d_veh_base = nullptr;
     long long *d_step = nullptr, *d_metrics = nullptr;
     int32_t* d_scen_ctl = nullptr;    // per scenario: SC_FROZEN / SC_RETIRE
@@ -112,8 +114,7 @@ struct MossHandle {
     void* d_stay = nullptr;  // SV<Real>[cap]
     void* d_ea = nullptr;    // RecA<Real>[cap]
     RecB* d_eb = nullptr;
-    int32_t *d_enext = nullptr, *d_enter = nullptr, *d_leave = nullptr, *d_lbefore = nullptr,
-            *d_tile_leave = nullptr, *d_tile_prefix = nullptr;
+    int32_t *d_enext = nullptr, *d_enter = nullptr, *d_leave = nullptr;
     unsigned long long *d_head = nullptr, *d_lane_tiles = nullptr;
     void* d_cands = nullptr;  // Cand<Real>[cap]
     unsigned long long* d_gap_head = nullptr;
@@ -366,6 +367,7 @@ Ctx<Real> make_ctx(MossHandle* h, int cur) {
     c.q_off = h->d_q_off; c.q_ids = h->d_q_ids; c.q_head = h->d_q_head;
     c.start_lanes = h->d_start_lanes; c.n_start = (int)h->start_lanes.size();
     c.key0 = h->d_key0; c.key1 = h->d_key1; c.veh_base = h->d_veh_base; c.scen_step = h->d_step;
+    c.scen_lanes = h->d_scen_lanes;
     c.scen_ctl = h->d_scen_ctl; c.stop_at = h->d_stop_at;
     c.metrics = h->d_metrics;
     for (int k = 0; k < 2; ++k) {
@@ -375,8 +377,7 @@ Ctx<Real> make_ctx(MossHandle* h, int cur) {
     }
     c.code = h->d_code; c.stay = (SV<Real>*)h->d_stay;
     c.ea = (RecA<Real>*)h->d_ea; c.eb = h->d_eb; c.enext = h->d_enext; c.head = h->d_head;
-    c.enter = h->d_enter; c.leave = h->d_leave; c.lbefore = h->d_lbefore;
-    c.tile_leave = h->d_tile_leave; c.tile_prefix = h->d_tile_prefix; c.lane_tiles = h->d_lane_tiles;
+    c.enter = h->d_enter; c.leave = h->d_leave; c.lane_tiles = h->d_lane_tiles;
     c.cands = (Cand<Real>*)h->d_cands; c.gap_head = h->d_gap_head;
     c.n_lane_tiles = h->n_lane_tiles; c.max_slot_tiles = h->max_slot_tiles;
     c.n_junc_chunks = h->n_junc_chunks; c.cnt = h->d_cnt + cur;
@@ -404,7 +405,7 @@ Grids grids(const MossHandle* h) {
     // the lane scan's tickets, plus (MOSS_FOLD_RESOLVE) the candidate and
     // max-pressure chunks in front of them: their number is known on the
     // device only, so the grid takes every resident block it may need
-    const int tickets = h->n_lane_tiles + 1 + h->n_junc_chunks + (MOSS_FOLD_RESOLVE ? (h->n_jj + TILE - 1) / TILE + 8 : 0);
+    const int tickets = h->n_lane_tiles + h->n_junc_chunks + (MOSS_FOLD_RESOLVE ? (h->n_jj + TILE - 1) / TILE + 8 : 0);
     g.lanescan = std::max(1, std::min(tickets, h->sm_count * h->cfg_lanescan));
     g.place = std::max(1, std::min(2 * h->max_slot_tiles, h->sm_count * h->cfg_place));
     return g;
@@ -540,6 +541,7 @@ int check_device(MossHandle* h) {
 void fill_scenario(MossHandle* h, int k, const MossNetwork& nt, const MossVehicles& vh, const MossParams& pr,
                    int LO, int JO, int VO, int RO, int PO, int ROFF) {
     const int NRL = nt.n_road_lanes;
+    h->scen_lanes[k] = make_int4(LO, LO + NRL, LO + nt.n_lanes, 0);
     std::vector<int32_t> road_of(NRL);
     for (int r = 0; r < nt.n_roads; ++r)
         for (int l = nt.road_lane_off[r]; l < nt.road_lane_off[r + 1]; ++l) road_of[l] = r;
@@ -741,6 +743,7 @@ int device_setup(MossHandle* h, void* stream) {
     TRY(upload(h, &h->d_start_lanes, h->start_lanes));
     TRY(upload(h, &h->d_key0, h->key0));
     TRY(upload(h, &h->d_key1, h->key1));
+    TRY(upload(h, &h->d_scen_lanes, h->scen_lanes));
     TRY(upload(h, &h->d_veh_base, std::vector<int32_t>(h->scen_veh_off.begin(), h->scen_veh_off.end() - 1)));
     TRY(upload(h, &h->d_step, std::vector<long long>(n, 0)));
     TRY(upload(h, &h->d_metrics, std::vector<long long>((size_t)n * M_NFIELDS, 0)));
@@ -765,15 +768,9 @@ int device_setup(MossHandle* h, void* stream) {
     TRY(upload(h, &h->d_head, std::vector<unsigned long long>(NL, 0ull)));
     TRY(upload(h, &h->d_enter, std::vector<int32_t>(NL, 0)));
     TRY(upload(h, &h->d_leave, std::vector<int32_t>(NL, 0)));
-    TRY(dalloc(h, &h->d_lbefore, NL));
     h->n_lane_tiles = (NL + LANESCAN_TILE - 1) / LANESCAN_TILE;
     h->max_slot_tiles = (NV + TILE - 1) / TILE + 1;
-    // tile counter arrays padded for the 16-byte loads of the tile-prefix scan
-    const int tile_cap = ((h->max_slot_tiles + 4 * LANESCAN_THREADS - 1) / (4 * LANESCAN_THREADS)) *
-                         (4 * LANESCAN_THREADS);
     h->n_junc_chunks = (NJ + JUNC_CHUNK - 1) / JUNC_CHUNK;
-    TRY(upload(h, &h->d_tile_leave, std::vector<int32_t>(tile_cap, 0)));
-    TRY(upload(h, &h->d_tile_prefix, std::vector<int32_t>(tile_cap, 0)));
     TRY(upload(h, &h->d_lane_tiles, std::vector<unsigned long long>(h->n_lane_tiles, 0ull)));
     std::vector<Counters> c0(2, Counters{});
     c0[0].tag = 1;
@@ -829,6 +826,7 @@ int create_impl(int n, const MossNetwork* nets, const MossVehicles* vehs, const 
     h->start_lane.resize(NV); h->v0f.resize(NV); h->veh_scen.resize(NV);
     h->scen_veh_off.assign(n + 1, 0); h->scen_lane_off.assign(n + 1, 0); h->scen_junc_off.assign(n + 1, 0);
     h->scen_road_off.assign(n + 1, 0);
+    h->scen_lanes.assign(n, make_int4(0, 0, 0, 0));
     h->scen_nv.assign(n, 0); h->scen_nl.assign(n, 0); h->scen_nj.assign(n, 0); h->scen_nr.assign(n, 0);
     h->jl_plans.assign(tot_lanes, 0xff);
     h->road_span.assign(tot_roads, make_int2(0, 0));
@@ -946,6 +944,7 @@ int create_slots_impl(int n, const MossSlotCaps* caps, const MossParams* prm, vo
     h->start_lane.assign(V, 0); h->v0f.assign(V, 1.0f); h->veh_scen.assign(V, 0);
     h->scen_veh_off.assign(n + 1, 0); h->scen_lane_off.assign(n + 1, 0); h->scen_junc_off.assign(n + 1, 0);
     h->scen_road_off.assign(n + 1, 0);
+    h->scen_lanes.assign(n, make_int4(0, 0, 0, 0));
     h->scen_nv.assign(n, 0); h->scen_nl.assign(n, 0); h->scen_nj.assign(n, 0); h->scen_nr.assign(n, 0);
     h->jl_plans.assign(L, 0xff);
     h->road_span.assign(R, make_int2(0, 0));
@@ -1044,11 +1043,11 @@ int load_slot_impl(MossHandle* h, int k, const MossNetwork* net, const MossVehic
         junc[q].scen = k;
     }
     const std::vector<int4> mp0(S.nj_cap, make_int4(0, 1, -1, 0));
-    const size_t need = 16 * 24 + sizeof(LaneInfo) * S.nl_cap + sizeof(JuncInfo) * S.nj_cap + 8 * (size_t)S.np_cap +
+    const size_t need = 16 * 26 + sizeof(LaneInfo) * S.nl_cap + sizeof(JuncInfo) * S.nj_cap + 8 * (size_t)S.np_cap +
                         sizeof(int4) * S.nj_cap + 4 * (size_t)(S.nj_cap + 1) + 8 * (size_t)S.njj_cap +
                         sizeof(int2) * S.nr_cap + 4 * (size_t)S.nl_cap + sizeof(int2) * (size_t)S.nv_cap +
                         4 * (size_t)S.nq_cap + 12 * (size_t)S.nv_cap + 4 * (size_t)(S.nl_cap + 1) +
-                        8 * (size_t)S.nl_cap + 16;
+                        8 * (size_t)S.nl_cap + 16 + sizeof(int4);
     TRY(stage_reserve(h, need));
     Stager st{h};
     TRY(st.put(h->d_lane, h->lanes, S.LO, S.nl_cap));
@@ -1073,6 +1072,7 @@ int load_slot_impl(MossHandle* h, int k, const MossNetwork* net, const MossVehic
     TRY(st.put(h->d_start_lanes, h->start_lanes, S.SO, S.nl_cap));
     TRY(st.put(h->d_key0, h->key0, k, 1));
     TRY(st.put(h->d_key1, h->key1, k, 1));
+    TRY(st.put(h->d_scen_lanes, h->scen_lanes, k, 1));
     CK(cudaEventRecord(h->load_free, h->stream));
     // fixed-time policy (0), no manual phase, no pressure, every vehicle
     // waiting (0) without flags, clock and metrics at 0, running (control 0),

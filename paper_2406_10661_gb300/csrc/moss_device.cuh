@@ -199,6 +199,7 @@ struct Ctx {
     const uint32_t* key0;
     const uint32_t* key1;
     const int32_t* veh_base;  // first global vehicle id of the scenario
+    const int4* scen_lanes;   // first lane, first junction lane, end of the lanes in use
     long long* scen_step;
     long long* metrics;  // [n_scen][M_NFIELDS]
     int32_t* scen_ctl;   // [n_scen] SC_* bits (slot batches; 0 otherwise)
@@ -214,9 +215,6 @@ struct Ctx {
     unsigned long long* head;  // [n_lanes] (tag << 32 | entrant) or stale
     int32_t* enter;       // [n_lanes], zeroed by k_lanescan after use
     int32_t* leave;       // [n_lanes], zeroed by k_lanescan after use
-    int32_t* lbefore;     // [n_lanes] leavers in lanes before l
-    int32_t* tile_leave;  // [slot tiles] leavers per tile of the current snapshot
-    int32_t* tile_prefix; // [slot tiles] leavers before the tile
     Cand<Real>* cands;    // this step's lane-change candidates (cnt->n_cand of them)
     unsigned long long* gap_head;  // [n_veh + n_lanes + 1] (tag << 32 | candidate) or stale
     unsigned long long* lane_tiles;

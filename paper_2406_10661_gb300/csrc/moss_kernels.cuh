@@ -237,8 +237,7 @@ __device__ __forceinline__ void mobil_finish(const Ctx<Real>& c, const MobilQueu
         return;
     }
     const long long t = c.scen_step[sc];
-    if (integrate_emit(c, acc, i, E, EB, own, lane, D.flag ? F_FLAGGED : 0, own.overlap != 0, t, sc, tag))
-        atomicAdd(&c.tile_leave[i / TILE], 1);
+    integrate_emit(c, acc, i, E, EB, own, lane, D.flag ? F_FLAGGED : 0, own.overlap != 0, t, sc, tag);
 }
 
 // ---------------------------------------------------------------------------
@@ -254,6 +253,75 @@ __device__ __forceinline__ void mobil_finish(const Ctx<Real>& c, const MobilQueu
 #ifndef MOSS_DECIDE_MIN_BLOCKS
 #define MOSS_DECIDE_MIN_BLOCKS 5
 #endif
+// The run of slot tiles of work block vb of n_work.  A vehicle on a road lane
+// costs about twice one on a junction lane (MOBIL, longer neighbour
+// searches), so the runs split the snapshot by weight: 2 per road-lane slot,
+// 1 per junction-lane slot, from the current lane offsets at the lane ranges
+// of each scenario (road lanes first, then junction lanes).  Warp 0
+// computes it; the runs are contiguous and cover every tile.
+__device__ __forceinline__ long long run_weight(int a, int b, int e) { return 2ll * (b - a) + (e - b); }
+
+template <typename Real>
+__device__ __forceinline__ void decide_run(const Ctx<Real>& c, int n_tiles, int n_work, int vb, int* tb, int* te) {
+    __shared__ int s_run[2];
+    if (threadIdx.x < 32) {
+        const int wl = threadIdx.x;
+        long long tot = 0;
+        for (int k0 = 0; k0 < c.n_scen; k0 += 32) {
+            long long w = 0;
+            if (k0 + wl < c.n_scen) {
+                const int4 L = c.scen_lanes[k0 + wl];
+                w = run_weight(c.cur.off[L.x], c.cur.off[L.y], c.cur.off[L.z]);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+            tot += w;
+        }
+        // weights T0, T1 -> slots (scan of the scenarios' weights)
+        const long long T[2] = {tot * vb / n_work, tot * (vb + 1) / n_work};
+        int slot[2] = {-1, -1};
+        long long carry = 0;
+        for (int k0 = 0; k0 < c.n_scen && (slot[0] < 0 || slot[1] < 0); k0 += 32) {
+            const int k = k0 + wl;
+            int a = 0, b = 0, e = 0;
+            long long w = 0;
+            if (k < c.n_scen) {
+                const int4 L = c.scen_lanes[k];
+                a = c.cur.off[L.x]; b = c.cur.off[L.y]; e = c.cur.off[L.z];
+                w = run_weight(a, b, e);
+            }
+            long long P = w;  // inclusive prefix over the chunk
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long y = __shfl_up_sync(0xffffffffu, P, o);
+                if (wl >= o) P += y;
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                // the first scenario whose weight reaches past T (m and
+                // slot[q] are the same on every lane: the branch is uniform)
+                const unsigned m = __ballot_sync(0xffffffffu, k < c.n_scen && carry + P > T[q]);
+                if (slot[q] < 0 && m) {
+                    const int src = __ffs(m) - 1;
+                    const long long local = T[q] - (carry + __shfl_sync(0xffffffffu, P - w, src));
+                    const int sa = __shfl_sync(0xffffffffu, a, src), sb = __shfl_sync(0xffffffffu, b, src);
+                    slot[q] = local < 2ll * (sb - sa) ? sa + (int)(local / 2) : sb + (int)(local - 2ll * (sb - sa));
+                }
+            }
+            carry += __shfl_sync(0xffffffffu, P, 31);
+        }
+        if (wl == 0) {
+            const int n = c.cnt->n_cur;
+            const int s0 = slot[0] < 0 ? n : slot[0], s1 = slot[1] < 0 ? n : slot[1];
+            s_run[0] = min(n_tiles, (s0 + TILE / 2) / TILE);
+            s_run[1] = vb == n_work - 1 ? n_tiles : min(n_tiles, (s1 + TILE / 2) / TILE);
+        }
+    }
+    __syncthreads();
+    *tb = s_run[0];
+    *te = s_run[1];
+}
+
 // The work of block vb of nvb (k_decide's grid, or a virtual block of the
 // single-launch step): vb < n_work takes a run of slot tiles, the others run
 // the insertion.
@@ -270,8 +338,8 @@ __device__ __forceinline__ void decide_block(const Ctx<Real>& c, int n_work, int
     const int n_tiles = (n + TILE - 1) / TILE;
     // each block takes a contiguous run of tiles: a thread's scenario (and so
     // its metric partials) changes rarely, and neighbouring lanes stay close
-    const int per = (n_tiles + n_work - 1) / n_work;
-    const int t_beg = vb * per, t_end = min(n_tiles, t_beg + per);
+    int t_beg, t_end;
+    decide_run(c, n_tiles, n_work, vb, &t_beg, &t_end);
     MetricAcc acc;
     macc_reset(acc, -1);
     __shared__ MobilQueue<Real> q;
@@ -281,7 +349,6 @@ __device__ __forceinline__ void decide_block(const Ctx<Real>& c, int n_work, int
     for (int tile = t_beg;; ++tile) {
         const bool last = tile >= t_end;
         const int i = tile * TILE + threadIdx.x;
-        int leaver = 0;
         if (!last && i < n) {
             const RecA<Real> E = c.cur.a[i];
             const RecB EB = c.cur.b[i];
@@ -304,7 +371,6 @@ __device__ __forceinline__ void decide_block(const Ctx<Real>& c, int n_work, int
                         c.code[i] = C_ARRIVE;
                         c.vstatus[E.id] = 2;
                         atomicAdd(&c.leave[lane], 1);
-                        leaver = 1;
                     } else {
                         c.code[i] = C_STAY;
                         SV<Real> w;
@@ -334,13 +400,10 @@ __device__ __forceinline__ void decide_block(const Ctx<Real>& c, int n_work, int
                         }
                         fl = D.flag ? F_FLAGGED : 0;
                     }
-                    if (!cand) leaver = integrate_emit(c, acc, i, E, EB, P.own, lane, fl, P.own.overlap != 0, t, sc, tag);
+                    if (!cand) integrate_emit(c, acc, i, E, EB, P.own, lane, fl, P.own.overlap != 0, t, sc, tag);
                 }
             }
         }
-        // leavers of this tile (k_lanescan zeroes the counters after reading them)
-        const unsigned lb = __ballot_sync(0xffffffffu, leaver);
-        if ((threadIdx.x & 31) == 0 && lb) atomicAdd(&c.tile_leave[tile], __popc(lb));
         // MOBIL over the last 32 entries of the warp's queue once it holds
         // 32, and over what is left after the last tile
         __syncwarp();
@@ -416,8 +479,7 @@ __device__ __forceinline__ void resolve_one(const Ctx<Real>& c, MetricAcc& acc, 
             la.stop = (C.bits & CB_STOP) != 0;
             la.overlap = (C.bits & CB_OVERLAP) != 0;
         }
-        if (integrate_emit(c, acc, i, E, EB, la, nlane, fl, (C.bits & CB_OVERLAP) != 0, t, sc, tag))
-            atomicAdd(&c.tile_leave[i / TILE], 1);
+        integrate_emit(c, acc, i, E, EB, la, nlane, fl, (C.bits & CB_OVERLAP) != 0, t, sc, tag);
     }
 }
 
@@ -461,9 +523,9 @@ __device__ __forceinline__ long long block_exclusive_scan(long long x, long long
 }
 
 // One lane tile of k_lanescan (LANESCAN_TILE lanes).  newsize(l) = size(l) -
-// leave(l) + enter(l); two exclusive prefix sums (new sizes, leavers) over
-// lanes in one decoupled look-back pass; tile words pack (flag:2 |
-// leavers:31 | sizes:31).  Warp w takes 512 consecutive lanes of the tile in
+// leave(l) + enter(l); its exclusive prefix sum over lanes (the next lane
+// offsets) in one decoupled look-back pass; tile words pack (flag:2 |
+// sum:62).  Warp w takes 512 consecutive lanes of the tile in
 // 4 rounds of 128 (4 consecutive lanes per thread), so each 16-byte load and
 // store of a warp covers one contiguous 512-byte run.
 constexpr int LS_WARPS = LANESCAN_THREADS / 32;
@@ -478,7 +540,7 @@ __device__ __forceinline__ void lanescan_tile(const Ctx<Real>& c, int tile) {
     const int ln = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nl = c.n_lanes;
     const int wbase = tile * LANESCAN_TILE + w * (LANESCAN_TILE / LS_WARPS);
-    int ns[LS_ROUNDS][4], lv[LS_ROUNDS][4];
+    int ns[LS_ROUNDS][4];
     long long wpre[LS_ROUNDS];
     long long run = 0;
     // every load of the tile is issued before any result is used (and before
@@ -525,16 +587,15 @@ __device__ __forceinline__ void lanescan_tile(const Ctx<Real>& c, int tile) {
         // offset after the thread's 4th lane: the next thread's first
         int onx = __shfl_down_sync(0xffffffffu, o[r][0], 1);
         if (ln == 31) onx = o4[r];
-        long long rs = 0, rl = 0;
+        long long rs = 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const bool valid = l0 + j < nl;
             const int onext = j < 3 ? o[r][j + 1] : onx;
             ns[r][j] = valid ? (onext - o[r][j]) - lvv[r][j] + env[r][j] : 0;
-            lv[r][j] = valid ? lvv[r][j] : 0;
-            rs += ns[r][j]; rl += lv[r][j];
+            rs += ns[r][j];
         }
-        const long long p = (rl << 31) | rs;
+        const long long p = rs;
         long long incl = p;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -574,20 +635,19 @@ __device__ __forceinline__ void lanescan_tile(const Ctx<Real>& c, int tile) {
     for (int r = 0; r < LS_ROUNDS; ++r) {
         const int l0 = wbase + r * 128 + 4 * ln;
         const long long ex = base + wpre[r];
-        long long en = ex & ((1ll << 31) - 1), el = ex >> 31;
-        int on[4], lb[4];
+        long long en = ex;
+        int on[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            on[j] = (int)en; lb[j] = (int)el;
-            en += ns[r][j]; el += lv[r][j];
+            on[j] = (int)en;
+            en += ns[r][j];
         }
         if (l0 + 4 <= nl) {
             *reinterpret_cast<int4*>(c.nxt.off + l0) = make_int4(on[0], on[1], on[2], on[3]);
-            *reinterpret_cast<int4*>(c.lbefore + l0) = make_int4(lb[0], lb[1], lb[2], lb[3]);
         } else {
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-                if (l0 + j < nl) { c.nxt.off[l0 + j] = on[j]; c.lbefore[l0 + j] = lb[j]; }
+                if (l0 + j < nl) c.nxt.off[l0 + j] = on[j];
         }
         if (l0 < nl && nl <= l0 + 4) {  // this thread holds the last lane
             c.nxt.off[nl] = (int)en;
@@ -596,64 +656,9 @@ __device__ __forceinline__ void lanescan_tile(const Ctx<Real>& c, int tile) {
     }
 }
 
-// Exclusive prefix of the leavers per slot tile of the current snapshot (one
-// block; the counters are zeroed for the next step).  Chunks of TP_CHUNK
-// counters go through shared memory: 16-byte coalesced loads in, each thread
-// scans a contiguous run (the padding of one word per 32 keeps the run reads
-// free of bank conflicts), 16-byte coalesced stores out.  The counter arrays
-// are padded to a multiple of 1024 entries and hold zeros past the tiles in
-// use.
-constexpr int TP_CHUNK = 4096;
-__device__ __forceinline__ int tp_pad(int k) { return k + (k >> 5); }
-
-template <typename Real>
-__device__ __forceinline__ void tile_prefix_scan(const Ctx<Real>& c) {
-    __shared__ int sm[TP_CHUNK + TP_CHUNK / 32];
-    const int nt = (c.cnt->n_cur + TILE - 1) / TILE;
-    const int nt4 = ((nt + 4 * LANESCAN_THREADS - 1) / (4 * LANESCAN_THREADS)) * (4 * LANESCAN_THREADS);
-    long long carry = 0;
-    for (int c0 = 0; c0 < nt4; c0 += TP_CHUNK) {
-        const int m = min(TP_CHUNK, nt4 - c0);  // a multiple of 4 * LANESCAN_THREADS
-        // all loads first (one memory round trip), then the zeroing stores
-        int4 x[TP_CHUNK / (4 * LANESCAN_THREADS)];
-#pragma unroll
-        for (int q = 0; q < TP_CHUNK / (4 * LANESCAN_THREADS); ++q) {
-            const int k = 4 * threadIdx.x + q * 4 * LANESCAN_THREADS;
-            x[q] = k < m ? *reinterpret_cast<const int4*>(c.tile_leave + c0 + k) : make_int4(0, 0, 0, 0);
-        }
-#pragma unroll
-        for (int q = 0; q < TP_CHUNK / (4 * LANESCAN_THREADS); ++q) {
-            const int k = 4 * threadIdx.x + q * 4 * LANESCAN_THREADS;
-            if (k < m) {
-                *reinterpret_cast<int4*>(c.tile_leave + c0 + k) = make_int4(0, 0, 0, 0);
-                sm[tp_pad(k)] = x[q].x; sm[tp_pad(k + 1)] = x[q].y; sm[tp_pad(k + 2)] = x[q].z;
-                sm[tp_pad(k + 3)] = x[q].w;
-            }
-        }
-        __syncthreads();
-        const int per = m / LANESCAN_THREADS;
-        const int k0 = per * threadIdx.x;
-        long long sum = 0;
-        for (int j = 0; j < per; ++j) sum += sm[tp_pad(k0 + j)];
-        long long tot;
-        long long ex = block_exclusive_scan(sum, &tot) + carry;
-        for (int j = 0; j < per; ++j) {
-            const int x = sm[tp_pad(k0 + j)];
-            sm[tp_pad(k0 + j)] = (int)ex;
-            ex += x;
-        }
-        __syncthreads();
-        for (int k = 4 * threadIdx.x; k < m; k += 4 * LANESCAN_THREADS)
-            *reinterpret_cast<int4*>(c.tile_prefix + c0 + k) =
-                make_int4(sm[tp_pad(k)], sm[tp_pad(k + 1)], sm[tp_pad(k + 2)], sm[tp_pad(k + 3)]);
-        carry += tot;
-        __syncthreads();
-    }
-}
-
 // k_lanescan.  Tickets [0, n_lane_tiles): next-snapshot lane offsets (lane
-// tiles, above).  Ticket n_lane_tiles: the leaver prefix per slot tile.
-// Remaining tickets: signal states of the next step for chunks of junctions.
+// tiles, above).  Remaining tickets: signal states of the next step for
+// chunks of junctions.
 template <typename Real>
 __device__ __forceinline__ void lanescan_blocks(const Ctx<Real>& c) {
     __shared__ int s_tile;
@@ -671,7 +676,7 @@ __device__ __forceinline__ void lanescan_blocks(const Ctx<Real>& c) {
 #else
     const int n_res = 0;
 #endif
-    const int n_tickets = n_res + c.n_lane_tiles + 1 + c.n_junc_chunks;
+    const int n_tickets = n_res + c.n_lane_tiles + c.n_junc_chunks;
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(&c.cnt->ticket_lane, 1);
         __syncthreads();
@@ -680,12 +685,11 @@ __device__ __forceinline__ void lanescan_blocks(const Ctx<Real>& c) {
         if (tile >= n_tickets) return;
 #if MOSS_FOLD_RESOLVE
         if (tile < n_res) {
+            MetricAcc acc;
+            macc_reset(acc, -1);
             if (tile < r_cand) {
-                MetricAcc acc;
-                macc_reset(acc, -1);
                 const int k = tile * TILE + threadIdx.x;
                 if (k < nc) resolve_one(c, acc, k, nc, tag);
-                macc_flush_block<TILE>(acc, c.metrics);
             } else {
                 const int k = (tile - r_cand) * TILE + threadIdx.x;
                 if (k < c.n_jj) mp_accumulate(c, k);
@@ -695,9 +699,13 @@ __device__ __forceinline__ void lanescan_blocks(const Ctx<Real>& c) {
                 __threadfence();
                 atomicAdd(&c.cnt->res_done, 1);
             }
+            // the metric sums are read by no later ticket: after the signal
+            macc_flush_block<TILE>(acc, c.metrics);
             continue;
         }
-        if (!s_ready) {
+        // lane tiles read the enter / leave counts the candidates change;
+        // junction tickets read only the max-pressure sums
+        if (!s_ready && (tile - n_res < c.n_lane_tiles || *c.n_mp > 0)) {
             if (threadIdx.x == 0) {
                 cuda::atomic_ref<int, cuda::thread_scope_device> done(c.cnt->res_done);
                 long long spins = 0;
@@ -713,11 +721,9 @@ __device__ __forceinline__ void lanescan_blocks(const Ctx<Real>& c) {
 #endif
         if (tile < c.n_lane_tiles) {
             lanescan_tile(c, tile);
-        } else if (tile == c.n_lane_tiles) {
-            tile_prefix_scan(c);
         } else {
             // signal states of the next step
-            const int j0 = (tile - c.n_lane_tiles - 1) * JUNC_CHUNK;
+            const int j0 = (tile - c.n_lane_tiles) * JUNC_CHUNK;
             const int j = j0 + threadIdx.x;
             if (j < c.n_junctions && !c.scen_ctl[c.junc[j].scen])
                 c.junc_state[j] = c.junc_policy[j] == POL_MAXP ? mp_advance(c, j) : junction_state_at(c, j, 1);
@@ -739,13 +745,15 @@ __global__ void __launch_bounds__(LANESCAN_THREADS) k_lanescan(Ctx<Real> c) {
 // lane minus the leavers before it in the lane.  Then the entrants: rank =
 // stayers ahead + entrants ahead.  The last block to finish closes the step.
 template <typename Real>
-__device__ __forceinline__ int entrants_ahead(const Ctx<Real>& c, int lane, Real s, int id, int tag) {
+__device__ __forceinline__ int entrants_ahead(const Ctx<Real>& c, int lane, Real s, int id, int tag,
+                                              int* n_in = nullptr) {
     int cnt = 0, guard = 0;
     for (int q = list_head(c.head, lane, tag); q >= 0; q = c.enext[q]) {
         const RecA<Real> Q = c.ea[q];
         if (ahead(Q.s, Q.id, s, id)) ++cnt;
         if (++guard > c.n_veh) { atomicOr(c.err, ERR_RANGE); break; }
     }
+    if (n_in) *n_in = guard;
     return cnt;
 }
 
@@ -775,8 +783,11 @@ __device__ __forceinline__ void place_blocks(const Ctx<Real>& c, int vb, int nvb
             if (t == c.stop_at[s]) c.scen_ctl[s] = SC_FROZEN;  // reached its horizon
         }
     }
+    __shared__ int s_lpre[TILE];  // leavers among the tile's slots before each slot
+    __shared__ int s_first;       // start of the lane that holds the tile's first slot
     for (int tile = vb; tile < n_tiles; tile += nvb) {
-        const int i = tile * TILE + threadIdx.x;
+        const int t0 = tile * TILE;
+        const int i = t0 + threadIdx.x;
         const bool valid = i < n;
         const int8_t code = valid ? c.code[i] : C_STAY;
         RecA<Real> A;
@@ -791,14 +802,27 @@ __device__ __forceinline__ void place_blocks(const Ctx<Real>& c, int vb, int nvb
         const unsigned ball = __ballot_sync(0xffffffffu, leaver);
         const int wpre = __popc(ball & ((1u << lane_id) - 1));
         if (lane_id == 0) s_warp[warp] = __popc(ball);
+        if (threadIdx.x == 0) s_first = c.cur.off[A.lane];
         __syncthreads();
         int wbase = 0;
         for (int w = 0; w < warp; ++w) wbase += s_warp[w];
+        s_lpre[threadIdx.x] = wbase + wpre;
+        // leavers of the first lane in its slots before the tile (that lane
+        // alone can start before the tile)
+        const int f0 = s_first;
+        int pre0 = 0;
+        for (int k0 = t0; k0 > f0; k0 -= TILE) {
+            const int k = k0 - 1 - (int)threadIdx.x;
+            pre0 += __syncthreads_count(k >= f0 && c.code[k] != C_STAY);
+        }
         __syncthreads();
         if (valid && code == C_STAY) {
+            // its rank among the lane's stayers: slots ahead of it in the
+            // lane minus the leavers among them
             const int lane = A.lane;
-            const int leavers_before = c.tile_prefix[tile] + wbase + wpre;
-            const int stay_rank = (i - c.cur.off[lane]) - (leavers_before - c.lbefore[lane]);
+            const int ob = c.cur.off[lane];
+            const int lv = ob < t0 ? pre0 + s_lpre[threadIdx.x] : s_lpre[threadIdx.x] - s_lpre[ob - t0];
+            const int stay_rank = (i - ob) - lv;
             const int pos = c.nxt.off[lane] + stay_rank + entrants_ahead(c, lane, w.s, A.id, tag);
             if (pos < c.nxt.off[lane] || pos >= c.nxt.off[lane + 1]) {
                 atomicOr(c.err, ERR_RANGE);
@@ -809,23 +833,37 @@ __device__ __forceinline__ void place_blocks(const Ctx<Real>& c, int vb, int nvb
                 c.nxt.b[pos] = B;
             }
         }
+        __syncthreads();  // s_warp, s_lpre and s_first serve the next tile
     }
-    // entrants: one warp per entrant; the warp counts the stayers of the
-    // lane's old segment that are ahead of it, 32 slots per round
+    // entrants: one warp per entrant.  The stayers of a lane keep their
+    // order (nobody overtakes within a lane, R13), so the stayers behind an
+    // entrant form the rear of the lane's old segment: the warp counts them
+    // from the segment's end, 32 slots per round, and stops at the first
+    // round that holds a stayer ahead of the entrant (entrants join mostly
+    // at the rear of a lane: one round).  Stayers ahead = the lane's stayers
+    // (its next size minus its entrants) minus those behind.
     const int gwarp = vb * (TILE / 32) + warp, nwarps = nvb * (TILE / 32);
     for (int q = gwarp; q < n_ent; q += nwarps) {
         const RecA<Real> Q = c.ea[q];
         const int lane = Q.lane;
         const int b = c.cur.off[lane], e = c.cur.off[lane + 1];
-        int rank = 0;
-        for (int k = b + lane_id; k - lane_id < e; k += 32) {
-            const bool p = k < e && c.code[k] == C_STAY && ahead(c.stay[k].s, c.cur.a[k].id, Q.s, Q.id);
-            rank += __popc(__ballot_sync(0xffffffffu, p));
+        int behind = 0;
+        for (int k0 = e - 1; k0 >= b; k0 -= 32) {
+            const int k = k0 - lane_id;
+            bool st = false, ah = false;
+            if (k >= b && c.code[k] == C_STAY) {
+                st = true;
+                ah = ahead(c.stay[k].s, c.cur.a[k].id, Q.s, Q.id);
+            }
+            behind += __popc(__ballot_sync(0xffffffffu, st && !ah));
+            if (__any_sync(0xffffffffu, ah)) break;
         }
         if (lane_id == 0) {
-            rank += entrants_ahead(c, lane, Q.s, Q.id, tag);
-            const int pos = c.nxt.off[lane] + rank;
-            if (pos < c.nxt.off[lane] || pos >= c.nxt.off[lane + 1]) {
+            int n_in = 0;
+            const int ent_ahead = entrants_ahead(c, lane, Q.s, Q.id, tag, &n_in);
+            const int o0 = c.nxt.off[lane], o1 = c.nxt.off[lane + 1];
+            const int pos = o0 + (o1 - o0 - n_in - behind) + ent_ahead;
+            if (pos < o0 || pos >= o1) {
                 atomicOr(c.err, ERR_RANGE);
             } else {
                 c.nxt.a[pos] = Q;
