@@ -573,6 +573,7 @@ def run_batched(args, emit=True):
         tuned = batch.autotune(1)
         batch.step(args.warmup)
         batch.synchronize()
+        t_timed = int(batch.metrics(0)["step"])  # the step the timed steps start from
         u0 = sum(batch.metrics(i)["vehicle_updates"] for i in range(len(scens)))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if dist:
@@ -613,7 +614,7 @@ def run_batched(args, emit=True):
         if world == 1:
             for s_ in scens:
                 sim = binding.Simulation(s_.net, s_.veh, s_.params, precision=32, stream=stream.cuda_stream)
-                sim.step(pre + 9 + args.warmup)  # the batch's autotune advanced it by 9 steps
+                sim.step(t_timed)  # the same state as the batch's timed steps start from
                 sim.synchronize()
                 m0 = sim.metrics()["vehicle_updates"]
                 e0.record(stream)

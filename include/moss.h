@@ -466,14 +466,31 @@ int moss_set_step_mode(moss_t h, int mode);
 int moss_step_launches(moss_t h, int* out);
 
 /*
- * Autotuner of the launch schedule: times the next steps of the simulation
- * (9 x trial_steps of them; they are simulated normally, and the results do
- * not depend on the schedule) under candidate block counts per SM of the
- * step kernels, keeps the fastest (coordinate search: decide in {3,4,5},
- * lanescan in {1,2,4}, place in {4,8,16}) and re-captures the step graphs.
- * chosen3 (may be NULL) receives the chosen decide/lanescan/place values.
+ * Autotuner of the launch schedule (no counterpart in the paper): times the
+ * next steps of the simulation (16 x trial_steps of them, 14 without
+ * cooperative launch; they are simulated normally, and the results do not
+ * depend on the schedule) under candidate schedules, keeps the fastest by
+ * coordinate search over, in this order: k_decide blocks per SM {3,4,5}; the
+ * weight of a road-lane vehicle in the split of the snapshot into k_decide's
+ * block runs {1,2,3} (a junction-lane vehicle weighs 1); k_lanescan blocks
+ * per SM {1,2,4}; lanes per thread of a lane-scan tile {16,8}; k_place
+ * blocks per SM {4,8,16}; the step mode {0,1} (moss_set_step_mode).  Then it
+ * re-captures the step graphs.  chosen3 (may be NULL) receives the chosen
+ * decide/lanescan/place blocks per SM; moss_get_schedule returns all six.
  */
 int moss_autotune(moss_t h, int trial_steps, int* chosen3);
+
+/*
+ * The launch schedule (no counterpart in the paper): out6 / in6 = k_decide,
+ * k_lanescan and k_place blocks per SM, the road-lane weight of k_decide's
+ * runs, lanes per thread of a lane-scan tile (8 or 16) and the step mode (0
+ * or 1), as moss_autotune describes.  moss_set_schedule checks the ranges
+ * (blocks per SM 1..16 for k_decide, 1..32 for the others; weight 1..8),
+ * waits for the handle's stream and re-captures the step graphs; on an error
+ * the previous schedule stays.  Results never depend on the schedule.
+ */
+int moss_get_schedule(moss_t h, int* out6);
+int moss_set_schedule(moss_t h, const int* in6);
 
 /*
  * Failure-detection self-test (no counterpart in the paper).  Launches one

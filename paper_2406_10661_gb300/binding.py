@@ -146,6 +146,8 @@ SIGNATURES = {
     "moss_kernel_times": (ctypes.c_int, [_vp, _c_f64p, ctypes.POINTER(ctypes.c_int64)]),
     "moss_lane_offsets_noalloc": (ctypes.c_int, [ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "moss_autotune": (ctypes.c_int, [_vp, ctypes.c_int, _c_i32p]),
+    "moss_get_schedule": (ctypes.c_int, [_vp, _c_i32p]),
+    "moss_set_schedule": (ctypes.c_int, [_vp, _c_i32p]),
     "moss_set_step_mode": (ctypes.c_int, [_vp, ctypes.c_int]),
     "moss_step_launches": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "moss_selftest_bounded_wait": (ctypes.c_int, [_vp]),
@@ -277,11 +279,25 @@ class _Handle:
     def set_kernel_timing(self, on: bool) -> None:
         _check(self.lib.moss_set_kernel_timing(self.h, int(bool(on))), self.h)
 
+    SCHEDULE_KEYS = ("decide", "lanescan", "place", "road_weight", "lanes_per_thread", "step_mode")
+
     def autotune(self, trial_steps: int = 3):
-        """Pick the fastest launch schedule on the next 9 * trial_steps steps."""
+        """Pick the fastest launch schedule on the next 16 * trial_steps steps;
+        returns the whole schedule (``schedule()``)."""
         out = np.zeros(3, dtype=np.int32)
         _check(self.lib.moss_autotune(self.h, int(trial_steps), _ptr(out, ctypes.c_int32)), self.h)
-        return dict(zip(("decide", "lanescan", "place"), out.tolist()))
+        return self.schedule()
+
+    def schedule(self) -> Dict[str, int]:
+        out = np.zeros(6, dtype=np.int32)
+        _check(self.lib.moss_get_schedule(self.h, _ptr(out, ctypes.c_int32)), self.h)
+        return dict(zip(self.SCHEDULE_KEYS, out.tolist()))
+
+    def set_schedule(self, **kw) -> None:
+        cur = self.schedule()
+        cur.update(kw)
+        arr = np.array([cur[k] for k in self.SCHEDULE_KEYS], dtype=np.int32)
+        _check(self.lib.moss_set_schedule(self.h, _ptr(arr, ctypes.c_int32)), self.h)
 
     def metrics_enqueue(self, slot: int, scenario: int = 0) -> None:
         """Queue a copy of the metrics (as after the work enqueued so far) into

@@ -133,6 +133,8 @@ struct MossHandle {
 
     // launch configuration (blocks per SM) of the step kernels; moss_autotune picks them
     int cfg_decide = MOSS_DECIDE_MIN_BLOCKS, cfg_lanescan = 4, cfg_place = 8;
+    int cfg_runw = 2;    // weight of a road-lane slot in k_decide's runs
+    int cfg_lsr = 4;     // rounds of 128 lanes per warp in a lane-scan tile (4 or 2)
 
     int parity = 0;  // snapshot buffer holding the current step
     int step_mode = 0;               // 0: three kernels per step; 1: one cooperative launch
@@ -350,6 +352,12 @@ bool same_model(const MossParams& a, const MossParams& b) {
 size_t reca_size(int precision) { return precision == 64 ? sizeof(RecA<double>) : sizeof(RecA<float>); }
 size_t sv_size(int precision) { return precision == 64 ? sizeof(SV<double>) : sizeof(SV<float>); }
 
+// lane-scan tiles of a step with `rounds` rounds of 128 lanes per warp
+int lane_tiles(const MossHandle* h, int rounds) {
+    const int tile = LANESCAN_THREADS * 4 * rounds;
+    return (h->n_lanes + tile - 1) / tile;
+}
+
 template <typename Real>
 Ctx<Real> make_ctx(MossHandle* h, int cur) {
     Ctx<Real> c;
@@ -379,7 +387,8 @@ Ctx<Real> make_ctx(MossHandle* h, int cur) {
     c.ea = (RecA<Real>*)h->d_ea; c.eb = h->d_eb; c.enext = h->d_enext; c.head = h->d_head;
     c.enter = h->d_enter; c.leave = h->d_leave; c.lane_tiles = h->d_lane_tiles;
     c.cands = (Cand<Real>*)h->d_cands; c.gap_head = h->d_gap_head;
-    c.n_lane_tiles = h->n_lane_tiles; c.max_slot_tiles = h->max_slot_tiles;
+    c.n_lane_tiles = lane_tiles(h, h->cfg_lsr); c.max_slot_tiles = h->max_slot_tiles;
+    c.run_w = h->cfg_runw;
     c.n_junc_chunks = h->n_junc_chunks; c.cnt = h->d_cnt + cur;
     c.cnt_next = h->d_cnt + (1 - cur); c.err = &h->d_cnt[0].err;
     const MossParams& p = h->prm;
@@ -405,7 +414,7 @@ Grids grids(const MossHandle* h) {
     // the lane scan's tickets, plus (MOSS_FOLD_RESOLVE) the candidate and
     // max-pressure chunks in front of them: their number is known on the
     // device only, so the grid takes every resident block it may need
-    const int tickets = h->n_lane_tiles + h->n_junc_chunks + (MOSS_FOLD_RESOLVE ? (h->n_jj + TILE - 1) / TILE + 8 : 0);
+    const int tickets = lane_tiles(h, h->cfg_lsr) + h->n_junc_chunks + (MOSS_FOLD_RESOLVE ? (h->n_jj + TILE - 1) / TILE + 8 : 0);
     g.lanescan = std::max(1, std::min(tickets, h->sm_count * h->cfg_lanescan));
     g.place = std::max(1, std::min(2 * h->max_slot_tiles, h->sm_count * h->cfg_place));
     return g;
@@ -434,6 +443,7 @@ void enqueue_step(MossHandle* h, int cur, bool timed) {
     cudaStream_t s = h->stream;
     if (timed) cudaEventRecord(h->ev[0], s);
     if (h->step_mode == 1) {
+        c.n_lane_tiles = lane_tiles(h, 4);  // the single-launch step scans with the default tile
         const cudaError_t e = h->lane_groups ? launch_coop<Real, true>(h, c) : launch_coop<Real, false>(h, c);
         if (e != cudaSuccess) h->launch_err = e;
         if (timed)
@@ -447,7 +457,8 @@ void enqueue_step(MossHandle* h, int cur, bool timed) {
     k_resolve<Real><<<g.resolve, TILE, 0, s>>>(c);
 #endif
     if (timed) cudaEventRecord(h->ev[2], s);
-    k_lanescan<Real><<<g.lanescan, LANESCAN_THREADS, 0, s>>>(c);
+    if (h->cfg_lsr == 2) k_lanescan<Real, 2><<<g.lanescan, LANESCAN_THREADS, 0, s>>>(c);
+    else k_lanescan<Real, 4><<<g.lanescan, LANESCAN_THREADS, 0, s>>>(c);
     if (timed) cudaEventRecord(h->ev[3], s);
     k_place<Real><<<g.place, TILE, 0, s>>>(c);
     if (timed) cudaEventRecord(h->ev[4], s);
@@ -768,7 +779,7 @@ int device_setup(MossHandle* h, void* stream) {
     TRY(upload(h, &h->d_head, std::vector<unsigned long long>(NL, 0ull)));
     TRY(upload(h, &h->d_enter, std::vector<int32_t>(NL, 0)));
     TRY(upload(h, &h->d_leave, std::vector<int32_t>(NL, 0)));
-    h->n_lane_tiles = (NL + LANESCAN_TILE - 1) / LANESCAN_TILE;
+    h->n_lane_tiles = lane_tiles(h, 2);  // look-back words for the smaller tile
     h->max_slot_tiles = (NV + TILE - 1) / TILE + 1;
     h->n_junc_chunks = (NJ + JUNC_CHUNK - 1) / JUNC_CHUNK;
     TRY(upload(h, &h->d_lane_tiles, std::vector<unsigned long long>(h->n_lane_tiles, 0ull)));
@@ -1973,28 +1984,69 @@ int moss_autotune(moss_t h, int trial_steps, int* chosen3) {
     if (!h) return MOSS_EINVAL;
     if (trial_steps < 1) return fail(h, MOSS_EINVAL, "trial_steps must be >= 1");
     CK(cudaStreamSynchronize(h->stream));
-    // coordinate search over blocks per SM of each kernel; results do not
-    // depend on the launch configuration, only the time does
-    static const int cand_decide[] = {3, 4, 5};
-    static const int cand_lanescan[] = {1, 2, 4};
-    static const int cand_place[] = {4, 8, 16};
-    const int* cands[3] = {cand_decide, cand_lanescan, cand_place};
-    int* knobs[3] = {&h->cfg_decide, &h->cfg_lanescan, &h->cfg_place};
-    for (int d = 0; d < 3; ++d) {
-        int best = *knobs[d];
+    // coordinate search over the schedule: blocks per SM of each kernel, the
+    // road-lane weight of k_decide's runs, the lane-scan tile and the step
+    // mode; results do not depend on the schedule, only the time does
+    int coop = 0;
+    CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device));
+    struct Knob { int* v; int n; int c[3]; };
+    const Knob knobs[] = {
+        {&h->cfg_decide, 3, {3, 4, 5}},   {&h->cfg_runw, 3, {1, 2, 3}}, {&h->cfg_lanescan, 3, {1, 2, 4}},
+        {&h->cfg_lsr, 2, {4, 2, 0}},      {&h->cfg_place, 3, {4, 8, 16}}, {&h->step_mode, coop ? 2 : 1, {0, 1, 0}},
+    };
+    for (const Knob& kb : knobs) {
+        int best = *kb.v;
         double best_ms = 1e300;
-        for (int k = 0; k < 3; ++k) {
-            *knobs[d] = cands[d][k];
+        for (int k = 0; k < kb.n; ++k) {
+            *kb.v = kb.c[k];
+            h->launch_err = cudaSuccess;
             double ms = 0;
             TRY(time_steps(h, trial_steps, &ms));
-            if (ms < best_ms) { best_ms = ms; best = cands[d][k]; }
+            if (h->launch_err != cudaSuccess) {  // a mode this device cannot launch
+                h->launch_err = cudaSuccess;
+                continue;
+            }
+            if (ms < best_ms) { best_ms = ms; best = kb.c[k]; }
         }
-        *knobs[d] = best;
+        *kb.v = best;
     }
     destroy_graphs(h);
     TRY(build_graphs(h));
     if (chosen3) { chosen3[0] = h->cfg_decide; chosen3[1] = h->cfg_lanescan; chosen3[2] = h->cfg_place; }
     return check_device(h);
+}
+
+int moss_get_schedule(moss_t h, int* out6) {
+    if (!h || !out6) return MOSS_EINVAL;
+    out6[0] = h->cfg_decide; out6[1] = h->cfg_lanescan; out6[2] = h->cfg_place;
+    out6[3] = h->cfg_runw; out6[4] = 4 * h->cfg_lsr; out6[5] = h->step_mode;
+    return MOSS_OK;
+}
+
+int moss_set_schedule(moss_t h, const int* in6) {
+    if (!h || !in6) return MOSS_EINVAL;
+    if (in6[0] < 1 || in6[0] > 16 || in6[1] < 1 || in6[1] > 32 || in6[2] < 1 || in6[2] > 32 || in6[3] < 1 ||
+        in6[3] > 8 || (in6[4] != 8 && in6[4] != 16) || (in6[5] != 0 && in6[5] != 1))
+        return fail(h, MOSS_EINVAL, "schedule value out of range");
+    if (in6[5] == 1) {
+        int coop = 0;
+        CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device));
+        if (!coop) return fail(h, MOSS_EINVAL, "the device has no cooperative launch");
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    const int old[6] = {h->cfg_decide, h->cfg_lanescan, h->cfg_place, h->cfg_runw, h->cfg_lsr, h->step_mode};
+    h->cfg_decide = in6[0]; h->cfg_lanescan = in6[1]; h->cfg_place = in6[2];
+    h->cfg_runw = in6[3]; h->cfg_lsr = in6[4] / 4; h->step_mode = in6[5];
+    destroy_graphs(h);
+    const int rc = build_graphs(h);
+    if (rc != MOSS_OK) {
+        h->cfg_decide = old[0]; h->cfg_lanescan = old[1]; h->cfg_place = old[2];
+        h->cfg_runw = old[3]; h->cfg_lsr = old[4]; h->step_mode = old[5];
+        destroy_graphs(h);
+        TRY(build_graphs(h));
+        return rc;
+    }
+    return MOSS_OK;
 }
 
 int moss_selftest_bounded_wait(void* cuda_stream) {

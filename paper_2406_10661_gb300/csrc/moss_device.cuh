@@ -219,6 +219,7 @@ struct Ctx {
     unsigned long long* gap_head;  // [n_veh + n_lanes + 1] (tag << 32 | candidate) or stale
     unsigned long long* lane_tiles;
     int n_lane_tiles, max_slot_tiles, n_junc_chunks;
+    int run_w;           // weight of a road-lane slot in k_decide's runs (junction-lane slot: 1)
     Counters* cnt;       // this step's counters
     Counters* cnt_next;  // the next step's
     int* err;            // device error bits

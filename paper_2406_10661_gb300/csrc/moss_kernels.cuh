@@ -255,14 +255,22 @@ __device__ __forceinline__ void mobil_finish(const Ctx<Real>& c, const MobilQueu
 #endif
 // The run of slot tiles of work block vb of n_work.  A vehicle on a road lane
 // costs about twice one on a junction lane (MOBIL, longer neighbour
-// searches), so the runs split the snapshot by weight: 2 per road-lane slot,
-// 1 per junction-lane slot, from the current lane offsets at the lane ranges
-// of each scenario (road lanes first, then junction lanes).  Warp 0
-// computes it; the runs are contiguous and cover every tile.
-__device__ __forceinline__ long long run_weight(int a, int b, int e) { return 2ll * (b - a) + (e - b); }
+// searches), so the runs split the snapshot by weight: run_w (a schedule
+// choice, 2 by default) per road-lane slot, 1 per junction-lane slot, from
+// the current lane offsets at the lane ranges of each scenario (road lanes
+// first, then junction lanes), when blocks take four tiles or more each.
+// Warp 0 computes it; the runs are contiguous and cover every tile.
+__device__ __forceinline__ long long run_weight(int a, int b, int e, int w) { return (long long)w * (b - a) + (e - b); }
 
 template <typename Real>
 __device__ __forceinline__ void decide_run(const Ctx<Real>& c, int n_tiles, int n_work, int vb, int* tb, int* te) {
+    if (n_tiles < 4 * n_work) {
+        // a few tiles per block: weights at tile granularity would leave
+        // blocks idle; runs of equal tile counts (differing by one at most)
+        *tb = (int)((long long)vb * n_tiles / n_work);
+        *te = (int)((long long)(vb + 1) * n_tiles / n_work);
+        return;
+    }
     __shared__ int s_run[2];
     if (threadIdx.x < 32) {
         const int wl = threadIdx.x;
@@ -271,7 +279,7 @@ __device__ __forceinline__ void decide_run(const Ctx<Real>& c, int n_tiles, int 
             long long w = 0;
             if (k0 + wl < c.n_scen) {
                 const int4 L = c.scen_lanes[k0 + wl];
-                w = run_weight(c.cur.off[L.x], c.cur.off[L.y], c.cur.off[L.z]);
+                w = run_weight(c.cur.off[L.x], c.cur.off[L.y], c.cur.off[L.z], c.run_w);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
@@ -288,7 +296,7 @@ __device__ __forceinline__ void decide_run(const Ctx<Real>& c, int n_tiles, int 
             if (k < c.n_scen) {
                 const int4 L = c.scen_lanes[k];
                 a = c.cur.off[L.x]; b = c.cur.off[L.y]; e = c.cur.off[L.z];
-                w = run_weight(a, b, e);
+                w = run_weight(a, b, e, c.run_w);
             }
             long long P = w;  // inclusive prefix over the chunk
 #pragma unroll
@@ -305,7 +313,8 @@ __device__ __forceinline__ void decide_run(const Ctx<Real>& c, int n_tiles, int 
                     const int src = __ffs(m) - 1;
                     const long long local = T[q] - (carry + __shfl_sync(0xffffffffu, P - w, src));
                     const int sa = __shfl_sync(0xffffffffu, a, src), sb = __shfl_sync(0xffffffffu, b, src);
-                    slot[q] = local < 2ll * (sb - sa) ? sa + (int)(local / 2) : sb + (int)(local - 2ll * (sb - sa));
+                    const long long wr = (long long)c.run_w * (sb - sa);
+                    slot[q] = local < wr ? sa + (int)(local / c.run_w) : sb + (int)(local - wr);
                 }
             }
             carry += __shfl_sync(0xffffffffu, P, 31);
@@ -522,24 +531,25 @@ __device__ __forceinline__ long long block_exclusive_scan(long long x, long long
     return base + incl - x;
 }
 
-// One lane tile of k_lanescan (LANESCAN_TILE lanes).  newsize(l) = size(l) -
-// leave(l) + enter(l); its exclusive prefix sum over lanes (the next lane
-// offsets) in one decoupled look-back pass; tile words pack (flag:2 |
-// sum:62).  Warp w takes 512 consecutive lanes of the tile in
-// 4 rounds of 128 (4 consecutive lanes per thread), so each 16-byte load and
-// store of a warp covers one contiguous 512-byte run.
+// One lane tile of k_lanescan (LS_ROUNDS x 1024 lanes).  newsize(l) =
+// size(l) - leave(l) + enter(l); its exclusive prefix sum over lanes (the
+// next lane offsets) in one decoupled look-back pass; tile words pack
+// (flag:2 | sum:62).  Warp w takes LS_ROUNDS x 128 consecutive lanes of the
+// tile in LS_ROUNDS rounds of 128 (4 consecutive lanes per thread), so each
+// 16-byte load and store of a warp covers one contiguous 512-byte run.  The
+// tile size is a schedule choice (moss_autotune): 4 rounds (4096 lanes) or 2.
 constexpr int LS_WARPS = LANESCAN_THREADS / 32;
-constexpr int LS_ROUNDS = LANESCAN_TILE / LS_WARPS / 128;
-static_assert(LS_ROUNDS * 128 * LS_WARPS == LANESCAN_TILE, "lane tile = warps x rounds x 128 lanes");
+static_assert(LANESCAN_TILE == LS_WARPS * 128 * 4, "the default lane tile has 4 rounds");
 static_assert(JUNC_CHUNK == LANESCAN_THREADS, "one junction per thread");
 
-template <typename Real>
+template <typename Real, int LS_ROUNDS>
 __device__ __forceinline__ void lanescan_tile(const Ctx<Real>& c, int tile) {
+    constexpr int LS_TILE = LS_WARPS * 128 * LS_ROUNDS;
     __shared__ long long s_wsum[LS_WARPS];
     __shared__ unsigned long long s_prefix;
     const int ln = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nl = c.n_lanes;
-    const int wbase = tile * LANESCAN_TILE + w * (LANESCAN_TILE / LS_WARPS);
+    const int wbase = tile * LS_TILE + w * (LS_TILE / LS_WARPS);
     int ns[LS_ROUNDS][4];
     long long wpre[LS_ROUNDS];
     long long run = 0;
@@ -659,7 +669,7 @@ __device__ __forceinline__ void lanescan_tile(const Ctx<Real>& c, int tile) {
 // k_lanescan.  Tickets [0, n_lane_tiles): next-snapshot lane offsets (lane
 // tiles, above).  Remaining tickets: signal states of the next step for
 // chunks of junctions.
-template <typename Real>
+template <typename Real, int LS_ROUNDS = 4>
 __device__ __forceinline__ void lanescan_blocks(const Ctx<Real>& c) {
     __shared__ int s_tile;
 #if MOSS_FOLD_RESOLVE
@@ -720,7 +730,7 @@ __device__ __forceinline__ void lanescan_blocks(const Ctx<Real>& c) {
         tile -= n_res;
 #endif
         if (tile < c.n_lane_tiles) {
-            lanescan_tile(c, tile);
+            lanescan_tile<Real, LS_ROUNDS>(c, tile);
         } else {
             // signal states of the next step
             const int j0 = (tile - c.n_lane_tiles) * JUNC_CHUNK;
@@ -732,10 +742,10 @@ __device__ __forceinline__ void lanescan_blocks(const Ctx<Real>& c) {
     }
 }
 
-template <typename Real>
+template <typename Real, int LS_ROUNDS>
 __global__ void __launch_bounds__(LANESCAN_THREADS) k_lanescan(Ctx<Real> c) {
     if (*c.err & ERR_POISON) return;
-    lanescan_blocks(c);
+    lanescan_blocks<Real, LS_ROUNDS>(c);
 }
 
 // ---------------------------------------------------------------------------
@@ -783,8 +793,8 @@ __device__ __forceinline__ void place_blocks(const Ctx<Real>& c, int vb, int nvb
             if (t == c.stop_at[s]) c.scen_ctl[s] = SC_FROZEN;  // reached its horizon
         }
     }
-    __shared__ int s_lpre[TILE];  // leavers among the tile's slots before each slot
-    __shared__ int s_first;       // start of the lane that holds the tile's first slot
+    __shared__ int s_lpre[TILE + 1];  // leavers among the tile's slots before each slot (and in all)
+    __shared__ int s_first[2];        // start and end of the lane that holds the tile's first slot
     for (int tile = vb; tile < n_tiles; tile += nvb) {
         const int t0 = tile * TILE;
         const int i = t0 + threadIdx.x;
@@ -802,29 +812,47 @@ __device__ __forceinline__ void place_blocks(const Ctx<Real>& c, int vb, int nvb
         const unsigned ball = __ballot_sync(0xffffffffu, leaver);
         const int wpre = __popc(ball & ((1u << lane_id) - 1));
         if (lane_id == 0) s_warp[warp] = __popc(ball);
-        if (threadIdx.x == 0) s_first = c.cur.off[A.lane];
+        if (threadIdx.x == 0) {
+            s_first[0] = c.cur.off[A.lane];
+            s_first[1] = c.cur.off[A.lane + 1];
+        }
         __syncthreads();
         int wbase = 0;
         for (int w = 0; w < warp; ++w) wbase += s_warp[w];
         s_lpre[threadIdx.x] = wbase + wpre;
-        // leavers of the first lane in its slots before the tile (that lane
-        // alone can start before the tile)
-        const int f0 = s_first;
+        if (threadIdx.x == TILE - 1) s_lpre[TILE] = wbase + wpre + leaver;
+        // a lane that covers the whole tile: its leavers before the tile
+        const int f0 = s_first[0], f1 = s_first[1];
         int pre0 = 0;
-        for (int k0 = t0; k0 > f0; k0 -= TILE) {
-            const int k = k0 - 1 - (int)threadIdx.x;
-            pre0 += __syncthreads_count(k >= f0 && c.code[k] != C_STAY);
-        }
+        if (f0 < t0 && f1 > t0 + TILE)
+            for (int k0 = t0; k0 > f0; k0 -= TILE) {
+                const int k = k0 - 1 - (int)threadIdx.x;
+                pre0 += __syncthreads_count(k >= f0 && c.code[k] != C_STAY);
+            }
         __syncthreads();
         if (valid && code == C_STAY) {
-            // its rank among the lane's stayers: slots ahead of it in the
-            // lane minus the leavers among them
+            // its rank among the lane's stayers: from the lane's start (slots
+            // ahead of it minus the leavers among them) when the lane starts
+            // in the tile; from the lane's end (the lane's stayers minus
+            // those behind it) when the lane started before the tile and
+            // ends in it; else with the leavers before the tile counted above
             const int lane = A.lane;
-            const int ob = c.cur.off[lane];
-            const int lv = ob < t0 ? pre0 + s_lpre[threadIdx.x] : s_lpre[threadIdx.x] - s_lpre[ob - t0];
-            const int stay_rank = (i - ob) - lv;
-            const int pos = c.nxt.off[lane] + stay_rank + entrants_ahead(c, lane, w.s, A.id, tag);
-            if (pos < c.nxt.off[lane] || pos >= c.nxt.off[lane + 1]) {
+            const int ob = c.cur.off[lane], oe = c.cur.off[lane + 1];
+            const int o0 = c.nxt.off[lane], o1 = c.nxt.off[lane + 1];
+            int n_in = 0;
+            const int ent = entrants_ahead(c, lane, w.s, A.id, tag, &n_in);
+            const int x = threadIdx.x;
+            int stay_rank;
+            if (ob >= t0) {
+                stay_rank = (i - ob) - (s_lpre[x] - s_lpre[ob - t0]);
+            } else if (oe <= t0 + TILE) {
+                const int behind = (oe - 1 - i) - (s_lpre[oe - t0] - s_lpre[x + 1]);
+                stay_rank = (o1 - o0 - n_in) - 1 - behind;
+            } else {
+                stay_rank = (i - ob) - (pre0 + s_lpre[x]);
+            }
+            const int pos = o0 + stay_rank + ent;
+            if (pos < o0 || pos >= o1) {
                 atomicOr(c.err, ERR_RANGE);
             } else {
                 RecA<Real> O;

@@ -114,3 +114,53 @@ def test_allocator_with_one_function_is_refused():
     bad = binding.MossAllocator(binding.torch_allocator().alloc, binding.RELEASE_FN(), None)
     with pytest.raises(binding.MossError):
         binding.Simulation(scen.net, scen.veh, scen.params, allocator=bad)
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_schedules_give_the_same_results(precision):
+    """Every launch schedule (blocks per SM, the road-lane weight of the
+    decide runs, the lane-scan tile, the step mode) advances the simulation
+    identically; the autotuner steps it normally and reports its choice."""
+    scen = sc.medium_scenario(n=15_000)
+    ref = binding.Simulation(scen.net, scen.veh, scen.params, precision=precision)
+    ref.step(150)
+    want_state, want_metrics = ref.state(), ref.metrics()
+    schedules = [dict(decide=3, lanescan=1, place=4, road_weight=1, lanes_per_thread=8, step_mode=0),
+                 dict(decide=5, lanescan=2, place=16, road_weight=3, lanes_per_thread=16, step_mode=0),
+                 dict(decide=4, lanescan=4, place=8, road_weight=2, lanes_per_thread=8, step_mode=1)]
+    for sched in schedules:
+        sim = binding.Simulation(scen.net, scen.veh, scen.params, precision=precision)
+        sim.step(40)
+        sim.set_schedule(**sched)
+        assert sim.schedule() == sched
+        sim.step(110)
+        st = sim.state()
+        for k in want_state:
+            assert np.array_equal(st[k], want_state[k]), (sched, k)
+        assert sim.metrics() == want_metrics, sched
+        sim.close()
+    sim = binding.Simulation(scen.net, scen.veh, scen.params, precision=precision)
+    sim.step(100)
+    chosen = sim.autotune(2)  # 32 (or 28) more steps
+    assert set(chosen) == set(binding.Simulation.SCHEDULE_KEYS)
+    assert chosen["lanes_per_thread"] in (8, 16) and chosen["step_mode"] in (0, 1)
+    steps = 150 - sim.metrics()["step"]
+    assert steps >= 0
+    sim.step(steps)
+    st = sim.state()
+    for k in want_state:
+        assert np.array_equal(st[k], want_state[k]), k
+    sim.close()
+
+
+def test_schedule_out_of_range_refused():
+    scen = sc.small_scenario()
+    sim = binding.Simulation(scen.net, scen.veh, scen.params)
+    before = sim.schedule()
+    for bad in (dict(decide=0), dict(road_weight=9), dict(lanes_per_thread=12), dict(step_mode=2),
+                dict(place=33)):
+        with pytest.raises(binding.MossError):
+            sim.set_schedule(**bad)
+        assert sim.schedule() == before
+    sim.step(5)
+    assert sim.metrics()["step"] == 5
