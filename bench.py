@@ -37,7 +37,7 @@ sys.path.insert(0, ROOT)
 T_WARM = 3600   # the timed steps start at this step
 SPEC_BYTES = {  # algorithmic bytes per unit with FP32 state (32 B snapshot record per vehicle)
     "decide": 41.0,    # per active vehicle: read its 32 B record, write code + s' + v' (9 B)
-    "lanescan": 20.0,  # per lane: read 2 offsets + leave + enter, write offset + leavers-before
+    "lanescan": 16.0,  # per lane: read its offset + leave + enter, write its next offset
     "place": 73.0,     # per active vehicle: read code, s', v' and the 32 B record, write 32 B
 }
 STEP_BYTES = 64.0      # whole step: read and write one 8x4 B state record per vehicle update
