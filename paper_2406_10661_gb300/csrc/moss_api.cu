@@ -114,7 +114,7 @@ struct MossHandle {
     void* d_stay = nullptr;  // SV<Real>[cap]
     void* d_ea = nullptr;    // RecA<Real>[cap]
     RecB* d_eb = nullptr;
-    int32_t *d_enext = nullptr, *d_enter = nullptr, *d_leave = nullptr;
+    int32_t *d_enext = nullptr, *d_enter = nullptr, *d_leave = nullptr, *d_cand_late = nullptr;
     unsigned long long *d_head = nullptr, *d_lane_tiles = nullptr;
     void* d_cands = nullptr;  // Cand<Real>[cap]
     unsigned long long* d_gap_head = nullptr;
@@ -386,6 +386,7 @@ Ctx<Real> make_ctx(MossHandle* h, int cur) {
     c.code = h->d_code; c.stay = (SV<Real>*)h->d_stay;
     c.ea = (RecA<Real>*)h->d_ea; c.eb = h->d_eb; c.enext = h->d_enext; c.head = h->d_head;
     c.enter = h->d_enter; c.leave = h->d_leave; c.lane_tiles = h->d_lane_tiles;
+    c.cand_late = h->d_cand_late;
     c.cands = (Cand<Real>*)h->d_cands; c.gap_head = h->d_gap_head;
     c.n_lane_tiles = lane_tiles(h, h->cfg_lsr); c.max_slot_tiles = h->max_slot_tiles;
     c.run_w = h->cfg_runw;
@@ -773,6 +774,7 @@ int device_setup(MossHandle* h, void* stream) {
     TRY(dalloc(h, (char**)&h->d_ea, cap * ra));
     TRY(dalloc(h, &h->d_eb, cap));
     TRY(dalloc(h, &h->d_enext, cap));
+    TRY(dalloc(h, &h->d_cand_late, cap));
     TRY(dalloc(h, (char**)&h->d_cands,
                cap * (h->precision == 64 ? sizeof(Cand<double>) : sizeof(Cand<float>))));
     TRY(upload(h, &h->d_gap_head, std::vector<unsigned long long>(cap + NL + 1, 0ull)));
@@ -1832,7 +1834,7 @@ int moss_set_state(moss_t h, const MossState* in, int64_t step) {
     CK(cudaMemcpy(h->d_metrics + M_CUR_ACTIVE, cur, sizeof(cur), cudaMemcpyHostToDevice));
     Counters c{};
     CK(cudaMemcpy(&c, h->d_cnt + h->parity, sizeof(c), cudaMemcpyDeviceToHost));
-    c.n_cur = (int)n_act; c.n_ent = 0; c.n_cand = 0; c.ticket_lane = 0; c.res_done = 0;
+    c.n_cur = (int)n_act; c.n_ent = 0; c.n_cand = 0; c.n_late = 0; c.ticket_lane = 0; c.res_done = 0;
     CK(cudaMemcpy(h->d_cnt + h->parity, &c, sizeof(c), cudaMemcpyHostToDevice));
     TRY(junction_init(h, 0, h->n_junctions));
     CK(cudaStreamSynchronize(h->stream));

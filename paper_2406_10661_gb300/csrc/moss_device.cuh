@@ -78,6 +78,7 @@ struct Counters {
     int n_ent;       // entrants appended this step
     int n_cand;      // lane-change candidates listed this step (for k_resolve)
     int ticket_lane; // k_lanescan tickets
+    int n_late;      // candidates left to k_lanescan (past a k_decide block's own list)
     int tag;         // step tag of the per-lane lists (never 0)
     int err;         // device error bits (set 0 only)
     int n_mp;        // junctions under max pressure (set 0 only)
@@ -216,6 +217,7 @@ struct Ctx {
     int32_t* enter;       // [n_lanes], zeroed by k_lanescan after use
     int32_t* leave;       // [n_lanes], zeroed by k_lanescan after use
     Cand<Real>* cands;    // this step's lane-change candidates (cnt->n_cand of them)
+    int32_t* cand_late;   // indices of the candidates k_lanescan resolves (cnt->n_late)
     unsigned long long* gap_head;  // [n_veh + n_lanes + 1] (tag << 32 | candidate) or stale
     unsigned long long* lane_tiles;
     int n_lane_tiles, max_slot_tiles, n_junc_chunks;

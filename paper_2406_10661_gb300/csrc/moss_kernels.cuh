@@ -19,6 +19,23 @@ __device__ __forceinline__ void list_push(unsigned long long* head, int32_t* ene
 }
 
 // ---------------------------------------------------------------------------
+// A k_decide block's lane-change candidates: their indices in the candidate
+// list, resolved by the block once its run is done; past CAND_LOCAL of them
+// the rest go to the late list that k_lanescan's first tickets resolve.
+constexpr int CAND_LOCAL = 256;
+struct CandLocal {
+    int n;
+    int idx[CAND_LOCAL];
+};
+
+template <typename Real>
+__device__ __forceinline__ void note_candidate(const Ctx<Real>& c, CandLocal& cl, int k) {
+    const int j = atomicAdd(&cl.n, 1);
+    if (j < CAND_LOCAL) cl.idx[j] = k;
+    else c.cand_late[atomicAdd(&c.cnt->n_late, 1)] = k;
+}
+
+// ---------------------------------------------------------------------------
 // Departure insertion (R18) for start lane l: the head of its FIFO enters at
 // s = 0, v = 0 when due and the snapshot's rearmost vehicle on the lane has
 // s - len >= s0 (or the lane is empty).
@@ -164,7 +181,7 @@ __device__ __forceinline__ int integrate_emit(const Ctx<Real>& c, MetricAcc& acc
 // candidate list, linked into the list of its target gap.
 template <typename Real>
 __device__ __forceinline__ void list_candidate(const Ctx<Real>& c, int i, const RecA<Real>& E, const RecB& EB,
-                                               int sc, const Decision<Real>& D, int tag) {
+                                               int sc, const Decision<Real>& D, int tag, CandLocal& cl) {
     int gp;
     if (D.TF >= 0) gp = D.TF;
     else if (D.TL >= 0) gp = D.TL + 1;
@@ -190,255 +207,13 @@ __device__ __forceinline__ void list_candidate(const Ctx<Real>& c, int i, const 
         atomicExch(&c.gap_head[C.gap], ((unsigned long long)(unsigned)tag << 32) | (unsigned)k);
     C.next = (int)(prev >> 32) == tag ? (int)(unsigned)(prev & 0xffffffffull) : -1;
     c.cands[k] = C;
+    note_candidate(c, cl, k);
 }
 
 // ---------------------------------------------------------------------------
-// The vehicles whose attempt draw passed are queued in shared memory, one
-// queue of 64 entries per warp, and MOBIL runs over a warp's queue 32 at a
-// time: a warp otherwise carries the whole MOBIL evaluation of any one of
-// its lanes while the others idle.
-template <typename Real>
-struct MobilQueue {
-    Real a[2 * TILE], gap[2 * TILE], sgap[2 * TILE];  // own-lane kinematics (LaneAcc)
-    int i[2 * TILE], lane[2 * TILE], bits[2 * TILE], nl[2 * TILE];
-    float u_lc[2 * TILE], u_dir[2 * TILE];
-    int n[TILE / 32];
-};
-
-// MOBIL and the update of queued vehicle k (the snapshot and lane records
-// are read again; the own-lane part comes from the queue)
-template <typename Real, bool Groups>
-__device__ __forceinline__ void mobil_finish(const Ctx<Real>& c, const MobilQueue<Real>& q, int k, int n,
-                                             MetricAcc& acc, int tag) {
-    const int i = q.i[k], lane = q.lane[k];
-    const RecA<Real> E = c.cur.a[i];
-    const RecB EB = c.cur.b[i];
-    const LaneInfo li = c.lane[lane];
-    RecA<Real> OLr = no_rec<Real>(), OFr = no_rec<Real>();
-    float of_v0f = 0.0f;
-    if (i > 0) OLr = c.cur.a[i - 1];
-    if (i + 1 < n) {
-        OFr = c.cur.a[i + 1];
-        of_v0f = c.cur.b[i + 1].v0f;
-    }
-    LaneAcc<Real> own;
-    own.a = q.a[k]; own.gap = q.gap[k]; own.stop_gap = q.sgap[k];
-    const int bits = q.bits[k];
-    own.has_leader = bits & 1; own.stop = (bits >> 1) & 1; own.overlap = (bits >> 2) & 1;
-    own.nl = q.nl[k];
-    const int sc = li.scen;
-    if (sc != acc.scen) {
-        macc_flush_thread(acc, c.metrics);
-        macc_reset(acc, sc);
-    }
-    const Decision<Real> D = decide_mobil<Real, Groups>(c, E, EB, li, OLr, OFr, of_v0f, own, q.u_lc[k], q.u_dir[k]);
-    if (D.cand) {
-        list_candidate(c, i, E, EB, sc, D, tag);
-        return;
-    }
-    const long long t = c.scen_step[sc];
-    integrate_emit(c, acc, i, E, EB, own, lane, D.flag ? F_FLAGGED : 0, own.overlap != 0, t, sc, tag);
-}
-
-// ---------------------------------------------------------------------------
-// k_decide: blocks [0, n_work) take 256-slot tiles of the current snapshot
-// (one vehicle per thread); blocks [n_work, gridDim) run the insertion.
-// Per vehicle: the own-lane acceleration and the attempt draw, MOBIL if the
-// draw passed (from the warp's queue, above), then the update; lane-change
-// candidates are finished by k_resolve.
-// Groups: the network has lane groups (some road has a turn that not all of
-// its lanes serve), so the mandatory changes of R27 can occur; without them
-// that path is not compiled in.
-// MOSS_DECIDE_MIN_BLOCKS: resident blocks per SM the register budget targets.
-#ifndef MOSS_DECIDE_MIN_BLOCKS
-#define MOSS_DECIDE_MIN_BLOCKS 5
-#endif
-// The run of slot tiles of work block vb of n_work.  A vehicle on a road lane
-// costs about twice one on a junction lane (MOBIL, longer neighbour
-// searches), so the runs split the snapshot by weight: run_w (a schedule
-// choice, 2 by default) per road-lane slot, 1 per junction-lane slot, from
-// the current lane offsets at the lane ranges of each scenario (road lanes
-// first, then junction lanes), when blocks take four tiles or more each.
-// Warp 0 computes it; the runs are contiguous and cover every tile.
-__device__ __forceinline__ long long run_weight(int a, int b, int e, int w) { return (long long)w * (b - a) + (e - b); }
-
-template <typename Real>
-__device__ __forceinline__ void decide_run(const Ctx<Real>& c, int n_tiles, int n_work, int vb, int* tb, int* te) {
-    if (n_tiles < 4 * n_work) {
-        // a few tiles per block: weights at tile granularity would leave
-        // blocks idle; runs of equal tile counts (differing by one at most)
-        *tb = (int)((long long)vb * n_tiles / n_work);
-        *te = (int)((long long)(vb + 1) * n_tiles / n_work);
-        return;
-    }
-    __shared__ int s_run[2];
-    if (threadIdx.x < 32) {
-        const int wl = threadIdx.x;
-        long long tot = 0;
-        for (int k0 = 0; k0 < c.n_scen; k0 += 32) {
-            long long w = 0;
-            if (k0 + wl < c.n_scen) {
-                const int4 L = c.scen_lanes[k0 + wl];
-                w = run_weight(c.cur.off[L.x], c.cur.off[L.y], c.cur.off[L.z], c.run_w);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-            tot += w;
-        }
-        // weights T0, T1 -> slots (scan of the scenarios' weights)
-        const long long T[2] = {tot * vb / n_work, tot * (vb + 1) / n_work};
-        int slot[2] = {-1, -1};
-        long long carry = 0;
-        for (int k0 = 0; k0 < c.n_scen && (slot[0] < 0 || slot[1] < 0); k0 += 32) {
-            const int k = k0 + wl;
-            int a = 0, b = 0, e = 0;
-            long long w = 0;
-            if (k < c.n_scen) {
-                const int4 L = c.scen_lanes[k];
-                a = c.cur.off[L.x]; b = c.cur.off[L.y]; e = c.cur.off[L.z];
-                w = run_weight(a, b, e, c.run_w);
-            }
-            long long P = w;  // inclusive prefix over the chunk
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const long long y = __shfl_up_sync(0xffffffffu, P, o);
-                if (wl >= o) P += y;
-            }
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                // the first scenario whose weight reaches past T (m and
-                // slot[q] are the same on every lane: the branch is uniform)
-                const unsigned m = __ballot_sync(0xffffffffu, k < c.n_scen && carry + P > T[q]);
-                if (slot[q] < 0 && m) {
-                    const int src = __ffs(m) - 1;
-                    const long long local = T[q] - (carry + __shfl_sync(0xffffffffu, P - w, src));
-                    const int sa = __shfl_sync(0xffffffffu, a, src), sb = __shfl_sync(0xffffffffu, b, src);
-                    const long long wr = (long long)c.run_w * (sb - sa);
-                    slot[q] = local < wr ? sa + (int)(local / c.run_w) : sb + (int)(local - wr);
-                }
-            }
-            carry += __shfl_sync(0xffffffffu, P, 31);
-        }
-        if (wl == 0) {
-            const int n = c.cnt->n_cur;
-            const int s0 = slot[0] < 0 ? n : slot[0], s1 = slot[1] < 0 ? n : slot[1];
-            s_run[0] = min(n_tiles, (s0 + TILE / 2) / TILE);
-            s_run[1] = vb == n_work - 1 ? n_tiles : min(n_tiles, (s1 + TILE / 2) / TILE);
-        }
-    }
-    __syncthreads();
-    *tb = s_run[0];
-    *te = s_run[1];
-}
-
-// The work of block vb of nvb (k_decide's grid, or a virtual block of the
-// single-launch step): vb < n_work takes a run of slot tiles, the others run
-// the insertion.
-template <typename Real, bool Groups>
-__device__ __forceinline__ void decide_block(const Ctx<Real>& c, int n_work, int vb, int nvb) {
-    const int tag = c.cnt->tag;
-    if (vb >= n_work) {
-        const int stride = (nvb - n_work) * TILE;
-        for (int k = (vb - n_work) * TILE + threadIdx.x; k < c.n_start; k += stride)
-            insert_departure(c, c.start_lanes[k], tag);
-        return;
-    }
-    const int n = c.cnt->n_cur;
-    const int n_tiles = (n + TILE - 1) / TILE;
-    // each block takes a contiguous run of tiles: a thread's scenario (and so
-    // its metric partials) changes rarely, and neighbouring lanes stay close
-    int t_beg, t_end;
-    decide_run(c, n_tiles, n_work, vb, &t_beg, &t_end);
-    MetricAcc acc;
-    macc_reset(acc, -1);
-    __shared__ MobilQueue<Real> q;
-    const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31, qb = warp * 64;
-    if (wl == 0) q.n[warp] = 0;
-    __syncwarp();
-    for (int tile = t_beg;; ++tile) {
-        const bool last = tile >= t_end;
-        const int i = tile * TILE + threadIdx.x;
-        if (!last && i < n) {
-            const RecA<Real> E = c.cur.a[i];
-            const RecB EB = c.cur.b[i];
-            const RecA<Real> OLr = i > 0 ? c.cur.a[i - 1] : no_rec<Real>();
-            const int lane = E.lane;
-            if ((unsigned)lane >= (unsigned)c.n_lanes) {
-                atomicOr(c.err, ERR_RANGE);
-            } else {
-                const LaneInfo li = c.lane[lane];
-                const int sc = li.scen;
-                if (sc != acc.scen) {
-                    macc_flush_thread(acc, c.metrics);
-                    macc_reset(acc, sc);
-                }
-                const int ctl = c.scen_ctl[sc];
-                if (ctl) {
-                    // a slot that does not advance: a frozen one keeps its
-                    // vehicles as they are, a retiring one removes them
-                    if (ctl & SC_RETIRE) {
-                        c.code[i] = C_ARRIVE;
-                        c.vstatus[E.id] = 2;
-                        atomicAdd(&c.leave[lane], 1);
-                    } else {
-                        c.code[i] = C_STAY;
-                        SV<Real> w;
-                        w.s = E.s; w.v = E.v;
-                        c.stay[i] = w;
-                    }
-                } else {
-                    const long long t = c.scen_step[sc];
-                    const OwnPart<Real> P =
-                        decide_own<Real, Groups>(c, E, EB, li, OLr, t, c.key0[sc], c.key1[sc], c.veh_base[sc]);
-                    int fl = 0;
-                    bool cand = false;
-                    if (P.att) {
-                        acc.mob += 1;
-                        const int k = qb + warp_claim(&q.n[warp]);
-                        q.i[k] = i; q.lane[k] = lane;
-                        q.a[k] = P.own.a; q.gap[k] = P.own.gap; q.sgap[k] = P.own.stop_gap;
-                        q.bits[k] = (P.own.has_leader ? 1 : 0) | (P.own.stop ? 2 : 0) | (P.own.overlap ? 4 : 0);
-                        q.nl[k] = P.own.nl;
-                        q.u_lc[k] = P.u_lc; q.u_dir[k] = P.u_dir;
-                        cand = true;  // finished from the queue
-                    } else if (Groups && P.mand) {
-                        const Decision<Real> D = decide_mandatory(c, i, E, EB, li, P.own);
-                        if (D.cand) {
-                            list_candidate(c, i, E, EB, sc, D, tag);
-                            cand = true;
-                        }
-                        fl = D.flag ? F_FLAGGED : 0;
-                    }
-                    if (!cand) integrate_emit(c, acc, i, E, EB, P.own, lane, fl, P.own.overlap != 0, t, sc, tag);
-                }
-            }
-        }
-        // MOBIL over the last 32 entries of the warp's queue once it holds
-        // 32, and over what is left after the last tile
-        __syncwarp();
-        const int nq = q.n[warp];
-        const int take = last ? nq : (nq >= 32 ? 32 : 0);
-        if (take > 0) {
-            if (wl < take) mobil_finish<Real, Groups>(c, q, qb + nq - take + wl, n, acc, tag);
-            __syncwarp();
-            if (wl == 0) q.n[warp] = nq - take;
-            __syncwarp();
-        }
-        if (last) break;
-    }
-    macc_flush_block<TILE>(acc, c.metrics);
-}
-
-template <typename Real, bool Groups>
-__global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Real> c, int n_work) {
-    if (*c.err & ERR_POISON) return;
-    decide_block<Real, Groups>(c, n_work, blockIdx.x, gridDim.x);
-}
-
-// ---------------------------------------------------------------------------
-// k_resolve: the lane-change candidates of this step (grid-stride over the
-// list k_decide built).  Conflict rule R9: a candidate conflicts with the
-// candidates that enter the same lane from the other side into the same gap
+// Resolution of lane-change candidate k.  Conflict rule R9: a candidate
+// conflicts with the candidates that enter the same lane from the other side
+// into the same gap
 // (the other members of its gap list with the opposite direction); the
 // larger utility wins, ties to the smaller id.  Both sides compare the same
 // stored utilities, so the outcome is consistent.  Then the update on the
@@ -492,14 +267,280 @@ __device__ __forceinline__ void resolve_one(const Ctx<Real>& c, MetricAcc& acc, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// The vehicles whose attempt draw passed are queued in shared memory, one
+// queue of 64 entries per warp, and MOBIL runs over a warp's queue 32 at a
+// time: a warp otherwise carries the whole MOBIL evaluation of any one of
+// its lanes while the others idle.
+template <typename Real>
+struct MobilQueue {
+    Real a[2 * TILE], gap[2 * TILE], sgap[2 * TILE];  // own-lane kinematics (LaneAcc)
+    int i[2 * TILE], lane[2 * TILE], bits[2 * TILE], nl[2 * TILE];
+    float u_lc[2 * TILE], u_dir[2 * TILE];
+    int n[TILE / 32];
+};
+
+// MOBIL and the update of queued vehicle k (the snapshot and lane records
+// are read again; the own-lane part comes from the queue)
+template <typename Real, bool Groups>
+__device__ __forceinline__ void mobil_finish(const Ctx<Real>& c, const MobilQueue<Real>& q, int k, int n,
+                                             MetricAcc& acc, int tag, CandLocal& cl) {
+    const int i = q.i[k], lane = q.lane[k];
+    const RecA<Real> E = c.cur.a[i];
+    const RecB EB = c.cur.b[i];
+    const LaneInfo li = c.lane[lane];
+    RecA<Real> OLr = no_rec<Real>(), OFr = no_rec<Real>();
+    float of_v0f = 0.0f;
+    if (i > 0) OLr = c.cur.a[i - 1];
+    if (i + 1 < n) {
+        OFr = c.cur.a[i + 1];
+        of_v0f = c.cur.b[i + 1].v0f;
+    }
+    LaneAcc<Real> own;
+    own.a = q.a[k]; own.gap = q.gap[k]; own.stop_gap = q.sgap[k];
+    const int bits = q.bits[k];
+    own.has_leader = bits & 1; own.stop = (bits >> 1) & 1; own.overlap = (bits >> 2) & 1;
+    own.nl = q.nl[k];
+    const int sc = li.scen;
+    if (sc != acc.scen) {
+        macc_flush_thread(acc, c.metrics);
+        macc_reset(acc, sc);
+    }
+    const Decision<Real> D = decide_mobil<Real, Groups>(c, E, EB, li, OLr, OFr, of_v0f, own, q.u_lc[k], q.u_dir[k]);
+    if (D.cand) {
+        list_candidate(c, i, E, EB, sc, D, tag, cl);
+        return;
+    }
+    const long long t = c.scen_step[sc];
+    integrate_emit(c, acc, i, E, EB, own, lane, D.flag ? F_FLAGGED : 0, own.overlap != 0, t, sc, tag);
+}
+
+// ---------------------------------------------------------------------------
+// k_decide: blocks [0, n_work) take 256-slot tiles of the current snapshot
+// (one vehicle per thread); blocks [n_work, gridDim) run the insertion.
+// Per vehicle: the own-lane acceleration and the attempt draw, MOBIL if the
+// draw passed (from the warp's queue, above), then the update; lane-change
+// candidates are finished by k_resolve.
+// Groups: the network has lane groups (some road has a turn that not all of
+// its lanes serve), so the mandatory changes of R27 can occur; without them
+// that path is not compiled in.
+// MOSS_DECIDE_MIN_BLOCKS: resident blocks per SM the register budget targets.
+#ifndef MOSS_DECIDE_MIN_BLOCKS
+#define MOSS_DECIDE_MIN_BLOCKS 5
+#endif
+// The run of slots [*sb, *se) of work block vb of n_work.  A vehicle on a
+// road lane costs about twice one on a junction lane (MOBIL, longer
+// neighbour searches), so the runs split the snapshot by weight: run_w (a
+// schedule choice, 2 by default) per road-lane slot, 1 per junction-lane
+// slot, from the current lane offsets at the lane ranges of each scenario
+// (road lanes first, then junction lanes), when blocks take four tiles or
+// more each; then each end moves back to the start of its road.  The runs
+// are contiguous and cover every slot.
+__device__ __forceinline__ long long run_weight(int a, int b, int e, int w) { return (long long)w * (b - a) + (e - b); }
+
+// First slot of the road whose lane holds `slot` (a junction-lane slot
+// stays where it is): the block runs begin and end there, so the vehicles of
+// a road, and with them every rival of a lane-change candidate, lie in one run.
+template <typename Real>
+__device__ __forceinline__ int road_start(const Ctx<Real>& c, int slot, int n) {
+    if (slot <= 0) return 0;
+    if (slot >= n) return n;
+    const int lane = c.cur.a[slot].lane;
+    if ((unsigned)lane >= (unsigned)c.n_lanes) return slot;  // reported by the decision
+    const int lo = c.lane[lane].lo;
+    return lo >= 0 ? c.cur.off[lo] : slot;
+}
+
+template <typename Real>
+__device__ __forceinline__ void decide_run(const Ctx<Real>& c, int n, int n_work, int vb, int* sb, int* se) {
+    __shared__ int s_run[2];
+    const int n_tiles = (n + TILE - 1) / TILE;
+    if (n_tiles < 4 * n_work) {
+        // a few tiles per block: equal slot counts (weights would leave
+        // blocks idle at this granularity)
+        if (threadIdx.x == 0) {
+            s_run[0] = road_start(c, (int)((long long)vb * n / n_work), n);
+            s_run[1] = road_start(c, (int)((long long)(vb + 1) * n / n_work), n);
+        }
+    } else if (threadIdx.x < 32) {
+        const int wl = threadIdx.x;
+        long long tot = 0;
+        for (int k0 = 0; k0 < c.n_scen; k0 += 32) {
+            long long w = 0;
+            if (k0 + wl < c.n_scen) {
+                const int4 L = c.scen_lanes[k0 + wl];
+                w = run_weight(c.cur.off[L.x], c.cur.off[L.y], c.cur.off[L.z], c.run_w);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+            tot += w;
+        }
+        // weights T0, T1 -> slots (scan of the scenarios' weights)
+        const long long T[2] = {tot * vb / n_work, tot * (vb + 1) / n_work};
+        int slot[2] = {-1, -1};
+        long long carry = 0;
+        for (int k0 = 0; k0 < c.n_scen && (slot[0] < 0 || slot[1] < 0); k0 += 32) {
+            const int k = k0 + wl;
+            int a = 0, b = 0, e = 0;
+            long long w = 0;
+            if (k < c.n_scen) {
+                const int4 L = c.scen_lanes[k];
+                a = c.cur.off[L.x]; b = c.cur.off[L.y]; e = c.cur.off[L.z];
+                w = run_weight(a, b, e, c.run_w);
+            }
+            long long P = w;  // inclusive prefix over the chunk
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long y = __shfl_up_sync(0xffffffffu, P, o);
+                if (wl >= o) P += y;
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                // the first scenario whose weight reaches past T (m and
+                // slot[q] are the same on every lane: the branch is uniform)
+                const unsigned m = __ballot_sync(0xffffffffu, k < c.n_scen && carry + P > T[q]);
+                if (slot[q] < 0 && m) {
+                    const int src = __ffs(m) - 1;
+                    const long long local = T[q] - (carry + __shfl_sync(0xffffffffu, P - w, src));
+                    const int sa = __shfl_sync(0xffffffffu, a, src), sb = __shfl_sync(0xffffffffu, b, src);
+                    const long long wr = (long long)c.run_w * (sb - sa);
+                    slot[q] = local < wr ? sa + (int)(local / c.run_w) : sb + (int)(local - wr);
+                }
+            }
+            carry += __shfl_sync(0xffffffffu, P, 31);
+        }
+        if (wl == 0) {
+            const int s0 = slot[0] < 0 ? n : slot[0], s1 = slot[1] < 0 ? n : slot[1];
+            s_run[0] = road_start(c, s0, n);
+            s_run[1] = vb == n_work - 1 ? n : road_start(c, s1, n);
+        }
+    }
+    __syncthreads();
+    *sb = s_run[0];
+    *se = s_run[1];
+}
+
+// The work of block vb of nvb (k_decide's grid, or a virtual block of the
+// single-launch step): vb < n_work takes a run of slot tiles, the others run
+// the insertion.
+template <typename Real, bool Groups>
+__device__ __forceinline__ void decide_block(const Ctx<Real>& c, int n_work, int vb, int nvb) {
+    const int tag = c.cnt->tag;
+    if (vb >= n_work) {
+        const int stride = (nvb - n_work) * TILE;
+        for (int k = (vb - n_work) * TILE + threadIdx.x; k < c.n_start; k += stride)
+            insert_departure(c, c.start_lanes[k], tag);
+        return;
+    }
+    const int n = c.cnt->n_cur;
+    // each block takes a contiguous run of slots: a thread's scenario (and so
+    // its metric partials) changes rarely, neighbouring lanes stay close, and
+    // the run holds whole roads, so the block resolves its own lane-change
+    // candidates once its run is done (rule R9: rivals share the road)
+    __shared__ CandLocal cl;
+    __shared__ MobilQueue<Real> q;
+    if (threadIdx.x == 0) cl.n = 0;
+    int s_beg, s_end;
+    decide_run(c, n, n_work, vb, &s_beg, &s_end);
+    const int t_beg = s_beg / TILE, t_end = s_beg < s_end ? (s_end + TILE - 1) / TILE : t_beg;
+    MetricAcc acc;
+    macc_reset(acc, -1);
+    const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31, qb = warp * 64;
+    if (wl == 0) q.n[warp] = 0;
+    __syncwarp();
+    for (int tile = t_beg;; ++tile) {
+        const bool last = tile >= t_end;
+        const int i = tile * TILE + threadIdx.x;
+        if (!last && i >= s_beg && i < s_end) {
+            const RecA<Real> E = c.cur.a[i];
+            const RecB EB = c.cur.b[i];
+            const RecA<Real> OLr = i > 0 ? c.cur.a[i - 1] : no_rec<Real>();
+            const int lane = E.lane;
+            if ((unsigned)lane >= (unsigned)c.n_lanes) {
+                atomicOr(c.err, ERR_RANGE);
+            } else {
+                const LaneInfo li = c.lane[lane];
+                const int sc = li.scen;
+                if (sc != acc.scen) {
+                    macc_flush_thread(acc, c.metrics);
+                    macc_reset(acc, sc);
+                }
+                const int ctl = c.scen_ctl[sc];
+                if (ctl) {
+                    // a slot that does not advance: a frozen one keeps its
+                    // vehicles as they are, a retiring one removes them
+                    if (ctl & SC_RETIRE) {
+                        c.code[i] = C_ARRIVE;
+                        c.vstatus[E.id] = 2;
+                        atomicAdd(&c.leave[lane], 1);
+                    } else {
+                        c.code[i] = C_STAY;
+                        SV<Real> w;
+                        w.s = E.s; w.v = E.v;
+                        c.stay[i] = w;
+                    }
+                } else {
+                    const long long t = c.scen_step[sc];
+                    const OwnPart<Real> P =
+                        decide_own<Real, Groups>(c, E, EB, li, OLr, t, c.key0[sc], c.key1[sc], c.veh_base[sc]);
+                    int fl = 0;
+                    bool cand = false;
+                    if (P.att) {
+                        acc.mob += 1;
+                        const int k = qb + warp_claim(&q.n[warp]);
+                        q.i[k] = i; q.lane[k] = lane;
+                        q.a[k] = P.own.a; q.gap[k] = P.own.gap; q.sgap[k] = P.own.stop_gap;
+                        q.bits[k] = (P.own.has_leader ? 1 : 0) | (P.own.stop ? 2 : 0) | (P.own.overlap ? 4 : 0);
+                        q.nl[k] = P.own.nl;
+                        q.u_lc[k] = P.u_lc; q.u_dir[k] = P.u_dir;
+                        cand = true;  // finished from the queue
+                    } else if (Groups && P.mand) {
+                        const Decision<Real> D = decide_mandatory(c, i, E, EB, li, P.own);
+                        if (D.cand) {
+                            list_candidate(c, i, E, EB, sc, D, tag, cl);
+                            cand = true;
+                        }
+                        fl = D.flag ? F_FLAGGED : 0;
+                    }
+                    if (!cand) integrate_emit(c, acc, i, E, EB, P.own, lane, fl, P.own.overlap != 0, t, sc, tag);
+                }
+            }
+        }
+        // MOBIL over the last 32 entries of the warp's queue once it holds
+        // 32, and over what is left after the last tile
+        __syncwarp();
+        const int nq = q.n[warp];
+        const int take = last ? nq : (nq >= 32 ? 32 : 0);
+        if (take > 0) {
+            if (wl < take) mobil_finish<Real, Groups>(c, q, qb + nq - take + wl, n, acc, tag, cl);
+            __syncwarp();
+            if (wl == 0) q.n[warp] = nq - take;
+            __syncwarp();
+        }
+        if (last) break;
+    }
+    // the run's lane-change candidates (their rivals are all in this run)
+    __syncthreads();
+    const int ncl = min(cl.n, CAND_LOCAL);
+    for (int j = threadIdx.x; j < ncl; j += TILE) resolve_one(c, acc, cl.idx[j], c.n_veh, tag);
+    macc_flush_block<TILE>(acc, c.metrics);
+}
+
+template <typename Real, bool Groups>
+__global__ void __launch_bounds__(TILE, MOSS_DECIDE_MIN_BLOCKS) k_decide(Ctx<Real> c, int n_work) {
+    if (*c.err & ERR_POISON) return;
+    decide_block<Real, Groups>(c, n_work, blockIdx.x, gridDim.x);
+}
+
 template <typename Real>
 __global__ void __launch_bounds__(TILE) k_resolve(Ctx<Real> c) {
     if (*c.err & ERR_POISON) return;
-    const int nc = c.cnt->n_cand;
+    const int nc = c.cnt->n_late;
     const int tag = c.cnt->tag;
     MetricAcc acc;
     macc_reset(acc, -1);
-    for (int k = blockIdx.x * TILE + threadIdx.x; k < nc; k += gridDim.x * TILE) resolve_one(c, acc, k, nc, tag);
+    for (int k = blockIdx.x * TILE + threadIdx.x; k < nc; k += gridDim.x * TILE)
+        resolve_one(c, acc, c.cand_late[k], c.n_veh, tag);
     // the phase pressures of the max-pressure junctions (read by k_lanescan)
     if (*c.n_mp > 0)
         for (int k = blockIdx.x * TILE + threadIdx.x; k < c.n_jj; k += gridDim.x * TILE) mp_accumulate(c, k);
@@ -678,7 +719,7 @@ __device__ __forceinline__ void lanescan_blocks(const Ctx<Real>& c) {
     // of those are done (their blocks hold earlier tickets, so they are
     // running: the wait is bounded)
     __shared__ int s_ready;
-    const int nc = c.cnt->n_cand;
+    const int nc = c.cnt->n_late;  // candidates past the k_decide blocks' own lists
     const int tag = c.cnt->tag;
     const int r_cand = (nc + TILE - 1) / TILE;
     const int n_res = r_cand + (*c.n_mp > 0 ? (c.n_jj + TILE - 1) / TILE : 0);
@@ -699,7 +740,7 @@ __device__ __forceinline__ void lanescan_blocks(const Ctx<Real>& c) {
             macc_reset(acc, -1);
             if (tile < r_cand) {
                 const int k = tile * TILE + threadIdx.x;
-                if (k < nc) resolve_one(c, acc, k, nc, tag);
+                if (k < nc) resolve_one(c, acc, c.cand_late[k], c.n_veh, tag);
             } else {
                 const int k = (tile - r_cand) * TILE + threadIdx.x;
                 if (k < c.n_jj) mp_accumulate(c, k);
@@ -782,6 +823,7 @@ __device__ __forceinline__ void place_blocks(const Ctx<Real>& c, int vb, int nvb
         if (threadIdx.x == 0) {
             c.cnt_next->n_ent = 0;
             c.cnt_next->n_cand = 0;
+            c.cnt_next->n_late = 0;
             c.cnt_next->res_done = 0;
             c.cnt_next->ticket_lane = 0;
             c.cnt_next->tag = tag >= 0x3fffffff ? 1 : tag + 1;
