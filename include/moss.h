@@ -476,21 +476,24 @@ int moss_step_launches(moss_t h, int* out);
  * per SM {1,2,4}; lanes per thread of a lane-scan tile {16,8}; k_place
  * blocks per SM {4,8,16}; the step mode {0,1} (moss_set_step_mode).  Then it
  * re-captures the step graphs.  chosen3 (may be NULL) receives the chosen
- * decide/lanescan/place blocks per SM; moss_get_schedule returns all six.
+ * decide/lanescan/place blocks per SM; moss_get_schedule returns the whole schedule.
  */
 int moss_autotune(moss_t h, int trial_steps, int* chosen3);
 
 /*
- * The launch schedule (no counterpart in the paper): out6 / in6 = k_decide,
+ * The launch schedule (no counterpart in the paper): out7 / in7 = k_decide,
  * k_lanescan and k_place blocks per SM, the road-lane weight of k_decide's
- * runs, lanes per thread of a lane-scan tile (8 or 16) and the step mode (0
- * or 1), as moss_autotune describes.  moss_set_schedule checks the ranges
- * (blocks per SM 1..16 for k_decide, 1..32 for the others; weight 1..8),
- * waits for the handle's stream and re-captures the step graphs; on an error
- * the previous schedule stays.  Results never depend on the schedule.
+ * runs, lanes per thread of a lane-scan tile (8 or 16), the step mode (0 or
+ * 1), as moss_autotune describes, and the number of lane-change candidates
+ * a k_decide block resolves itself at the end of its run (0..256, default
+ * 256; the others are resolved by the first tickets of k_lanescan).
+ * moss_set_schedule checks the ranges (blocks per SM 1..16 for k_decide,
+ * 1..32 for the others; weight 1..8), waits for the handle's stream and
+ * re-captures the step graphs; on an error the previous schedule stays.
+ * Results never depend on the schedule.
  */
-int moss_get_schedule(moss_t h, int* out6);
-int moss_set_schedule(moss_t h, const int* in6);
+int moss_get_schedule(moss_t h, int* out7);
+int moss_set_schedule(moss_t h, const int* in7);
 
 /*
  * Failure-detection self-test (no counterpart in the paper).  Launches one

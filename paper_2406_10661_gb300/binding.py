@@ -279,7 +279,8 @@ class _Handle:
     def set_kernel_timing(self, on: bool) -> None:
         _check(self.lib.moss_set_kernel_timing(self.h, int(bool(on))), self.h)
 
-    SCHEDULE_KEYS = ("decide", "lanescan", "place", "road_weight", "lanes_per_thread", "step_mode")
+    SCHEDULE_KEYS = ("decide", "lanescan", "place", "road_weight", "lanes_per_thread", "step_mode",
+                     "candidates_per_block")
 
     def autotune(self, trial_steps: int = 3):
         """Pick the fastest launch schedule on the next 16 * trial_steps steps;
@@ -289,7 +290,7 @@ class _Handle:
         return self.schedule()
 
     def schedule(self) -> Dict[str, int]:
-        out = np.zeros(6, dtype=np.int32)
+        out = np.zeros(7, dtype=np.int32)
         _check(self.lib.moss_get_schedule(self.h, _ptr(out, ctypes.c_int32)), self.h)
         return dict(zip(self.SCHEDULE_KEYS, out.tolist()))
 

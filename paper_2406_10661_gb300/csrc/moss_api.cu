@@ -135,6 +135,7 @@ struct MossHandle {
     int cfg_decide = MOSS_DECIDE_MIN_BLOCKS, cfg_lanescan = 4, cfg_place = 8;
     int cfg_runw = 2;    // weight of a road-lane slot in k_decide's runs
     int cfg_lsr = 4;     // rounds of 128 lanes per warp in a lane-scan tile (4 or 2)
+    int cfg_ccap = 256;  // lane-change candidates a k_decide block resolves itself
 
     int parity = 0;  // snapshot buffer holding the current step
     int step_mode = 0;               // 0: three kernels per step; 1: one cooperative launch
@@ -390,6 +391,7 @@ Ctx<Real> make_ctx(MossHandle* h, int cur) {
     c.cands = (Cand<Real>*)h->d_cands; c.gap_head = h->d_gap_head;
     c.n_lane_tiles = lane_tiles(h, h->cfg_lsr); c.max_slot_tiles = h->max_slot_tiles;
     c.run_w = h->cfg_runw;
+    c.cand_cap = h->cfg_ccap;
     c.n_junc_chunks = h->n_junc_chunks; c.cnt = h->d_cnt + cur;
     c.cnt_next = h->d_cnt + (1 - cur); c.err = &h->d_cnt[0].err;
     const MossParams& p = h->prm;
@@ -2018,17 +2020,19 @@ int moss_autotune(moss_t h, int trial_steps, int* chosen3) {
     return check_device(h);
 }
 
-int moss_get_schedule(moss_t h, int* out6) {
-    if (!h || !out6) return MOSS_EINVAL;
-    out6[0] = h->cfg_decide; out6[1] = h->cfg_lanescan; out6[2] = h->cfg_place;
-    out6[3] = h->cfg_runw; out6[4] = 4 * h->cfg_lsr; out6[5] = h->step_mode;
+int moss_get_schedule(moss_t h, int* out7) {
+    if (!h || !out7) return MOSS_EINVAL;
+    out7[0] = h->cfg_decide; out7[1] = h->cfg_lanescan; out7[2] = h->cfg_place;
+    out7[3] = h->cfg_runw; out7[4] = 4 * h->cfg_lsr; out7[5] = h->step_mode; out7[6] = h->cfg_ccap;
     return MOSS_OK;
 }
 
-int moss_set_schedule(moss_t h, const int* in6) {
-    if (!h || !in6) return MOSS_EINVAL;
+int moss_set_schedule(moss_t h, const int* in7) {
+    if (!h || !in7) return MOSS_EINVAL;
+    const int* in6 = in7;
     if (in6[0] < 1 || in6[0] > 16 || in6[1] < 1 || in6[1] > 32 || in6[2] < 1 || in6[2] > 32 || in6[3] < 1 ||
-        in6[3] > 8 || (in6[4] != 8 && in6[4] != 16) || (in6[5] != 0 && in6[5] != 1))
+        in6[3] > 8 || (in6[4] != 8 && in6[4] != 16) || (in6[5] != 0 && in6[5] != 1) || in7[6] < 0 ||
+        in7[6] > CAND_LOCAL)
         return fail(h, MOSS_EINVAL, "schedule value out of range");
     if (in6[5] == 1) {
         int coop = 0;
@@ -2036,14 +2040,15 @@ int moss_set_schedule(moss_t h, const int* in6) {
         if (!coop) return fail(h, MOSS_EINVAL, "the device has no cooperative launch");
     }
     CK(cudaStreamSynchronize(h->stream));
-    const int old[6] = {h->cfg_decide, h->cfg_lanescan, h->cfg_place, h->cfg_runw, h->cfg_lsr, h->step_mode};
+    const int old[7] = {h->cfg_decide, h->cfg_lanescan, h->cfg_place, h->cfg_runw, h->cfg_lsr, h->step_mode,
+                        h->cfg_ccap};
     h->cfg_decide = in6[0]; h->cfg_lanescan = in6[1]; h->cfg_place = in6[2];
-    h->cfg_runw = in6[3]; h->cfg_lsr = in6[4] / 4; h->step_mode = in6[5];
+    h->cfg_runw = in6[3]; h->cfg_lsr = in6[4] / 4; h->step_mode = in6[5]; h->cfg_ccap = in7[6];
     destroy_graphs(h);
     const int rc = build_graphs(h);
     if (rc != MOSS_OK) {
         h->cfg_decide = old[0]; h->cfg_lanescan = old[1]; h->cfg_place = old[2];
-        h->cfg_runw = old[3]; h->cfg_lsr = old[4]; h->step_mode = old[5];
+        h->cfg_runw = old[3]; h->cfg_lsr = old[4]; h->step_mode = old[5]; h->cfg_ccap = old[6];
         destroy_graphs(h);
         TRY(build_graphs(h));
         return rc;

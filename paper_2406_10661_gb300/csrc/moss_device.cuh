@@ -222,6 +222,7 @@ struct Ctx {
     unsigned long long* lane_tiles;
     int n_lane_tiles, max_slot_tiles, n_junc_chunks;
     int run_w;           // weight of a road-lane slot in k_decide's runs (junction-lane slot: 1)
+    int cand_cap;        // lane-change candidates a k_decide block resolves itself (<= 256)
     Counters* cnt;       // this step's counters
     Counters* cnt_next;  // the next step's
     int* err;            // device error bits

@@ -20,8 +20,9 @@ __device__ __forceinline__ void list_push(unsigned long long* head, int32_t* ene
 
 // ---------------------------------------------------------------------------
 // A k_decide block's lane-change candidates: their indices in the candidate
-// list, resolved by the block once its run is done; past CAND_LOCAL of them
-// the rest go to the late list that k_lanescan's first tickets resolve.
+// list, resolved by the block once its run is done; past cand_cap of them (a
+// schedule value, at most CAND_LOCAL) the rest go to the late list that
+// k_lanescan's first tickets resolve.
 constexpr int CAND_LOCAL = 256;
 struct CandLocal {
     int n;
@@ -31,7 +32,7 @@ struct CandLocal {
 template <typename Real>
 __device__ __forceinline__ void note_candidate(const Ctx<Real>& c, CandLocal& cl, int k) {
     const int j = atomicAdd(&cl.n, 1);
-    if (j < CAND_LOCAL) cl.idx[j] = k;
+    if (j < c.cand_cap) cl.idx[j] = k;
     else c.cand_late[atomicAdd(&c.cnt->n_late, 1)] = k;
 }
 
@@ -521,7 +522,7 @@ __device__ __forceinline__ void decide_block(const Ctx<Real>& c, int n_work, int
     }
     // the run's lane-change candidates (their rivals are all in this run)
     __syncthreads();
-    const int ncl = min(cl.n, CAND_LOCAL);
+    const int ncl = min(cl.n, c.cand_cap);
     for (int j = threadIdx.x; j < ncl; j += TILE) resolve_one(c, acc, cl.idx[j], c.n_veh, tag);
     macc_flush_block<TILE>(acc, c.metrics);
 }

@@ -125,9 +125,12 @@ def test_schedules_give_the_same_results(precision):
     ref = binding.Simulation(scen.net, scen.veh, scen.params, precision=precision)
     ref.step(150)
     want_state, want_metrics = ref.state(), ref.metrics()
-    schedules = [dict(decide=3, lanescan=1, place=4, road_weight=1, lanes_per_thread=8, step_mode=0),
-                 dict(decide=5, lanescan=2, place=16, road_weight=3, lanes_per_thread=16, step_mode=0),
-                 dict(decide=4, lanescan=4, place=8, road_weight=2, lanes_per_thread=8, step_mode=1)]
+    schedules = [dict(decide=3, lanescan=1, place=4, road_weight=1, lanes_per_thread=8, step_mode=0,
+                      candidates_per_block=0),
+                 dict(decide=5, lanescan=2, place=16, road_weight=3, lanes_per_thread=16, step_mode=0,
+                      candidates_per_block=1),
+                 dict(decide=4, lanescan=4, place=8, road_weight=2, lanes_per_thread=8, step_mode=1,
+                      candidates_per_block=256)]
     for sched in schedules:
         sim = binding.Simulation(scen.net, scen.veh, scen.params, precision=precision)
         sim.step(40)
@@ -158,7 +161,7 @@ def test_schedule_out_of_range_refused():
     sim = binding.Simulation(scen.net, scen.veh, scen.params)
     before = sim.schedule()
     for bad in (dict(decide=0), dict(road_weight=9), dict(lanes_per_thread=12), dict(step_mode=2),
-                dict(place=33)):
+                dict(place=33), dict(candidates_per_block=257), dict(candidates_per_block=-1)):
         with pytest.raises(binding.MossError):
             sim.set_schedule(**bad)
         assert sim.schedule() == before
