@@ -472,7 +472,7 @@ int moss_step_launches(moss_t h, int* out);
  * depend on the schedule) under candidate schedules, keeps the fastest by
  * coordinate search over, in this order: k_decide blocks per SM {3,4,5}; the
  * weight of a road-lane vehicle in the split of the snapshot into k_decide's
- * block runs {1,2,3} (a junction-lane vehicle weighs 1); k_lanescan blocks
+ * block runs {0,1,2} (a junction-lane vehicle weighs 1; 0: the weight fitted each step); k_lanescan blocks
  * per SM {1,2,4}; lanes per thread of a lane-scan tile {16,8}; k_place
  * blocks per SM {4,8,16}; the step mode {0,1} (moss_set_step_mode).  Then it
  * re-captures the step graphs.  chosen3 (may be NULL) receives the chosen
@@ -483,12 +483,13 @@ int moss_autotune(moss_t h, int trial_steps, int* chosen3);
 /*
  * The launch schedule (no counterpart in the paper): out7 / in7 = k_decide,
  * k_lanescan and k_place blocks per SM, the road-lane weight of k_decide's
- * runs, lanes per thread of a lane-scan tile (8 or 16), the step mode (0 or
+ * runs (0: fitted each step from the previous step's run times, the
+ * default; 1..8: fixed), lanes per thread of a lane-scan tile (8 or 16), the step mode (0 or
  * 1), as moss_autotune describes, and the number of lane-change candidates
  * a k_decide block resolves itself at the end of its run (0..256, default
  * 256; the others are resolved by the first tickets of k_lanescan).
  * moss_set_schedule checks the ranges (blocks per SM 1..16 for k_decide,
- * 1..32 for the others; weight 1..8), waits for the handle's stream and
+ * 1..32 for the others; weight 0..8), waits for the handle's stream and
  * re-captures the step graphs; on an error the previous schedule stays.
  * Results never depend on the schedule.
  */

@@ -105,6 +105,7 @@ struct MossHandle {
     int32_t *d_q_off = nullptr, *d_q_ids = nullptr, *d_q_head = nullptr, *d_start_lanes = nullptr;
     uint32_t *d_key0 = nullptr, *d_key1 = nullptr;
     int4* d_scen_lanes = nullptr;
+    int4* d_runstat = nullptr;  // [RUNSTAT_MAX] k_decide run statistics for the run-weight fit
     int32_t* d_veh_base = nullptr;
     long long *d_step = nullptr, *d_metrics = nullptr;
     int32_t* d_scen_ctl = nullptr;    // per scenario: SC_FROZEN / SC_RETIRE
@@ -133,7 +134,7 @@ struct MossHandle {
 
     // launch configuration (blocks per SM) of the step kernels; moss_autotune picks them
     int cfg_decide = MOSS_DECIDE_MIN_BLOCKS, cfg_lanescan = 4, cfg_place = 8;
-    int cfg_runw = 2;    // weight of a road-lane slot in k_decide's runs
+    int cfg_runw = 0;    // weight of a road-lane slot in k_decide's runs (0: fitted each step)
     int cfg_lsr = 4;     // rounds of 128 lanes per warp in a lane-scan tile (4 or 2)
     int cfg_ccap = 256;  // lane-change candidates a k_decide block resolves itself
 
@@ -391,6 +392,7 @@ Ctx<Real> make_ctx(MossHandle* h, int cur) {
     c.cands = (Cand<Real>*)h->d_cands; c.gap_head = h->d_gap_head;
     c.n_lane_tiles = lane_tiles(h, h->cfg_lsr); c.max_slot_tiles = h->max_slot_tiles;
     c.run_w = h->cfg_runw;
+    c.runstat = h->d_runstat;
     c.cand_cap = h->cfg_ccap;
     c.n_junc_chunks = h->n_junc_chunks; c.cnt = h->d_cnt + cur;
     c.cnt_next = h->d_cnt + (1 - cur); c.err = &h->d_cnt[0].err;
@@ -417,7 +419,7 @@ Grids grids(const MossHandle* h) {
     // the lane scan's tickets, plus (MOSS_FOLD_RESOLVE) the candidate and
     // max-pressure chunks in front of them: their number is known on the
     // device only, so the grid takes every resident block it may need
-    const int tickets = lane_tiles(h, h->cfg_lsr) + h->n_junc_chunks + (MOSS_FOLD_RESOLVE ? (h->n_jj + TILE - 1) / TILE + 8 : 0);
+    const int tickets = 1 + lane_tiles(h, h->cfg_lsr) + h->n_junc_chunks + (MOSS_FOLD_RESOLVE ? (h->n_jj + TILE - 1) / TILE + 8 : 0);
     g.lanescan = std::max(1, std::min(tickets, h->sm_count * h->cfg_lanescan));
     g.place = std::max(1, std::min(2 * h->max_slot_tiles, h->sm_count * h->cfg_place));
     return g;
@@ -758,6 +760,7 @@ int device_setup(MossHandle* h, void* stream) {
     TRY(upload(h, &h->d_key0, h->key0));
     TRY(upload(h, &h->d_key1, h->key1));
     TRY(upload(h, &h->d_scen_lanes, h->scen_lanes));
+    TRY(upload(h, &h->d_runstat, std::vector<int4>(RUNSTAT_MAX, make_int4(0, 0, 0, 0))));
     TRY(upload(h, &h->d_veh_base, std::vector<int32_t>(h->scen_veh_off.begin(), h->scen_veh_off.end() - 1)));
     TRY(upload(h, &h->d_step, std::vector<long long>(n, 0)));
     TRY(upload(h, &h->d_metrics, std::vector<long long>((size_t)n * M_NFIELDS, 0)));
@@ -1995,7 +1998,7 @@ int moss_autotune(moss_t h, int trial_steps, int* chosen3) {
     CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device));
     struct Knob { int* v; int n; int c[3]; };
     const Knob knobs[] = {
-        {&h->cfg_decide, 3, {3, 4, 5}},   {&h->cfg_runw, 3, {1, 2, 3}}, {&h->cfg_lanescan, 3, {1, 2, 4}},
+        {&h->cfg_decide, 3, {3, 4, 5}},   {&h->cfg_runw, 3, {0, 1, 2}}, {&h->cfg_lanescan, 3, {1, 2, 4}},
         {&h->cfg_lsr, 2, {4, 2, 0}},      {&h->cfg_place, 3, {4, 8, 16}}, {&h->step_mode, coop ? 2 : 1, {0, 1, 0}},
     };
     for (const Knob& kb : knobs) {
@@ -2030,7 +2033,7 @@ int moss_get_schedule(moss_t h, int* out7) {
 int moss_set_schedule(moss_t h, const int* in7) {
     if (!h || !in7) return MOSS_EINVAL;
     const int* in6 = in7;
-    if (in6[0] < 1 || in6[0] > 16 || in6[1] < 1 || in6[1] > 32 || in6[2] < 1 || in6[2] > 32 || in6[3] < 1 ||
+    if (in6[0] < 1 || in6[0] > 16 || in6[1] < 1 || in6[1] > 32 || in6[2] < 1 || in6[2] > 32 || in6[3] < 0 ||
         in6[3] > 8 || (in6[4] != 8 && in6[4] != 16) || (in6[5] != 0 && in6[5] != 1) || in7[6] < 0 ||
         in7[6] > CAND_LOCAL)
         return fail(h, MOSS_EINVAL, "schedule value out of range");

@@ -68,6 +68,7 @@ constexpr int LANESCAN_THREADS = 256;
 constexpr int LANESCAN_ITEMS = 16;
 constexpr int LANESCAN_TILE = LANESCAN_THREADS * LANESCAN_ITEMS;
 constexpr int JUNC_CHUNK = 256;     // junctions per k_lanescan ticket (one per thread)
+constexpr int RUNSTAT_MAX = 4096;  // k_decide work blocks whose run statistics are kept
 constexpr long long SPIN_LIMIT = 1ll << 22;  // bounded waits (~0.5 s with backoff)
 
 // Step counters, one set per parity of the ping-pong snapshots: step t uses
@@ -83,6 +84,8 @@ struct Counters {
     int err;         // device error bits (set 0 only)
     int n_mp;        // junctions under max pressure (set 0 only)
     int res_done;    // k_lanescan tickets of candidate / pressure work finished
+    int run_wq;      // fitted weight of a road-lane slot in k_decide's runs, x256 (0: none yet)
+    int n_runs;      // k_decide work runs of this step (their statistics for the fit)
 };
 
 // the candidates are resolved in the first tickets of k_lanescan instead of a
@@ -221,7 +224,8 @@ struct Ctx {
     unsigned long long* gap_head;  // [n_veh + n_lanes + 1] (tag << 32 | candidate) or stale
     unsigned long long* lane_tiles;
     int n_lane_tiles, max_slot_tiles, n_junc_chunks;
-    int run_w;           // weight of a road-lane slot in k_decide's runs (junction-lane slot: 1)
+    int run_w;           // weight of a road-lane slot in k_decide's runs (junction-lane slot: 1); 0: fitted
+    int4* runstat;       // [RUNSTAT_MAX] per k_decide work block: duration (ns, lo/hi), road-lane and junction-lane slots
     int cand_cap;        // lane-change candidates a k_decide block resolves itself (<= 256)
     Counters* cnt;       // this step's counters
     Counters* cnt_next;  // the next step's

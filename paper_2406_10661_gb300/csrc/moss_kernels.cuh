@@ -337,7 +337,17 @@ __device__ __forceinline__ void mobil_finish(const Ctx<Real>& c, const MobilQueu
 // (road lanes first, then junction lanes), when blocks take four tiles or
 // more each; then each end moves back to the start of its road.  The runs
 // are contiguous and cover every slot.
-__device__ __forceinline__ long long run_weight(int a, int b, int e, int w) { return (long long)w * (b - a) + (e - b); }
+__device__ __forceinline__ long long run_weight(int a, int b, int e, int wq) {
+    return (long long)wq * (b - a) + 256ll * (e - b);
+}
+// road-lane slot weight x256 of this step's runs: the schedule's fixed value,
+// else the fit of the previous step's block times (1 before any)
+template <typename Real>
+__device__ __forceinline__ int run_wq(const Ctx<Real>& c) {
+    if (c.run_w > 0) return 256 * c.run_w;
+    const int f = c.cnt->run_wq;
+    return f > 0 ? f : 256;
+}
 
 // First slot of the road whose lane holds `slot` (a junction-lane slot
 // stays where it is): the block runs begin and end there, so the vehicles of
@@ -365,12 +375,13 @@ __device__ __forceinline__ void decide_run(const Ctx<Real>& c, int n, int n_work
         }
     } else if (threadIdx.x < 32) {
         const int wl = threadIdx.x;
+        const int wq = run_wq(c);
         long long tot = 0;
         for (int k0 = 0; k0 < c.n_scen; k0 += 32) {
             long long w = 0;
             if (k0 + wl < c.n_scen) {
                 const int4 L = c.scen_lanes[k0 + wl];
-                w = run_weight(c.cur.off[L.x], c.cur.off[L.y], c.cur.off[L.z], c.run_w);
+                w = run_weight(c.cur.off[L.x], c.cur.off[L.y], c.cur.off[L.z], wq);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
@@ -387,7 +398,7 @@ __device__ __forceinline__ void decide_run(const Ctx<Real>& c, int n, int n_work
             if (k < c.n_scen) {
                 const int4 L = c.scen_lanes[k];
                 a = c.cur.off[L.x]; b = c.cur.off[L.y]; e = c.cur.off[L.z];
-                w = run_weight(a, b, e, c.run_w);
+                w = run_weight(a, b, e, wq);
             }
             long long P = w;  // inclusive prefix over the chunk
 #pragma unroll
@@ -404,8 +415,8 @@ __device__ __forceinline__ void decide_run(const Ctx<Real>& c, int n, int n_work
                     const int src = __ffs(m) - 1;
                     const long long local = T[q] - (carry + __shfl_sync(0xffffffffu, P - w, src));
                     const int sa = __shfl_sync(0xffffffffu, a, src), sb = __shfl_sync(0xffffffffu, b, src);
-                    const long long wr = (long long)c.run_w * (sb - sa);
-                    slot[q] = local < wr ? sa + (int)(local / c.run_w) : sb + (int)(local - wr);
+                    const long long wr = (long long)wq * (sb - sa);
+                    slot[q] = local < wr ? sa + (int)(local / wq) : sb + (int)((local - wr) / 256);
                 }
             }
             carry += __shfl_sync(0xffffffffu, P, 31);
@@ -440,7 +451,12 @@ __device__ __forceinline__ void decide_block(const Ctx<Real>& c, int n_work, int
     // candidates once its run is done (rule R9: rivals share the road)
     __shared__ CandLocal cl;
     __shared__ MobilQueue<Real> q;
-    if (threadIdx.x == 0) cl.n = 0;
+    __shared__ int s_road;  // road-lane vehicles of the run (for the run-weight fit)
+    unsigned long long t_start = 0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
+    if (threadIdx.x == 0) { cl.n = 0; s_road = 0; }
+    if (vb == 0 && threadIdx.x == 0) c.cnt->n_runs = n_work;
+    int n_road = 0;
     int s_beg, s_end;
     decide_run(c, n, n_work, vb, &s_beg, &s_end);
     const int t_beg = s_beg / TILE, t_end = s_beg < s_end ? (s_end + TILE - 1) / TILE : t_beg;
@@ -461,6 +477,7 @@ __device__ __forceinline__ void decide_block(const Ctx<Real>& c, int n_work, int
                 atomicOr(c.err, ERR_RANGE);
             } else {
                 const LaneInfo li = c.lane[lane];
+                n_road += li.lo >= 0;
                 const int sc = li.scen;
                 if (sc != acc.scen) {
                     macc_flush_thread(acc, c.metrics);
@@ -524,7 +541,16 @@ __device__ __forceinline__ void decide_block(const Ctx<Real>& c, int n_work, int
     __syncthreads();
     const int ncl = min(cl.n, c.cand_cap);
     for (int j = threadIdx.x; j < ncl; j += TILE) resolve_one(c, acc, cl.idx[j], c.n_veh, tag);
-    macc_flush_block<TILE>(acc, c.metrics);
+    if (n_road) atomicAdd(&s_road, n_road);
+    macc_flush_block<TILE>(acc, c.metrics);  // (its barriers also complete s_road)
+    // the run's statistics for the next step's weight fit (run_fit)
+    if (threadIdx.x == 0 && vb < RUNSTAT_MAX) {
+        unsigned long long t_end = 0;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
+        const long long dt = (long long)(t_end - t_start);
+        const int ns = s_end - s_beg;
+        c.runstat[vb] = make_int4((int)min(dt, (long long)INT_MAX), s_road, ns - s_road, 1);
+    }
 }
 
 template <typename Real, bool Groups>
@@ -708,9 +734,56 @@ __device__ __forceinline__ void lanescan_tile(const Ctx<Real>& c, int tile) {
     }
 }
 
-// k_lanescan.  Tickets [0, n_lane_tiles): next-snapshot lane offsets (lane
-// tiles, above).  Remaining tickets: signal states of the next step for
-// chunks of junctions.
+// Fit of the cost of a road-lane and a junction-lane vehicle in k_decide
+// from this step's work blocks: least squares of run time ~ c_road x (road
+// slots) + c_junction x (junction slots) over the runs; the next step splits
+// its runs with the weight c_road / c_junction (clamped to [0.5, 4]; the
+// previous weight when the fit is degenerate, e.g. no junction vehicles).
+// One block (a ticket of k_lanescan); the statistics are cleared for the next
+// step.
+template <typename Real>
+__device__ void run_fit(const Ctx<Real>& c) {
+    __shared__ double s_sum[5][TILE / 32];
+    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // RR, RJ, JJ, dR, dJ
+    const int nr = min(c.cnt->n_runs, RUNSTAT_MAX);
+    for (int k = threadIdx.x; k < nr; k += TILE) {
+        const int4 r = c.runstat[k];
+        if (!r.w) continue;
+        const double d = r.x, R = r.y, J = r.z;
+        v[0] += R * R; v[1] += R * J; v[2] += J * J; v[3] += d * R; v[4] += d * J;
+        c.runstat[k] = make_int4(0, 0, 0, 0);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        double x = v[q];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) s_sum[q][warp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t[5];
+        for (int q = 0; q < 5; ++q) {
+            t[q] = 0.0;
+            for (int w = 0; w < TILE / 32; ++w) t[q] += s_sum[q][w];
+        }
+        int wq = c.cnt->run_wq;
+        const double det = t[0] * t[2] - t[1] * t[1];
+        if (det > 1e-9 * t[0] * t[2] && t[2] > 0.0) {
+            const double cr = (t[3] * t[2] - t[4] * t[1]) / det, cj = (t[0] * t[4] - t[1] * t[3]) / det;
+            if (cr > 0.0 && cj > 0.0) {
+                const double w = fmin(4.0, fmax(0.5, cr / cj));
+                wq = (int)(w * 256.0 + 0.5);
+            }
+        }
+        c.cnt_next->run_wq = wq;
+    }
+}
+
+// k_lanescan.  Ticket 0: the run-weight fit.  Then (the first tickets below)
+// the late candidates and max-pressure sums, the next-snapshot lane offsets
+// (lane tiles, above), and the signal states of the next step for chunks of
+// junctions.
 template <typename Real, int LS_ROUNDS = 4>
 __device__ __forceinline__ void lanescan_blocks(const Ctx<Real>& c) {
     __shared__ int s_tile;
@@ -728,13 +801,20 @@ __device__ __forceinline__ void lanescan_blocks(const Ctx<Real>& c) {
 #else
     const int n_res = 0;
 #endif
-    const int n_tickets = n_res + c.n_lane_tiles + c.n_junc_chunks;
+    const int n_tickets = 1 + n_res + c.n_lane_tiles + c.n_junc_chunks;
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(&c.cnt->ticket_lane, 1);
         __syncthreads();
         int tile = s_tile;
         __syncthreads();
         if (tile >= n_tickets) return;
+        // ticket 0: the run-weight fit of k_decide's runs (needs nothing else)
+        if (tile == 0) {
+            run_fit(c);
+            __syncthreads();
+            continue;
+        }
+        tile -= 1;
 #if MOSS_FOLD_RESOLVE
         if (tile < n_res) {
             MetricAcc acc;
