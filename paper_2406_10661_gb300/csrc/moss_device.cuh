@@ -17,15 +17,17 @@
 //               randomized MOBIL decision (App. B.3; run from a per-warp
 //               shared-memory queue of the vehicles whose attempt draw
 //               passed), ballistic integration with clamps, transfer at lane
-//               ends and arrival (App. B.2 update stream 1); lane-change
-//               candidates are listed for the resolution; extra blocks run
-//               the departure insertion (App. B.2 update stream 3);
-//   k_lanescan  first tickets: deterministic conflict resolution between
-//               candidates entering the same gap from both sides, and their
-//               update; max-pressure phase sums (§3.2); then per-lane sizes of
-//               the next snapshot -> offsets (single-pass decoupled look-back
-//               scan), prefix of leavers per slot tile, signal states of the
-//               next step (§3.2 policies);
+//               ends and arrival (App. B.2 update stream 1); each block
+//               takes a run of whole roads and at its end resolves the
+//               lane-change candidates of its run (deterministic conflict
+//               rule between candidates entering the same gap from both
+//               sides); extra blocks run the departure insertion (App. B.2
+//               update stream 3);
+//   k_lanescan  first tickets: the fit of the next step's run weight, the
+//               candidates past a decide block's own list, max-pressure
+//               phase sums (§3.2); then per-lane sizes of the next snapshot
+//               -> offsets (single-pass decoupled look-back scan), signal
+//               states of the next step (§3.2 policies);
 //   k_place     writes the next snapshot: vehicles that kept their lane keep
 //               their relative order (no overtaking within a lane), vehicles
 //               that entered a lane are merged by (s, id).
@@ -88,8 +90,8 @@ struct Counters {
     int n_runs;      // k_decide work runs of this step (their statistics for the fit)
 };
 
-// the candidates are resolved in the first tickets of k_lanescan instead of a
-// kernel of their own
+// the candidates past a decide block's own list are resolved in the first
+// tickets of k_lanescan instead of a kernel of their own
 #ifndef MOSS_FOLD_RESOLVE
 #define MOSS_FOLD_RESOLVE 1
 #endif

@@ -873,9 +873,9 @@ __global__ void __launch_bounds__(LANESCAN_THREADS) k_lanescan(Ctx<Real> c) {
 // ---------------------------------------------------------------------------
 // k_place: writes the next snapshot.  Stayer tiles (one per block iteration):
 // a vehicle that kept its lane goes to off'[lane] + (stayers ahead of it in
-// the lane) + (entrants ahead of it); stayers ahead = its slot rank in the
-// lane minus the leavers before it in the lane.  Then the entrants: rank =
-// stayers ahead + entrants ahead.  The last block to finish closes the step.
+// the lane) + (entrants ahead of it), its stayers ahead counted in its tile
+// (below).  Then the entrants: rank = stayers ahead + entrants ahead.  Block
+// 0 prepares the next step's counters and advances the scenarios' clocks.
 template <typename Real>
 __device__ __forceinline__ int entrants_ahead(const Ctx<Real>& c, int lane, Real s, int id, int tag,
                                               int* n_in = nullptr) {
