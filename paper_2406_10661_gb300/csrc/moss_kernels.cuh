@@ -739,41 +739,42 @@ __device__ __forceinline__ void lanescan_tile(const Ctx<Real>& c, int tile) {
 // slots) + c_junction x (junction slots) over the runs; the next step splits
 // its runs with the weight c_road / c_junction (clamped to [0.5, 4]; the
 // previous weight when the fit is degenerate, e.g. no junction vehicles).
-// One block (a ticket of k_lanescan); the statistics are cleared for the next
+// One block (a ticket of k_lanescan); every work run rewrites its entry each
 // step.
 template <typename Real>
 __device__ void run_fit(const Ctx<Real>& c) {
-    __shared__ double s_sum[5][TILE / 32];
-    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // RR, RJ, JJ, dR, dJ
+    // FP32 sums of normalised values (slots in thousands, times in units of
+    // 100 us): the five sums stay within a few thousand for any run count
+    __shared__ float s_sum[5][TILE / 32];
+    float v[5] = {0.f, 0.f, 0.f, 0.f, 0.f};  // RR, RJ, JJ, dR, dJ
     const int nr = min(c.cnt->n_runs, RUNSTAT_MAX);
     for (int k = threadIdx.x; k < nr; k += TILE) {
         const int4 r = c.runstat[k];
         if (!r.w) continue;
-        const double d = r.x, R = r.y, J = r.z;
+        const float d = 1e-5f * (float)r.x, R = 1e-3f * (float)r.y, J = 1e-3f * (float)r.z;
         v[0] += R * R; v[1] += R * J; v[2] += J * J; v[3] += d * R; v[4] += d * J;
-        c.runstat[k] = make_int4(0, 0, 0, 0);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-        double x = v[q];
+        float x = v[q];
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
         if (lane == 0) s_sum[q][warp] = x;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t[5];
+        float t[5];
         for (int q = 0; q < 5; ++q) {
-            t[q] = 0.0;
+            t[q] = 0.f;
             for (int w = 0; w < TILE / 32; ++w) t[q] += s_sum[q][w];
         }
         int wq = c.cnt->run_wq;
-        const double det = t[0] * t[2] - t[1] * t[1];
-        if (det > 1e-9 * t[0] * t[2] && t[2] > 0.0) {
-            const double cr = (t[3] * t[2] - t[4] * t[1]) / det, cj = (t[0] * t[4] - t[1] * t[3]) / det;
-            if (cr > 0.0 && cj > 0.0) {
-                const double w = fmin(4.0, fmax(0.5, cr / cj));
-                wq = (int)(w * 256.0 + 0.5);
+        const float det = t[0] * t[2] - t[1] * t[1];
+        if (det > 1e-4f * t[0] * t[2] && t[2] > 0.f) {
+            const float cr = (t[3] * t[2] - t[4] * t[1]) / det, cj = (t[0] * t[4] - t[1] * t[3]) / det;
+            if (cr > 0.f && cj > 0.f) {
+                const float w = fminf(4.f, fmaxf(0.5f, cr / cj));
+                wq = (int)(w * 256.f + 0.5f);
             }
         }
         c.cnt_next->run_wq = wq;
